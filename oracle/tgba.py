@@ -1,0 +1,116 @@
+"""Effective Hamiltonian, eigenpairs and the spectral sums (Eq. 2, 8-10, S4, S6).
+
+Test infrastructure only.  Everything in float64 / complex128 with numpy/LAPACK.
+"""
+import math
+
+import numpy as np
+
+from . import basis as bs
+from . import elements as el
+from . import modes as md
+
+
+def heff(ns, r, X, N, h_x):
+    """H = diag(E^(0)) + <phi|V|phi'> with <V> = -N h_x X between NS and R states (Eq. 2, S4).
+    Basis order: NS states, then R states."""
+    a, b = len(ns), len(r)
+    H = np.zeros((a + b, a + b), dtype=np.complex128)
+    H[np.arange(a + b), np.arange(a + b)] = [s.E for s in ns] + [s.E for s in r]
+    H[:a, a:] = -N * h_x * X
+    H[a:, :a] = np.conj(H[:a, a:]).T
+    return H
+
+
+def x_full(X):
+    """<phi|sigma^x_1|phi'> over the whole sector basis: [[0, X], [X^H, 0]]."""
+    a, b = X.shape
+    Y = np.zeros((a + b, a + b), dtype=np.complex128)
+    Y[:a, a:] = X
+    Y[a:, :a] = np.conj(X).T
+    return Y
+
+
+def eigh(H):
+    """Eigenpairs, ascending; columns of U are the eigenvectors (U = M^T in Eq. 1's notation)."""
+    return np.linalg.eigh(H)
+
+
+def lorentzian(x, eta):
+    return (eta / math.pi) / (x * x + eta * eta)
+
+
+def omega_grid(w_min, w_max, n_w):
+    """w_i = w_min + i (w_max - w_min)/(n_w - 1)."""
+    if n_w == 1:
+        return np.array([float(w_min)])
+    return w_min + (w_max - w_min) * np.arange(n_w) / (n_w - 1)
+
+
+def dsf_weights(E, U, Xf, N):
+    """Eq. 9 at k = 0 with the matrix element of the Dynamic-structure-factor section:
+    <psi_0|sigma^x_{k=0}|psi_a> = sqrt(N) sum M(0)^*_{0mu} <phi_mu|sigma^x_1|phi_nu> M_{a nu}.
+    Returns (E_a - E_0, w_a = N |u_0^H Xf u_a|^2) for every eigenstate a (elastic term included)."""
+    u0 = U[:, 0]
+    amp = np.conj(U).T @ (Xf.conj().T @ u0)      # amp_a = u_a^H Xf^H u_0 = conj(u_0^H Xf u_a)
+    w = N * np.abs(amp) ** 2
+    return E - E[0], w
+
+
+def dsf(E, U, Xf, N, w_min, w_max, n_w, eta):
+    """S(k=0, w) = 2 pi sum_a w_a L_eta(w - (E_a - E_0)), L_eta the normalised Lorentzian."""
+    dE, w = dsf_weights(E, U, Xf, N)
+    om = omega_grid(w_min, w_max, n_w)
+    return 2.0 * math.pi * (lorentzian(om[:, None] - dE[None, :], eta) @ w)
+
+
+def vacuum_phase(N, h0):
+    """s with |s| = 1 that makes <Phi0|sigma^x_1|Phi0> = Re(s z) > 0, z = <0_NS|sigma_1|0_R>
+    at the initial field (Fig. 2 caption: the superposition with positive magnetisation)."""
+    z = el.vacuum_sigma(N, h0)
+    return np.conj(z) / abs(z)
+
+
+def initial_overlaps(N, h, h0, ns, r, n_threads=0):
+    """c0 = <phi(h)|Phi0> with Phi0 = (|0_NS(h0)> + s |0_R(h0)>)/sqrt(2), by direct Pfaffians."""
+    s = vacuum_phase(N, h0)
+    c_ns = el.overlaps(N, h, h0, md.NS, ns, n_threads) / math.sqrt(2.0)
+    c_r = s * el.overlaps(N, h, h0, md.R, r, n_threads) / math.sqrt(2.0)
+    return np.concatenate([c_ns, c_r])
+
+
+def time_grid(t_max, n_t):
+    """t_i = i t_max / (n_t - 1)."""
+    if n_t == 1:
+        return np.zeros(1)
+    return t_max * np.arange(n_t) / (n_t - 1)
+
+
+def quench_coefficients(E, U, c0, t):
+    """B(t) = M^T e^{-iEt} M^* c0 = U e^{-iEt} U^H c0 (Eq. 10); columns indexed by t."""
+    a = np.conj(U).T @ c0
+    return U @ (np.exp(-1j * np.outer(E, t)) * a[:, None])
+
+
+def magnetisation(B, Xf, c0):
+    """<sigma^x>(t) = B^H Xf B / ||c0||^2 (normalised by the retained weight, Quench section)."""
+    val = np.einsum("it,ij,jt->t", np.conj(B), Xf, B)
+    return val.real / float(np.vdot(c0, c0).real)
+
+
+def sector(N, h, m, max_qp, e_cut=None, max_per_parity=None, n_threads=0):
+    """Basis and X block of sector m at transverse field h."""
+    ns, r = bs.sector_basis(N, h, m, max_qp, e_cut, max_per_parity)
+    X = el.x_block(N, h, ns, r, n_threads)
+    return ns, r, X
+
+
+def quench(N, h, h0, h_x, max_qp, e_cut, t_max, n_t, max_per_parity=None, n_threads=0):
+    """<sigma^x>(t) after the quench (h0, 0) -> (h, h_x) in the k = 0 sector."""
+    ns, r, X = sector(N, h, 0, max_qp, e_cut, max_per_parity, n_threads)
+    H = heff(ns, r, X, N, h_x)
+    E, U = eigh(H)
+    c0 = initial_overlaps(N, h, h0, ns, r, n_threads)
+    t = time_grid(t_max, n_t)
+    B = quench_coefficients(E, U, c0, t)
+    return t, magnetisation(B, x_full(X), c0), c0
