@@ -1,0 +1,168 @@
+/*
+ * tgba.h - C ABI of the GB300 TGBA library (libtgba.so).
+ *
+ * The Truncated Gaussian Basis Approach (arXiv:2410.04204) for the Ising chain
+ *     H = -sum sx_j sx_{j+1} - h_z sum sz_j - h_x sum sx_j      (Eq. 3, periodic, L even)
+ * builds, per momentum sector, the effective Hamiltonian
+ *     H_ab = E^(0)_a delta_ab + <phi_a|V|phi_b>                  (Eq. 2)
+ * over retained eigenstates phi of the free part H0 (fermionic Gaussian states, Eq. 6-7),
+ * with <phi_a|V|phi_b> = -L h_x <phi_a|c_1 + c_1^dag|phi_b> (Eq. S4) evaluated as Pfaffians
+ * (Eq. S1-S2), diagonalises it (Eq. 1), and evaluates the dynamic structure factor (Eq. 9)
+ * and quench dynamics (Eq. 10).
+ *
+ * Conventions shared by every call
+ *  - Errors: every call returns a tgba_status; nothing throws across the ABI.  Argument errors
+ *    are detected on the host before any launch.  tgba_last_error() returns a thread-local
+ *    message for the last failing call on this thread.  There is no CPU fallback: without a
+ *    usable CUDA device, calls that compute return TGBA_ECUDA.
+ *  - Ownership: handles (tgba_basis, tgba_screen) are created and freed by the library and
+ *    own the device memory they need.  Output buffers are allocated by the caller; "_dev"
+ *    arguments are device pointers, "_host" arguments host pointers.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  All
+ *    device work of a call is ordered on that stream; calls return once the work is enqueued
+ *    unless stated otherwise.  Device-side numeric faults (a NaN pivot, a non-real contraction
+ *    table) are reported through a status word that the next synchronising call reads.
+ *  - Complex numbers are interleaved (re, im) pairs of doubles (complex128).
+ *  - Basis order inside a sector: the NS states (fermion parity Q = +1) first, then the R states
+ *    (Q = -1); within a parity by quasiparticle number M, then energy, then mode indices.
+ *  - Modes: mode index i of parity P is momentum k = pi n / L with n = -(L-1) + 2i (NS) or
+ *    n = -(L-2) + 2i (R; i = L-1 is k = pi), i.e. modes in ascending k.
+ */
+#ifndef TGBA_H
+#define TGBA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TGBA_OK = 0,
+  TGBA_EINVAL = 1,     /* bad argument (checked on the host, nothing launched) */
+  TGBA_ENOMEM = 2,     /* device or host allocation failed */
+  TGBA_ECUDA = 3,      /* CUDA / cuSOLVER error, or no usable device */
+  TGBA_ENUMERIC = 4,   /* NaN/Inf in a Pfaffian, singular vacuum block, non-real table */
+  TGBA_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+  TGBA_ELIMIT = 6      /* a size limit of the library was exceeded */
+} tgba_status;
+
+/* Model (Eq. 3).  L even, 4 <= L <= 120; J > 0 (energies scale as H(J,h,hx) = J H(1,h/J,hx/J)).
+   h_z > 0 is the transverse field.  h_x is not used by tgba_build_basis (V enters later). */
+typedef struct { int32_t L; double J; double h_z; double h_x; } tgba_model;
+
+/* Truncation (Method section; Appendix B).  Keep states with M <= max_qp quasiparticles
+   (0 <= max_qp <= 16, even M only) and, if e_cut >= 0, energy E - E_NS,vacuum <= e_cut (+1e-9);
+   then, if max_per_parity > 0, the max_per_parity lowest in (E, M, modes) of each parity. */
+typedef struct { int32_t max_qp; double e_cut; int64_t max_per_parity; } tgba_trunc;
+
+typedef struct tgba_basis_s* tgba_basis;     /* opaque, library-owned */
+typedef struct tgba_screen_s* tgba_screen;   /* opaque, library-owned */
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char* tgba_last_error(void);
+
+/* Number of CUDA devices the library can use (0 if none); never fails. */
+int32_t tgba_device_count(void);
+
+/* ---------------------------------------------------------------- basis (Eq. 6-7, Method)
+ * Enumerate, per requested momentum sector K = 2 pi m / L, the H0 eigenstates
+ * d^dag_{k1}...d^dag_{kM}|0>_{NS/R} (M even, sum k = K mod 2 pi), truncate them, and upload the
+ * state tables to the current device.  sectors_m: n_sectors distinct values in [0, L).
+ * Host work plus synchronous uploads; on success *out owns device memory until
+ * tgba_basis_free.  TGBA_ELIMIT if a sector would exceed 2^31 elements. */
+tgba_status tgba_build_basis(const tgba_model* model, const int32_t* sectors_m, int32_t n_sectors,
+                             const tgba_trunc* trunc, tgba_basis* out);
+
+/* Sizes and (optionally) state data of sector index s (0 <= s < n_sectors).
+   n_ns, n_r: number of NS and R states.  Optional host outputs (NULL to skip), each sized for
+   n_ns + n_r states in basis order: E0 (energies E^(0)), parity (0 = NS, 1 = R), nqp (M) and
+   modes ([state][max_qp] ascending mode indices, -1 padded). */
+tgba_status tgba_basis_info(tgba_basis b, int32_t s, int64_t* n_ns, int64_t* n_r, double* E0_host,
+                            uint8_t* parity_host, uint8_t* nqp_host, int16_t* modes_host);
+
+/* Totals: number of sectors, sum over sectors of n_ns * n_r (the Pfaffian elements) and of
+   (n_ns + n_r)^2 (the H_eff entries, i.e. the complex128 count tgba_assemble_heff writes). */
+tgba_status tgba_basis_totals(tgba_basis b, int32_t* n_sectors, int64_t* n_elements, int64_t* n_heff);
+
+tgba_status tgba_basis_free(tgba_basis b);
+
+/* ---------------------------------------------------------------- Pfaffian stage (App. A)
+ * Computes, for every sector, X_ab = <phi_a^NS| c_1 + c_1^dag |phi_b^R> (Eq. S4) for all NS x R
+ * pairs and keeps them in the basis handle (device memory owned by the library), where
+ * tgba_assemble_heff, tgba_dsf and tgba_quench reuse them for any h_x.  Steps: the
+ * contraction table of the Bogoliubov operators (the Schur complement of Eq. S2's matrix on
+ * the vacuum operators) and then one small real Pfaffian per element, of size M_a + M_b,
+ * batched over all sectors and sizes.  screen: NULL for the exact assembly, or a trained pair
+ * screener; pairs it predicts with |V_ab| = L h_x |X_ab| < screen_tau (at screen_hx) are set to
+ * 0 without a Pfaffian.  Asynchronous on `stream`. */
+tgba_status tgba_compute_x(tgba_basis b, tgba_screen screen, double screen_tau, double screen_hx, void* stream);
+
+/* Number of pairs the last tgba_compute_x evaluated by Pfaffian (after screening); blocks on
+   the stream of that call. */
+tgba_status tgba_x_stats(tgba_basis b, int64_t* n_evaluated, int64_t* n_screened);
+
+/* Copy sector s's X block, complex128 [n_ns][n_r] row-major in basis order, to x_dev. */
+tgba_status tgba_x_export(tgba_basis b, int32_t s, double* x_dev, void* stream);
+
+/* X for an explicit list of pairs of sector s: pairs_dev int32 [n][2] = (NS index, R index)
+   in basis order; out_dev complex128 [n].  Uses the contraction table (computing it if needed).  Indices outside the sector give
+   TGBA_EINVAL (NaN is written for them); blocks on `stream`. */
+tgba_status tgba_x_pairs(tgba_basis b, int32_t s, const int32_t* pairs_dev, int64_t n_pairs,
+                         double* out_dev, void* stream);
+
+/* Contraction table and vacuum element: c0_host (complex, 2 doubles) receives
+   C0 = <0_NS|c_1 + c_1^dag|0_R>; table_dev (optional, 2L x 2L doubles row-major) receives the
+   real table R.  Blocks on `stream`. */
+tgba_status tgba_table(tgba_basis b, double* c0_host, double* table_dev, void* stream);
+
+/* ---------------------------------------------------------------- H_eff (Eq. 2, S4)
+ * Writes, for every sector in order, H = diag(E^(0)) - L h_x [[0, X], [X^H, 0]] as a dense
+ * complex128 (n x n, n = n_ns + n_r) column-major matrix; the sectors follow each other in
+ * heff_dev (total size from tgba_basis_totals).  Runs tgba_compute_x(b, screen, ...) first if
+ * the handle holds no X for that screen.  Asynchronous on `stream`. */
+tgba_status tgba_assemble_heff(tgba_basis b, double h_x, tgba_screen screen, double screen_tau,
+                               double* heff_dev, void* stream);
+
+/* ---------------------------------------------------------------- diagonalisation (Eq. 1)
+ * Eigenvalues (ascending, all sectors concatenated: sector s at offset sum of previous n) of
+ * the H_eff that tgba_assemble_heff writes for this h_x, computed from the handle's X.  The
+ * sector matrices are real symmetric after a diagonal change of phase of the basis states, so
+ * the library diagonalises them with the FP64 real symmetric solver (cuSOLVER syevd);
+ * evals_dev receives all eigenvalues.  Blocks on `stream`. */
+tgba_status tgba_eigvals(tgba_basis b, double h_x, double* evals_dev, void* stream);
+
+/* ---------------------------------------------------------------- S(k=0, w) (Eq. 8-9)
+ * Dynamic structure factor of sector index s (which must be the k = 0 sector, m = 0):
+ * S(w_i) = 2 pi sum_a w_a L_eta(w_i - (E_a - E_0)), w_a = L |<psi_0|sigma^x_1|psi_a>|^2,
+ * L_eta(x) = (eta/pi)/(x^2 + eta^2), w_i = w_min + i (w_max - w_min)/(n_w - 1).
+ * Weights in FP64; the Lorentzian sum in FP32 with FP32 accumulation.  S_dev: float [n_w].
+ * Optional: evals_dev (double, first n_ev eigenvalues), weights_dev (double [n], w_a) and
+ * dE_dev (double [n], E_a - E_0).  Blocks on `stream`. */
+tgba_status tgba_dsf(tgba_basis b, int32_t s, double h_x, double w_min, double w_max, int32_t n_w, double eta,
+                     float* S_dev, double* evals_dev, int32_t n_ev, double* weights_dev, double* dE_dev,
+                     void* stream);
+
+/* ---------------------------------------------------------------- quench (Eq. 10)
+ * <sigma^x>(t) after the quench from Phi0 = (|0_NS(h_z0)> + s|0_R(h_z0)>)/sqrt 2 (ground states
+ * of the h_x = 0 chain at h_z0, s making <sigma^x>(0) > 0) to the basis' model with
+ * longitudinal field hx_variants[v].  Sector index s must be k = 0.  Variant v keeps the states
+ * of the basis with E - E_NS,vacuum <= ecut_variants[v] (+1e-9; a negative value keeps all), so
+ * variants with growing cutoffs are nested truncations (Method section, Fig. 2: several chi).
+ * B(t) = M^T e^{-iEt} M^* c0 with c0 = <phi|Phi0> (Eq. S6), <sigma^x>(t) = B^H X B / ||c0||^2
+ * on t_i = i t_max/(n_t - 1).  mx_dev: double [n_variants][n_t]; norm_dev (optional): double
+ * [n_variants], ||c0||^2 of each variant; chi_host (optional): int64 [n_variants], the retained
+ * basis size of each variant.  Blocks on `stream`. */
+tgba_status tgba_quench(tgba_basis b, int32_t s, double h_z0, const double* hx_variants,
+                        const double* ecut_variants, int32_t n_variants, double t_max, int32_t n_t,
+                        double* mx_dev, double* norm_dev, int64_t* chi_host, void* stream);
+
+/* ---------------------------------------------------------------- measurement helper
+ * Achieved FP64 rate of a DFMA-chain kernel on the current device (GFLOP/s, best of `reps`),
+ * the denominator for FP64 roofline fractions. */
+tgba_status tgba_fp64_peak(int32_t reps, double* gflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TGBA_H */

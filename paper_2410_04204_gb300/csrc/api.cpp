@@ -1,0 +1,361 @@
+// The C ABI declared in include/tgba.h: argument checks, handle life cycle, device uploads,
+// status words, and the order of the stages of each call.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <set>
+#include <string>
+
+#include "tgba_internal.h"
+
+namespace tgba {
+
+static thread_local std::string g_last_error;
+
+tgba_status fail(tgba_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+tgba_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? TGBA_ENOMEM : TGBA_ECUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+tgba_status check_status(Basis& b, cudaStream_t st) {
+  unsigned w = 0;
+  TGBA_CUDA(cudaMemcpyAsync(&w, b.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  TGBA_CUDA(cudaStreamSynchronize(st));
+  if (w == 0) return TGBA_OK;
+  TGBA_CUDA(cudaMemsetAsync(b.d_status, 0, sizeof(unsigned), st));
+  TGBA_CUDA(cudaStreamSynchronize(st));
+  if (w & kStTimeout) return fail(TGBA_ETIMEOUT, "a bounded device wait gave up");
+  if (w & kStBadIndex) return fail(TGBA_EINVAL, "a pair index was outside the sector");
+  if (w & kStTableSingular) return fail(TGBA_ENUMERIC, "the vacuum block of the contraction matrix is singular");
+  if (w & kStTableImag) return fail(TGBA_ENUMERIC, "the gauge-rotated contraction table is not real");
+  return fail(TGBA_ENUMERIC, "a Pfaffian produced NaN or Inf");
+}
+
+tgba_status scratch(Basis& b, int64_t doubles, double** out) {
+  if (doubles > b.scratch_cap) {
+    if (b.d_scratch) cudaFree(b.d_scratch);
+    b.d_scratch = nullptr;
+    b.scratch_cap = 0;
+    cudaError_t e = cudaMalloc(&b.d_scratch, doubles * sizeof(double));
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(TGBA_ENOMEM, "device scratch of " + std::to_string(doubles * 8) + " bytes"); }
+    b.scratch_cap = doubles;
+  }
+  *out = b.d_scratch;
+  return TGBA_OK;
+}
+
+static void release(Basis* b) {
+  void* ptrs[] = {b->d_E_ns, b->d_E_r, b->d_M_ns, b->d_M_r, b->d_sel_ns, b->d_sel_r, b->d_modes_ns, b->d_modes_r,
+                  b->d_theta, b->d_nlab, b->d_table, b->d_c0, b->d_work, b->d_P, b->d_tiles, b->d_status,
+                  b->d_eig_a, b->d_eig_w, b->d_eig_work, b->d_eig_info, b->d_scratch};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (b->solver) destroy_solver(b->solver);
+  if (b->blas) destroy_blas(b->blas);
+  delete b;
+}
+
+template <class T>
+static tgba_status upload(T** dst, const T* src, size_t count) {
+  size_t bytes = std::max<size_t>(1, count) * sizeof(T);
+  TGBA_CUDA(cudaMalloc((void**)dst, bytes));
+  if (count) TGBA_CUDA(cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice));
+  return TGBA_OK;
+}
+
+static tgba_status require_device() {
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    return fail(TGBA_ECUDA, "no usable CUDA device");
+  }
+  return TGBA_OK;
+}
+
+static tgba_status build(const tgba_model* model, const int32_t* sectors, int32_t n_sectors, const tgba_trunc* trunc,
+                         Basis* b) {
+  tgba_status r = enumerate_basis(*model, sectors, n_sectors, *trunc, *b);
+  if (r != TGBA_OK) return r;
+  TGBA_CUDA(cudaGetDevice(&b->device));
+  const int L = b->L, q = b->max_qp;
+  const size_t nns = b->ns.E.size(), nr = b->r.E.size();
+  // table rows: NS mode i -> L-1-i (rows ascend as modes descend), R mode i -> L+i
+  std::vector<uint8_t> sel_ns(std::max<size_t>(1, nns * q), 0), sel_r(std::max<size_t>(1, nr * q), 0);
+  for (size_t s = 0; s < nns; ++s) {
+    const int M = b->ns.M[s];
+    for (int u = 0; u < M; ++u) sel_ns[s * q + u] = (uint8_t)(L - 1 - b->ns.modes[s * q + (M - 1 - u)]);
+  }
+  for (size_t s = 0; s < nr; ++s) {
+    const int M = b->r.M[s];
+    for (int u = 0; u < M; ++u) sel_r[s * q + u] = (uint8_t)(L + b->r.modes[s * q + u]);
+  }
+  if ((r = upload(&b->d_E_ns, b->ns.E.data(), nns)) != TGBA_OK) return r;
+  if ((r = upload(&b->d_E_r, b->r.E.data(), nr)) != TGBA_OK) return r;
+  if ((r = upload(&b->d_M_ns, b->ns.M.data(), nns)) != TGBA_OK) return r;
+  if ((r = upload(&b->d_M_r, b->r.M.data(), nr)) != TGBA_OK) return r;
+  if ((r = upload(&b->d_sel_ns, sel_ns.data(), nns * q)) != TGBA_OK) return r;
+  if ((r = upload(&b->d_sel_r, sel_r.data(), nr * q)) != TGBA_OK) return r;
+  if ((r = upload(&b->d_modes_ns, b->ns.modes.data(), nns * q)) != TGBA_OK) return r;
+  if ((r = upload(&b->d_modes_r, b->r.modes.data(), nr * q)) != TGBA_OK) return r;
+  Modes mns = make_modes(L, 0, b->h), mr = make_modes(L, 1, b->h);
+  std::vector<double> th(2 * L);
+  std::vector<int> nl(2 * L);
+  for (int i = 0; i < L; ++i) {
+    th[i] = mns.theta[i]; th[L + i] = mr.theta[i];
+    nl[i] = mns.nlab[i]; nl[L + i] = mr.nlab[i];
+  }
+  b->vac_norm = mns.norm * mr.norm;
+  if ((r = upload(&b->d_theta, th.data(), th.size())) != TGBA_OK) return r;
+  if ((r = upload(&b->d_nlab, nl.data(), nl.size())) != TGBA_OK) return r;
+  TGBA_CUDA(cudaMalloc((void**)&b->d_table, sizeof(double) * 4 * L * L));
+  TGBA_CUDA(cudaMalloc((void**)&b->d_c0, sizeof(double) * 4));
+  TGBA_CUDA(cudaMalloc((void**)&b->d_work, sizeof(double) * 2 * 16 * L * L));
+  TGBA_CUDA(cudaMalloc((void**)&b->d_P, sizeof(double) * std::max<int64_t>(1, b->n_elements)));
+  TGBA_CUDA(cudaMalloc((void**)&b->d_status, sizeof(unsigned)));
+  TGBA_CUDA(cudaMemset(b->d_status, 0, sizeof(unsigned)));
+  build_tiles(*b, 0, b->tiles, b->tile_class_begin);
+  if ((r = upload(&b->d_tiles, b->tiles.data(), b->tiles.size())) != TGBA_OK) return r;
+  return TGBA_OK;
+}
+
+static tgba_status ensure_table(Basis& b, cudaStream_t st) {
+  if (b.table_valid) return TGBA_OK;
+  tgba_status r = build_table(b, st);
+  if (r != TGBA_OK) return r;
+  TGBA_CUDA(cudaMemcpyAsync(b.c0_host, b.d_c0, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  r = check_status(b, st);     // synchronises
+  if (r != TGBA_OK) b.table_valid = false;
+  return r;
+}
+
+static tgba_status compute_x(Basis& b, const void* screen, double tau, cudaStream_t st) {
+  if (screen != nullptr) return fail(TGBA_EINVAL, "pair screening is not available in this build");
+  b.table_valid = false;                 // the table is part of the stage
+  tgba_status r = ensure_table(b, st);
+  if (r != TGBA_OK) return r;
+  if ((r = run_pfaffians(b, nullptr, st)) != TGBA_OK) return r;
+  b.x_valid = true;
+  b.x_screen = screen;
+  b.x_tau = tau;
+  b.x_evaluated = b.n_elements;
+  b.x_screened = 0;
+  return TGBA_OK;
+}
+
+}  // namespace tgba
+
+using namespace tgba;
+
+#define BASIS_OK(b)                                                   \
+  do {                                                                \
+    if ((b) == nullptr) return fail(TGBA_EINVAL, "null basis handle"); \
+  } while (0)
+
+extern "C" {
+
+const char* tgba_last_error(void) { return g_last_error.c_str(); }
+
+int32_t tgba_device_count(void) {
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+tgba_status tgba_build_basis(const tgba_model* model, const int32_t* sectors_m, int32_t n_sectors,
+                             const tgba_trunc* trunc, tgba_basis* out) {
+  g_last_error.clear();
+  if (!model || !sectors_m || !trunc || !out) return fail(TGBA_EINVAL, "null argument");
+  *out = nullptr;
+  if (model->L < 4 || model->L > kMaxL || model->L % 2) return fail(TGBA_EINVAL, "L must be even, 4 <= L <= 120");
+  if (!(model->J > 0) || !std::isfinite(model->J)) return fail(TGBA_EINVAL, "J must be positive");
+  if (!(model->h_z > 0) || !std::isfinite(model->h_z)) return fail(TGBA_EINVAL, "h_z must be positive");
+  if (n_sectors < 1 || n_sectors > model->L) return fail(TGBA_EINVAL, "need 1..L sectors");
+  std::set<int> seen;
+  for (int s = 0; s < n_sectors; ++s) {
+    if (sectors_m[s] < 0 || sectors_m[s] >= model->L) return fail(TGBA_EINVAL, "sector m outside [0, L)");
+    if (!seen.insert(sectors_m[s]).second) return fail(TGBA_EINVAL, "repeated sector");
+  }
+  if (trunc->max_qp < 0 || trunc->max_qp > kMaxQp) return fail(TGBA_EINVAL, "max_qp must be in [0, 16]");
+  if (std::isnan(trunc->e_cut)) return fail(TGBA_EINVAL, "e_cut is NaN");
+  tgba_status r = require_device();
+  if (r != TGBA_OK) return r;
+  Basis* b = new (std::nothrow) Basis();
+  if (!b) return fail(TGBA_ENOMEM, "host allocation");
+  r = build(model, sectors_m, n_sectors, trunc, b);
+  if (r != TGBA_OK) {
+    release(b);
+    return r;
+  }
+  *out = (tgba_basis)b;
+  return TGBA_OK;
+}
+
+tgba_status tgba_basis_info(tgba_basis h, int32_t s, int64_t* n_ns, int64_t* n_r, double* E0, uint8_t* parity,
+                            uint8_t* nqp, int16_t* modes) {
+  Basis* b = (Basis*)h;
+  BASIS_OK(b);
+  if (s < 0 || s >= (int)b->sectors.size()) return fail(TGBA_EINVAL, "sector index out of range");
+  const Sector& sec = b->sectors[s];
+  if (n_ns) *n_ns = sec.n_ns;
+  if (n_r) *n_r = sec.n_r;
+  const int q = b->max_qp;
+  for (int64_t i = 0; i < sec.n_ns + sec.n_r; ++i) {
+    const bool ns = i < sec.n_ns;
+    const StateTable& T = ns ? b->ns : b->r;
+    const int64_t j = ns ? sec.ns_off + i : sec.r_off + (i - sec.n_ns);
+    if (E0) E0[i] = T.E[j];
+    if (parity) parity[i] = ns ? 0 : 1;
+    if (nqp) nqp[i] = T.M[j];
+    if (modes) std::memcpy(modes + i * q, T.modes.data() + j * q, q * sizeof(int16_t));
+  }
+  return TGBA_OK;
+}
+
+tgba_status tgba_basis_totals(tgba_basis h, int32_t* n_sectors, int64_t* n_elements, int64_t* n_heff) {
+  Basis* b = (Basis*)h;
+  BASIS_OK(b);
+  if (n_sectors) *n_sectors = (int32_t)b->sectors.size();
+  if (n_elements) *n_elements = b->n_elements;
+  if (n_heff) *n_heff = b->n_heff;
+  return TGBA_OK;
+}
+
+tgba_status tgba_basis_free(tgba_basis h) {
+  if (h) release((Basis*)h);
+  return TGBA_OK;
+}
+
+tgba_status tgba_compute_x(tgba_basis h, tgba_screen screen, double tau, double screen_hx, void* stream) {
+  Basis* b = (Basis*)h;
+  BASIS_OK(b);
+  (void)screen_hx;
+  return compute_x(*b, screen, tau, (cudaStream_t)stream);
+}
+
+tgba_status tgba_x_stats(tgba_basis h, int64_t* n_evaluated, int64_t* n_screened) {
+  Basis* b = (Basis*)h;
+  BASIS_OK(b);
+  if (!b->x_valid) return fail(TGBA_EINVAL, "no X computed yet");
+  if (n_evaluated) *n_evaluated = b->x_evaluated;
+  if (n_screened) *n_screened = b->x_screened;
+  return TGBA_OK;
+}
+
+tgba_status tgba_x_export(tgba_basis h, int32_t s, double* x_dev, void* stream) {
+  Basis* b = (Basis*)h;
+  BASIS_OK(b);
+  if (s < 0 || s >= (int)b->sectors.size()) return fail(TGBA_EINVAL, "sector index out of range");
+  if (!b->x_valid) return fail(TGBA_EINVAL, "no X computed yet: call tgba_compute_x");
+  if (!x_dev && b->sectors[s].n_ns * b->sectors[s].n_r > 0) return fail(TGBA_EINVAL, "null output");
+  return export_x(*b, s, x_dev, (cudaStream_t)stream);
+}
+
+tgba_status tgba_x_pairs(tgba_basis h, int32_t s, const int32_t* pairs_dev, int64_t n_pairs, double* out_dev,
+                         void* stream) {
+  Basis* b = (Basis*)h;
+  BASIS_OK(b);
+  if (s < 0 || s >= (int)b->sectors.size()) return fail(TGBA_EINVAL, "sector index out of range");
+  if (n_pairs < 0 || (n_pairs > 0 && (!pairs_dev || !out_dev))) return fail(TGBA_EINVAL, "bad pair list");
+  cudaStream_t st = (cudaStream_t)stream;
+  tgba_status r = ensure_table(*b, st);
+  if (r != TGBA_OK) return r;
+  if ((r = run_pfaffian_pairs(*b, s, pairs_dev, n_pairs, out_dev, st)) != TGBA_OK) return r;
+  return check_status(*b, st);
+}
+
+tgba_status tgba_table(tgba_basis h, double* c0_host, double* table_dev, void* stream) {
+  Basis* b = (Basis*)h;
+  BASIS_OK(b);
+  cudaStream_t st = (cudaStream_t)stream;
+  tgba_status r = ensure_table(*b, st);
+  if (r != TGBA_OK) return r;
+  if (c0_host) { c0_host[0] = b->c0_host[0]; c0_host[1] = b->c0_host[1]; }
+  if (table_dev)
+    TGBA_CUDA(cudaMemcpyAsync(table_dev, b->d_table, sizeof(double) * 4 * b->L * b->L, cudaMemcpyDeviceToDevice, st));
+  TGBA_CUDA(cudaStreamSynchronize(st));
+  return TGBA_OK;
+}
+
+tgba_status tgba_assemble_heff(tgba_basis h, double h_x, tgba_screen screen, double tau, double* heff_dev,
+                               void* stream) {
+  Basis* b = (Basis*)h;
+  BASIS_OK(b);
+  if (!std::isfinite(h_x)) return fail(TGBA_EINVAL, "h_x must be finite");
+  if (!heff_dev && b->n_heff > 0) return fail(TGBA_EINVAL, "null output");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!b->x_valid || b->x_screen != (const void*)screen || (screen && b->x_tau != tau)) {
+    tgba_status r = compute_x(*b, screen, tau, st);
+    if (r != TGBA_OK) return r;
+  }
+  return assemble_heff(*b, h_x, heff_dev, st);
+}
+
+tgba_status tgba_eigvals(tgba_basis h, double h_x, double* evals_dev, void* stream) {
+  Basis* b = (Basis*)h;
+  BASIS_OK(b);
+  if (!std::isfinite(h_x)) return fail(TGBA_EINVAL, "h_x must be finite");
+  if (!b->x_valid) return fail(TGBA_EINVAL, "no X computed yet: call tgba_compute_x");
+  if (!evals_dev && b->n_states > 0) return fail(TGBA_EINVAL, "null output");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (size_t s = 0; s < b->sectors.size(); ++s) {
+    const Sector& sec = b->sectors[s];
+    const int64_t n = sec.n_ns + sec.n_r;
+    if (n == 0) continue;
+    double* A;
+    tgba_status r = scratch(*b, n * n, &A);
+    if (r != TGBA_OK) return r;
+    if ((r = build_real_heff(*b, (int)s, h_x, A, nullptr, sec.n_ns, nullptr, sec.n_r, st)) != TGBA_OK) return r;
+    if ((r = eig_sym(*b, n, A, evals_dev + sec.ev_off, false, st)) != TGBA_OK) return r;
+  }
+  return check_status(*b, st);
+}
+
+tgba_status tgba_dsf(tgba_basis h, int32_t s, double h_x, double w_min, double w_max, int32_t n_w, double eta,
+                     float* S_dev, double* evals_dev, int32_t n_ev, double* weights_dev, double* dE_dev,
+                     void* stream) {
+  Basis* b = (Basis*)h;
+  BASIS_OK(b);
+  if (s < 0 || s >= (int)b->sectors.size()) return fail(TGBA_EINVAL, "sector index out of range");
+  if (b->sectors[s].m != 0) return fail(TGBA_EINVAL, "S(k=0, w) needs the k = 0 sector");
+  if (n_w < 1 || !S_dev) return fail(TGBA_EINVAL, "need n_w >= 1 and an output buffer");
+  if (!(eta > 0) || !std::isfinite(w_min) || !std::isfinite(w_max) || !std::isfinite(h_x))
+    return fail(TGBA_EINVAL, "eta must be positive and the grid finite");
+  if (!b->x_valid) return fail(TGBA_EINVAL, "no X computed yet: call tgba_compute_x");
+  return dsf(*b, s, h_x, w_min, w_max, n_w, eta, S_dev, evals_dev, n_ev, weights_dev, dE_dev, (cudaStream_t)stream);
+}
+
+tgba_status tgba_quench(tgba_basis h, int32_t s, double h_z0, const double* hx_variants, const double* ecut_variants,
+                        int32_t n_variants, double t_max, int32_t n_t, double* mx_dev, double* norm_dev,
+                        int64_t* chi_host, void* stream) {
+  Basis* b = (Basis*)h;
+  BASIS_OK(b);
+  if (s < 0 || s >= (int)b->sectors.size()) return fail(TGBA_EINVAL, "sector index out of range");
+  if (b->sectors[s].m != 0) return fail(TGBA_EINVAL, "the quench needs the k = 0 sector");
+  if (n_variants < 1 || !hx_variants || !ecut_variants || !mx_dev || n_t < 1)
+    return fail(TGBA_EINVAL, "need variants, n_t >= 1 and an output buffer");
+  if (!(h_z0 > 0) || !std::isfinite(t_max) || t_max < 0) return fail(TGBA_EINVAL, "need h_z0 > 0 and t_max >= 0");
+  if (!b->x_valid) return fail(TGBA_EINVAL, "no X computed yet: call tgba_compute_x");
+  return quench(*b, s, h_z0, hx_variants, ecut_variants, n_variants, t_max, n_t, mx_dev, norm_dev, chi_host,
+                (cudaStream_t)stream);
+}
+
+tgba_status tgba_fp64_peak(int32_t reps, double* gflops) {
+  if (!gflops || reps < 1) return fail(TGBA_EINVAL, "bad arguments");
+  tgba_status r = require_device();
+  if (r != TGBA_OK) return r;
+  return fp64_peak(reps, gflops);
+}
+
+}  // extern "C"

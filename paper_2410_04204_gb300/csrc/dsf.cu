@@ -1,0 +1,148 @@
+// Dynamic structure factor at k = 0 (row a8; Eq. 8-9 and the matrix element that follows them):
+//   S(w) = 2 pi sum_a w_a L_eta(w - (E_a - E_0)),   w_a = L |<psi_0|sigma^x_1|psi_a>|^2,
+//   L_eta(x) = (eta/pi) / (x^2 + eta^2).
+// The weights are computed in FP64 in the real gauge (w_a = L (u_a^T X~ u_0)^2 with X~ the
+// real-gauge <phi|sigma^x_1|phi'>), then the Lorentzian sum runs in FP32 with FP32
+// accumulation.  To keep the FP32 sum accurate near the peaks, w_i and E_a - E_0 are each
+// carried as an unevaluated float pair (hi + lo), and x = (w_hi - e_hi) + (w_lo - e_lo): the
+// first difference is exact when the two are within a factor of two (Sterbenz), which is where
+// the Lorentzian is largest.  Each lane sums a strided share of the states, then a warp-shuffle
+// tree adds the 32 partial sums.
+#include <algorithm>
+
+#include "tgba_internal.h"
+
+namespace tgba {
+namespace {
+
+// v = X~full u0 (c = |C0|):  v_ns[a] = c sum_b P[a][b] u0[kn + b],  v_r[b] = c sum_a P[a][b] u0[a]
+__global__ void sigma_rows(int64_t n_ns, int64_t n_r, const double* __restrict__ P, const double* __restrict__ u0,
+                           const double* __restrict__ c0, double* __restrict__ v) {
+  const double c = sqrt(c0[0] * c0[0] + c0[1] * c0[1]);
+  const int lane = threadIdx.x & 31;
+  for (int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < n_ns;
+       a += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    double acc = 0.0;
+    for (int64_t b = lane; b < n_r; b += 32) acc = fma(P[a * n_r + b], u0[n_ns + b], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) v[a] = c * acc;
+  }
+}
+
+__global__ void sigma_cols(int64_t n_ns, int64_t n_r, const double* __restrict__ P, const double* __restrict__ u0,
+                           const double* __restrict__ c0, double* __restrict__ v) {
+  const double c = sqrt(c0[0] * c0[0] + c0[1] * c0[1]);
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n_r; b += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int64_t a = 0; a < n_ns; ++a) acc = fma(P[a * n_r + b], u0[a], acc);
+    v[n_ns + b] = c * acc;
+  }
+}
+
+// w_a = L (sum_i U[i][a] v_i)^2, dE_a = E_a - E_0, and the float pairs of the FP32 stage.
+__global__ void weights_kernel(int64_t n, const double* __restrict__ U, const double* __restrict__ v,
+                               const double* __restrict__ E, double L, double two_eta, double* __restrict__ w,
+                               double* __restrict__ dE, float* __restrict__ e_hi, float* __restrict__ e_lo,
+                               float* __restrict__ cw) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < n;
+       a += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    double acc = 0.0;
+    for (int64_t i = lane; i < n; i += 32) acc = fma(U[a * n + i], v[i], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      const double wa = L * acc * acc, d = E[a] - E[0];
+      w[a] = wa;
+      dE[a] = d;
+      const float hi = (float)d;
+      e_hi[a] = hi;
+      e_lo[a] = (float)(d - (double)hi);
+      cw[a] = (float)(two_eta * wa);      // 2 pi * (eta / pi) * w_a
+    }
+  }
+}
+
+constexpr int kWPerWarp = 4;
+
+__global__ void lorentz_kernel(int n_w, double w_min, double w_span, int64_t n, const float* __restrict__ e_hi,
+                               const float* __restrict__ e_lo, const float* __restrict__ cw, float eta2,
+                               float* __restrict__ S) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int i0 = warp * kWPerWarp;
+  if (i0 >= n_w) return;
+  float wh[kWPerWarp], wl[kWPerWarp], acc[kWPerWarp];
+#pragma unroll
+  for (int q = 0; q < kWPerWarp; ++q) {
+    const int i = min(i0 + q, n_w - 1);
+    const double w = n_w > 1 ? w_min + (w_span * i) / (n_w - 1) : w_min;
+    wh[q] = (float)w;
+    wl[q] = (float)(w - (double)wh[q]);
+    acc[q] = 0.0f;
+  }
+  for (int64_t a = lane; a < n; a += 32) {
+    const float eh = e_hi[a], el = e_lo[a], c = cw[a];
+#pragma unroll
+    for (int q = 0; q < kWPerWarp; ++q) {
+      const float x = (wh[q] - eh) + (wl[q] - el);
+      acc[q] += c / fmaf(x, x, eta2);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kWPerWarp; ++q) {
+    float s = acc[q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0 && i0 + q < n_w) S[i0 + q] = s;
+  }
+}
+
+}  // namespace
+
+tgba_status dsf(Basis& b, int s, double h_x, double w_min, double w_max, int n_w, double eta, float* S,
+                double* evals, int n_ev, double* weights, double* dE, cudaStream_t st) {
+  const Sector& sec = b.sectors[s];
+  const int64_t n = sec.n_ns + sec.n_r;
+  if (n == 0) return fail(TGBA_EINVAL, "empty sector");
+  // scratch: A (n x n), E (n), v (n), w (n), dE (n), 3 float arrays (n)
+  const int64_t need = n * n + 5 * n + (3 * n + 1) / 2 + 8;
+  if (need > b.eig_a_cap) {
+    if (b.d_eig_a) cudaFree(b.d_eig_a);
+    b.d_eig_a = nullptr;
+    b.eig_a_cap = 0;
+    if (cudaMalloc(&b.d_eig_a, need * sizeof(double)) != cudaSuccess) return fail(TGBA_ENOMEM, "DSF scratch");
+    b.eig_a_cap = need;
+  }
+  double* A = b.d_eig_a;
+  double* E = A + n * n;
+  double* v = E + n;
+  double* w = v + n;
+  double* d = w + n;
+  float* e_hi = (float*)(d + n);
+  float* e_lo = e_hi + n;
+  float* cw = e_lo + n;
+  tgba_status r = build_real_heff(b, s, h_x, A, nullptr, sec.n_ns, nullptr, sec.n_r, st);
+  if (r != TGBA_OK) return r;
+  if ((r = eig_sym(b, n, A, E, true, st)) != TGBA_OK) return r;
+  const double* P = b.d_P + sec.x_off;
+  if (sec.n_ns > 0 && sec.n_r > 0) {
+    sigma_rows<<<(int)std::min<int64_t>((sec.n_ns * 32 + 255) / 256, 152 * 16), 256, 0, st>>>(sec.n_ns, sec.n_r, P, A,
+                                                                                            b.d_c0, v);
+    sigma_cols<<<(int)std::min<int64_t>((sec.n_r + 255) / 256, 152 * 16), 256, 0, st>>>(sec.n_ns, sec.n_r, P, A,
+                                                                                       b.d_c0, v);
+  } else {
+    TGBA_CUDA(cudaMemsetAsync(v, 0, n * sizeof(double), st));
+  }
+  weights_kernel<<<(int)std::min<int64_t>((n * 32 + 255) / 256, 152 * 16), 256, 0, st>>>(
+      n, A, v, E, (double)b.L, 2.0 * eta, w, d, e_hi, e_lo, cw);
+  const int warps = (n_w + kWPerWarp - 1) / kWPerWarp;
+  lorentz_kernel<<<(warps * 32 + 255) / 256, 256, 0, st>>>(n_w, w_min, w_max - w_min, n, e_hi, e_lo, cw,
+                                                          (float)(eta * eta), S);
+  TGBA_CUDA(cudaGetLastError());
+  if (evals && n_ev > 0)
+    TGBA_CUDA(cudaMemcpyAsync(evals, E, std::min<int64_t>(n_ev, n) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (weights) TGBA_CUDA(cudaMemcpyAsync(weights, w, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (dE) TGBA_CUDA(cudaMemcpyAsync(dE, d, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return check_status(b, st);
+}
+
+}  // namespace tgba

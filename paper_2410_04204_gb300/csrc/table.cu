@@ -1,0 +1,219 @@
+// Contraction table of the Bogoliubov operators (row a3 of the hot path).
+//
+// For <phi_a^NS| c_1 + c_1^dag |phi_b^R> the paper writes both states as Bogoliubov operators on
+// the Jordan-Wigner vacuum, so the element is the Pfaffian of the skew matrix A of pairwise
+// contractions <O_a O_b> (Eq. S1-S2) over the operator string
+//   [NS vacuum bra: d_k^dag, k ascending] [NS excitations: d_p, p descending] [c_1 + c_1^dag]
+//   [R excitations: d_q^dag (c_pi^dag at pi), q ascending] [R vacuum: d_k, k != pi, descending]
+// of which one element keeps the 2L vacuum/sigma operators F and the M + M' excitation
+// operators of the two states.  Ordering the rows as [F | E] (a permutation of sign +1 for the
+// kept subsets, because M and M' are even), Pf(A[F u sel]) = Pf(A_FF) Pf(S[sel, sel]) with the
+// Schur complement S = A_EE + A_FE^T A_FF^{-1} A_FE.  This kernel forms A over all 4L operators
+// and eliminates the F block by Parlett-Reid steps with pivoting inside F; what is left of the
+// E block is S, and the product of pivots is Pf(A_FF).
+//
+// Diagonal gauge: with psi_a = -s_a k_a - pi/4 (s = +1 for NS bra operators, -1 for R ket
+// operators), R_ab = e^{-i(psi_a + psi_b)} S_ab is real, so Pf(S[sel]) = e^{i sum psi} Pf(R[sel]);
+// within a momentum sector sum s k = 0 mod 2 pi and the phase is (-i)^{n/2}.  The kernel stores R
+// and records max |Im| of the rotated entries so a violation is reported, never dropped.
+//
+// The sums over sites j = 1..L are closed-form geometric series of plane waves.
+#include <cmath>
+
+#include "tgba_internal.h"
+
+namespace tgba {
+namespace {
+
+enum { K_C = 0, K_CDAG = 1, K_D = 2, K_DDAG = 3, K_SIGMA = 4 };
+
+struct Op {
+  int kind, n, pos;   // kind, momentum label (k = pi n / L), position in the operator string
+  double theta;
+};
+
+struct cd { double x, y; };
+__device__ __forceinline__ cd mk(double x, double y) { return cd{x, y}; }
+__device__ __forceinline__ cd add(cd a, cd b) { return cd{a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ cd sub(cd a, cd b) { return cd{a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ cd mul(cd a, cd b) { return cd{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ __forceinline__ cd scal(cd a, double s) { return cd{a.x * s, a.y * s}; }
+__device__ __forceinline__ double abs2(cd a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ cd inv(cd a) { double d = abs2(a); return cd{a.x / d, -a.y / d}; }
+__device__ __forceinline__ cd expi(double t) { double s, c; sincos(t, &s, &c); return cd{c, s}; }
+
+// Plane-wave parts of an operator: O = u sum_j e^{i su k j} c_j^dag / sqrt(L) + v sum_j e^{i sv k j} c_j / sqrt(L)
+__device__ void plane(const Op& o, cd& u, int& su, cd& v, int& sv) {
+  double s, c;
+  sincos(0.5 * o.theta, &s, &c);
+  u = mk(0, 0); v = mk(0, 0); su = 1; sv = 1;
+  switch (o.kind) {
+    case K_C: v = mk(1, 0); sv = -1; break;
+    case K_CDAG: u = mk(1, 0); su = 1; break;
+    case K_D: v = mk(s, 0); sv = -1; u = mk(0, -c); su = -1; break;      // s c_k - i c c_{-k}^dag
+    case K_DDAG: u = mk(s, 0); su = 1; v = mk(0, c); sv = 1; break;      // s c_k^dag + i c c_{-k}
+  }
+}
+
+// sum_{j=1}^{L} e^{i pi nq j / L}
+__device__ cd geo(int nq, int L) {
+  int r = ((nq % (2 * L)) + 2 * L) % (2 * L);
+  if (r == 0) return mk((double)L, 0);
+  if (r % 2 == 0) return mk(0, 0);
+  double q = M_PI * (double)r / L;
+  return mk(-1.0, cos(0.5 * q) / sin(0.5 * q));       // -1 + i cot(q/2)
+}
+
+// <0| O_a O_b |0>_c = sum_j V_a(j) U_b(j)
+__device__ cd contract(const Op& a, const Op& b, int L) {
+  const double rl = 1.0 / sqrt((double)L);
+  if (a.kind == K_SIGMA) {            // V_a(j) = delta_{j1}: U_b(1)
+    cd u, v; int su, sv;
+    plane(b, u, su, v, sv);
+    return scal(mul(u, expi(su * M_PI * b.n / L)), rl);
+  }
+  cd ua, va, ub, vb; int sua, sva, sub_, svb;
+  plane(a, ua, sua, va, sva);
+  if (b.kind == K_SIGMA) {            // U_b(j) = delta_{j1}: V_a(1)
+    return scal(mul(va, expi(sva * M_PI * a.n / L)), rl);
+  }
+  plane(b, ub, sub_, vb, svb);
+  cd g = geo(sva * a.n + sub_ * b.n, L);
+  return scal(mul(mul(va, ub), g), 1.0 / L);
+}
+
+__device__ Op op_of(int g, int L, const int* nlab, const double* theta) {
+  // nlab/theta: NS modes [0, L), R modes [L, 2L), each ascending in k
+  Op o;
+  if (g < L) {                                       // NS vacuum (bra): d_k^dag, ascending
+    o.kind = K_DDAG; o.n = nlab[g]; o.theta = theta[g]; o.pos = g;
+  } else if (g == L) {
+    o.kind = K_SIGMA; o.n = 0; o.theta = 0; o.pos = 2 * L;
+  } else if (g < 2 * L) {                            // R vacuum (ket): d_k, k != pi, descending
+    int i = (L - 2) - (g - L - 1);
+    o.kind = K_D; o.n = nlab[L + i]; o.theta = theta[L + i]; o.pos = 2 * L + g;
+  } else if (g < 3 * L) {                            // NS excitations (bra): d_p, descending
+    int e = g - 2 * L, i = L - 1 - e;
+    o.kind = K_D; o.n = nlab[i]; o.theta = theta[i]; o.pos = L + e;
+  } else {                                           // R excitations (ket), ascending
+    int e = g - 2 * L, i = e - L;
+    int n = nlab[L + i];
+    o.kind = (n == L) ? K_CDAG : K_DDAG; o.n = n; o.theta = theta[L + i]; o.pos = L + 1 + e;
+  }
+  return o;
+}
+
+__device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMax((unsigned long long*)addr, (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void __launch_bounds__(1024) table_kernel(int L, const int* nlab, const double* theta, double vac_norm,
+                                                     cd* A, double* R, double* c0, unsigned* status) {
+  const int n4 = 4 * L, n2 = 2 * L;
+  __shared__ cd tau[4 * kMaxL];
+  __shared__ int s_piv;
+  __shared__ cd s_pf;
+  // 1) A over all operators, rows/cols in the order [F | E]
+  for (int idx = threadIdx.x; idx < n4 * n4; idx += blockDim.x) {
+    int g = idx / n4, h = idx % n4;
+    if (g > h) continue;
+    cd val = mk(0, 0);
+    if (g != h) {
+      Op a = op_of(g, L, nlab, theta), b = op_of(h, L, nlab, theta);
+      val = (a.pos < b.pos) ? contract(a, b, L) : scal(contract(b, a, L), -1.0);
+    }
+    A[(size_t)g * n4 + h] = val;
+    A[(size_t)h * n4 + g] = scal(val, -1.0);
+  }
+  if (threadIdx.x == 0) s_pf = mk(1, 0);
+  __syncthreads();
+  // 2) Parlett-Reid on the F block, updating the whole trailing matrix
+  for (int k = 0; k < n2; k += 2) {
+    if (threadIdx.x < 32) {
+      double best = -1; int bi = k + 1;
+      for (int i = k + 1 + threadIdx.x; i < n2; i += 32) {
+        double v = abs2(A[(size_t)i * n4 + k]);
+        if (v > best) { best = v; bi = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (threadIdx.x == 0) s_piv = bi;
+    }
+    __syncthreads();
+    const int p = s_piv, r = k + 1;
+    if (p != r) {
+      for (int j = threadIdx.x; j < n4; j += blockDim.x) {
+        cd t = A[(size_t)r * n4 + j]; A[(size_t)r * n4 + j] = A[(size_t)p * n4 + j]; A[(size_t)p * n4 + j] = t;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+        cd t = A[(size_t)i * n4 + r]; A[(size_t)i * n4 + r] = A[(size_t)i * n4 + p]; A[(size_t)i * n4 + p] = t;
+      }
+      __syncthreads();
+    }
+    const cd a = A[(size_t)k * n4 + r];
+    if (threadIdx.x == 0) {
+      s_pf = mul(s_pf, a);
+      if (p != r) s_pf = scal(s_pf, -1.0);
+    }
+    const cd ia = inv(a);
+    for (int j = k + 2 + threadIdx.x; j < n4; j += blockDim.x) tau[j] = mul(A[(size_t)k * n4 + j], ia);
+    __syncthreads();
+    const int m = n4 - (k + 2);
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+      int i = k + 2 + idx / m, j = k + 2 + idx % m;
+      if (i >= j) continue;
+      // A_ij += A[k+1][i] tau_j - tau_i A[k+1][j]
+      cd v = add(A[(size_t)i * n4 + j], sub(mul(A[(size_t)r * n4 + i], tau[j]), mul(tau[i], A[(size_t)r * n4 + j])));
+      A[(size_t)i * n4 + j] = v;
+      A[(size_t)j * n4 + i] = scal(v, -1.0);
+    }
+    __syncthreads();
+  }
+  // 3) gauge rotation of the Schur complement to the real table
+  for (int idx = threadIdx.x; idx < n2 * n2; idx += blockDim.x) {
+    int a = idx / n2, b = idx % n2;
+    double val = 0;
+    if (a != b) {
+      cd s = A[(size_t)(n2 + a) * n4 + (n2 + b)];
+      int ia = a < L ? (L - 1 - a) : (L + (a - L)), ib = b < L ? (L - 1 - b) : (L + (b - L));
+      int sa = a < L ? 1 : -1, sb = b < L ? 1 : -1;
+      // R = i e^{i(s_a k_a + s_b k_b)} S
+      cd rot = mul(mk(0, 1), expi(M_PI * (double)(sa * nlab[ia] + sb * nlab[ib]) / L));
+      cd v = mul(rot, s);
+      val = v.x;
+      atomic_max_pos(c0 + 2, fabs(v.y));
+      atomic_max_pos(c0 + 3, fabs(v.x));
+    }
+    R[idx] = val;
+  }
+  if (threadIdx.x == 0) {
+    cd pf = s_pf;
+    c0[0] = pf.x * vac_norm;
+    c0[1] = pf.y * vac_norm;
+    if (!(abs2(pf) > 1e-200) || !isfinite(pf.x) || !isfinite(pf.y)) atomicOr(status, kStTableSingular);
+  }
+}
+
+__global__ void table_check(const double* c0, unsigned* status) {
+  if (!(c0[2] <= 1e-9 * c0[3])) atomicOr(status, kStTableImag);
+}
+
+}  // namespace
+
+tgba_status build_table(Basis& b, cudaStream_t st) {
+  const int L = b.L;
+  TGBA_CUDA(cudaMemsetAsync(b.d_c0, 0, 4 * sizeof(double), st));
+  table_kernel<<<1, 1024, 0, st>>>(L, b.d_nlab, b.d_theta, b.vac_norm, (cd*)b.d_work, b.d_table, b.d_c0, b.d_status);
+  TGBA_CUDA(cudaGetLastError());
+  table_check<<<1, 1, 0, st>>>(b.d_c0, b.d_status);
+  TGBA_CUDA(cudaGetLastError());
+  b.table_valid = true;
+  return TGBA_OK;
+}
+
+}  // namespace tgba

@@ -1,0 +1,166 @@
+// Internal declarations shared by the translation units of libtgba.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tgba.h"
+
+namespace tgba {
+
+constexpr int kMaxQp = 16;        // quasiparticles per state
+constexpr int kMaxL = 120;        // 2L excitation operators must index a uint8 table row
+constexpr int kMaxN = 2 * kMaxQp; // largest Pfaffian M_a + M_b
+
+// Device status word bits (tgba_status is derived from them at the next sync).
+enum : unsigned { kStNan = 1u, kStTableImag = 2u, kStTableSingular = 4u, kStTimeout = 8u, kStBadIndex = 16u };
+
+// A contiguous run of states with the same quasiparticle number.
+struct Group { int M; int64_t begin, end; };
+
+struct Sector {
+  int32_t m = 0;
+  int64_t n_ns = 0, n_r = 0;
+  int64_t ns_off = 0, r_off = 0;   // first state of the sector in the per-parity arrays
+  int64_t x_off = 0;               // first element of the sector's X block ([n_ns][n_r])
+  int64_t h_off = 0;               // first complex entry of the sector's H_eff
+  int64_t ev_off = 0;              // first eigenvalue of the sector
+  std::vector<Group> g_ns, g_r;
+};
+
+// Per-parity state tables, all sectors concatenated, in basis order.
+struct StateTable {
+  std::vector<double> E;
+  std::vector<uint8_t> M;
+  std::vector<int16_t> modes;      // [state][max_qp], ascending mode indices, -1 padded
+};
+
+// Work unit of the Pfaffian stage: up to `count` consecutive elements of a rectangle of
+// pairs with uniform (M_a, M_b), laid out row-major (row = NS state, column = R state).
+struct Tile {
+  int64_t out0;   // element index of the rectangle's first pair in the X cache
+  int64_t ns0;    // global NS state index of the rectangle's first row
+  int64_t r0;     // global R state index of the rectangle's first column
+  int32_t ld;     // row stride of the sector's X block (n_r)
+  int32_t w;      // rectangle width
+  int32_t lin0;   // first linear index (within the rectangle) of this tile
+  int32_t count;  // elements in this tile
+  int32_t n;      // Pfaffian size M_a + M_b
+  int32_t Ma;     // quasiparticles of the NS state
+};
+
+// Single-particle data of one parity at field h (Eq. 7, S3), host side.
+struct Modes {
+  int N = 0, parity = 0;
+  double h = 0;
+  std::vector<int> nlab;           // k = pi nlab / N, ascending
+  std::vector<double> eps, theta, ex;
+  double e_vac = 0, norm = 1;
+};
+Modes make_modes(int N, int parity, double h);
+
+struct Basis;
+
+// basis.cpp
+tgba_status enumerate_basis(const tgba_model& model, const int32_t* sectors, int n_sectors,
+                            const tgba_trunc& tr, Basis& b);
+void build_tiles(const Basis& b, int tile_elems, std::vector<Tile>& tiles, std::vector<int>& class_begin);
+
+struct Basis {
+  int L = 0;
+  double J = 1, h = 1;             // h = h_z / J
+  int max_qp = 0;
+  double e_cut = -1;
+  int64_t cap = 0;
+  double e_ns_vac = 0;             // NS vacuum energy (in units of J)
+  std::vector<Sector> sectors;
+  StateTable ns, r;
+  int64_t n_elements = 0, n_heff = 0, n_states = 0;
+  int max_n = 0;                   // largest M_a + M_b in the basis
+
+  // device copies
+  int device = 0;
+  double* d_E_ns = nullptr; double* d_E_r = nullptr;
+  uint8_t* d_M_ns = nullptr; uint8_t* d_M_r = nullptr;
+  uint8_t* d_sel_ns = nullptr; uint8_t* d_sel_r = nullptr;   // [state][max_qp] table rows
+  int16_t* d_modes_ns = nullptr; int16_t* d_modes_r = nullptr; // [state][max_qp] mode indices
+  // mode data at h (host-computed, Eq. 7): theta of NS then R modes, and the labels n
+  double* d_theta = nullptr;       // [2L]
+  int* d_nlab = nullptr;           // [2L]
+  double vac_norm = 1;             // n_NS n_R (Eq. S3)
+  // contraction table
+  double* d_table = nullptr;       // R, 2L x 2L row-major
+  double* d_c0 = nullptr;          // C0 (re, im), then diagnostics: max |Im| residual, max |R|
+  double c0_host[2] = {0, 0};
+  double* d_work = nullptr;        // 4L x 4L complex scratch of the table build
+  bool table_valid = false;
+  // Pfaffian stage
+  double* d_P = nullptr;           // X_ab = C0 (-i)^{(M_a+M_b)/2} P_ab, P real, [n_elements]
+  bool x_valid = false;
+  const void* x_screen = nullptr;
+  double x_tau = 0;
+  int64_t x_evaluated = 0, x_screened = 0;
+  std::vector<Tile> tiles;
+  std::vector<int> tile_class_begin;   // tiles sorted by size class; class c = [begin[c], begin[c+1])
+  Tile* d_tiles = nullptr;
+  unsigned* d_status = nullptr;
+  // eigen solver scratch
+  void* solver = nullptr;          // cusolverDnHandle_t
+  void* blas = nullptr;            // cublasHandle_t
+  double* d_eig_a = nullptr; double* d_eig_w = nullptr; double* d_eig_work = nullptr;
+  double* d_scratch = nullptr; int64_t scratch_cap = 0;
+  int* d_eig_info = nullptr;
+  int64_t eig_a_cap = 0, eig_work_cap = 0;
+};
+
+// error helpers (api.cpp)
+tgba_status fail(tgba_status st, const std::string& msg);
+tgba_status cuda_fail(cudaError_t e, const char* what);
+
+// table.cu
+tgba_status build_table(Basis& b, cudaStream_t st);
+
+// pfaffian.cu
+tgba_status run_pfaffians(Basis& b, const uint8_t* d_mask, cudaStream_t st);
+tgba_status run_pfaffian_pairs(Basis& b, int s, const int32_t* pairs, int64_t n, double* out, cudaStream_t st);
+
+// assemble.cu
+tgba_status assemble_heff(Basis& b, double h_x, double* heff, cudaStream_t st);
+tgba_status export_x(Basis& b, int s, double* x, cudaStream_t st);
+tgba_status build_real_heff(Basis& b, int s, double h_x, double* a, const int32_t* idx_ns, int64_t kn,
+                            const int32_t* idx_r, int64_t kr, cudaStream_t st);
+
+// eig.cu / quench.cu: library handles
+void destroy_solver(void* h);
+void destroy_blas(void* h);
+
+// eig.cu
+tgba_status eig_sym(Basis& b, int64_t n, double* a, double* w, bool vectors, cudaStream_t st);
+
+// dsf.cu
+tgba_status dsf(Basis& b, int s, double h_x, double w_min, double w_max, int n_w, double eta, float* S,
+                double* evals, int n_ev, double* weights, double* dE, cudaStream_t st);
+
+// quench.cu
+tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* ecut, int nv, double t_max,
+                   int n_t, double* mx, double* norm, int64_t* chi, cudaStream_t st);
+
+// status word
+tgba_status check_status(Basis& b, cudaStream_t st);
+
+// device scratch owned by the handle (grown on demand)
+tgba_status scratch(Basis& b, int64_t doubles, double** out);
+
+// peak.cu
+tgba_status fp64_peak(int reps, double* gflops);
+
+}  // namespace tgba
+
+#define TGBA_CUDA(call)                                            \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return ::tgba::cuda_fail(e_, #call);    \
+  } while (0)

@@ -1,0 +1,216 @@
+"""Thin Python binding of libtgba.so (include/tgba.h), with the C names.
+
+Argument marshalling only: every step runs in the library's CUDA kernels (and its cuSOLVER /
+cuBLAS calls).  Device buffers are torch CUDA tensors allocated by the caller; streams default
+to torch's current stream.  There is no fallback: if the library is not built or cannot be
+loaded, the first call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+TGBA_OK, TGBA_EINVAL, TGBA_ENOMEM, TGBA_ECUDA, TGBA_ENUMERIC, TGBA_ETIMEOUT, TGBA_ELIMIT = range(7)
+_NAMES = {0: "TGBA_OK", 1: "TGBA_EINVAL", 2: "TGBA_ENOMEM", 3: "TGBA_ECUDA", 4: "TGBA_ENUMERIC",
+          5: "TGBA_ETIMEOUT", 6: "TGBA_ELIMIT"}
+
+# every symbol include/tgba.h declares
+SYMBOLS = ("tgba_last_error", "tgba_device_count", "tgba_build_basis", "tgba_basis_info", "tgba_basis_totals",
+           "tgba_basis_free", "tgba_compute_x", "tgba_x_stats", "tgba_x_export", "tgba_x_pairs", "tgba_table",
+           "tgba_assemble_heff", "tgba_eigvals", "tgba_dsf", "tgba_quench", "tgba_fp64_peak")
+
+
+class TgbaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (_NAMES.get(code, code), msg))
+        self.code = code
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("J", ctypes.c_double), ("h_z", ctypes.c_double), ("h_x", ctypes.c_double)]
+
+
+class _Trunc(ctypes.Structure):
+    _fields_ = [("max_qp", ctypes.c_int32), ("e_cut", ctypes.c_double), ("max_per_parity", ctypes.c_int64)]
+
+
+_lib = None
+_P, _I32, _I64, _D, _VP = ctypes.POINTER, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+
+
+def lib():
+    """Load libtgba.so (built in-tree by paper_2410_04204_gb300/build.py)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libtgba.so is not built (%s); run paper_2410_04204_gb300.build.build()" % _build.LIB)
+        L = ctypes.CDLL(_build.LIB)
+        sig = {
+            "tgba_last_error": (ctypes.c_char_p, []),
+            "tgba_device_count": (_I32, []),
+            "tgba_build_basis": (_I32, [_P(_Model), _P(_I32), _I32, _P(_Trunc), _P(_VP)]),
+            "tgba_basis_info": (_I32, [_VP, _I32, _P(_I64), _P(_I64), _VP, _VP, _VP, _VP]),
+            "tgba_basis_totals": (_I32, [_VP, _P(_I32), _P(_I64), _P(_I64)]),
+            "tgba_basis_free": (_I32, [_VP]),
+            "tgba_compute_x": (_I32, [_VP, _VP, _D, _D, _VP]),
+            "tgba_x_stats": (_I32, [_VP, _P(_I64), _P(_I64)]),
+            "tgba_x_export": (_I32, [_VP, _I32, _VP, _VP]),
+            "tgba_x_pairs": (_I32, [_VP, _I32, _VP, _I64, _VP, _VP]),
+            "tgba_table": (_I32, [_VP, _VP, _VP, _VP]),
+            "tgba_assemble_heff": (_I32, [_VP, _D, _VP, _D, _VP, _VP]),
+            "tgba_eigvals": (_I32, [_VP, _D, _VP, _VP]),
+            "tgba_dsf": (_I32, [_VP, _I32, _D, _D, _D, _I32, _D, _VP, _VP, _I32, _VP, _VP, _VP]),
+            "tgba_quench": (_I32, [_VP, _I32, _D, _VP, _VP, _I32, _D, _I32, _VP, _VP, _VP, _VP]),
+            "tgba_fp64_peak": (_I32, [_I32, _P(_D)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code):
+    if code != TGBA_OK:
+        raise TgbaError(code, lib().tgba_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(stream)
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _cuda_tensor(t, dtype, numel=None, name="buffer"):
+    import torch
+    if t is None:
+        return
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous CUDA %s tensor" % (name, dtype))
+    if numel is not None and t.numel() < numel:
+        raise ValueError("%s holds %d elements, needs %d" % (name, t.numel(), numel))
+
+
+def tgba_device_count():
+    return int(lib().tgba_device_count())
+
+
+def tgba_build_basis(L, h_z, sectors, max_qp, e_cut=-1.0, max_per_parity=0, J=1.0):
+    """Returns the basis handle (int)."""
+    m = _Model(int(L), float(J), float(h_z), 0.0)
+    t = _Trunc(int(max_qp), -1.0 if e_cut is None else float(e_cut), int(max_per_parity or 0))
+    sec = np.ascontiguousarray(np.asarray(list(sectors), dtype=np.int32))
+    h = _VP()
+    _check(lib().tgba_build_basis(ctypes.byref(m), sec.ctypes.data_as(_P(_I32)), len(sec), ctypes.byref(t),
+                                  ctypes.byref(h)))
+    return h.value
+
+
+def tgba_basis_info(b, s, max_qp):
+    """Sizes and state tables of sector s (numpy, basis order)."""
+    n_ns, n_r = _I64(), _I64()
+    _check(lib().tgba_basis_info(b, s, ctypes.byref(n_ns), ctypes.byref(n_r), None, None, None, None))
+    n = n_ns.value + n_r.value
+    E = np.zeros(n, np.float64)
+    par = np.zeros(n, np.uint8)
+    nqp = np.zeros(n, np.uint8)
+    modes = np.zeros((n, max(1, max_qp)), np.int16)
+    _check(lib().tgba_basis_info(b, s, ctypes.byref(n_ns), ctypes.byref(n_r), E.ctypes.data, par.ctypes.data,
+                                 nqp.ctypes.data, modes.ctypes.data))
+    return dict(n_ns=n_ns.value, n_r=n_r.value, E0=E, parity=par, nqp=nqp, modes=modes[:, :max_qp])
+
+
+def tgba_basis_totals(b):
+    ns, ne, nh = _I32(), _I64(), _I64()
+    _check(lib().tgba_basis_totals(b, ctypes.byref(ns), ctypes.byref(ne), ctypes.byref(nh)))
+    return ns.value, ne.value, nh.value
+
+
+def tgba_basis_free(b):
+    _check(lib().tgba_basis_free(b))
+
+
+def tgba_compute_x(b, screen=None, screen_tau=0.0, screen_hx=0.0, stream=None):
+    _check(lib().tgba_compute_x(b, screen, float(screen_tau), float(screen_hx), _stream(stream)))
+
+
+def tgba_x_stats(b):
+    ev, sc = _I64(), _I64()
+    _check(lib().tgba_x_stats(b, ctypes.byref(ev), ctypes.byref(sc)))
+    return ev.value, sc.value
+
+
+def tgba_x_export(b, s, x_out, stream=None):
+    """x_out: complex128 CUDA tensor with n_ns * n_r elements."""
+    import torch
+    _cuda_tensor(x_out, torch.complex128, name="x_out")
+    _check(lib().tgba_x_export(b, s, _ptr(x_out), _stream(stream)))
+
+
+def tgba_x_pairs(b, s, pairs, out, stream=None):
+    """pairs: int32 CUDA tensor [n, 2] (NS index, R index); out: complex128 CUDA tensor [n]."""
+    import torch
+    _cuda_tensor(pairs, torch.int32, name="pairs")
+    _cuda_tensor(out, torch.complex128, pairs.shape[0], name="out")
+    _check(lib().tgba_x_pairs(b, s, _ptr(pairs), pairs.shape[0], _ptr(out), _stream(stream)))
+
+
+def tgba_table(b, table_out=None, stream=None):
+    """Returns C0 (complex); fills table_out (float64 CUDA tensor, 2L x 2L) if given."""
+    import torch
+    _cuda_tensor(table_out, torch.float64, name="table_out")
+    c0 = np.zeros(2)
+    _check(lib().tgba_table(b, c0.ctypes.data, _ptr(table_out), _stream(stream)))
+    return complex(c0[0], c0[1])
+
+
+def tgba_assemble_heff(b, h_x, heff_out, screen=None, screen_tau=0.0, stream=None):
+    """heff_out: complex128 CUDA tensor with n_heff elements (all sectors, column-major each)."""
+    import torch
+    _cuda_tensor(heff_out, torch.complex128, name="heff_out")
+    _check(lib().tgba_assemble_heff(b, float(h_x), screen, float(screen_tau), _ptr(heff_out), _stream(stream)))
+
+
+def tgba_eigvals(b, h_x, evals_out, stream=None):
+    import torch
+    _cuda_tensor(evals_out, torch.float64, name="evals_out")
+    _check(lib().tgba_eigvals(b, float(h_x), _ptr(evals_out), _stream(stream)))
+
+
+def tgba_dsf(b, s, h_x, w_min, w_max, n_w, eta, S_out, evals_out=None, n_ev=0, weights_out=None, dE_out=None,
+             stream=None):
+    import torch
+    _cuda_tensor(S_out, torch.float32, n_w, name="S_out")
+    for t in (evals_out, weights_out, dE_out):
+        _cuda_tensor(t, torch.float64)
+    _check(lib().tgba_dsf(b, s, float(h_x), float(w_min), float(w_max), int(n_w), float(eta), _ptr(S_out),
+                          _ptr(evals_out), int(n_ev), _ptr(weights_out), _ptr(dE_out), _stream(stream)))
+
+
+def tgba_quench(b, s, h_z0, hx_variants, ecut_variants, t_max, n_t, mx_out, norm_out=None, stream=None):
+    """Returns the retained basis size of each variant."""
+    import torch
+    hx = np.ascontiguousarray(np.asarray(hx_variants, np.float64))
+    ec = np.ascontiguousarray(np.asarray(ecut_variants, np.float64))
+    if hx.shape != ec.shape:
+        raise ValueError("one cutoff per h_x variant")
+    _cuda_tensor(mx_out, torch.float64, len(hx) * n_t, name="mx_out")
+    _cuda_tensor(norm_out, torch.float64, len(hx), name="norm_out")
+    chi = np.zeros(len(hx), np.int64)
+    _check(lib().tgba_quench(b, s, float(h_z0), hx.ctypes.data, ec.ctypes.data, len(hx), float(t_max), int(n_t),
+                             _ptr(mx_out), _ptr(norm_out), chi.ctypes.data, _stream(stream)))
+    return chi
+
+
+def tgba_fp64_peak(reps=5):
+    g = _D()
+    _check(lib().tgba_fp64_peak(int(reps), ctypes.byref(g)))
+    return g.value
