@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark of the TGBA hot path on GB300 (one JSON line on stdout).
+
+Workload (default): every momentum sector of the L = 24 chain at h_z = 1, M <= 6
+quasiparticles, energy cutoff 11.925 above the NS vacuum (~900 x 900 NS x R states per
+sector), longitudinal fields h_x = 0.05 and 0.1.  One step = the whole hot path on it:
+contraction table, Pfaffians of all NS x R pairs of all sectors (one X serves both h_x), then
+for each h_x the dense complex H_eff of every sector and all its eigenvalues.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+value = H_eff (Pfaffian) elements of the step, summed over ranks, per second of the step
+time (CUDA events on the launching stream, max over ranks).  Under torchrun every rank runs
+its own copy of the workload (weak scaling, no data-path collective).  --impl reference times
+the CPU oracle (direct Pfaffians of size 2N+M+M', numpy eigensolver) on the host cores on a
+bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H_eff elements/sec (FP64 Pfaffian) and % FP64 peak; screened vs plain speedup @1e-6"
+UNIT = "H_eff elements/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-budget-s", type=float, default=12.0)
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def workload_config(w, n_elements=None, n_states=None):
+    cfg = {"workload": w.name, "L": w.L, "h_z": w.h_z, "h_x": list(w.h_x), "sectors": len(w.sectors),
+           "max_qp": w.max_qp, "e_cut": w.e_cut}
+    if n_elements is not None:
+        cfg["elements"] = n_elements
+        cfg["states"] = n_states
+    return cfg
+
+
+# ------------------------------------------------------------------ clocks during the timed region
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.dev = device_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ the oracle on the host cores
+def oracle_sample(w, budget_s, tag=0):
+    """Time the oracle on a bounded, seeded sample of the workload and extrapolate to one step.
+
+    Sample: pairs drawn uniformly from the oracle's own basis of a few sectors, each evaluated
+    by a direct Pfaffian of size 2N+M+M' (Appendix A as written), and one complex128 numpy
+    eigvalsh of a sector-sized Hermitian matrix.  Step estimate = elements x (time per pair) +
+    2 h_x x sum over sectors of the eigensolve time scaled by (n / n_ref)^3."""
+    import numpy as np
+
+    from oracle import basis as obs
+    from oracle import elements as oel
+    from paper_2410_04204_gb300 import inputs
+
+    g = inputs.rng(100 + tag)
+    sectors = sorted(g.choice(w.sectors, size=min(3, len(w.sectors)), replace=False).tolist())
+    bases = {m: obs.sector_basis(w.L, w.h_z, m, w.max_qp, w.e_cut, w.max_per_parity) for m in sectors}
+    sizes = {m: (len(ns), len(r)) for m, (ns, r) in bases.items()}
+    t_pairs, n_pairs, threads = 0.0, 0, 1
+    while t_pairs < 0.6 * budget_s and n_pairs < 65536:
+        batch = []
+        for m in sectors:
+            ns, r = bases[m]
+            if ns and r:
+                for a, bb in inputs.sample_pairs(len(ns), len(r), 256, tag=1000 * tag + m + n_pairs):
+                    batch.append((ns[a].modes, r[bb].modes))
+        t0 = time.perf_counter()
+        _, threads = oel.x_elements(w.L, w.h_z, batch, return_threads=True)
+        t_pairs += time.perf_counter() - t0
+        n_pairs += len(batch)
+    n_ref = max(a + b for a, b in sizes.values())
+    h = g.standard_normal((n_ref, n_ref)) + 1j * g.standard_normal((n_ref, n_ref))
+    h = h + h.conj().T
+    t0 = time.perf_counter()
+    np.linalg.eigvalsh(h)
+    t_eig = time.perf_counter() - t0
+    return dict(t_pair=t_pairs / n_pairs, n_pairs=n_pairs, t_eig=t_eig, n_ref=n_ref, threads=threads,
+                sectors=sectors)
+
+
+def oracle_step_seconds(w, s, sector_sizes):
+    n_el = sum(a * b for a, b in sector_sizes)
+    t = n_el * s["t_pair"]
+    for a, b in sector_sizes:
+        t += len(w.h_x) * s["t_eig"] * ((a + b) / s["n_ref"]) ** 3
+    return t, n_el
+
+
+def oracle_sector_sizes(w):
+    from oracle import basis as obs
+    out = []
+    for m in w.sectors:
+        ns, r = obs.sector_basis(w.L, w.h_z, m, w.max_qp, w.e_cut, w.max_per_parity)
+        out.append((len(ns), len(r)))
+    return out
+
+
+def sample_text(s):
+    return ("%d seeded pairs from sectors %s by direct Pfaffian, %d threads; one complex128 eigvalsh "
+            "of n=%d; extrapolated to the full step" % (s["n_pairs"], s["sectors"], s["threads"], s["n_ref"]))
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2410_04204_gb300 import inputs
+    w = inputs.SECTORS_L24
+    sizes = oracle_sector_sizes(w)
+    budget = max(2.0, args.cpu_budget_s / 2)
+    for k in range(args.warmup):
+        oracle_sample(w, 0.2 * budget, tag=k)
+    vals, secs = [], []
+    for k in range(args.steps):
+        s = oracle_sample(w, budget, tag=100 + k)
+        t, n_el = oracle_step_seconds(w, s, sizes)
+        vals.append(n_el / t)
+        secs.append(t)
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w, sum(a * b for a, b in sizes), sum(a + b for a, b in sizes)),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": s["threads"], "kind": "oracle", "sample": sample_text(s)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ the GPU path
+def run_gb300(args):
+    import torch
+
+    from paper_2410_04204_gb300 import build as libbuild
+    from paper_2410_04204_gb300 import inputs, tgba
+
+    rank, local_rank, world = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    if not os.path.exists(libbuild.LIB):
+        libbuild.build()
+    w = inputs.SECTORS_L24
+    stream = torch.cuda.current_stream()
+    peak_gflops = tgba.tgba_fp64_peak(5)
+    b = tgba.tgba_build_basis(w.L, w.h_z, w.sectors, w.max_qp, w.e_cut)
+    n_sec, n_el, n_heff = tgba.tgba_basis_totals(b)
+    sizes = [(tgba.tgba_basis_info(b, s, w.max_qp)["n_ns"], tgba.tgba_basis_info(b, s, w.max_qp)["n_r"]) for s in range(n_sec)]
+    n_states = sum(a + c for a, c in sizes)
+    H = torch.empty(n_heff, dtype=torch.complex128, device="cuda")
+    evs = {hx: torch.empty(n_states, dtype=torch.float64, device="cuda") for hx in w.h_x}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MiB > L2
+
+    def step():
+        tgba.tgba_compute_x(b)
+        for hx in w.h_x:
+            tgba.tgba_assemble_heff(b, hx, H)
+            tgba.tgba_eigvals(b, hx, evs[hx])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    step_ms, pf_ms, tab_ms = [], [], []
+    launches0 = tgba.tgba_profile(b)["kernel_launches"]
+    clocks = Clocks(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()                      # evict the L2 between steps (outside the step events)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        prof = tgba.tgba_profile(b)
+        pf_ms.append(prof["pfaffian_ms"])
+        tab_ms.append(prof["table_ms"])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = tgba.tgba_profile(b)["kernel_launches"] - launches0
+    step_ms = [a.elapsed_time(c) for a, c in ev]
+    ms = statistics.mean(step_ms)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    prof = tgba.tgba_profile(b)
+    pf_mean = statistics.mean(pf_ms)
+    achieved = prof["pfaffian_flops"] / (pf_mean * 1e-3) / 1e9
+    value = world * n_el / (ms * 1e-3)
+
+    # end to end through the public API with host buffers: host enumeration and upload of the
+    # state tables, the step, and the eigenvalues read back to pinned host memory
+    host_ev = torch.empty(n_states, dtype=torch.float64, pin_memory=True)
+    e2e_s, h2d = [], 0
+    for k in range(max(1, args.e2e_steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b2 = tgba.tgba_build_basis(w.L, w.h_z, w.sectors, w.max_qp, w.e_cut)
+        tgba.tgba_compute_x(b2)
+        for hx in w.h_x:
+            tgba.tgba_assemble_heff(b2, hx, H)
+            tgba.tgba_eigvals(b2, hx, evs[hx])
+            host_ev.copy_(evs[hx], non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_s.append(time.perf_counter() - t0)
+        h2d = tgba.tgba_profile(b2)["upload_bytes"]
+        tgba.tgba_basis_free(b2)
+    e2e_value = world * n_el / statistics.mean(e2e_s)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(workload_config(w, n_el, n_states),
+                           l2="256 MiB buffer written between steps, outside the step events"),
+            "roofline": {"bound": "alu", "kernel": "pf_tiles (FP64 Parlett-Reid Pfaffians)",
+                         "achieved": achieved, "peak": peak_gflops, "unit": "GFLOP/s",
+                         "frac": achieved / peak_gflops, "traffic": None,
+                         "peak_source": "live FP64 DFMA-chain kernel (tgba_fp64_peak); MEASURED_PEAKS.json has no FP64 entry",
+                         "flops_per_launch": prof["pfaffian_flops"], "pfaffian_ms": pf_mean,
+                         "launches_per_stage": prof["pfaffian_launches"]},
+            "stages_ms": {"table": statistics.mean(tab_ms), "pfaffian": pf_mean,
+                          "heff_and_eigvals": ms - statistics.mean(tab_ms) - pf_mean},
+            "pfaffian_stage": {"elements_per_s": n_el / (pf_mean * 1e-3),
+                               "elements_per_s_with_table": n_el / ((pf_mean + statistics.mean(tab_ms)) * 1e-3)},
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": n_states * 8 * len(w.h_x)},
+            "gpu_launches": launches}
+    tgba.tgba_basis_free(b)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s = oracle_sample(w, args.cpu_budget_s)
+        t_cpu, _ = oracle_step_seconds(w, s, oracle_sector_sizes(w))
+        line["cpu_baseline"] = {"value": n_el / t_cpu, "unit": UNIT, "cores": s["threads"], "kind": "oracle",
+                                "sample": sample_text(s)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -157,6 +157,21 @@ tgba_status tgba_quench(tgba_basis b, int32_t s, double h_z0, const double* hx_v
                         const double* ecut_variants, int32_t n_variants, double t_max, int32_t n_t,
                         double* mx_dev, double* norm_dev, int64_t* chi_host, void* stream);
 
+/* ---------------------------------------------------------------- measurement
+ * Profile of a basis handle.  table_ms / pfaffian_ms: device time of the contraction table and
+ * of the Pfaffian kernels of the last tgba_compute_x, from CUDA events recorded on its stream
+ * (blocks until they complete).  pfaffian_flops: algorithmic FP64 flops of one Pfaffian stage,
+ * sum over elements of F(n) = sum_{m = n-2, n-4, ..., 2} [2 m (m-1) + m] (the real-arithmetic
+ * Parlett-Reid count: two FMAs per updated entry, one multiply per Gauss-vector entry).
+ * pfaffian_launches: kernel launches of one Pfaffian stage.  kernel_launches: all kernel
+ * launches this handle has made (this library's kernels only, not cuSOLVER/cuBLAS).
+ * upload_bytes: host-to-device bytes of tgba_build_basis. */
+typedef struct {
+  double table_ms, pfaffian_ms, pfaffian_flops;
+  int64_t pfaffian_launches, kernel_launches, upload_bytes, evaluated;
+} tgba_prof;
+tgba_status tgba_profile(tgba_basis b, tgba_prof* out);
+
 /* ---------------------------------------------------------------- measurement helper
  * Achieved FP64 rate of a DFMA-chain kernel on the current device (GFLOP/s, best of `reps`),
  * the denominator for FP64 roofline fractions. */

@@ -58,16 +58,20 @@ static void release(Basis* b) {
                   b->d_eig_a, b->d_eig_w, b->d_eig_work, b->d_eig_info, b->d_scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (int e = 0; e < 3; ++e)
+    if (b->ev[e]) cudaEventDestroy(b->ev[e]);
   if (b->solver) destroy_solver(b->solver);
   if (b->blas) destroy_blas(b->blas);
+  if (b->eig_pool) destroy_eig_pool(b->eig_pool);
   delete b;
 }
 
 template <class T>
-static tgba_status upload(T** dst, const T* src, size_t count) {
+static tgba_status upload(T** dst, const T* src, size_t count, int64_t* counter) {
   size_t bytes = std::max<size_t>(1, count) * sizeof(T);
   TGBA_CUDA(cudaMalloc((void**)dst, bytes));
   if (count) TGBA_CUDA(cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice));
+  *counter += (int64_t)(count * sizeof(T));
   return TGBA_OK;
 }
 
@@ -98,14 +102,14 @@ static tgba_status build(const tgba_model* model, const int32_t* sectors, int32_
     const int M = b->r.M[s];
     for (int u = 0; u < M; ++u) sel_r[s * q + u] = (uint8_t)(L + b->r.modes[s * q + u]);
   }
-  if ((r = upload(&b->d_E_ns, b->ns.E.data(), nns)) != TGBA_OK) return r;
-  if ((r = upload(&b->d_E_r, b->r.E.data(), nr)) != TGBA_OK) return r;
-  if ((r = upload(&b->d_M_ns, b->ns.M.data(), nns)) != TGBA_OK) return r;
-  if ((r = upload(&b->d_M_r, b->r.M.data(), nr)) != TGBA_OK) return r;
-  if ((r = upload(&b->d_sel_ns, sel_ns.data(), nns * q)) != TGBA_OK) return r;
-  if ((r = upload(&b->d_sel_r, sel_r.data(), nr * q)) != TGBA_OK) return r;
-  if ((r = upload(&b->d_modes_ns, b->ns.modes.data(), nns * q)) != TGBA_OK) return r;
-  if ((r = upload(&b->d_modes_r, b->r.modes.data(), nr * q)) != TGBA_OK) return r;
+  if ((r = upload(&b->d_E_ns, b->ns.E.data(), nns, &b->upload_bytes)) != TGBA_OK) return r;
+  if ((r = upload(&b->d_E_r, b->r.E.data(), nr, &b->upload_bytes)) != TGBA_OK) return r;
+  if ((r = upload(&b->d_M_ns, b->ns.M.data(), nns, &b->upload_bytes)) != TGBA_OK) return r;
+  if ((r = upload(&b->d_M_r, b->r.M.data(), nr, &b->upload_bytes)) != TGBA_OK) return r;
+  if ((r = upload(&b->d_sel_ns, sel_ns.data(), nns * q, &b->upload_bytes)) != TGBA_OK) return r;
+  if ((r = upload(&b->d_sel_r, sel_r.data(), nr * q, &b->upload_bytes)) != TGBA_OK) return r;
+  if ((r = upload(&b->d_modes_ns, b->ns.modes.data(), nns * q, &b->upload_bytes)) != TGBA_OK) return r;
+  if ((r = upload(&b->d_modes_r, b->r.modes.data(), nr * q, &b->upload_bytes)) != TGBA_OK) return r;
   Modes mns = make_modes(L, 0, b->h), mr = make_modes(L, 1, b->h);
   std::vector<double> th(2 * L);
   std::vector<int> nl(2 * L);
@@ -114,8 +118,8 @@ static tgba_status build(const tgba_model* model, const int32_t* sectors, int32_
     nl[i] = mns.nlab[i]; nl[L + i] = mr.nlab[i];
   }
   b->vac_norm = mns.norm * mr.norm;
-  if ((r = upload(&b->d_theta, th.data(), th.size())) != TGBA_OK) return r;
-  if ((r = upload(&b->d_nlab, nl.data(), nl.size())) != TGBA_OK) return r;
+  if ((r = upload(&b->d_theta, th.data(), th.size(), &b->upload_bytes)) != TGBA_OK) return r;
+  if ((r = upload(&b->d_nlab, nl.data(), nl.size(), &b->upload_bytes)) != TGBA_OK) return r;
   TGBA_CUDA(cudaMalloc((void**)&b->d_table, sizeof(double) * 4 * L * L));
   TGBA_CUDA(cudaMalloc((void**)&b->d_c0, sizeof(double) * 4));
   TGBA_CUDA(cudaMalloc((void**)&b->d_work, sizeof(double) * 2 * 16 * L * L));
@@ -123,7 +127,15 @@ static tgba_status build(const tgba_model* model, const int32_t* sectors, int32_
   TGBA_CUDA(cudaMalloc((void**)&b->d_status, sizeof(unsigned)));
   TGBA_CUDA(cudaMemset(b->d_status, 0, sizeof(unsigned)));
   build_tiles(*b, 0, b->tiles, b->tile_class_begin);
-  if ((r = upload(&b->d_tiles, b->tiles.data(), b->tiles.size())) != TGBA_OK) return r;
+  for (const Tile& t : b->tiles) {
+    double f = 0;
+    for (int m = t.n - 2; m >= 2; m -= 2) f += 2.0 * m * (m - 1) + m;
+    b->pf_flops += f * t.count;
+  }
+  for (int c = 0; c + 1 < (int)b->tile_class_begin.size(); ++c)
+    if (b->tile_class_begin[c + 1] > b->tile_class_begin[c]) ++b->pf_launches;
+  for (int e = 0; e < 3; ++e) TGBA_CUDA(cudaEventCreate(&b->ev[e]));
+  if ((r = upload(&b->d_tiles, b->tiles.data(), b->tiles.size(), &b->upload_bytes)) != TGBA_OK) return r;
   return TGBA_OK;
 }
 
@@ -140,9 +152,13 @@ static tgba_status ensure_table(Basis& b, cudaStream_t st) {
 static tgba_status compute_x(Basis& b, const void* screen, double tau, cudaStream_t st) {
   if (screen != nullptr) return fail(TGBA_EINVAL, "pair screening is not available in this build");
   b.table_valid = false;                 // the table is part of the stage
+  TGBA_CUDA(cudaEventRecord(b.ev[0], st));
   tgba_status r = ensure_table(b, st);
   if (r != TGBA_OK) return r;
+  TGBA_CUDA(cudaEventRecord(b.ev[1], st));
   if ((r = run_pfaffians(b, nullptr, st)) != TGBA_OK) return r;
+  TGBA_CUDA(cudaEventRecord(b.ev[2], st));
+  b.ev_recorded = true;
   b.x_valid = true;
   b.x_screen = screen;
   b.x_tau = tau;
@@ -309,16 +325,8 @@ tgba_status tgba_eigvals(tgba_basis h, double h_x, double* evals_dev, void* stre
   if (!b->x_valid) return fail(TGBA_EINVAL, "no X computed yet: call tgba_compute_x");
   if (!evals_dev && b->n_states > 0) return fail(TGBA_EINVAL, "null output");
   cudaStream_t st = (cudaStream_t)stream;
-  for (size_t s = 0; s < b->sectors.size(); ++s) {
-    const Sector& sec = b->sectors[s];
-    const int64_t n = sec.n_ns + sec.n_r;
-    if (n == 0) continue;
-    double* A;
-    tgba_status r = scratch(*b, n * n, &A);
-    if (r != TGBA_OK) return r;
-    if ((r = build_real_heff(*b, (int)s, h_x, A, nullptr, sec.n_ns, nullptr, sec.n_r, st)) != TGBA_OK) return r;
-    if ((r = eig_sym(*b, n, A, evals_dev + sec.ev_off, false, st)) != TGBA_OK) return r;
-  }
+  tgba_status r = eig_all_sectors(*b, h_x, evals_dev, st);
+  if (r != TGBA_OK) return r;
   return check_status(*b, st);
 }
 
@@ -349,6 +357,27 @@ tgba_status tgba_quench(tgba_basis h, int32_t s, double h_z0, const double* hx_v
   if (!b->x_valid) return fail(TGBA_EINVAL, "no X computed yet: call tgba_compute_x");
   return quench(*b, s, h_z0, hx_variants, ecut_variants, n_variants, t_max, n_t, mx_dev, norm_dev, chi_host,
                 (cudaStream_t)stream);
+}
+
+tgba_status tgba_profile(tgba_basis h, tgba_prof* out) {
+  Basis* b = (Basis*)h;
+  BASIS_OK(b);
+  if (!out) return fail(TGBA_EINVAL, "null output");
+  std::memset(out, 0, sizeof(*out));
+  if (b->ev_recorded) {
+    float t0 = 0, t1 = 0;
+    TGBA_CUDA(cudaEventSynchronize(b->ev[2]));
+    TGBA_CUDA(cudaEventElapsedTime(&t0, b->ev[0], b->ev[1]));
+    TGBA_CUDA(cudaEventElapsedTime(&t1, b->ev[1], b->ev[2]));
+    out->table_ms = t0;
+    out->pfaffian_ms = t1;
+  }
+  out->pfaffian_flops = b->pf_flops;
+  out->pfaffian_launches = b->pf_launches;
+  out->kernel_launches = b->launches.load();
+  out->upload_bytes = b->upload_bytes;
+  out->evaluated = b->x_evaluated;
+  return TGBA_OK;
 }
 
 tgba_status tgba_fp64_peak(int32_t reps, double* gflops) {

@@ -97,6 +97,7 @@ tgba_status assemble_heff(Basis& b, double h_x, double* heff, cudaStream_t st) {
                                         b.d_M_ns + sec.ns_off, b.d_M_r + sec.r_off, b.d_P + sec.x_off, b.d_c0, scale,
                                         (double2*)heff + sec.h_off);
     TGBA_CUDA(cudaGetLastError());
+    ++b.launches;
   }
   return TGBA_OK;
 }
@@ -108,6 +109,7 @@ tgba_status export_x(Basis& b, int s, double* x, cudaStream_t st) {
   export_kernel<<<grid_for(work, 256), 256, 0, st>>>(sec.n_ns, sec.n_r, b.d_M_ns + sec.ns_off, b.d_M_r + sec.r_off,
                                                      b.d_P + sec.x_off, b.d_c0, (double2*)x);
   TGBA_CUDA(cudaGetLastError());
+  ++b.launches;
   return TGBA_OK;
 }
 
@@ -120,6 +122,7 @@ tgba_status build_real_heff(Basis& b, int s, double h_x, double* a, const int32_
                                                          b.d_E_r + sec.r_off, b.d_P + sec.x_off, b.d_c0,
                                                          -b.L * h_x, a);
   TGBA_CUDA(cudaGetLastError());
+  ++b.launches;
   return TGBA_OK;
 }
 

@@ -129,6 +129,7 @@ tgba_status dsf(Basis& b, int s, double h_x, double w_min, double w_max, int n_w
                                                                                             b.d_c0, v);
     sigma_cols<<<(int)std::min<int64_t>((sec.n_r + 255) / 256, 152 * 16), 256, 0, st>>>(sec.n_ns, sec.n_r, P, A,
                                                                                        b.d_c0, v);
+    b.launches += 2;
   } else {
     TGBA_CUDA(cudaMemsetAsync(v, 0, n * sizeof(double), st));
   }
@@ -138,6 +139,7 @@ tgba_status dsf(Basis& b, int s, double h_x, double w_min, double w_max, int n_w
   lorentz_kernel<<<(warps * 32 + 255) / 256, 256, 0, st>>>(n_w, w_min, w_max - w_min, n, e_hi, e_lo, cw,
                                                           (float)(eta * eta), S);
   TGBA_CUDA(cudaGetLastError());
+  b.launches += 2;
   if (evals && n_ev > 0)
     TGBA_CUDA(cudaMemcpyAsync(evals, E, std::min<int64_t>(n_ev, n) * sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (weights) TGBA_CUDA(cudaMemcpyAsync(weights, w, n * sizeof(double), cudaMemcpyDeviceToDevice, st));

@@ -183,6 +183,7 @@ tgba_status launch_class(Basis& b, int t0, int t1, const uint8_t* mask, cudaStre
   kern<<<grid, T, smem, st>>>(b.d_tiles, t0, t1, b.d_table, 2 * b.L, b.d_sel_ns, b.d_sel_r, b.max_qp, mask, b.d_P,
                               b.d_status);
   TGBA_CUDA(cudaGetLastError());
+  ++b.launches;
   return TGBA_OK;
 }
 
@@ -198,6 +199,7 @@ tgba_status launch_pairs(Basis& b, int s, const int32_t* pairs, int64_t n, doubl
   kern<<<(int)blocks, T, smem, st>>>(pairs, n, sec.ns_off, sec.r_off, sec.n_ns, sec.n_r, b.d_table, 2 * b.L, b.d_sel_ns, b.d_sel_r,
                                      b.d_M_ns, b.d_M_r, b.max_qp, b.d_c0, out, b.d_status);
   TGBA_CUDA(cudaGetLastError());
+  ++b.launches;
   return TGBA_OK;
 }
 

@@ -207,6 +207,7 @@ tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* e
                                                  b.d_modes_ns, b.d_modes_r, b.max_qp, b.d_nlab, dth_dev, base[0],
                                                  base[1], s_re, s_im, g_re, g_im, L, c, norm2);
     TGBA_CUDA(cudaGetLastError());
+    ++b.launches;
     // a = U~^T c~0: two real products (strided complex input)
     const double one = 1.0, zero = 0.0;
     cublasStatus_t cs = cublasDgemv(bh, CUBLAS_OP_T, (int)n, (int)n, &one, U, (int)n, c, 2, &zero, a, 1);
@@ -215,6 +216,7 @@ tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* e
     if (kn > 0 && kr > 0) {
       gather_kernel<<<blocks_for(kn * kr), 256, 0, st>>>(kn, kr, idx, idx + kn, sec.n_r, b.d_P + sec.x_off, Q);
       TGBA_CUDA(cudaGetLastError());
+      ++b.launches;
     }
     const double cq = cabs;
     const double dt = n_t > 1 ? t_max / (n_t - 1) : 0.0;
@@ -222,6 +224,7 @@ tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* e
       const int cnt = std::min(nb, n_t - t0);
       phase_kernel<<<blocks_for(n * cnt), 256, 0, st>>>(n, nb, t0, dt, E, a, Y);
       TGBA_CUDA(cudaGetLastError());
+      ++b.launches;
       cs = cublasDgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, (int)n, 2 * nb, (int)n, &one, U, (int)n, Y, (int)n, &zero, B, (int)n);
       if (cs != CUBLAS_STATUS_SUCCESS) return blas_fail(cs, "gemm U Y");
       TGBA_CUDA(cudaMemsetAsync(XB, 0, 2 * n * nb * sizeof(double), st));
@@ -236,6 +239,7 @@ tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* e
       }
       quad_kernel<<<(cnt * 32 + 255) / 256, 256, 0, st>>>(n, nb, cnt, B, XB, norm2, mx + (int64_t)v * n_t + t0);
       TGBA_CUDA(cudaGetLastError());
+      ++b.launches;
     }
     if (norm_out) TGBA_CUDA(cudaMemcpyAsync(norm_out + v, norm2, sizeof(double), cudaMemcpyDeviceToDevice, st));
   }

@@ -212,6 +212,7 @@ tgba_status build_table(Basis& b, cudaStream_t st) {
   TGBA_CUDA(cudaGetLastError());
   table_check<<<1, 1, 0, st>>>(b.d_c0, b.d_status);
   TGBA_CUDA(cudaGetLastError());
+  b.launches += 2;
   b.table_valid = true;
   return TGBA_OK;
 }

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -107,11 +108,18 @@ struct Basis {
   std::vector<int> tile_class_begin;   // tiles sorted by size class; class c = [begin[c], begin[c+1])
   Tile* d_tiles = nullptr;
   unsigned* d_status = nullptr;
+  // measurement
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  bool ev_recorded = false;
+  std::atomic<int64_t> launches{0};
+  int64_t upload_bytes = 0, pf_launches = 0;
+  double pf_flops = 0;
   // eigen solver scratch
   void* solver = nullptr;          // cusolverDnHandle_t
   void* blas = nullptr;            // cublasHandle_t
   double* d_eig_a = nullptr; double* d_eig_w = nullptr; double* d_eig_work = nullptr;
   double* d_scratch = nullptr; int64_t scratch_cap = 0;
+  void* eig_pool = nullptr;        // concurrent eigen-solver workers (eig.cu)
   int* d_eig_info = nullptr;
   int64_t eig_a_cap = 0, eig_work_cap = 0;
 };
@@ -139,6 +147,10 @@ void destroy_blas(void* h);
 
 // eig.cu
 tgba_status eig_sym(Basis& b, int64_t n, double* a, double* w, bool vectors, cudaStream_t st);
+// eigenvalues of every sector's real-gauge H_eff at h_x, sector s written at evals + ev_off,
+// spread over concurrent workers (own stream, solver handle and workspace each)
+tgba_status eig_all_sectors(Basis& b, double h_x, double* evals, cudaStream_t st);
+void destroy_eig_pool(void* pool);
 
 // dsf.cu
 tgba_status dsf(Basis& b, int s, double h_x, double w_min, double w_max, int n_w, double eta, float* S,

@@ -19,7 +19,7 @@ _NAMES = {0: "TGBA_OK", 1: "TGBA_EINVAL", 2: "TGBA_ENOMEM", 3: "TGBA_ECUDA", 4: 
 # every symbol include/tgba.h declares
 SYMBOLS = ("tgba_last_error", "tgba_device_count", "tgba_build_basis", "tgba_basis_info", "tgba_basis_totals",
            "tgba_basis_free", "tgba_compute_x", "tgba_x_stats", "tgba_x_export", "tgba_x_pairs", "tgba_table",
-           "tgba_assemble_heff", "tgba_eigvals", "tgba_dsf", "tgba_quench", "tgba_fp64_peak")
+           "tgba_assemble_heff", "tgba_eigvals", "tgba_dsf", "tgba_quench", "tgba_profile", "tgba_fp64_peak")
 
 
 class TgbaError(RuntimeError):
@@ -34,6 +34,12 @@ class _Model(ctypes.Structure):
 
 class _Trunc(ctypes.Structure):
     _fields_ = [("max_qp", ctypes.c_int32), ("e_cut", ctypes.c_double), ("max_per_parity", ctypes.c_int64)]
+
+
+class _Prof(ctypes.Structure):
+    _fields_ = [("table_ms", ctypes.c_double), ("pfaffian_ms", ctypes.c_double), ("pfaffian_flops", ctypes.c_double),
+                ("pfaffian_launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("upload_bytes", ctypes.c_int64), ("evaluated", ctypes.c_int64)]
 
 
 _lib = None
@@ -63,6 +69,7 @@ def lib():
             "tgba_eigvals": (_I32, [_VP, _D, _VP, _VP]),
             "tgba_dsf": (_I32, [_VP, _I32, _D, _D, _D, _I32, _D, _VP, _VP, _I32, _VP, _VP, _VP]),
             "tgba_quench": (_I32, [_VP, _I32, _D, _VP, _VP, _I32, _D, _I32, _VP, _VP, _VP, _VP]),
+            "tgba_profile": (_I32, [_VP, _P(_Prof)]),
             "tgba_fp64_peak": (_I32, [_I32, _P(_D)]),
         }
         for name, (res, args) in sig.items():
@@ -208,6 +215,13 @@ def tgba_quench(b, s, h_z0, hx_variants, ecut_variants, t_max, n_t, mx_out, norm
     _check(lib().tgba_quench(b, s, float(h_z0), hx.ctypes.data, ec.ctypes.data, len(hx), float(t_max), int(n_t),
                              _ptr(mx_out), _ptr(norm_out), chi.ctypes.data, _stream(stream)))
     return chi
+
+
+def tgba_profile(b):
+    """Stage times of the last tgba_compute_x and the handle's counters (dict)."""
+    p = _Prof()
+    _check(lib().tgba_profile(b, ctypes.byref(p)))
+    return {k: getattr(p, k) for k, _ in _Prof._fields_}
 
 
 def tgba_fp64_peak(reps=5):
