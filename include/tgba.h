@@ -125,12 +125,15 @@ tgba_status tgba_assemble_heff(tgba_basis b, double h_x, tgba_screen screen, dou
                                double* heff_dev, void* stream);
 
 /* ---------------------------------------------------------------- diagonalisation (Eq. 1)
- * Eigenvalues (ascending, all sectors concatenated: sector s at offset sum of previous n) of
- * the H_eff that tgba_assemble_heff writes for this h_x, computed from the handle's X.  The
- * sector matrices are real symmetric after a diagonal change of phase of the basis states, so
- * the library diagonalises them with the FP64 real symmetric solver (cuSOLVER syevd);
- * evals_dev receives all eigenvalues.  Blocks on `stream`. */
-tgba_status tgba_eigvals(tgba_basis b, double h_x, double* evals_dev, void* stream);
+ * All eigenvalues, ascending, of the H_eff that tgba_assemble_heff writes, for each of the n_hx
+ * longitudinal fields h_x[i], computed from the handle's X.  evals_dev: double
+ * [n_hx][n_states] (n_states = sum over sectors of n_ns + n_r); field i, sector s starts at
+ * i * n_states + (sum of the sizes of sectors before s).  The sector matrices are real
+ * symmetric after a diagonal change of phase of the basis states, so every (field, sector)
+ * matrix goes into one batched FP64 real symmetric solve (cuSOLVER XsyevBatched), each padded
+ * to the largest sector size with decoupled diagonal entries above its Gershgorin bound.
+ * Blocks on `stream`. */
+tgba_status tgba_eigvals(tgba_basis b, const double* h_x, int32_t n_hx, double* evals_dev, void* stream);
 
 /* ---------------------------------------------------------------- S(k=0, w) (Eq. 8-9)
  * Dynamic structure factor of sector index s (which must be the k = 0 sector, m = 0):
@@ -157,6 +160,37 @@ tgba_status tgba_quench(tgba_basis b, int32_t s, double h_z0, const double* hx_v
                         const double* ecut_variants, int32_t n_variants, double t_max, int32_t n_t,
                         double* mx_dev, double* norm_dev, int64_t* chi_host, void* stream);
 
+/* ---------------------------------------------------------------- learned pair screener
+ * Not in the paper (the paper has no counterpart): a 3-layer MLP (width 256, ReLU, FP32
+ * parameters) that predicts log10|X_ab| from the two quasiparticle momentum sets, trained on
+ * exact elements of the Pfaffian path, and used by tgba_compute_x to skip the Pfaffians of pairs
+ * it predicts below the threshold.  Features (D = 20): k/pi of the NS state's modes (ascending,
+ * zero padded to 8), k/pi of the R state's modes, M_a/8, M_b/8, 24/L, 1.  Target:
+ * log10|X| + (M_a+M_b)/2 log10(L/24), clipped at -30.  Parameters, flat FP32: W1 [256][20],
+ * b1 [256], W2 [256][256], b2 [256], w3 [256], b3 [1].  A pair is skipped when
+ * predicted log10|V| = y - (M_a+M_b)/2 log10(L/24) + log10(L |h_x|) < log10(tau) - margin, with
+ * margin = 3 x the validation RMSE of training (always kept: states with more than 8
+ * quasiparticles).  Layer 2 of the inference runs on the tensor cores in BF16. */
+
+/* A screener with the given parameters (params_host: n floats, see above) or, if params_host is
+   NULL, He-normal weights drawn from `seed`.  width must be 256. */
+tgba_status tgba_screen_create(int32_t width, const float* params_host, uint64_t seed, tgba_screen* out);
+tgba_status tgba_screen_nparams(tgba_screen s, int64_t* n);
+tgba_status tgba_screen_params(tgba_screen s, float* params_host);
+/* Forward and back-propagation of one batch (no update): x_dev float [B][20], t_dev float [B];
+   grad_dev float [nparams] receives d(mean (y - t)^2)/d params, loss_host the loss. */
+tgba_status tgba_screen_grad(tgba_screen s, const float* x_dev, const float* t_dev, int64_t B, float* grad_dev,
+                             double* loss_host, void* stream);
+/* Train a new screener on n_samples pairs drawn uniformly (SplitMix64 from `seed`) from all
+   NS x R pairs of the given bases, labelled by their exact X: Adam, batches of 4096, `epochs`
+   passes, the last 5 % held out.  stats_host (optional, 4 doubles): train RMSE, validation RMSE,
+   margin, seconds.  Blocks on `stream`. */
+tgba_status tgba_screen_train(const tgba_basis* sets, int32_t n_sets, int64_t n_samples, uint64_t seed,
+                              int32_t width, int32_t epochs, tgba_screen* out, double* stats_host, void* stream);
+/* Predicted y (see above) of every pair of sector s: pred_dev float [n_ns][n_r]. */
+tgba_status tgba_screen_predict(tgba_screen s, tgba_basis b, int32_t sector, float* pred_dev, void* stream);
+tgba_status tgba_screen_free(tgba_screen s);
+
 /* ---------------------------------------------------------------- measurement
  * Profile of a basis handle.  table_ms / pfaffian_ms: device time of the contraction table and
  * of the Pfaffian kernels of the last tgba_compute_x, from CUDA events recorded on its stream
@@ -171,6 +205,37 @@ typedef struct {
   int64_t pfaffian_launches, kernel_launches, upload_bytes, evaluated;
 } tgba_prof;
 tgba_status tgba_profile(tgba_basis b, tgba_prof* out);
+
+/* ---------------------------------------------------------------- learned pair screener
+ * Not in the paper (the paper has no counterpart): a 3-layer MLP (width 256, ReLU, FP32
+ * parameters) that predicts log10|X_ab| from the two quasiparticle momentum sets, trained on
+ * exact elements of the Pfaffian path, and used by tgba_compute_x to skip the Pfaffians of pairs
+ * it predicts below the threshold.  Features (D = 20): k/pi of the NS state's modes (ascending,
+ * zero padded to 8), k/pi of the R state's modes, M_a/8, M_b/8, 24/L, 1.  Target:
+ * log10|X| + (M_a+M_b)/2 log10(L/24), clipped at -30.  Parameters, flat FP32: W1 [256][20],
+ * b1 [256], W2 [256][256], b2 [256], w3 [256], b3 [1].  A pair is skipped when
+ * predicted log10|V| = y - (M_a+M_b)/2 log10(L/24) + log10(L |h_x|) < log10(tau) - margin, with
+ * margin = 3 x the validation RMSE of training (always kept: states with more than 8
+ * quasiparticles).  Layer 2 of the inference runs on the tensor cores in BF16. */
+
+/* A screener with the given parameters (params_host: n floats, see above) or, if params_host is
+   NULL, He-normal weights drawn from `seed`.  width must be 256. */
+tgba_status tgba_screen_create(int32_t width, const float* params_host, uint64_t seed, tgba_screen* out);
+tgba_status tgba_screen_nparams(tgba_screen s, int64_t* n);
+tgba_status tgba_screen_params(tgba_screen s, float* params_host);
+/* Forward and back-propagation of one batch (no update): x_dev float [B][20], t_dev float [B];
+   grad_dev float [nparams] receives d(mean (y - t)^2)/d params, loss_host the loss. */
+tgba_status tgba_screen_grad(tgba_screen s, const float* x_dev, const float* t_dev, int64_t B, float* grad_dev,
+                             double* loss_host, void* stream);
+/* Train a new screener on n_samples pairs drawn uniformly (SplitMix64 from `seed`) from all
+   NS x R pairs of the given bases, labelled by their exact X: Adam, batches of 4096, `epochs`
+   passes, the last 5 % held out.  stats_host (optional, 4 doubles): train RMSE, validation RMSE,
+   margin, seconds.  Blocks on `stream`. */
+tgba_status tgba_screen_train(const tgba_basis* sets, int32_t n_sets, int64_t n_samples, uint64_t seed,
+                              int32_t width, int32_t epochs, tgba_screen* out, double* stats_host, void* stream);
+/* Predicted y (see above) of every pair of sector s: pred_dev float [n_ns][n_r]. */
+tgba_status tgba_screen_predict(tgba_screen s, tgba_basis b, int32_t sector, float* pred_dev, void* stream);
+tgba_status tgba_screen_free(tgba_screen s);
 
 /* ---------------------------------------------------------------- measurement helper
  * Achieved FP64 rate of a DFMA-chain kernel on the current device (GFLOP/s, best of `reps`),

@@ -55,14 +55,13 @@ tgba_status scratch(Basis& b, int64_t doubles, double** out) {
 static void release(Basis* b) {
   void* ptrs[] = {b->d_E_ns, b->d_E_r, b->d_M_ns, b->d_M_r, b->d_sel_ns, b->d_sel_r, b->d_modes_ns, b->d_modes_r,
                   b->d_theta, b->d_nlab, b->d_table, b->d_c0, b->d_work, b->d_P, b->d_tiles, b->d_status,
-                  b->d_eig_a, b->d_eig_w, b->d_eig_work, b->d_eig_info, b->d_scratch};
+                  b->d_eig_a, b->d_eig_w, b->d_eig_work, b->d_eig_info, b->d_scratch, b->d_mask};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int e = 0; e < 3; ++e)
     if (b->ev[e]) cudaEventDestroy(b->ev[e]);
   if (b->solver) destroy_solver(b->solver);
   if (b->blas) destroy_blas(b->blas);
-  if (b->eig_pool) destroy_eig_pool(b->eig_pool);
   delete b;
 }
 
@@ -149,14 +148,22 @@ static tgba_status ensure_table(Basis& b, cudaStream_t st) {
   return r;
 }
 
-static tgba_status compute_x(Basis& b, const void* screen, double tau, cudaStream_t st) {
-  if (screen != nullptr) return fail(TGBA_EINVAL, "pair screening is not available in this build");
+static tgba_status compute_x(Basis& b, Screen* screen, double tau, double hx, cudaStream_t st) {
+  if (screen && !(tau > 0)) return fail(TGBA_EINVAL, "screening needs tau > 0");
   b.table_valid = false;                 // the table is part of the stage
   TGBA_CUDA(cudaEventRecord(b.ev[0], st));
   tgba_status r = ensure_table(b, st);
   if (r != TGBA_OK) return r;
   TGBA_CUDA(cudaEventRecord(b.ev[1], st));
-  if ((r = run_pfaffians(b, nullptr, st)) != TGBA_OK) return r;
+  const uint8_t* mask = nullptr;
+  if (screen) {
+    if (!b.d_mask) TGBA_CUDA(cudaMalloc(&b.d_mask, std::max<int64_t>(1, b.n_elements)));
+    for (size_t s = 0; s < b.sectors.size(); ++s)
+      if ((r = screen_score(*screen, b, (int)s, tau, hx, nullptr, b.d_mask + b.sectors[s].x_off, st)) != TGBA_OK)
+        return r;
+    mask = b.d_mask;
+  }
+  if ((r = run_pfaffians(b, mask, st)) != TGBA_OK) return r;
   TGBA_CUDA(cudaEventRecord(b.ev[2], st));
   b.ev_recorded = true;
   b.x_valid = true;
@@ -164,6 +171,12 @@ static tgba_status compute_x(Basis& b, const void* screen, double tau, cudaStrea
   b.x_tau = tau;
   b.x_evaluated = b.n_elements;
   b.x_screened = 0;
+  if (screen) {
+    int64_t kept = 0;
+    if ((r = count_mask(b, &kept, st)) != TGBA_OK) return r;
+    b.x_evaluated = kept;
+    b.x_screened = b.n_elements - kept;
+  }
   return TGBA_OK;
 }
 
@@ -256,8 +269,7 @@ tgba_status tgba_basis_free(tgba_basis h) {
 tgba_status tgba_compute_x(tgba_basis h, tgba_screen screen, double tau, double screen_hx, void* stream) {
   Basis* b = (Basis*)h;
   BASIS_OK(b);
-  (void)screen_hx;
-  return compute_x(*b, screen, tau, (cudaStream_t)stream);
+  return compute_x(*b, (Screen*)screen, tau, screen_hx, (cudaStream_t)stream);
 }
 
 tgba_status tgba_x_stats(tgba_basis h, int64_t* n_evaluated, int64_t* n_screened) {
@@ -312,20 +324,22 @@ tgba_status tgba_assemble_heff(tgba_basis h, double h_x, tgba_screen screen, dou
   if (!heff_dev && b->n_heff > 0) return fail(TGBA_EINVAL, "null output");
   cudaStream_t st = (cudaStream_t)stream;
   if (!b->x_valid || b->x_screen != (const void*)screen || (screen && b->x_tau != tau)) {
-    tgba_status r = compute_x(*b, screen, tau, st);
+    tgba_status r = compute_x(*b, (Screen*)screen, tau, h_x, st);
     if (r != TGBA_OK) return r;
   }
   return assemble_heff(*b, h_x, heff_dev, st);
 }
 
-tgba_status tgba_eigvals(tgba_basis h, double h_x, double* evals_dev, void* stream) {
+tgba_status tgba_eigvals(tgba_basis h, const double* h_x, int32_t n_hx, double* evals_dev, void* stream) {
   Basis* b = (Basis*)h;
   BASIS_OK(b);
-  if (!std::isfinite(h_x)) return fail(TGBA_EINVAL, "h_x must be finite");
+  if (!h_x || n_hx < 1) return fail(TGBA_EINVAL, "need at least one h_x");
+  for (int i = 0; i < n_hx; ++i)
+    if (!std::isfinite(h_x[i])) return fail(TGBA_EINVAL, "h_x must be finite");
   if (!b->x_valid) return fail(TGBA_EINVAL, "no X computed yet: call tgba_compute_x");
   if (!evals_dev && b->n_states > 0) return fail(TGBA_EINVAL, "null output");
   cudaStream_t st = (cudaStream_t)stream;
-  tgba_status r = eig_all_sectors(*b, h_x, evals_dev, st);
+  tgba_status r = eig_all_sectors(*b, h_x, n_hx, evals_dev, st);
   if (r != TGBA_OK) return r;
   return check_status(*b, st);
 }
@@ -357,6 +371,62 @@ tgba_status tgba_quench(tgba_basis h, int32_t s, double h_z0, const double* hx_v
   if (!b->x_valid) return fail(TGBA_EINVAL, "no X computed yet: call tgba_compute_x");
   return quench(*b, s, h_z0, hx_variants, ecut_variants, n_variants, t_max, n_t, mx_dev, norm_dev, chi_host,
                 (cudaStream_t)stream);
+}
+
+tgba_status tgba_screen_create(int32_t width, const float* params_host, uint64_t seed, tgba_screen* out) {
+  if (!out || width != 256) return fail(TGBA_EINVAL, "width must be 256 and out non-null");
+  tgba_status r = require_device();
+  if (r != TGBA_OK) return r;
+  Screen* s = nullptr;
+  if ((r = screen_create(width, params_host, seed, &s)) != TGBA_OK) return r;
+  *out = (tgba_screen)s;
+  return TGBA_OK;
+}
+
+tgba_status tgba_screen_nparams(tgba_screen s, int64_t* n) {
+  if (!s || !n) return fail(TGBA_EINVAL, "null argument");
+  *n = screen_nparams((Screen*)s);
+  return TGBA_OK;
+}
+
+tgba_status tgba_screen_params(tgba_screen s, float* params_host) {
+  if (!s || !params_host) return fail(TGBA_EINVAL, "null argument");
+  return screen_params(*(Screen*)s, params_host);
+}
+
+tgba_status tgba_screen_grad(tgba_screen s, const float* x_dev, const float* t_dev, int64_t B, float* grad_dev,
+                             double* loss_host, void* stream) {
+  if (!s || !x_dev || !t_dev || !grad_dev || !loss_host || B < 1) return fail(TGBA_EINVAL, "bad arguments");
+  return screen_grad(*(Screen*)s, x_dev, t_dev, B, grad_dev, loss_host, (cudaStream_t)stream);
+}
+
+tgba_status tgba_screen_train(const tgba_basis* sets, int32_t n_sets, int64_t n_samples, uint64_t seed, int32_t width,
+                              int32_t epochs, tgba_screen* out, double* stats_host, void* stream) {
+  if (!sets || n_sets < 1 || n_samples < 20 || epochs < 1 || width != 256 || !out)
+    return fail(TGBA_EINVAL, "need bases, n_samples >= 20, epochs >= 1, width 256");
+  std::vector<Basis*> v;
+  for (int i = 0; i < n_sets; ++i) {
+    if (!sets[i]) return fail(TGBA_EINVAL, "null basis handle");
+    v.push_back((Basis*)sets[i]);
+  }
+  Screen* s = nullptr;
+  tgba_status r = screen_train(v.data(), n_sets, n_samples, seed, width, epochs, &s, stats_host, (cudaStream_t)stream);
+  if (r != TGBA_OK) return r;
+  *out = (tgba_screen)s;
+  return TGBA_OK;
+}
+
+tgba_status tgba_screen_predict(tgba_screen s, tgba_basis h, int32_t sector, float* pred_dev, void* stream) {
+  Basis* b = (Basis*)h;
+  BASIS_OK(b);
+  if (!s || !pred_dev) return fail(TGBA_EINVAL, "null argument");
+  if (sector < 0 || sector >= (int)b->sectors.size()) return fail(TGBA_EINVAL, "sector index out of range");
+  return screen_score(*(Screen*)s, *b, sector, 1.0, 1.0, pred_dev, nullptr, (cudaStream_t)stream);
+}
+
+tgba_status tgba_screen_free(tgba_screen s) {
+  screen_free((Screen*)s);
+  return TGBA_OK;
 }
 
 tgba_status tgba_profile(tgba_basis h, tgba_prof* out) {

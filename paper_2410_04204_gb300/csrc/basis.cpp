@@ -11,10 +11,19 @@
 
 namespace tgba {
 
-// Size classes of the Pfaffian kernel: largest n handled and threads per block.
-const int kClassN[] = {8, 12, 16, 20, 24, 32};
-const int kClassThreads[] = {256, 256, 128, 128, 64, 32};
-const int kNumClasses = 6;
+// Size classes of the Pfaffian kernels.  Classes 0..7: exact n = 0, 2, ..., 14 (register
+// kernel, 128 threads); classes 8..11: n <= 16, 20, 24, 32 (shared-memory kernel).
+int tile_class(int n) {
+  if (n <= 14) return n / 2;
+  if (n <= 16) return 8;
+  if (n <= 20) return 9;
+  if (n <= 24) return 10;
+  return 11;
+}
+int class_threads(int c) {
+  static const int t[kNumClasses] = {128, 128, 128, 128, 128, 128, 128, 128, 128, 128, 64, 32};
+  return t[c];
+}
 
 Modes make_modes(int N, int parity, double h) {
   Modes md;
@@ -193,10 +202,9 @@ void build_tiles(const Basis& b, int /*unused*/, std::vector<Tile>& tiles, std::
     for (const Group& ga : sec.g_ns)
       for (const Group& gb : sec.g_r) {
         int n = ga.M + gb.M;
-        int c = 0;
-        while (kClassN[c] < n) ++c;
+        int c = tile_class(n);
         int64_t rows = ga.end - ga.begin, w = gb.end - gb.begin, total = rows * w;
-        int per_tile = kClassThreads[c];
+        int per_tile = class_threads(c);
         for (int64_t lin = 0; lin < total; lin += per_tile) {
           Tile t;
           t.out0 = sec.x_off + ga.begin * sec.n_r + gb.begin;

@@ -3,9 +3,8 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
-#include <cstdlib>
 #include <string>
-#include <thread>
+#include <utility>
 #include <vector>
 
 #include "tgba_internal.h"
@@ -64,132 +63,121 @@ tgba_status eig_sym(Basis& b, int64_t n, double* a, double* w, bool vectors, cud
 namespace tgba {
 namespace {
 
-struct EigWorker {
-  cudaStream_t st = nullptr;
-  cudaEvent_t done = nullptr;
-  cusolverDnHandle_t h = nullptr;
-  cusolverDnParams_t params = nullptr;
-  double* A = nullptr;
-  int64_t a_cap = 0;
-  void* work = nullptr;
-  size_t work_cap = 0;
-  std::vector<char> host;
-  int* info = nullptr;
-  int device = 0;
-  tgba_status status = TGBA_OK;
-  std::string msg;
-};
-
-struct EigPool {
-  std::vector<EigWorker> w;
-};
-
-int pool_size() {
-  const char* e = std::getenv("TGBA_EIG_WORKERS");
-  int n = e ? std::atoi(e) : 8;
-  return std::max(1, std::min(n, 32));
+// Slot q of the batch holds sector s at field hx[h]: its real-gauge H~ (n_s x n_s) in the
+// top-left corner of an n_max x n_max matrix, zeros elsewhere.
+__global__ void heff_real_padded(int64_t kn, int64_t kr, int64_t n_max, int64_t n_r, const double* __restrict__ E_ns,
+                                 const double* __restrict__ E_r, const double* __restrict__ P,
+                                 const double* __restrict__ c0, double scale, double* __restrict__ A) {
+  const int64_t n = kn + kr;
+  const double c = scale * sqrt(c0[0] * c0[0] + c0[1] * c0[1]);
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n_max * n_max;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t col = idx / n_max, row = idx - col * n_max;
+    double v = 0.0;
+    if (row < n && col < n) {
+      if (row == col) v = row < kn ? E_ns[row] : E_r[row - kn];
+      else if (row < kn && col >= kn) v = c * P[row * n_r + (col - kn)];
+      else if (row >= kn && col < kn) v = c * P[col * n_r + (row - kn)];
+    }
+    A[idx] = v;
+  }
 }
 
-// One worker's share: build H~ of each sector, syevd (eigenvalues only) into evals.
-void run_worker(Basis& b, EigWorker& w, const std::vector<int>& mine, double h_x, double* evals) {
-  w.status = TGBA_OK;
-  if (cudaSetDevice(w.device) != cudaSuccess) { w.status = TGBA_ECUDA; w.msg = "cudaSetDevice"; return; }
-  for (int s : mine) {
-    const Sector& sec = b.sectors[s];
-    const int64_t n = sec.n_ns + sec.n_r;
-    if (n * n > w.a_cap) {
-      if (w.A) cudaFree(w.A);
-      w.A = nullptr; w.a_cap = 0;
-      if (cudaMalloc(&w.A, n * n * sizeof(double)) != cudaSuccess) { w.status = TGBA_ENOMEM; w.msg = "eigen-solver matrix"; return; }
-      w.a_cap = n * n;
-    }
-    tgba_status r = build_real_heff(b, s, h_x, w.A, nullptr, sec.n_ns, nullptr, sec.n_r, w.st);
-    if (r != TGBA_OK) { w.status = r; w.msg = "H_eff"; return; }
-    size_t dev_bytes = 0, host_bytes = 0;
-    cusolverStatus_t cs = cusolverDnXsyevd_bufferSize(w.h, w.params, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n,
-                                                      CUDA_R_64F, w.A, n, CUDA_R_64F, evals + sec.ev_off, CUDA_R_64F,
-                                                      &dev_bytes, &host_bytes);
-    if (cs != CUSOLVER_STATUS_SUCCESS) { w.status = TGBA_ECUDA; w.msg = "syevd buffer size"; return; }
-    if (dev_bytes > w.work_cap) {
-      if (w.work) cudaFree(w.work);
-      w.work = nullptr; w.work_cap = 0;
-      if (cudaMalloc(&w.work, dev_bytes) != cudaSuccess) { w.status = TGBA_ENOMEM; w.msg = "eigen-solver workspace"; return; }
-      w.work_cap = dev_bytes;
-    }
-    if (w.host.size() < std::max<size_t>(1, host_bytes)) w.host.resize(std::max<size_t>(1, host_bytes));
-    cs = cusolverDnXsyevd(w.h, w.params, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n, CUDA_R_64F, w.A, n,
-                          CUDA_R_64F, evals + sec.ev_off, CUDA_R_64F, w.work, dev_bytes, w.host.data(), host_bytes,
-                          w.info);
-    if (cs != CUSOLVER_STATUS_SUCCESS) { w.status = TGBA_ECUDA; w.msg = "syevd"; return; }
-    int info = 0;
-    if (cudaMemcpyAsync(&info, w.info, sizeof(int), cudaMemcpyDeviceToHost, w.st) != cudaSuccess ||
-        cudaStreamSynchronize(w.st) != cudaSuccess) { w.status = TGBA_ECUDA; w.msg = "syevd info"; return; }
-    if (info != 0) { w.status = TGBA_ENUMERIC; w.msg = "syevd did not converge"; return; }
+// Gershgorin upper bound of the spectrum of the n x n corner, then the padding diagonal
+// entries set just above it, so the n true eigenvalues are the n smallest of the slot.
+__global__ void pad_kernel(int64_t n, int64_t n_max, double* __restrict__ A) {
+  __shared__ double red[32];
+  double best = -1e300;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    double r = A[i * n_max + i];
+    for (int64_t j = 0; j < n; ++j)
+      if (j != i) r += fabs(A[j * n_max + i]);
+    best = fmax(best, r);
   }
-  if (cudaEventRecord(w.done, w.st) != cudaSuccess) { w.status = TGBA_ECUDA; w.msg = "event"; }
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    best = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : -1e300;
+    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (threadIdx.x == 0) red[0] = best;
+  }
+  __syncthreads();
+  const double pad = red[0] + 1.0;
+  for (int64_t i = n + threadIdx.x; i < n_max; i += blockDim.x) A[i * n_max + i] = pad;
 }
 
 }  // namespace
 
-void destroy_eig_pool(void* pool) {
-  EigPool* p = (EigPool*)pool;
-  for (EigWorker& w : p->w) {
-    if (w.params) cusolverDnDestroyParams(w.params);
-    if (w.h) cusolverDnDestroy(w.h);
-    if (w.A) cudaFree(w.A);
-    if (w.work) cudaFree(w.work);
-    if (w.info) cudaFree(w.info);
-    if (w.done) cudaEventDestroy(w.done);
-    if (w.st) cudaStreamDestroy(w.st);
-  }
-  delete p;
-}
-
-tgba_status eig_all_sectors(Basis& b, double h_x, double* evals, cudaStream_t st) {
-  EigPool* pool = (EigPool*)b.eig_pool;
-  if (pool == nullptr) {
-    pool = new EigPool();
-    b.eig_pool = pool;
-    pool->w.resize(pool_size());
-    for (EigWorker& w : pool->w) {
-      w.device = b.device;
-      TGBA_CUDA(cudaStreamCreateWithFlags(&w.st, cudaStreamNonBlocking));
-      TGBA_CUDA(cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming));
-      TGBA_CUDA(cudaMalloc(&w.info, sizeof(int)));
-      if (cusolverDnCreate(&w.h) != CUSOLVER_STATUS_SUCCESS) return fail(TGBA_ECUDA, "cuSOLVER create");
-      if (cusolverDnCreateParams(&w.params) != CUSOLVER_STATUS_SUCCESS) return fail(TGBA_ECUDA, "cuSOLVER params");
-      cusolverDnSetStream(w.h, w.st);
+tgba_status eig_all_sectors(Basis& b, const double* hx, int n_hx, double* evals, cudaStream_t st) {
+  int64_t n_max = 0;
+  std::vector<std::pair<int, int>> slots;     // (h index, sector)
+  for (int h = 0; h < n_hx; ++h)
+    for (size_t s = 0; s < b.sectors.size(); ++s) {
+      const int64_t n = b.sectors[s].n_ns + b.sectors[s].n_r;
+      if (n == 0) continue;
+      n_max = std::max(n_max, n);
+      slots.emplace_back(h, (int)s);
     }
+  if (slots.empty()) return TGBA_OK;
+  const int64_t B = (int64_t)slots.size();
+  double* A;
+  tgba_status r = scratch(b, B * n_max * n_max + B * n_max + B, &A);
+  if (r != TGBA_OK) return r;
+  double* W = A + B * n_max * n_max;
+  int* info = (int*)(W + B * n_max);
+  for (int64_t q = 0; q < B; ++q) {
+    const Sector& sec = b.sectors[slots[q].second];
+    double* Aq = A + q * n_max * n_max;
+    const int64_t work = n_max * n_max;
+    const int grid = (int)std::min<int64_t>((work + 255) / 256, 152 * 32);
+    heff_real_padded<<<grid, 256, 0, st>>>(sec.n_ns, sec.n_r, n_max, sec.n_r, b.d_E_ns + sec.ns_off,
+                                          b.d_E_r + sec.r_off, b.d_P + sec.x_off, b.d_c0, -b.L * hx[slots[q].first], Aq);
+    pad_kernel<<<1, 1024, 0, st>>>(sec.n_ns + sec.n_r, n_max, Aq);
+    TGBA_CUDA(cudaGetLastError());
+    b.launches += 2;
   }
-  // longest-processing-time assignment of sectors (cost ~ n^3) to workers
-  std::vector<int> order(b.sectors.size());
-  for (size_t s = 0; s < order.size(); ++s) order[s] = (int)s;
-  auto size = [&](int s) { return b.sectors[s].n_ns + b.sectors[s].n_r; };
-  std::sort(order.begin(), order.end(), [&](int x, int y) { return size(x) > size(y); });
-  const int W = (int)pool->w.size();
-  std::vector<std::vector<int>> share(W);
-  std::vector<double> load(W, 0.0);
-  for (int s : order) {
-    if (size(s) == 0) continue;
-    int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-    share[k].push_back(s);
-    load[k] += (double)size(s) * size(s) * size(s);
+  cusolverDnHandle_t h = (cusolverDnHandle_t)b.solver;
+  if (h == nullptr) {
+    cusolverStatus_t cs = cusolverDnCreate(&h);
+    if (cs != CUSOLVER_STATUS_SUCCESS) return solver_fail(cs, "create");
+    b.solver = h;
   }
-  cudaEvent_t ready;
-  TGBA_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
-  TGBA_CUDA(cudaEventRecord(ready, st));
-  for (EigWorker& w : pool->w) TGBA_CUDA(cudaStreamWaitEvent(w.st, ready, 0));
-  std::vector<std::thread> threads;
-  for (int k = 0; k < W; ++k)
-    if (!share[k].empty()) threads.emplace_back(run_worker, std::ref(b), std::ref(pool->w[k]), std::cref(share[k]), h_x, evals);
-  for (std::thread& t : threads) t.join();
-  cudaEventDestroy(ready);
-  for (int k = 0; k < W; ++k) {
-    if (share[k].empty()) continue;
-    EigWorker& w = pool->w[k];
-    if (w.status != TGBA_OK) return fail(w.status, "eigen-solver worker: " + w.msg);
-    TGBA_CUDA(cudaStreamWaitEvent(st, w.done, 0));
+  cusolverDnSetStream(h, st);
+  cusolverDnParams_t params;
+  cusolverStatus_t cs = cusolverDnCreateParams(&params);
+  if (cs != CUSOLVER_STATUS_SUCCESS) return solver_fail(cs, "params");
+  size_t dev_bytes = 0, host_bytes = 0;
+  cs = cusolverDnXsyevBatched_bufferSize(h, params, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n_max,
+                                         CUDA_R_64F, A, n_max, CUDA_R_64F, W, CUDA_R_64F, &dev_bytes, &host_bytes, B);
+  if (cs != CUSOLVER_STATUS_SUCCESS) { cusolverDnDestroyParams(params); return solver_fail(cs, "syevBatched buffer"); }
+  if ((int64_t)dev_bytes > b.eig_work_cap) {
+    if (b.d_eig_work) cudaFree(b.d_eig_work);
+    b.d_eig_work = nullptr;
+    b.eig_work_cap = 0;
+    if (cudaMalloc(&b.d_eig_work, dev_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      cusolverDnDestroyParams(params);
+      return fail(TGBA_ENOMEM, "batched eigen-solver workspace");
+    }
+    b.eig_work_cap = (int64_t)dev_bytes;
   }
+  std::vector<char> host_work(std::max<size_t>(1, host_bytes));
+  cs = cusolverDnXsyevBatched(h, params, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, n_max, CUDA_R_64F, A,
+                              n_max, CUDA_R_64F, W, CUDA_R_64F, b.d_eig_work, dev_bytes, host_work.data(), host_bytes,
+                              info, B);
+  cusolverDnDestroyParams(params);
+  if (cs != CUSOLVER_STATUS_SUCCESS) return solver_fail(cs, "syevBatched");
+  std::vector<int> hinfo(B);
+  TGBA_CUDA(cudaMemcpyAsync(hinfo.data(), info, B * sizeof(int), cudaMemcpyDeviceToHost, st));
+  for (int64_t q = 0; q < B; ++q) {
+    const Sector& sec = b.sectors[slots[q].second];
+    TGBA_CUDA(cudaMemcpyAsync(evals + (int64_t)slots[q].first * b.n_states + sec.ev_off, W + q * n_max,
+                              (sec.n_ns + sec.n_r) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  TGBA_CUDA(cudaStreamSynchronize(st));
+  for (int64_t q = 0; q < B; ++q)
+    if (hinfo[q] != 0) return fail(TGBA_ENUMERIC, "batched eigen-solver did not converge (info " + std::to_string(hinfo[q]) + ")");
   return TGBA_OK;
 }
 

@@ -14,16 +14,15 @@
 // multiply per step) issues FP64 instructions.
 //
 // Work: tiles of up to THREADS elements with uniform n (see build_tiles), grouped in size
-// classes; one persistent launch per class walks its tiles with a grid-stride loop.
+// classes; one persistent launch per class walks its tiles with a grid-stride loop.  Sizes
+// n <= 14 run the register-resident kernel of pfaffian_reg.cuh, one class per exact n; larger
+// sizes run the shared-memory kernel below.
 #include <algorithm>
 
+#include "pfaffian_reg.cuh"
 #include "tgba_internal.h"
 
 namespace tgba {
-
-extern const int kClassN[];
-extern const int kClassThreads[];
-extern const int kNumClasses;
 
 namespace {
 
@@ -127,6 +126,44 @@ __global__ void __launch_bounds__(T) pf_tiles(const Tile* __restrict__ tiles, in
   }
 }
 
+// Register-resident variant for one exact size N <= 14 (see pfaffian_reg.cuh).
+template <int N, int T>
+__global__ void __launch_bounds__(T) pf_tiles_reg(const Tile* __restrict__ tiles, int t_begin, int t_end,
+                                                  const double* __restrict__ R, int two_l,
+                                                  const uint8_t* __restrict__ sel_ns, const uint8_t* __restrict__ sel_r,
+                                                  int max_qp, const uint8_t* __restrict__ mask, double* __restrict__ P,
+                                                  unsigned* status) {
+  for (int t = t_begin + blockIdx.x; t < t_end; t += gridDim.x) {
+    const Tile tl = tiles[t];
+    const int e = threadIdx.x;
+    if (e >= tl.count) continue;
+    const int lin = tl.lin0 + e;
+    const int row = lin / tl.w, col = lin - (lin / tl.w) * tl.w;
+    const int64_t out = tl.out0 + (int64_t)row * tl.ld + col;
+    if (mask != nullptr && mask[out] == 0) { P[out] = 0.0; continue; }
+    if constexpr (N == 0) {
+      P[out] = 1.0;
+    } else {
+      const int ma = tl.Ma;
+      const uint8_t* sa = sel_ns + (size_t)(tl.ns0 + row) * max_qp;
+      const uint8_t* sb = sel_r + (size_t)(tl.r0 + col) * max_qp;
+      int sel[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) sel[i] = i < ma ? sa[i] : sb[i - ma];
+      double W[N][N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const double* Ri = R + (size_t)sel[i] * two_l;
+#pragma unroll
+        for (int j = i + 1; j < N; ++j) W[i][j] = __ldg(Ri + sel[j]);
+      }
+      const double pf = pfaffian_regs<N>(W);
+      if (!is_finite_bits(pf)) atomicOr(status, kStNan);
+      P[out] = pf;
+    }
+  }
+}
+
 // One thread per explicit (a, b) pair; sizes vary per thread.
 template <int NMAX, int T>
 __global__ void __launch_bounds__(T) pf_pairs(const int32_t* __restrict__ pairs, int64_t n_pairs, int64_t ns_off,
@@ -187,6 +224,24 @@ tgba_status launch_class(Basis& b, int t0, int t1, const uint8_t* mask, cudaStre
   return TGBA_OK;
 }
 
+template <int N>
+tgba_status launch_reg(Basis& b, int t0, int t1, const uint8_t* mask, cudaStream_t st) {
+  if (t1 <= t0) return TGBA_OK;
+  constexpr int T = 128;
+  auto kern = pf_tiles_reg<N, T>;
+  TGBA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+  int per_sm = 0, sms = 0;
+  TGBA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, 0));
+  TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
+  if (per_sm < 1) return fail(TGBA_ELIMIT, "register Pfaffian kernel does not fit on an SM");
+  const int grid = std::min(t1 - t0, per_sm * sms);
+  kern<<<grid, T, 0, st>>>(b.d_tiles, t0, t1, b.d_table, 2 * b.L, b.d_sel_ns, b.d_sel_r, b.max_qp, mask, b.d_P,
+                           b.d_status);
+  TGBA_CUDA(cudaGetLastError());
+  ++b.launches;
+  return TGBA_OK;
+}
+
 template <int NMAX, int T>
 tgba_status launch_pairs(Basis& b, int s, const int32_t* pairs, int64_t n, double* out, cudaStream_t st) {
   const size_t smem = (size_t)Packed<NMAX>::kEntries * T * sizeof(double);
@@ -208,13 +263,19 @@ tgba_status launch_pairs(Basis& b, int s, const int32_t* pairs, int64_t n, doubl
 tgba_status run_pfaffians(Basis& b, const uint8_t* mask, cudaStream_t st) {
   const std::vector<int>& cb = b.tile_class_begin;
   tgba_status r;
-  // one launch per size class, largest Pfaffians first
-  if ((r = launch_class<32, 32>(b, cb[5], cb[6], mask, st)) != TGBA_OK) return r;
-  if ((r = launch_class<24, 64>(b, cb[4], cb[5], mask, st)) != TGBA_OK) return r;
-  if ((r = launch_class<20, 128>(b, cb[3], cb[4], mask, st)) != TGBA_OK) return r;
-  if ((r = launch_class<16, 128>(b, cb[2], cb[3], mask, st)) != TGBA_OK) return r;
-  if ((r = launch_class<12, 256>(b, cb[1], cb[2], mask, st)) != TGBA_OK) return r;
-  if ((r = launch_class<8, 256>(b, cb[0], cb[1], mask, st)) != TGBA_OK) return r;
+  // one launch per size class, largest Pfaffians first (class layout: see tile_class)
+  if ((r = launch_class<32, 32>(b, cb[11], cb[12], mask, st)) != TGBA_OK) return r;
+  if ((r = launch_class<24, 64>(b, cb[10], cb[11], mask, st)) != TGBA_OK) return r;
+  if ((r = launch_class<20, 128>(b, cb[9], cb[10], mask, st)) != TGBA_OK) return r;
+  if ((r = launch_class<16, 128>(b, cb[8], cb[9], mask, st)) != TGBA_OK) return r;
+  if ((r = launch_reg<14>(b, cb[7], cb[8], mask, st)) != TGBA_OK) return r;
+  if ((r = launch_reg<12>(b, cb[6], cb[7], mask, st)) != TGBA_OK) return r;
+  if ((r = launch_reg<10>(b, cb[5], cb[6], mask, st)) != TGBA_OK) return r;
+  if ((r = launch_reg<8>(b, cb[4], cb[5], mask, st)) != TGBA_OK) return r;
+  if ((r = launch_reg<6>(b, cb[3], cb[4], mask, st)) != TGBA_OK) return r;
+  if ((r = launch_reg<4>(b, cb[2], cb[3], mask, st)) != TGBA_OK) return r;
+  if ((r = launch_reg<2>(b, cb[1], cb[2], mask, st)) != TGBA_OK) return r;
+  if ((r = launch_reg<0>(b, cb[0], cb[1], mask, st)) != TGBA_OK) return r;
   return TGBA_OK;
 }
 

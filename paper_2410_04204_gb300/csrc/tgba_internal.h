@@ -15,6 +15,7 @@ namespace tgba {
 constexpr int kMaxQp = 16;        // quasiparticles per state
 constexpr int kMaxL = 120;        // 2L excitation operators must index a uint8 table row
 constexpr int kMaxN = 2 * kMaxQp; // largest Pfaffian M_a + M_b
+constexpr int kNumClasses = 12;   // Pfaffian size classes (basis.cpp: tile_class)
 
 // Device status word bits (tgba_status is derived from them at the next sync).
 enum : unsigned { kStNan = 1u, kStTableImag = 2u, kStTableSingular = 4u, kStTimeout = 8u, kStBadIndex = 16u };
@@ -100,6 +101,7 @@ struct Basis {
   bool table_valid = false;
   // Pfaffian stage
   double* d_P = nullptr;           // X_ab = C0 (-i)^{(M_a+M_b)/2} P_ab, P real, [n_elements]
+  uint8_t* d_mask = nullptr;       // screening decisions (1 = Pfaffian evaluated), [n_elements]
   bool x_valid = false;
   const void* x_screen = nullptr;
   double x_tau = 0;
@@ -119,7 +121,6 @@ struct Basis {
   void* blas = nullptr;            // cublasHandle_t
   double* d_eig_a = nullptr; double* d_eig_w = nullptr; double* d_eig_work = nullptr;
   double* d_scratch = nullptr; int64_t scratch_cap = 0;
-  void* eig_pool = nullptr;        // concurrent eigen-solver workers (eig.cu)
   int* d_eig_info = nullptr;
   int64_t eig_a_cap = 0, eig_work_cap = 0;
 };
@@ -147,10 +148,9 @@ void destroy_blas(void* h);
 
 // eig.cu
 tgba_status eig_sym(Basis& b, int64_t n, double* a, double* w, bool vectors, cudaStream_t st);
-// eigenvalues of every sector's real-gauge H_eff at h_x, sector s written at evals + ev_off,
-// spread over concurrent workers (own stream, solver handle and workspace each)
-tgba_status eig_all_sectors(Basis& b, double h_x, double* evals, cudaStream_t st);
-void destroy_eig_pool(void* pool);
+// eigenvalues of every sector's real-gauge H_eff at each of n_hx fields, one batched solve;
+// field h, sector s written at evals + h * n_states + ev_off
+tgba_status eig_all_sectors(Basis& b, const double* hx, int n_hx, double* evals, cudaStream_t st);
 
 // dsf.cu
 tgba_status dsf(Basis& b, int s, double h_x, double w_min, double w_max, int n_w, double eta, float* S,
@@ -159,6 +159,19 @@ tgba_status dsf(Basis& b, int s, double h_x, double w_min, double w_max, int n_w
 // quench.cu
 tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* ecut, int nv, double t_max,
                    int n_t, double* mx, double* norm, int64_t* chi, cudaStream_t st);
+
+// screen.cu
+struct Screen;
+tgba_status screen_create(int H, const float* params, uint64_t seed, Screen** out);
+void screen_free(Screen* s);
+int64_t screen_nparams(const Screen* s);
+tgba_status screen_params(Screen& s, float* host);
+tgba_status screen_grad(Screen& s, const float* x, const float* t, int64_t B, float* grad, double* loss, cudaStream_t st);
+tgba_status screen_train(Basis** sets, int n_sets, int64_t n_samples, uint64_t seed, int H, int epochs, Screen** out,
+                         double* stats, cudaStream_t st);
+tgba_status screen_score(Screen& s, Basis& b, int sidx, double tau, double hx, float* pred, uint8_t* mask,
+                         cudaStream_t st);
+tgba_status count_mask(Basis& b, int64_t* kept, cudaStream_t st);   // number of 1 bytes in d_mask
 
 // status word
 tgba_status check_status(Basis& b, cudaStream_t st);

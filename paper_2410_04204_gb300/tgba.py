@@ -19,7 +19,9 @@ _NAMES = {0: "TGBA_OK", 1: "TGBA_EINVAL", 2: "TGBA_ENOMEM", 3: "TGBA_ECUDA", 4: 
 # every symbol include/tgba.h declares
 SYMBOLS = ("tgba_last_error", "tgba_device_count", "tgba_build_basis", "tgba_basis_info", "tgba_basis_totals",
            "tgba_basis_free", "tgba_compute_x", "tgba_x_stats", "tgba_x_export", "tgba_x_pairs", "tgba_table",
-           "tgba_assemble_heff", "tgba_eigvals", "tgba_dsf", "tgba_quench", "tgba_profile", "tgba_fp64_peak")
+           "tgba_assemble_heff", "tgba_eigvals", "tgba_dsf", "tgba_quench", "tgba_screen_create",
+           "tgba_screen_nparams", "tgba_screen_params", "tgba_screen_grad", "tgba_screen_train",
+           "tgba_screen_predict", "tgba_screen_free", "tgba_profile", "tgba_fp64_peak")
 
 
 class TgbaError(RuntimeError):
@@ -66,9 +68,16 @@ def lib():
             "tgba_x_pairs": (_I32, [_VP, _I32, _VP, _I64, _VP, _VP]),
             "tgba_table": (_I32, [_VP, _VP, _VP, _VP]),
             "tgba_assemble_heff": (_I32, [_VP, _D, _VP, _D, _VP, _VP]),
-            "tgba_eigvals": (_I32, [_VP, _D, _VP, _VP]),
+            "tgba_eigvals": (_I32, [_VP, _VP, _I32, _VP, _VP]),
             "tgba_dsf": (_I32, [_VP, _I32, _D, _D, _D, _I32, _D, _VP, _VP, _I32, _VP, _VP, _VP]),
             "tgba_quench": (_I32, [_VP, _I32, _D, _VP, _VP, _I32, _D, _I32, _VP, _VP, _VP, _VP]),
+            "tgba_screen_create": (_I32, [_I32, _VP, ctypes.c_uint64, _P(_VP)]),
+            "tgba_screen_nparams": (_I32, [_VP, _P(_I64)]),
+            "tgba_screen_params": (_I32, [_VP, _VP]),
+            "tgba_screen_grad": (_I32, [_VP, _VP, _VP, _I64, _VP, _P(_D), _VP]),
+            "tgba_screen_train": (_I32, [_VP, _I32, _I64, ctypes.c_uint64, _I32, _I32, _P(_VP), _VP, _VP]),
+            "tgba_screen_predict": (_I32, [_VP, _VP, _I32, _VP, _VP]),
+            "tgba_screen_free": (_I32, [_VP]),
             "tgba_profile": (_I32, [_VP, _P(_Prof)]),
             "tgba_fp64_peak": (_I32, [_I32, _P(_D)]),
         }
@@ -187,9 +196,11 @@ def tgba_assemble_heff(b, h_x, heff_out, screen=None, screen_tau=0.0, stream=Non
 
 
 def tgba_eigvals(b, h_x, evals_out, stream=None):
+    """h_x: one field or a list; evals_out: float64 CUDA tensor [len(h_x) * n_states]."""
     import torch
+    hx = np.ascontiguousarray(np.atleast_1d(np.asarray(h_x, np.float64)))
     _cuda_tensor(evals_out, torch.float64, name="evals_out")
-    _check(lib().tgba_eigvals(b, float(h_x), _ptr(evals_out), _stream(stream)))
+    _check(lib().tgba_eigvals(b, hx.ctypes.data, len(hx), _ptr(evals_out), _stream(stream)))
 
 
 def tgba_dsf(b, s, h_x, w_min, w_max, n_w, eta, S_out, evals_out=None, n_ev=0, weights_out=None, dE_out=None,
@@ -215,6 +226,57 @@ def tgba_quench(b, s, h_z0, hx_variants, ecut_variants, t_max, n_t, mx_out, norm
     _check(lib().tgba_quench(b, s, float(h_z0), hx.ctypes.data, ec.ctypes.data, len(hx), float(t_max), int(n_t),
                              _ptr(mx_out), _ptr(norm_out), chi.ctypes.data, _stream(stream)))
     return chi
+
+
+def tgba_screen_create(width=256, params=None, seed=0):
+    """params: float32 numpy array of tgba_screen_nparams entries, or None for a seeded init."""
+    h = _VP()
+    p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+    _check(lib().tgba_screen_create(int(width), None if p is None else p.ctypes.data, int(seed), ctypes.byref(h)))
+    return h.value
+
+
+def tgba_screen_nparams(s):
+    n = _I64()
+    _check(lib().tgba_screen_nparams(s, ctypes.byref(n)))
+    return n.value
+
+
+def tgba_screen_params(s):
+    out = np.zeros(tgba_screen_nparams(s), np.float32)
+    _check(lib().tgba_screen_params(s, out.ctypes.data))
+    return out
+
+
+def tgba_screen_grad(s, x, t, grad_out, stream=None):
+    """x: float32 CUDA [B, 20], t: float32 CUDA [B], grad_out: float32 CUDA [nparams]; returns the loss."""
+    import torch
+    for name, v in (("x", x), ("t", t), ("grad_out", grad_out)):
+        _cuda_tensor(v, torch.float32, name=name)
+    loss = _D()
+    _check(lib().tgba_screen_grad(s, _ptr(x), _ptr(t), int(t.shape[0]), _ptr(grad_out), ctypes.byref(loss),
+                                  _stream(stream)))
+    return loss.value
+
+
+def tgba_screen_train(bases, n_samples, seed, epochs, width=256, stream=None):
+    """Returns (screen handle, dict of training statistics)."""
+    arr = (_VP * len(bases))(*bases)
+    h = _VP()
+    st = np.zeros(4)
+    _check(lib().tgba_screen_train(arr, len(bases), int(n_samples), int(seed), int(width), int(epochs), ctypes.byref(h),
+                                   st.ctypes.data, _stream(stream)))
+    return h.value, dict(train_rmse=st[0], val_rmse=st[1], margin=st[2], seconds=st[3])
+
+
+def tgba_screen_predict(s, b, sector, pred_out, stream=None):
+    import torch
+    _cuda_tensor(pred_out, torch.float32, name="pred_out")
+    _check(lib().tgba_screen_predict(s, b, int(sector), _ptr(pred_out), _stream(stream)))
+
+
+def tgba_screen_free(s):
+    _check(lib().tgba_screen_free(s))
 
 
 def tgba_profile(b):
