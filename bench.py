@@ -289,7 +289,9 @@ def run_gb300(args):
                          "frac": achieved / peak_gflops, "traffic": None,
                          "peak_source": "live FP64 DFMA-chain kernel (tgba_fp64_peak); MEASURED_PEAKS.json has no FP64 entry",
                          "flops_per_launch": prof["pfaffian_flops"], "pfaffian_ms": pf_mean,
-                         "launches_per_stage": prof["pfaffian_launches"]},
+                         "launches_per_stage": prof["pfaffian_launches"],
+                         "autotune": {"mode": prof["tune_mode"], "threads": prof["tune_threads"],
+                                      "candidates_ms": [round(x, 3) for x in prof["tune_ms"]]}},
             "stages_ms": {"table": statistics.mean(tab_ms), "pfaffian": pf_mean,
                           "heff_and_eigvals": ms - statistics.mean(tab_ms) - pf_mean},
             "pfaffian_stage": {"elements_per_s": n_el / (pf_mean * 1e-3),

@@ -199,10 +199,16 @@ tgba_status tgba_screen_free(tgba_screen s);
  * Parlett-Reid count: two FMAs per updated entry, one multiply per Gauss-vector entry).
  * pfaffian_launches: kernel launches of one Pfaffian stage.  kernel_launches: all kernel
  * launches this handle has made (this library's kernels only, not cuSOLVER/cuBLAS).
- * upload_bytes: host-to-device bytes of tgba_build_basis. */
+ * upload_bytes: host-to-device bytes of tgba_build_basis.  tune_mode / tune_threads: the launch
+ * shape the autotuner chose for the register-resident sizes (0: one launch per size, 1: one
+ * persistent queue launch, 3: the queue with a register cap for occupancy; threads per block),
+ * tune_ms: its measured stage time (ms) for each candidate in the order {0,64}, {0,128},
+ * {0,256}, {1,64}, {1,128}, {1,256}, {3,128} (0 where not measured). */
 typedef struct {
   double table_ms, pfaffian_ms, pfaffian_flops;
   int64_t pfaffian_launches, kernel_launches, upload_bytes, evaluated;
+  int32_t tune_mode, tune_threads;
+  double tune_ms[8];
 } tgba_prof;
 tgba_status tgba_profile(tgba_basis b, tgba_prof* out);
 

@@ -54,12 +54,17 @@ tgba_status scratch(Basis& b, int64_t doubles, double** out) {
 
 static void release(Basis* b) {
   void* ptrs[] = {b->d_E_ns, b->d_E_r, b->d_M_ns, b->d_M_r, b->d_sel_ns, b->d_sel_r, b->d_modes_ns, b->d_modes_r,
-                  b->d_theta, b->d_nlab, b->d_table, b->d_c0, b->d_work, b->d_P, b->d_tiles, b->d_status,
-                  b->d_eig_a, b->d_eig_w, b->d_eig_work, b->d_eig_info, b->d_scratch, b->d_mask};
+                  b->d_theta, b->d_nlab, b->d_table, b->d_c0, b->d_work, b->d_P, b->d_status,
+                  b->d_eig_a, b->d_eig_w, b->d_eig_work, b->d_eig_info, b->d_scratch, b->d_mask,
+                  b->d_reg_rects, b->d_counter};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int e = 0; e < 3; ++e)
     if (b->ev[e]) cudaEventDestroy(b->ev[e]);
+  for (RectList& L : b->rect_lists)
+    if (L.d_rects) cudaFree(L.d_rects);
+  if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
   if (b->solver) destroy_solver(b->solver);
   if (b->blas) destroy_blas(b->blas);
   delete b;
@@ -125,47 +130,105 @@ static tgba_status build(const tgba_model* model, const int32_t* sectors, int32_
   TGBA_CUDA(cudaMalloc((void**)&b->d_P, sizeof(double) * std::max<int64_t>(1, b->n_elements)));
   TGBA_CUDA(cudaMalloc((void**)&b->d_status, sizeof(unsigned)));
   TGBA_CUDA(cudaMemset(b->d_status, 0, sizeof(unsigned)));
-  build_tiles(*b, 0, b->tiles, b->tile_class_begin);
-  for (const Tile& t : b->tiles) {
-    double f = 0;
-    for (int m = t.n - 2; m >= 2; m -= 2) f += 2.0 * m * (m - 1) + m;
-    b->pf_flops += f * t.count;
+  TGBA_CUDA(cudaMalloc((void**)&b->d_counter, sizeof(unsigned long long)));
+  build_rects(*b);
+  for (RectList& L : b->rect_lists) {
+    for (const Rect& t : L.rects) {
+      double f = 0;
+      for (int m = t.n - 2; m >= 2; m -= 2) f += 2.0 * m * (m - 1) + m;   // F(n), real Parlett-Reid
+      b->pf_flops += f * (double)t.rows * t.w;
+    }
+    if (!L.rects.empty() && (r = upload(&L.d_rects, L.rects.data(), L.rects.size(), &b->upload_bytes)) != TGBA_OK)
+      return r;
   }
-  for (int c = 0; c + 1 < (int)b->tile_class_begin.size(); ++c)
-    if (b->tile_class_begin[c + 1] > b->tile_class_begin[c]) ++b->pf_launches;
+  if ((r = upload(&b->d_reg_rects, b->reg_rects.data(), b->reg_rects.size(), &b->upload_bytes)) != TGBA_OK) return r;
   for (int e = 0; e < 3; ++e) TGBA_CUDA(cudaEventCreate(&b->ev[e]));
-  if ((r = upload(&b->d_tiles, b->tiles.data(), b->tiles.size(), &b->upload_bytes)) != TGBA_OK) return r;
+  if ((r = plan_pfaffians(*b)) != TGBA_OK) return r;
+  return TGBA_OK;
+}
+
+static tgba_status ensure_c0_host(Basis& b, cudaStream_t st) {
+  if (b.c0_host_valid) return TGBA_OK;
+  TGBA_CUDA(cudaMemcpyAsync(b.c0_host, b.d_c0, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  tgba_status r = check_status(b, st);     // synchronises
+  if (r != TGBA_OK) {
+    b.table_valid = false;
+    return r;
+  }
+  b.c0_host_valid = true;
   return TGBA_OK;
 }
 
 static tgba_status ensure_table(Basis& b, cudaStream_t st) {
-  if (b.table_valid) return TGBA_OK;
-  tgba_status r = build_table(b, st);
-  if (r != TGBA_OK) return r;
-  TGBA_CUDA(cudaMemcpyAsync(b.c0_host, b.d_c0, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  r = check_status(b, st);     // synchronises
-  if (r != TGBA_OK) b.table_valid = false;
-  return r;
+  if (!b.table_valid) {
+    tgba_status r = build_table(b, st);
+    if (r != TGBA_OK) return r;
+    b.c0_host_valid = false;
+  }
+  return ensure_c0_host(b, st);
+}
+
+// The stage without screening: contraction table, then the Pfaffians.  The first call builds the
+// table eagerly, runs the autotuner, then captures the stage (with its timing events) into a
+// CUDA graph on a private stream; every call launches that graph on the caller's stream.
+static tgba_status compute_x_graph(Basis& b, cudaStream_t st) {
+  tgba_status r;
+  if (!b.tuned) {
+    if ((r = ensure_table(b, st)) != TGBA_OK) return r;
+    if ((r = autotune_pfaffians(b, st)) != TGBA_OK) return r;
+  }
+  if (!b.graph_exec) {
+    cudaStream_t cs;
+    TGBA_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const int64_t before = b.launches.load();
+    TGBA_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaEventRecordWithFlags(b.ev[0], cs, cudaEventRecordExternal);
+    r = build_table(b, cs);
+    if (r == TGBA_OK) {
+      cudaEventRecordWithFlags(b.ev[1], cs, cudaEventRecordExternal);
+      r = run_pfaffians(b, nullptr, cs);
+      cudaEventRecordWithFlags(b.ev[2], cs, cudaEventRecordExternal);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (r != TGBA_OK) { if (g) cudaGraphDestroy(g); return r; }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    b.graph = g;
+    TGBA_CUDA(cudaGraphInstantiate(&b.graph_exec, b.graph, 0));
+    b.graph_launches = b.launches.load() - before;
+    b.launches -= b.graph_launches;        // counted when the graph runs
+  }
+  TGBA_CUDA(cudaGraphLaunch(b.graph_exec, st));
+  b.launches += b.graph_launches;
+  b.table_valid = true;
+  b.c0_host_valid = false;
+  b.ev_recorded = true;
+  return TGBA_OK;
 }
 
 static tgba_status compute_x(Basis& b, Screen* screen, double tau, double hx, cudaStream_t st) {
   if (screen && !(tau > 0)) return fail(TGBA_EINVAL, "screening needs tau > 0");
-  b.table_valid = false;                 // the table is part of the stage
-  TGBA_CUDA(cudaEventRecord(b.ev[0], st));
-  tgba_status r = ensure_table(b, st);
-  if (r != TGBA_OK) return r;
-  TGBA_CUDA(cudaEventRecord(b.ev[1], st));
-  const uint8_t* mask = nullptr;
-  if (screen) {
+  tgba_status r;
+  if (!screen) {
+    if ((r = compute_x_graph(b, st)) != TGBA_OK) return r;
+  } else {
+    if (!b.tuned) {
+      if ((r = ensure_table(b, st)) != TGBA_OK) return r;
+      if ((r = autotune_pfaffians(b, st)) != TGBA_OK) return r;
+    }
+    TGBA_CUDA(cudaEventRecord(b.ev[0], st));
+    if ((r = build_table(b, st)) != TGBA_OK) return r;
+    b.c0_host_valid = false;
+    TGBA_CUDA(cudaEventRecord(b.ev[1], st));
     if (!b.d_mask) TGBA_CUDA(cudaMalloc(&b.d_mask, std::max<int64_t>(1, b.n_elements)));
     for (size_t s = 0; s < b.sectors.size(); ++s)
       if ((r = screen_score(*screen, b, (int)s, tau, hx, nullptr, b.d_mask + b.sectors[s].x_off, st)) != TGBA_OK)
         return r;
-    mask = b.d_mask;
+    if ((r = run_pfaffians(b, b.d_mask, st)) != TGBA_OK) return r;
+    TGBA_CUDA(cudaEventRecord(b.ev[2], st));
+    b.ev_recorded = true;
   }
-  if ((r = run_pfaffians(b, mask, st)) != TGBA_OK) return r;
-  TGBA_CUDA(cudaEventRecord(b.ev[2], st));
-  b.ev_recorded = true;
   b.x_valid = true;
   b.x_screen = screen;
   b.x_tau = tau;
@@ -369,6 +432,8 @@ tgba_status tgba_quench(tgba_basis h, int32_t s, double h_z0, const double* hx_v
     return fail(TGBA_EINVAL, "need variants, n_t >= 1 and an output buffer");
   if (!(h_z0 > 0) || !std::isfinite(t_max) || t_max < 0) return fail(TGBA_EINVAL, "need h_z0 > 0 and t_max >= 0");
   if (!b->x_valid) return fail(TGBA_EINVAL, "no X computed yet: call tgba_compute_x");
+  tgba_status r = ensure_c0_host(*b, (cudaStream_t)stream);
+  if (r != TGBA_OK) return r;
   return quench(*b, s, h_z0, hx_variants, ecut_variants, n_variants, t_max, n_t, mx_dev, norm_dev, chi_host,
                 (cudaStream_t)stream);
 }
@@ -443,10 +508,13 @@ tgba_status tgba_profile(tgba_basis h, tgba_prof* out) {
     out->pfaffian_ms = t1;
   }
   out->pfaffian_flops = b->pf_flops;
-  out->pfaffian_launches = b->pf_launches;
+  out->pfaffian_launches = (int64_t)b->pf_plan.size();
   out->kernel_launches = b->launches.load();
   out->upload_bytes = b->upload_bytes;
   out->evaluated = b->x_evaluated;
+  out->tune_mode = b->tuned ? b->tune_mode : -1;
+  out->tune_threads = b->tune_threads;
+  for (size_t i = 0; i < b->tune_log.size() && i < 8; ++i) out->tune_ms[i] = b->tune_log[i].ms;
   return TGBA_OK;
 }
 

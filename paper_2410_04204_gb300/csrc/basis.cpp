@@ -20,10 +20,6 @@ int tile_class(int n) {
   if (n <= 24) return 10;
   return 11;
 }
-int class_threads(int c) {
-  static const int t[kNumClasses] = {128, 128, 128, 128, 128, 128, 128, 128, 128, 128, 64, 32};
-  return t[c];
-}
 
 Modes make_modes(int N, int parity, double h) {
   Modes md;
@@ -195,39 +191,54 @@ tgba_status enumerate_basis(const tgba_model& model, const int32_t* sectors, int
   return TGBA_OK;
 }
 
-void build_tiles(const Basis& b, int /*unused*/, std::vector<Tile>& tiles, std::vector<int>& class_begin) {
-  std::vector<std::vector<Tile>> per(kNumClasses);
+void build_rects(Basis& b) {
+  b.rect_lists.assign(kNumClasses, RectList());
+  for (int c = 0; c < kNumClasses; ++c) b.rect_lists[c].nmax = c < 8 ? 2 * c : c == 8 ? 16 : c == 9 ? 20 : c == 10 ? 24 : 32;
   for (size_t s = 0; s < b.sectors.size(); ++s) {
     const Sector& sec = b.sectors[s];
     for (const Group& ga : sec.g_ns)
       for (const Group& gb : sec.g_r) {
-        int n = ga.M + gb.M;
-        int c = tile_class(n);
-        int64_t rows = ga.end - ga.begin, w = gb.end - gb.begin, total = rows * w;
-        int per_tile = class_threads(c);
-        for (int64_t lin = 0; lin < total; lin += per_tile) {
-          Tile t;
-          t.out0 = sec.x_off + ga.begin * sec.n_r + gb.begin;
-          t.ns0 = sec.ns_off + ga.begin;
-          t.r0 = sec.r_off + gb.begin;
-          t.ld = (int32_t)sec.n_r;
-          t.w = (int32_t)w;
-          t.lin0 = (int32_t)lin;
-          t.count = (int32_t)std::min<int64_t>(per_tile, total - lin);
-          t.n = n;
-          t.Ma = ga.M;
-          per[c].push_back(t);
-        }
+        Rect r;
+        r.out0 = sec.x_off + ga.begin * sec.n_r + gb.begin;
+        r.ns0 = sec.ns_off + ga.begin;
+        r.r0 = sec.r_off + gb.begin;
+        r.ld = (int32_t)sec.n_r;
+        r.w = (int32_t)(gb.end - gb.begin);
+        r.rows = (int32_t)(ga.end - ga.begin);
+        r.n = ga.M + gb.M;
+        r.Ma = ga.M;
+        r.pad = 0;
+        r.tile0 = 0;
+        b.rect_lists[tile_class(r.n)].rects.push_back(r);
       }
   }
-  tiles.clear();
-  class_begin.assign(kNumClasses + 1, 0);
+  std::vector<Rect> all_reg;
+  b.max_reg_n = 0;
   for (int c = 0; c < kNumClasses; ++c) {
-    class_begin[c] = (int)tiles.size();
-    std::stable_sort(per[c].begin(), per[c].end(), [](const Tile& x, const Tile& y) { return x.n > y.n; });
-    tiles.insert(tiles.end(), per[c].begin(), per[c].end());
+    RectList& Lc = b.rect_lists[c];
+    std::stable_sort(Lc.rects.begin(), Lc.rects.end(), [](const Rect& x, const Rect& y) { return x.n > y.n; });
+    int64_t t = 0;
+    for (Rect& r : Lc.rects) {
+      r.tile0 = t;
+      t += ((int64_t)r.rows * r.w + 31) / 32;
+    }
+    Lc.n_tiles = t;
+    Lc.n_rects = (int)Lc.rects.size();
+    if (Lc.nmax <= 14)
+      for (const Rect& r : Lc.rects) {
+        all_reg.push_back(r);
+        b.max_reg_n = std::max(b.max_reg_n, r.n);
+      }
   }
-  class_begin[kNumClasses] = (int)tiles.size();
+  std::stable_sort(all_reg.begin(), all_reg.end(), [](const Rect& x, const Rect& y) { return x.n > y.n; });
+  int64_t t = 0;
+  for (Rect& r : all_reg) {
+    r.tile0 = t;
+    t += ((int64_t)r.rows * r.w + 31) / 32;
+  }
+  b.reg_tiles_total = t;
+  b.reg_rects_total = (int)all_reg.size();
+  b.reg_rects = all_reg;
 }
 
 }  // namespace tgba

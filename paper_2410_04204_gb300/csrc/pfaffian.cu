@@ -4,20 +4,22 @@
 // (table rows of b's R excitation operators, ascending), n = M_a + M_b, and
 //     P_ab = Pf(R[sel, sel]),   X_ab = C0 (-i)^{n/2} P_ab
 // with R the real contraction table.  Pf is computed by Parlett-Reid reduction with partial
-// pivoting in FP64, one thread per element.  The n x n strict upper triangle lives in shared
-// memory laid out [entry][thread], so the 32 lanes of a warp touch 32 consecutive doubles.
+// pivoting in FP64, one thread per element.
 //
-// GB300 runs FP64 at 1/64 of its FP32 rate, so the kernel is bound by the FP64 pipe alone: the
-// per-step pivot search compares magnitudes as integers (the bit pattern of |x|), index
-// arithmetic and shared-memory traffic are integer/LSU work, and only the elimination itself
-// (one FMA pair per updated entry, one multiply per Gauss-vector entry, one reciprocal and one
-// multiply per step) issues FP64 instructions.
+// GB300 runs FP64 at 1/64 of its FP32 rate, so the kernels are bound by the FP64 pipe alone:
+// the pivot search compares magnitudes as integers, the row/column exchange moves 32-bit
+// halves with integer selects, sign flips are integer XORs, and only the elimination (one FMA
+// pair per updated entry, one multiply per Gauss-vector entry, one reciprocal and one multiply
+// per step) issues FP64 instructions.
 //
-// Work: tiles of up to THREADS elements with uniform n (see build_tiles), grouped in size
-// classes; one persistent launch per class walks its tiles with a grid-stride loop.  Sizes
-// n <= 14 run the register-resident kernel of pfaffian_reg.cuh, one class per exact n; larger
-// sizes run the shared-memory kernel below.
+// Work: the NS x R grid of each sector is cut into rectangles of uniform (M_a, M_b), hence of
+// uniform n (see build_rects), and each rectangle into tiles of 32 consecutive pairs; a warp
+// owns a tile.  Sizes n <= 14 keep the whole matrix in registers (pfaffian_reg.cuh), either as
+// one static launch per size or as one persistent launch over all of them that hands out tiles,
+// largest n first, through an atomic counter; the autotuner of this file times both shapes and
+// keeps the faster.  Sizes n >= 16 keep the matrix in shared memory laid out [entry][thread].
 #include <algorithm>
+#include <string>
 
 #include "pfaffian_reg.cuh"
 #include "tgba_internal.h"
@@ -30,11 +32,32 @@ template <int NMAX>
 struct Packed {
   // strict upper triangle of an NMAX x NMAX matrix, row-major
   static __device__ __forceinline__ int idx(int i, int j) { return i * (2 * NMAX - i - 1) / 2 + (j - i - 1); }
-  static constexpr int kEntries = NMAX * (NMAX - 1) / 2;
 };
 
-__device__ __forceinline__ unsigned long long mag(double x) {
-  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+struct Args {
+  const Rect* rects;
+  int n_rects;
+  int64_t n_tiles;
+  const double* R;
+  int two_l;
+  const uint8_t* sel_ns;
+  const uint8_t* sel_r;
+  int max_qp;
+  const uint8_t* mask;
+  double* P;
+  unsigned* status;
+  unsigned long long* counter;
+};
+
+// rectangle holding tile t (rects sorted by tile0)
+__device__ __forceinline__ int find_rect(const Rect* __restrict__ rects, int n, int64_t t) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (rects[mid].tile0 <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
 }
 
 // Pf of the n x n skew matrix whose strict upper triangle is in W (packed, stride T).
@@ -44,11 +67,10 @@ __device__ double pfaffian_smem(double* W, int n) {
   double pf = 1.0;
   for (int k = 0; k + 1 < n; k += 2) {
     const int r = k + 1;
-    // pivot: largest |W(k, x)|, x > k
     int p = r;
-    unsigned long long best = mag(W[P::idx(k, r) * T]);
+    unsigned long long best = abs_bits(W[P::idx(k, r) * T]);
     for (int x = r + 1; x < n; ++x) {
-      unsigned long long v = mag(W[P::idx(k, x) * T]);
+      unsigned long long v = abs_bits(W[P::idx(k, x) * T]);
       if (v > best) { best = v; p = x; }
     }
     if (p != r) {
@@ -56,22 +78,22 @@ __device__ double pfaffian_smem(double* W, int n) {
       double t = W[P::idx(k, r) * T]; W[P::idx(k, r) * T] = W[P::idx(k, p) * T]; W[P::idx(k, p) * T] = t;
       for (int x = r + 1; x < p; ++x) {
         double a = W[P::idx(r, x) * T], c = W[P::idx(x, p) * T];
-        W[P::idx(r, x) * T] = -c;
-        W[P::idx(x, p) * T] = -a;
+        W[P::idx(r, x) * T] = neg(c);
+        W[P::idx(x, p) * T] = neg(a);
       }
-      W[P::idx(r, p) * T] = -W[P::idx(r, p) * T];
+      W[P::idx(r, p) * T] = neg(W[P::idx(r, p) * T]);
       for (int x = p + 1; x < n; ++x) {
         double a = W[P::idx(r, x) * T];
         W[P::idx(r, x) * T] = W[P::idx(p, x) * T];
         W[P::idx(p, x) * T] = a;
       }
-      pf = -pf;
+      pf = neg(pf);
     }
     const double a = W[P::idx(k, r) * T];
-    if (a == 0.0) return 0.0;          // the whole column is zero: Pf = 0 exactly
+    if (is_zero(a)) return 0.0;        // the whole column is zero: Pf = 0 exactly
     pf *= a;
     if (k + 2 >= n) break;
-    const double ia = 1.0 / a;
+    const double ia = recip_nr(a);
     for (int j = k + 2; j < n; ++j) W[P::idx(k, j) * T] *= ia;     // Gauss vector tau_j
     // trailing update: W_ij += W(r, i) tau_j - tau_i W(r, j),  k+2 <= i < j < n
     for (int i = k + 2; i < n - 1; ++i) {
@@ -92,75 +114,108 @@ __device__ double pfaffian_smem(double* W, int n) {
   return pf;
 }
 
+struct Elem {
+  int64_t out;
+  const uint8_t* sa;
+  const uint8_t* sb;
+  bool live;
+};
+
+__device__ __forceinline__ Elem locate(const Args& g, const Rect& rc, int64_t tile, int lane) {
+  Elem e;
+  const int64_t lin = (tile - rc.tile0) * 32 + lane;
+  e.live = lin < (int64_t)rc.rows * rc.w;
+  const int row = (int)(lin / rc.w), col = (int)(lin - (lin / rc.w) * rc.w);
+  e.out = rc.out0 + (int64_t)row * rc.ld + col;
+  e.sa = g.sel_ns + (size_t)(rc.ns0 + row) * g.max_qp;
+  e.sb = g.sel_r + (size_t)(rc.r0 + col) * g.max_qp;
+  return e;
+}
+
+// one element of exact size N in registers
+template <int N>
+__device__ __forceinline__ void element_reg(const Args& g, const Elem& e, int ma) {
+  if (g.mask != nullptr && g.mask[e.out] == 0) { g.P[e.out] = 0.0; return; }
+  if constexpr (N == 0) {
+    g.P[e.out] = 1.0;
+  } else {
+    int sel[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) sel[i] = i < ma ? e.sa[i] : e.sb[i - ma];
+    double W[N][N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const double* Ri = g.R + (size_t)sel[i] * g.two_l;
+#pragma unroll
+      for (int j = i + 1; j < N; ++j) W[i][j] = __ldg(Ri + sel[j]);
+    }
+    const double pf = pfaffian_regs<N>(W);
+    if (!is_finite_bits(pf)) atomicOr(g.status, kStNan);
+    g.P[e.out] = pf;
+  }
+}
+
+// One static launch per exact size N: warps walk the tiles with a grid stride.
+template <int N, int T>
+__global__ void __launch_bounds__(T) pf_reg_class(Args g) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wstride = (int64_t)gridDim.x * (T / 32);
+  for (int64_t t = (int64_t)blockIdx.x * (T / 32) + (threadIdx.x >> 5); t < g.n_tiles; t += wstride) {
+    const Rect rc = g.rects[find_rect(g.rects, g.n_rects, t)];
+    const Elem e = locate(g, rc, t, lane);
+    if (e.live) element_reg<N>(g, e, rc.Ma);
+  }
+}
+
+template <int N, int NMAXR>
+__device__ __forceinline__ void dispatch_n(int n, const Args& g, const Elem& e, int ma) {
+  if constexpr (N <= NMAXR) {
+    if (n == N) { element_reg<N>(g, e, ma); return; }
+    dispatch_n<N + 2, NMAXR>(n, g, e, ma);
+  }
+}
+
+// One persistent launch over every size n <= NMAXR: a warp takes the next tile (largest n
+// first) from an atomic counter until the list is exhausted.  MINB > 0 asks the compiler for
+// MINB resident blocks per SM (a register cap that trades a few registers for occupancy).
+template <int NMAXR, int T, int MINB>
+__global__ void __launch_bounds__(T, MINB) pf_reg_queue(Args g) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(g.counter, 1ull);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if ((int64_t)t >= g.n_tiles) return;
+    const Rect rc = g.rects[find_rect(g.rects, g.n_rects, (int64_t)t)];
+    const Elem e = locate(g, rc, (int64_t)t, lane);
+    if (e.live) dispatch_n<0, NMAXR>(rc.n, g, e, rc.Ma);
+  }
+}
+
+// Shared-memory variant for 16 <= n <= NMAX.
 template <int NMAX, int T>
-__global__ void __launch_bounds__(T) pf_tiles(const Tile* __restrict__ tiles, int t_begin, int t_end,
-                                              const double* __restrict__ R, int two_l,
-                                              const uint8_t* __restrict__ sel_ns, const uint8_t* __restrict__ sel_r,
-                                              int max_qp, const uint8_t* __restrict__ mask, double* __restrict__ P,
-                                              unsigned* status) {
+__global__ void __launch_bounds__(T) pf_smem(Args g) {
   extern __shared__ double smem[];
   double* W = smem + threadIdx.x;
-  for (int t = t_begin + blockIdx.x; t < t_end; t += gridDim.x) {
-    const Tile tl = tiles[t];
-    const int e = threadIdx.x;
-    if (e >= tl.count) continue;
-    const int lin = tl.lin0 + e;
-    const int row = lin / tl.w, col = lin - (lin / tl.w) * tl.w;
-    const int64_t out = tl.out0 + (int64_t)row * tl.ld + col;
-    if (mask != nullptr && mask[out] == 0) { P[out] = 0.0; continue; }
-    const int n = tl.n, ma = tl.Ma;
-    const uint8_t* sa = sel_ns + (size_t)(tl.ns0 + row) * max_qp;
-    const uint8_t* sb = sel_r + (size_t)(tl.r0 + col) * max_qp;
-    // gather R[sel_i][sel_j], i < j, from the (L2-resident) table
+  const int lane = threadIdx.x & 31;
+  const int64_t wstride = (int64_t)gridDim.x * (T / 32);
+  for (int64_t t = (int64_t)blockIdx.x * (T / 32) + (threadIdx.x >> 5); t < g.n_tiles; t += wstride) {
+    const Rect rc = g.rects[find_rect(g.rects, g.n_rects, t)];
+    const Elem e = locate(g, rc, t, lane);
+    if (!e.live) continue;
+    if (g.mask != nullptr && g.mask[e.out] == 0) { g.P[e.out] = 0.0; continue; }
+    const int n = rc.n, ma = rc.Ma;
     for (int i = 0; i < n - 1; ++i) {
-      const int si = i < ma ? sa[i] : sb[i - ma];
-      const double* Ri = R + (size_t)si * two_l;
+      const int si = i < ma ? e.sa[i] : e.sb[i - ma];
+      const double* Ri = g.R + (size_t)si * g.two_l;
       for (int j = i + 1; j < n; ++j) {
-        const int sj = j < ma ? sa[j] : sb[j - ma];
+        const int sj = j < ma ? e.sa[j] : e.sb[j - ma];
         W[Packed<NMAX>::idx(i, j) * T] = __ldg(Ri + sj);
       }
     }
     const double pf = pfaffian_smem<NMAX, T>(W, n);
-    if (!isfinite(pf)) atomicOr(status, kStNan);
-    P[out] = pf;
-  }
-}
-
-// Register-resident variant for one exact size N <= 14 (see pfaffian_reg.cuh).
-template <int N, int T>
-__global__ void __launch_bounds__(T) pf_tiles_reg(const Tile* __restrict__ tiles, int t_begin, int t_end,
-                                                  const double* __restrict__ R, int two_l,
-                                                  const uint8_t* __restrict__ sel_ns, const uint8_t* __restrict__ sel_r,
-                                                  int max_qp, const uint8_t* __restrict__ mask, double* __restrict__ P,
-                                                  unsigned* status) {
-  for (int t = t_begin + blockIdx.x; t < t_end; t += gridDim.x) {
-    const Tile tl = tiles[t];
-    const int e = threadIdx.x;
-    if (e >= tl.count) continue;
-    const int lin = tl.lin0 + e;
-    const int row = lin / tl.w, col = lin - (lin / tl.w) * tl.w;
-    const int64_t out = tl.out0 + (int64_t)row * tl.ld + col;
-    if (mask != nullptr && mask[out] == 0) { P[out] = 0.0; continue; }
-    if constexpr (N == 0) {
-      P[out] = 1.0;
-    } else {
-      const int ma = tl.Ma;
-      const uint8_t* sa = sel_ns + (size_t)(tl.ns0 + row) * max_qp;
-      const uint8_t* sb = sel_r + (size_t)(tl.r0 + col) * max_qp;
-      int sel[N];
-#pragma unroll
-      for (int i = 0; i < N; ++i) sel[i] = i < ma ? sa[i] : sb[i - ma];
-      double W[N][N];
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        const double* Ri = R + (size_t)sel[i] * two_l;
-#pragma unroll
-        for (int j = i + 1; j < N; ++j) W[i][j] = __ldg(Ri + sel[j]);
-      }
-      const double pf = pfaffian_regs<N>(W);
-      if (!is_finite_bits(pf)) atomicOr(status, kStNan);
-      P[out] = pf;
-    }
+    if (!is_finite_bits(pf)) atomicOr(g.status, kStNan);
+    g.P[e.out] = pf;
   }
 }
 
@@ -194,96 +249,180 @@ __global__ void __launch_bounds__(T) pf_pairs(const int32_t* __restrict__ pairs,
       }
     }
     const double pf = pfaffian_smem<NMAX, T>(W, n);
-    if (!isfinite(pf)) atomicOr(status, kStNan);
+    if (!is_finite_bits(pf)) atomicOr(status, kStNan);
     // X = C0 (-i)^{n/2} pf
     double re = c0[0] * pf, im = c0[1] * pf;
     switch ((n / 2) & 3) {
       case 0: out[2 * q] = re; out[2 * q + 1] = im; break;
-      case 1: out[2 * q] = im; out[2 * q + 1] = -re; break;
-      case 2: out[2 * q] = -re; out[2 * q + 1] = -im; break;
-      default: out[2 * q] = -im; out[2 * q + 1] = re; break;
+      case 1: out[2 * q] = im; out[2 * q + 1] = neg(re); break;
+      case 2: out[2 * q] = neg(re); out[2 * q + 1] = neg(im); break;
+      default: out[2 * q] = neg(im); out[2 * q + 1] = re; break;
     }
   }
 }
 
-template <int NMAX, int T>
-tgba_status launch_class(Basis& b, int t0, int t1, const uint8_t* mask, cudaStream_t st) {
-  if (t1 <= t0) return TGBA_OK;
-  const size_t smem = (size_t)Packed<NMAX>::kEntries * T * sizeof(double);
-  auto kern = pf_tiles<NMAX, T>;
-  TGBA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0, sms = 0;
-  TGBA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem));
-  TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
-  if (per_sm < 1) return fail(TGBA_ELIMIT, "Pfaffian kernel does not fit on an SM");
-  const int grid = std::min(t1 - t0, per_sm * sms);
-  kern<<<grid, T, smem, st>>>(b.d_tiles, t0, t1, b.d_table, 2 * b.L, b.d_sel_ns, b.d_sel_r, b.max_qp, mask, b.d_P,
-                              b.d_status);
-  TGBA_CUDA(cudaGetLastError());
-  ++b.launches;
-  return TGBA_OK;
+using KernelFn = void (*)(Args);
+
+// kernel of (kind, size, threads); kind 0: static launch of one exact size, 1: queue over all
+// register sizes, 3: the same queue with a register cap for occupancy, 2: shared memory
+KernelFn kernel_of(int kind, int n, int T) {
+#define K_CLASS(N)                                      \
+  if (n == N) {                                         \
+    if (T == 64) return pf_reg_class<N, 64>;            \
+    if (T == 128) return pf_reg_class<N, 128>;          \
+    if (T == 256) return pf_reg_class<N, 256>;          \
+  }
+  if (kind == 0) {
+    K_CLASS(0) K_CLASS(2) K_CLASS(4) K_CLASS(6) K_CLASS(8) K_CLASS(10) K_CLASS(12) K_CLASS(14)
+  }
+#undef K_CLASS
+  if (kind == 1) {              // queue, default register allocation
+    if (n <= 12) {
+      if (T == 64) return pf_reg_queue<12, 64, 1>;
+      if (T == 128) return pf_reg_queue<12, 128, 1>;
+      if (T == 256) return pf_reg_queue<12, 256, 1>;
+    } else {
+      if (T == 64) return pf_reg_queue<14, 64, 1>;
+      if (T == 128) return pf_reg_queue<14, 128, 1>;
+      if (T == 256) return pf_reg_queue<14, 256, 1>;
+    }
+  }
+  if (kind == 3 && T == 128) {  // queue capped for three 128-thread blocks per SM
+    if (n <= 12) return pf_reg_queue<12, 128, 3>;
+    return pf_reg_queue<14, 128, 2>;
+  }
+  if (kind == 2) {
+    if (n <= 16 && T == 128) return pf_smem<16, 128>;
+    if (n <= 20 && T == 128) return pf_smem<20, 128>;
+    if (n <= 24 && T == 64) return pf_smem<24, 64>;
+    if (n <= 32 && T == 32) return pf_smem<32, 32>;
+  }
+  return nullptr;
 }
 
-template <int N>
-tgba_status launch_reg(Basis& b, int t0, int t1, const uint8_t* mask, cudaStream_t st) {
-  if (t1 <= t0) return TGBA_OK;
-  constexpr int T = 128;
-  auto kern = pf_tiles_reg<N, T>;
-  TGBA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
-  int per_sm = 0, sms = 0;
-  TGBA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, 0));
-  TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
-  if (per_sm < 1) return fail(TGBA_ELIMIT, "register Pfaffian kernel does not fit on an SM");
-  const int grid = std::min(t1 - t0, per_sm * sms);
-  kern<<<grid, T, 0, st>>>(b.d_tiles, t0, t1, b.d_table, 2 * b.L, b.d_sel_ns, b.d_sel_r, b.max_qp, mask, b.d_P,
-                           b.d_status);
-  TGBA_CUDA(cudaGetLastError());
-  ++b.launches;
-  return TGBA_OK;
-}
-
-template <int NMAX, int T>
-tgba_status launch_pairs(Basis& b, int s, const int32_t* pairs, int64_t n, double* out, cudaStream_t st) {
-  const size_t smem = (size_t)Packed<NMAX>::kEntries * T * sizeof(double);
-  auto kern = pf_pairs<NMAX, T>;
-  TGBA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int sms = 0;
-  TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
-  const int64_t blocks = std::min<int64_t>((n + T - 1) / T, (int64_t)sms * 8);
-  const Sector& sec = b.sectors[s];
-  kern<<<(int)blocks, T, smem, st>>>(pairs, n, sec.ns_off, sec.r_off, sec.n_ns, sec.n_r, b.d_table, 2 * b.L, b.d_sel_ns, b.d_sel_r,
-                                     b.d_M_ns, b.d_M_r, b.max_qp, b.d_c0, out, b.d_status);
-  TGBA_CUDA(cudaGetLastError());
-  ++b.launches;
-  return TGBA_OK;
+size_t smem_of(int kind, int n, int T) {
+  if (kind != 2) return 0;
+  const int nmax = n <= 16 ? 16 : n <= 20 ? 20 : n <= 24 ? 24 : 32;
+  return (size_t)(nmax * (nmax - 1) / 2) * T * sizeof(double);
 }
 
 }  // namespace
 
-tgba_status run_pfaffians(Basis& b, const uint8_t* mask, cudaStream_t st) {
-  const std::vector<int>& cb = b.tile_class_begin;
-  tgba_status r;
-  // one launch per size class, largest Pfaffians first (class layout: see tile_class)
-  if ((r = launch_class<32, 32>(b, cb[11], cb[12], mask, st)) != TGBA_OK) return r;
-  if ((r = launch_class<24, 64>(b, cb[10], cb[11], mask, st)) != TGBA_OK) return r;
-  if ((r = launch_class<20, 128>(b, cb[9], cb[10], mask, st)) != TGBA_OK) return r;
-  if ((r = launch_class<16, 128>(b, cb[8], cb[9], mask, st)) != TGBA_OK) return r;
-  if ((r = launch_reg<14>(b, cb[7], cb[8], mask, st)) != TGBA_OK) return r;
-  if ((r = launch_reg<12>(b, cb[6], cb[7], mask, st)) != TGBA_OK) return r;
-  if ((r = launch_reg<10>(b, cb[5], cb[6], mask, st)) != TGBA_OK) return r;
-  if ((r = launch_reg<8>(b, cb[4], cb[5], mask, st)) != TGBA_OK) return r;
-  if ((r = launch_reg<6>(b, cb[3], cb[4], mask, st)) != TGBA_OK) return r;
-  if ((r = launch_reg<4>(b, cb[2], cb[3], mask, st)) != TGBA_OK) return r;
-  if ((r = launch_reg<2>(b, cb[1], cb[2], mask, st)) != TGBA_OK) return r;
-  if ((r = launch_reg<0>(b, cb[0], cb[1], mask, st)) != TGBA_OK) return r;
+// Launch list for the current tuning choice (rect lists: see build_rects).
+tgba_status plan_pfaffians(Basis& b) {
+  b.pf_plan.clear();
+  int sms = 0;
+  TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
+  bool queued = false;
+  for (size_t li = 0; li < b.rect_lists.size(); ++li) {
+    const RectList& L = b.rect_lists[li];
+    if (L.n_tiles == 0) continue;
+    int kind, size, T;
+    if (L.nmax <= 14) {
+      if (b.tune_mode == 1 || b.tune_mode == 3) {
+        if (queued) continue;              // one queue launch covers every register size
+        queued = true;
+        kind = b.tune_mode; size = b.max_reg_n; T = b.tune_threads;
+      } else {
+        kind = 0; size = L.nmax; T = b.tune_threads;
+      }
+    } else {
+      kind = 2; size = L.nmax;
+      T = L.nmax <= 20 ? 128 : L.nmax <= 24 ? 64 : 32;
+    }
+    KernelFn k = kernel_of(kind, size, T);
+    if (!k) return fail(TGBA_ELIMIT, "no Pfaffian kernel for size " + std::to_string(size));
+    const size_t smem = smem_of(kind, size, T);
+    TGBA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (kind != 2) TGBA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+    int per_sm = 0;
+    TGBA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T, smem));
+    if (per_sm < 1) return fail(TGBA_ELIMIT, "Pfaffian kernel does not fit on an SM");
+    PfLaunch pl;
+    pl.kind = kind; pl.size = size; pl.threads = T; pl.smem = smem;
+    pl.list = (int)li;
+    const int64_t tiles = (kind == 1 || kind == 3) ? b.reg_tiles_total : L.n_tiles;
+    pl.grid = (int)std::max<int64_t>(1, std::min<int64_t>((tiles + T / 32 - 1) / (T / 32), (int64_t)per_sm * sms));
+    b.pf_plan.push_back(pl);
+  }
   return TGBA_OK;
+}
+
+tgba_status run_pfaffians(Basis& b, const uint8_t* mask, cudaStream_t st) {
+  for (const PfLaunch& pl : b.pf_plan) {
+    const RectList& L = b.rect_lists[pl.list];
+    Args g;
+    const bool queue = pl.kind == 1 || pl.kind == 3;
+    g.rects = queue ? b.d_reg_rects : L.d_rects;
+    g.n_rects = queue ? b.reg_rects_total : L.n_rects;
+    g.n_tiles = queue ? b.reg_tiles_total : L.n_tiles;
+    g.R = b.d_table; g.two_l = 2 * b.L; g.sel_ns = b.d_sel_ns; g.sel_r = b.d_sel_r; g.max_qp = b.max_qp;
+    g.mask = mask; g.P = b.d_P; g.status = b.d_status; g.counter = b.d_counter;
+    if (queue) TGBA_CUDA(cudaMemsetAsync(b.d_counter, 0, sizeof(unsigned long long), st));
+    kernel_of(pl.kind, pl.size, pl.threads)<<<pl.grid, pl.threads, pl.smem, st>>>(g);
+    TGBA_CUDA(cudaGetLastError());
+    ++b.launches;
+  }
+  return TGBA_OK;
+}
+
+// Autotuner: time every launch shape of the register sizes on this basis (CUDA events on the
+// stream, best of two runs each) and keep the fastest.
+tgba_status autotune_pfaffians(Basis& b, cudaStream_t st) {
+  struct Cand { int mode, threads; };
+  const Cand cands[] = {{0, 64}, {0, 128}, {0, 256}, {1, 64}, {1, 128}, {1, 256}, {3, 128}};
+  cudaEvent_t e0, e1;
+  TGBA_CUDA(cudaEventCreate(&e0));
+  TGBA_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  Cand pick = {0, 128};
+  b.tune_log.clear();
+  tgba_status r = TGBA_OK;
+  for (const Cand& c : cands) {
+    b.tune_mode = c.mode;
+    b.tune_threads = c.threads;
+    if ((r = plan_pfaffians(b)) != TGBA_OK) break;
+    float t = 1e30f;
+    for (int rep = 0; rep < 2 && r == TGBA_OK; ++rep) {
+      cudaEventRecord(e0, st);
+      if ((r = run_pfaffians(b, nullptr, st)) != TGBA_OK) break;
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t = std::min(t, ms);
+    }
+    if (r != TGBA_OK) break;
+    b.tune_log.push_back(TuneEntry{c.mode, c.threads, t});
+    if (t < best) { best = t; pick = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (r != TGBA_OK) return r;
+  b.tune_mode = pick.mode;
+  b.tune_threads = pick.threads;
+  b.tuned = true;
+  return plan_pfaffians(b);
 }
 
 tgba_status run_pfaffian_pairs(Basis& b, int s, const int32_t* pairs, int64_t n, double* out, cudaStream_t st) {
   if (n == 0) return TGBA_OK;
-  if (b.max_n <= 12) return launch_pairs<12, 128>(b, s, pairs, n, out, st);
-  if (b.max_n <= 20) return launch_pairs<20, 64>(b, s, pairs, n, out, st);
-  return launch_pairs<32, 32>(b, s, pairs, n, out, st);
+  const Sector& sec = b.sectors[s];
+  int sms = 0;
+  TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
+  auto go = [&](auto kern, int T, int nmax) -> tgba_status {
+    const size_t smem = (size_t)(nmax * (nmax - 1) / 2) * T * sizeof(double);
+    TGBA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t blocks = std::min<int64_t>((n + T - 1) / T, (int64_t)sms * 8);
+    kern<<<(int)blocks, T, smem, st>>>(pairs, n, sec.ns_off, sec.r_off, sec.n_ns, sec.n_r, b.d_table, 2 * b.L,
+                                       b.d_sel_ns, b.d_sel_r, b.d_M_ns, b.d_M_r, b.max_qp, b.d_c0, out, b.d_status);
+    TGBA_CUDA(cudaGetLastError());
+    ++b.launches;
+    return TGBA_OK;
+  };
+  if (b.max_n <= 12) return go(pf_pairs<12, 128>, 128, 12);
+  if (b.max_n <= 20) return go(pf_pairs<20, 64>, 64, 20);
+  return go(pf_pairs<32, 32>, 32, 32);
 }
 
 }  // namespace tgba

@@ -13,23 +13,55 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
   return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 
-// sign flip and zero / finiteness tests on the bit pattern: integer ops, off the FP64 pipe
-__device__ __forceinline__ double neg(double x) {
-  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+// Every data movement of the pivot exchange works on the two 32-bit halves of a double with
+// integer selects: a conditional 64-bit move written as a double select may otherwise become
+// a predicated FP64 add on the (1/64-rate) FP64 pipe.
+__device__ __forceinline__ double sel(bool s, double y, double x) {        // s ? y : x
+  const int lo = s ? __double2loint(y) : __double2loint(x);
+  const int hi = s ? __double2hiint(y) : __double2hiint(x);
+  return __hiloint2double(hi, lo);
 }
+__device__ __forceinline__ double flip_if(bool s, double x) {               // s ? -x : x
+  return __hiloint2double(__double2hiint(x) ^ (s ? (int)0x80000000 : 0), __double2loint(x));
+}
+__device__ __forceinline__ double neg(double x) { return flip_if(true, x); }
 __device__ __forceinline__ bool is_zero(double x) { return abs_bits(x) == 0ull; }
 __device__ __forceinline__ bool is_finite_bits(double x) { return abs_bits(x) < 0x7ff0000000000000ull; }
 
+// 1/a for the pivot: a single-precision seed, then two Newton-Raphson steps for f(x) = 1/x - a,
+// x <- x + x (1 - a x), each squaring the relative error (2^-22 -> 2^-44 -> below double
+// rounding).  The seed is built from the double's bit fields with integer operations (sign,
+// exponent rebased from 1023 to 127, top 23 mantissa bits) and its reciprocal taken in FP32, so
+// the FP64 pipe sees only the four FMAs.  |a| outside [2^-100, 2^100] (never a usable pivot
+// here, but possible in principle) takes the library reciprocal instead.
+__device__ __forceinline__ double recip_nr(double a) {
+  const int hi = __double2hiint(a), lo = __double2loint(a);
+  const int e = (hi >> 20) & 0x7ff;
+  if (e < 1023 - 100 || e > 1023 + 100) return __drcp_rn(a);
+  const unsigned fbits = ((unsigned)hi & 0x80000000u) | ((unsigned)(e - 1023 + 127) << 23) |
+                         (((unsigned)hi & 0x000fffffu) << 3) | ((unsigned)lo >> 29);
+  const float rf = __frcp_rn(__uint_as_float(fbits));
+  // back to double bits: sign, exponent rebased from 127 to 1023, mantissa widened
+  const unsigned rb = __float_as_uint(rf);
+  const int re = (int)((rb >> 23) & 0xff) - 127 + 1023;
+  double x = __hiloint2double((int)((rb & 0x80000000u) | ((unsigned)re << 20) | ((rb & 0x7fffffu) >> 3)),
+                              (int)(rb << 29));
+  double err = fma(-a, x, 1.0);
+  x = fma(x, err, x);
+  err = fma(-a, x, 1.0);
+  return fma(x, err, x);
+}
+
 __device__ __forceinline__ void cswap(bool s, double& a, double& b) {
   const double x = a, y = b;
-  a = s ? y : x;
-  b = s ? x : y;
+  a = sel(s, y, x);
+  b = sel(s, x, y);
 }
 
 __device__ __forceinline__ void cswap_neg(bool s, double& a, double& b) {
   const double x = a, y = b;
-  a = s ? neg(y) : x;
-  b = s ? neg(x) : y;
+  a = sel(s, neg(y), x);
+  b = sel(s, neg(x), y);
 }
 
 // If s: exchange rows/columns R and C (R < C) of the trailing matrix (rows >= K, R = K + 1).
@@ -39,7 +71,7 @@ __device__ __forceinline__ void exchange(bool s, double (&W)[N][N]) {
   cswap(s, W[K][R], W[K][C]);
 #pragma unroll
   for (int x = R + 1; x < C; ++x) cswap_neg(s, W[R][x], W[x][C]);
-  W[R][C] = s ? neg(W[R][C]) : W[R][C];
+  W[R][C] = flip_if(s, W[R][C]);
 #pragma unroll
   for (int x = C + 1; x < N; ++x) cswap(s, W[R][x], W[C][x]);
 }
@@ -70,10 +102,10 @@ struct Eliminate {
     }
     ExchangeAll<N, K, R + 1>::run(p, W);
     const double a = W[K][R];
-    pf = (p != R) ? neg(pf) : pf;
+    pf = flip_if(p != R, pf);
     pf *= a;
     if (K + 2 < N) {
-      const double ia = is_zero(a) ? 0.0 : __drcp_rn(a);   // a == 0: whole column zero, pf is already 0
+      const double ia = sel(is_zero(a), 0.0, recip_nr(a));   // a == 0: whole column zero, pf is already 0
 #pragma unroll
       for (int j = K + 2; j < N; ++j) W[K][j] *= ia;       // Gauss vector tau_j
 #pragma unroll

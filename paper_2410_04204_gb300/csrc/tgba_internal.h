@@ -40,19 +40,34 @@ struct StateTable {
   std::vector<int16_t> modes;      // [state][max_qp], ascending mode indices, -1 padded
 };
 
-// Work unit of the Pfaffian stage: up to `count` consecutive elements of a rectangle of
-// pairs with uniform (M_a, M_b), laid out row-major (row = NS state, column = R state).
-struct Tile {
+// Work of the Pfaffian stage: a rectangle of pairs with uniform (M_a, M_b), laid out row-major
+// (row = NS state, column = R state), cut into tiles of 32 consecutive pairs (one per warp).
+struct Rect {
   int64_t out0;   // element index of the rectangle's first pair in the X cache
   int64_t ns0;    // global NS state index of the rectangle's first row
   int64_t r0;     // global R state index of the rectangle's first column
+  int64_t tile0;  // index of the rectangle's first tile within its list
   int32_t ld;     // row stride of the sector's X block (n_r)
   int32_t w;      // rectangle width
-  int32_t lin0;   // first linear index (within the rectangle) of this tile
-  int32_t count;  // elements in this tile
+  int32_t rows;   // rectangle height
   int32_t n;      // Pfaffian size M_a + M_b
   int32_t Ma;     // quasiparticles of the NS state
+  int32_t pad;
 };
+
+// Rectangles of one size class: exact n for n <= 14 (register kernels), n <= 16/20/24/32 above.
+struct RectList {
+  int nmax = 0;
+  std::vector<Rect> rects;        // sorted by n descending, tile0 prefix
+  int64_t n_tiles = 0;
+  Rect* d_rects = nullptr;
+  int n_rects = 0;
+};
+
+// One kernel launch of the Pfaffian stage (kind 0: one exact register size, 1: queue over all
+// register sizes, 2: shared-memory class).
+struct PfLaunch { int kind, size, threads, grid, list; size_t smem; };
+struct TuneEntry { int mode, threads; float ms; };
 
 // Single-particle data of one parity at field h (Eq. 7, S3), host side.
 struct Modes {
@@ -69,7 +84,7 @@ struct Basis;
 // basis.cpp
 tgba_status enumerate_basis(const tgba_model& model, const int32_t* sectors, int n_sectors,
                             const tgba_trunc& tr, Basis& b);
-void build_tiles(const Basis& b, int tile_elems, std::vector<Tile>& tiles, std::vector<int>& class_begin);
+void build_rects(Basis& b);
 
 struct Basis {
   int L = 0;
@@ -106,9 +121,21 @@ struct Basis {
   const void* x_screen = nullptr;
   double x_tau = 0;
   int64_t x_evaluated = 0, x_screened = 0;
-  std::vector<Tile> tiles;
-  std::vector<int> tile_class_begin;   // tiles sorted by size class; class c = [begin[c], begin[c+1])
-  Tile* d_tiles = nullptr;
+  std::vector<RectList> rect_lists;    // one per size class (basis.cpp: tile_class)
+  std::vector<Rect> reg_rects;         // all register-size rectangles, n descending, one tile prefix
+  Rect* d_reg_rects = nullptr;
+  int reg_rects_total = 0;
+  int64_t reg_tiles_total = 0;
+  int max_reg_n = 0;
+  unsigned long long* d_counter = nullptr;   // work counter of the queue launch
+  std::vector<PfLaunch> pf_plan;
+  int tune_mode = 0, tune_threads = 128;
+  bool tuned = false;
+  std::vector<TuneEntry> tune_log;
+  cudaGraph_t graph = nullptr;         // table + Pfaffian stage, captured once
+  cudaGraphExec_t graph_exec = nullptr;
+  bool c0_host_valid = false;
+  int64_t graph_launches = 0;          // kernel launches inside the graph
   unsigned* d_status = nullptr;
   // measurement
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -133,6 +160,8 @@ tgba_status cuda_fail(cudaError_t e, const char* what);
 tgba_status build_table(Basis& b, cudaStream_t st);
 
 // pfaffian.cu
+tgba_status plan_pfaffians(Basis& b);
+tgba_status autotune_pfaffians(Basis& b, cudaStream_t st);
 tgba_status run_pfaffians(Basis& b, const uint8_t* d_mask, cudaStream_t st);
 tgba_status run_pfaffian_pairs(Basis& b, int s, const int32_t* pairs, int64_t n, double* out, cudaStream_t st);
 

@@ -41,7 +41,8 @@ class _Trunc(ctypes.Structure):
 class _Prof(ctypes.Structure):
     _fields_ = [("table_ms", ctypes.c_double), ("pfaffian_ms", ctypes.c_double), ("pfaffian_flops", ctypes.c_double),
                 ("pfaffian_launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("upload_bytes", ctypes.c_int64), ("evaluated", ctypes.c_int64)]
+                ("upload_bytes", ctypes.c_int64), ("evaluated", ctypes.c_int64),
+                ("tune_mode", ctypes.c_int32), ("tune_threads", ctypes.c_int32), ("tune_ms", ctypes.c_double * 8)]
 
 
 _lib = None
@@ -283,7 +284,9 @@ def tgba_profile(b):
     """Stage times of the last tgba_compute_x and the handle's counters (dict)."""
     p = _Prof()
     _check(lib().tgba_profile(b, ctypes.byref(p)))
-    return {k: getattr(p, k) for k, _ in _Prof._fields_}
+    out = {k: getattr(p, k) for k, _ in _Prof._fields_}
+    out["tune_ms"] = list(p.tune_ms)[:7]
+    return out
 
 
 def tgba_fp64_peak(reps=5):

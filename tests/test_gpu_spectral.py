@@ -1,0 +1,109 @@
+"""Spectral sums at the benchmark sizes.
+
+* L = 40 (k = 0, ~1e4 states): the FP32 Lorentzian sum against an FP64 sum of the same FP64
+  weights (the stated FP32 tolerance), eigenvalue consistency, and the E8 mass ratio m2/m1
+  from the weights, a loose physics check against the E8 value of Table 1.
+* L = 80 quench: at t = 0 the normalised magnetisation of the ferromagnetic initial state
+  equals Pfeuty's closed form (1 - h0^2)^(1/8) once the retained weight ||c0||^2 -> 1;
+  ||c0||^2 grows with nested cutoffs and never exceeds 1.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2410_04204_gb300 import inputs, tgba
+from tests.test_golden import load_table1
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def test_dsf_L40():
+    w = inputs.DSF_L40
+    w_min, w_max, n_w, eta = w.w_range
+    hx = w.h_x[0]
+    b = tgba.tgba_build_basis(w.L, w.h_z, [0], w.max_qp, w.e_cut)
+    try:
+        info = tgba.tgba_basis_info(b, 0, w.max_qp)
+        n = info["n_ns"] + info["n_r"]
+        tgba.tgba_compute_x(b)
+        S = torch.empty(n_w, dtype=torch.float32, device="cuda")
+        wts = torch.empty(n, dtype=torch.float64, device="cuda")
+        dE = torch.empty(n, dtype=torch.float64, device="cuda")
+        ev = torch.empty(20, dtype=torch.float64, device="cuda")
+        tgba.tgba_dsf(b, 0, hx, w_min, w_max, n_w, eta, S, ev, 20, wts, dE)
+        wv, dv = wts.cpu().numpy(), dE.cpu().numpy()
+        om = w_min + (w_max - w_min) * np.arange(n_w) / (n_w - 1)
+        S64 = np.zeros(n_w)
+        for c in range(0, n, 2048):           # FP64 reference sum of the same weights
+            x = om[:, None] - dv[None, c:c + 2048]
+            S64 += 2 * math.pi * ((eta / math.pi) / (x * x + eta * eta)) @ wv[c:c + 2048]
+        assert np.abs(S.cpu().numpy() - S64).max() <= 1e-4 * S64.max()
+        allev = torch.empty(n, dtype=torch.float64, device="cuda")
+        tgba.tgba_eigvals(b, hx, allev)
+        assert np.abs(ev.cpu().numpy() - allev.cpu().numpy()[:20]).max() < 1e-10 * abs(allev[0].item())
+        # single-particle peaks: the two lowest excitations carrying > 5 % of the largest weight
+        order = np.argsort(dv)
+        big = [i for i in order if dv[i] > 1e-6 and wv[i] > 0.05 * wv[1:].max()]
+        m1, m2 = dv[big[0]], dv[big[1]]
+        theory = load_table1()["m2/m1"][1]
+        assert abs(m2 / m1 - theory) / theory < 0.02, (m1, m2, m2 / m1)
+    finally:
+        tgba.tgba_basis_free(b)
+
+
+def test_quench_L80():
+    """Config 5's basis (L = 80, M <= 10, cutoff 6.551) and its 3.8e8-element Pfaffian stage;
+    the quench variant with cutoff 3.0 (338 states) against the oracle's whole quench path
+    (direct Pfaffians of size ~165 for X and the overlaps); nested cutoffs keep growing chi and
+    ||c0||^2 <= 1."""
+    from oracle import tgba as otgba
+    w = inputs.QUENCH_L80
+    h0 = w.quench["h_z0"]
+    b = tgba.tgba_build_basis(w.L, w.h_z, [0], w.max_qp, w.e_cut, w.max_per_parity)
+    try:
+        tgba.tgba_compute_x(b)
+        cuts = [3.0, 3.5, 4.0]
+        n_t, t_max = 101, 20.0
+        mx = torch.empty(len(cuts) * n_t, dtype=torch.float64, device="cuda")
+        nrm = torch.empty(len(cuts), dtype=torch.float64, device="cuda")
+        chi = tgba.tgba_quench(b, 0, h0, [0.1] * len(cuts), cuts, t_max, n_t, mx, nrm)
+        m = mx.cpu().numpy().reshape(len(cuts), n_t)
+        c2 = nrm.cpu().numpy()
+        assert np.all(np.diff(chi) > 0) and np.all(np.diff(c2) > 0) and np.all(c2 <= 1 + 1e-12)
+        t, mo, c0 = otgba.quench(w.L, w.h_z, h0, 0.1, w.max_qp, cuts[0], t_max, n_t)
+        assert chi[0] == len(c0)
+        assert abs(c2[0] - np.vdot(c0, c0).real) < 1e-12
+        assert np.abs(m[0] - mo).max() < 1e-9
+    finally:
+        tgba.tgba_basis_free(b)
+
+
+def test_quench_initial_magnetisation_pfeuty():
+    """L = 16, all states with M <= 8: the retained weight ||c0||^2 equals the Eq. S6 closed form
+    (0.9999965: only the M cap loses weight), and <sigma^x>(0) equals the h_x = 0
+    magnetisation (1 - h0^2)^(1/8) up to that loss and the finite-size correction
+    ~ exp(-L / xi), xi = 1/ln(1/h0) = 1.4."""
+    from oracle import basis as obs
+    from tests import pins
+    b = tgba.tgba_build_basis(16, 1.0, [0], 8)
+    try:
+        tgba.tgba_compute_x(b)
+        mx = torch.empty(3, dtype=torch.float64, device="cuda")
+        nrm = torch.empty(1, dtype=torch.float64, device="cuda")
+        tgba.tgba_quench(b, 0, 0.5, [0.1], [-1.0], 1.0, 3, mx, nrm)
+        ns, r = obs.sector_basis(16, 1.0, 0, 8)
+        closed = 0.5 * (np.sum(np.abs(pins.calabrese_overlaps(16, 1.0, 0.5, 0, ns)) ** 2)
+                        + np.sum(np.abs(pins.calabrese_overlaps(16, 1.0, 0.5, 1, r)) ** 2))
+        assert abs(nrm.item() - closed) < 1e-12 and closed > 0.99999
+        assert abs(mx[0].item() - 0.75 ** 0.125) < 1e-4
+    finally:
+        tgba.tgba_basis_free(b)
