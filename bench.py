@@ -191,6 +191,18 @@ def run_reference(args):
     return 0
 
 
+def aggregate(ms_local, n_elements, world, dist=None, device=None):
+    """Whole-job throughput under weak scaling: every rank processes its own copy of the
+    workload, the step time is the slowest rank's, value = world * elements / time."""
+    ms = float(ms_local)
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * n_elements / (ms * 1e-3)
+
+
 # ------------------------------------------------------------------ the GPU path
 def run_gb300(args):
     import torch
@@ -250,15 +262,10 @@ def run_gb300(args):
     clk = clocks.stop()
     launches = tgba.tgba_profile(b)["kernel_launches"] - launches0
     step_ms = [a.elapsed_time(c) for a, c in ev]
-    ms = statistics.mean(step_ms)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, value = aggregate(statistics.mean(step_ms), n_el, world, dist, "cuda")
     prof = tgba.tgba_profile(b)
     pf_mean = statistics.mean(pf_ms)
     achieved = prof["pfaffian_flops"] / (pf_mean * 1e-3) / 1e9
-    value = world * n_el / (ms * 1e-3)
 
     # end to end through the public API with host buffers: host enumeration and upload of the
     # state tables, the step, and the eigenvalues read back to pinned host memory
