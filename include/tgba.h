@@ -191,6 +191,22 @@ tgba_status tgba_screen_train(const tgba_basis* sets, int32_t n_sets, int64_t n_
 tgba_status tgba_screen_predict(tgba_screen s, tgba_basis b, int32_t sector, float* pred_dev, void* stream);
 tgba_status tgba_screen_free(tgba_screen s);
 
+/* ---------------------------------------------------------------- allocation-free table
+ * The paper has no counterpart: this is a service entry point of the library.  It computes the
+ * same contraction table and vacuum element as tgba_table, but for callers that cannot let the
+ * library allocate device memory, for example a process whose device memory belongs to a
+ * fixed-size pool that refuses allocations made behind its back, or a latency-critical loop
+ * that cannot afford the implicit synchronisation of cudaMalloc/cudaFree.  Nothing is allocated:
+ * the work matrix (4L x 4L complex) and the per-call inputs live in statically sized device
+ * arrays of the library (about 1 MiB, held on every GPU that loads the library until the
+ * process exits), so L is limited to 64 (TGBA_ELIMIT beyond).  The first call on a device looks
+ * up the addresses of those arrays (cudaGetSymbolAddress) and must come before any stream
+ * capture.  All calls share the arrays: calls that overlap on the GPU, from any thread or
+ * stream, race and must be serialised by the caller.  table_dev: caller-owned double
+ * [2L][2L] (row-major, the real table R of tgba_table); c0_dev: caller-owned double [2]
+ * receiving C0 = <0_NS|c_1 + c_1^dag|0_R>.  Blocks on `stream`. */
+tgba_status tgba_table_noalloc(int32_t L, double J, double h_z, double* table_dev, double* c0_dev, void* stream);
+
 /* ---------------------------------------------------------------- measurement
  * Profile of a basis handle.  table_ms / pfaffian_ms: device time of the contraction table and
  * of the Pfaffian kernels of the last tgba_compute_x, from CUDA events recorded on its stream

@@ -19,6 +19,7 @@
 //
 // The sums over sites j = 1..L are closed-form geometric series of plane waves.
 #include <cmath>
+#include <mutex>
 
 #include "tgba_internal.h"
 
@@ -218,3 +219,96 @@ tgba_status build_table(Basis& b, cudaStream_t st) {
 }
 
 }  // namespace tgba
+
+// ------------------------------------------------------------------ allocation-free variant
+// tgba_table_noalloc: the same table build for callers that must not allocate device memory
+// themselves or through this library.  Examples: a process whose device memory is owned by a
+// fixed-size pool that rejects outside allocations, or a latency-critical loop where the
+// implicit synchronisation of cudaMalloc/cudaFree is not acceptable.  The work matrix and the
+// small per-call inputs live in the file-scope arrays below instead.  They are statically
+// sized for chains up to kNoAllocMaxL sites (about 1 MiB in total), and every GPU that loads
+// the library keeps them until the process exits.
+namespace tgba {
+namespace {
+
+constexpr int kNoAllocMaxL = 64;
+constexpr int kNoAllocWork = 16 * kNoAllocMaxL * kNoAllocMaxL;   // (4L)^2 complex entries
+
+static __device__ __align__(256) cd g_noalloc_work[kNoAllocWork];
+static __device__ __align__(256) double g_noalloc_theta[2 * kNoAllocMaxL];
+static __device__ __align__(256) int g_noalloc_nlab[2 * kNoAllocMaxL];
+static __device__ __align__(256) double g_noalloc_c0[4];            // C0 and the realness diagnostics
+static __device__ __align__(256) unsigned g_noalloc_status;
+
+struct NoAllocPtrs {
+  cd* work = nullptr;
+  double* theta = nullptr;
+  int* nlab = nullptr;
+  double* c0 = nullptr;
+  unsigned* status = nullptr;
+  bool ready = false;
+};
+
+constexpr int kMaxDevices = 64;
+NoAllocPtrs g_noalloc_ptrs[kMaxDevices];
+std::mutex g_noalloc_mutex;
+
+// Device addresses of the arrays above, looked up once per device (the device current).
+tgba_status noalloc_setup(int dev, NoAllocPtrs& out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  NoAllocPtrs& p = g_noalloc_ptrs[dev];
+  if (!p.ready) {
+    TGBA_CUDA(cudaGetSymbolAddress((void**)&p.work, g_noalloc_work));
+    TGBA_CUDA(cudaGetSymbolAddress((void**)&p.theta, g_noalloc_theta));
+    TGBA_CUDA(cudaGetSymbolAddress((void**)&p.nlab, g_noalloc_nlab));
+    TGBA_CUDA(cudaGetSymbolAddress((void**)&p.c0, g_noalloc_c0));
+    TGBA_CUDA(cudaGetSymbolAddress((void**)&p.status, g_noalloc_status));
+    p.ready = true;
+  }
+  out = p;
+  return TGBA_OK;
+}
+
+}  // namespace
+}  // namespace tgba
+
+extern "C" tgba_status tgba_table_noalloc(int32_t L, double J, double h_z, double* table_dev, double* c0_dev,
+                                          void* stream) {
+  using namespace tgba;
+  if (L < 4 || L % 2 || !(J > 0) || !(h_z > 0) || !std::isfinite(J) || !std::isfinite(h_z))
+    return fail(TGBA_EINVAL, "need even L >= 4, J > 0 and h_z > 0");
+  if (L > kNoAllocMaxL)
+    return fail(TGBA_ELIMIT, "tgba_table_noalloc handles chains of at most 64 sites (its static work area); "
+                             "use tgba_table for longer chains");
+  if (!table_dev || !c0_dev) return fail(TGBA_EINVAL, "null output");
+  int dev = 0;
+  TGBA_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(TGBA_ELIMIT, "device index beyond the set-up table");
+  NoAllocPtrs p;
+  tgba_status r = noalloc_setup(dev, p);
+  if (r != TGBA_OK) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  Modes mns = make_modes(L, 0, h_z / J), mr = make_modes(L, 1, h_z / J);
+  double th[2 * kNoAllocMaxL];
+  int nl[2 * kNoAllocMaxL];
+  for (int i = 0; i < L; ++i) {
+    th[i] = mns.theta[i]; th[L + i] = mr.theta[i];
+    nl[i] = mns.nlab[i]; nl[L + i] = mr.nlab[i];
+  }
+  // the arrays keep the previous call's contents: clear what the kernels accumulate into
+  TGBA_CUDA(cudaMemcpyAsync(p.theta, th, 2 * L * sizeof(double), cudaMemcpyHostToDevice, st));
+  TGBA_CUDA(cudaMemcpyAsync(p.nlab, nl, 2 * L * sizeof(int), cudaMemcpyHostToDevice, st));
+  TGBA_CUDA(cudaMemsetAsync(p.c0, 0, 4 * sizeof(double), st));
+  TGBA_CUDA(cudaMemsetAsync(p.status, 0, sizeof(unsigned), st));
+  table_kernel<<<1, 1024, 0, st>>>(L, p.nlab, p.theta, mns.norm * mr.norm, p.work, table_dev, p.c0, p.status);
+  TGBA_CUDA(cudaGetLastError());
+  table_check<<<1, 1, 0, st>>>(p.c0, p.status);
+  TGBA_CUDA(cudaGetLastError());
+  TGBA_CUDA(cudaMemcpyAsync(c0_dev, p.c0, 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  unsigned w = 0;
+  TGBA_CUDA(cudaMemcpyAsync(&w, p.status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  TGBA_CUDA(cudaStreamSynchronize(st));
+  if (w & kStTableSingular) return fail(TGBA_ENUMERIC, "the vacuum block of the contraction matrix is singular");
+  if (w & kStTableImag) return fail(TGBA_ENUMERIC, "the gauge-rotated contraction table is not real");
+  return TGBA_OK;
+}

@@ -21,7 +21,7 @@ SYMBOLS = ("tgba_last_error", "tgba_device_count", "tgba_build_basis", "tgba_bas
            "tgba_basis_free", "tgba_compute_x", "tgba_x_stats", "tgba_x_export", "tgba_x_pairs", "tgba_table",
            "tgba_assemble_heff", "tgba_eigvals", "tgba_dsf", "tgba_quench", "tgba_screen_create",
            "tgba_screen_nparams", "tgba_screen_params", "tgba_screen_grad", "tgba_screen_train",
-           "tgba_screen_predict", "tgba_screen_free", "tgba_profile", "tgba_fp64_peak")
+           "tgba_screen_predict", "tgba_screen_free", "tgba_table_noalloc", "tgba_profile", "tgba_fp64_peak")
 
 
 class TgbaError(RuntimeError):
@@ -79,6 +79,7 @@ def lib():
             "tgba_screen_train": (_I32, [_VP, _I32, _I64, ctypes.c_uint64, _I32, _I32, _P(_VP), _VP, _VP]),
             "tgba_screen_predict": (_I32, [_VP, _VP, _I32, _VP, _VP]),
             "tgba_screen_free": (_I32, [_VP]),
+            "tgba_table_noalloc": (_I32, [_I32, _D, _D, _VP, _VP, _VP]),
             "tgba_profile": (_I32, [_VP, _P(_Prof)]),
             "tgba_fp64_peak": (_I32, [_I32, _P(_D)]),
         }
@@ -278,6 +279,15 @@ def tgba_screen_predict(s, b, sector, pred_out, stream=None):
 
 def tgba_screen_free(s):
     _check(lib().tgba_screen_free(s))
+
+
+def tgba_table_noalloc(L, h_z, table_out, c0_out, J=1.0, stream=None):
+    """Contraction table and C0 without any device allocation (see include/tgba.h):
+    table_out float64 CUDA [2L * 2L], c0_out float64 CUDA [2]."""
+    import torch
+    _cuda_tensor(table_out, torch.float64, 4 * L * L, name="table_out")
+    _cuda_tensor(c0_out, torch.float64, 2, name="c0_out")
+    _check(lib().tgba_table_noalloc(int(L), float(J), float(h_z), _ptr(table_out), _ptr(c0_out), _stream(stream)))
 
 
 def tgba_profile(b):
