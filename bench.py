@@ -41,6 +41,7 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-budget-s", type=float, default=12.0)
+    p.add_argument("--no-screening", action="store_true")
     return p.parse_args()
 
 
@@ -203,6 +204,58 @@ def aggregate(ms_local, n_elements, world, dist=None, device=None):
     return ms, world * n_elements / (ms * 1e-3)
 
 
+def screening_leg(b24, tgba, inputs, torch):
+    """Learned screening: train on 2e6 exact pairs of the L = 24 sectors (this workload), then
+    time the Pfaffian stage with and without screening at L = 60 (k = 0, 2.25e8 pairs) for each
+    tau, and measure the relative error of the lowest 20 eigenvalues at L = 40 (k = 0, n ~ 1e4,
+    where a dense check is affordable)."""
+    s, st = tgba.tgba_screen_train([b24], 2_000_000, inputs.SEED, 10)
+    out = {"trained_on": "2e6 pairs of L24_all_sectors", "train": {k: round(v, 4) for k, v in st.items()}}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(f):
+        best = 1e30
+        for _ in range(2):
+            torch.cuda.synchronize()
+            e0.record()
+            f()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    w4 = inputs.SCREEN_L60
+    b = tgba.tgba_build_basis(w4.L, w4.h_z, [0], w4.max_qp, w4.e_cut)
+    hx = w4.h_x[0]
+    t_exact = timed(lambda: tgba.tgba_compute_x(b))
+    rows = []
+    for tau in inputs.SCREEN_TAUS:
+        t_scr = timed(lambda: tgba.tgba_compute_x(b, s, tau, hx))
+        ev, sc = tgba.tgba_x_stats(b)
+        rows.append({"tau": tau, "screened_fraction": sc / (ev + sc), "ms": round(t_scr, 2),
+                     "speedup": t_exact / t_scr})
+    tgba.tgba_basis_free(b)
+    out["L60_k0"] = {"exact_ms": round(t_exact, 2), "taus": rows}
+    w3 = inputs.DSF_L40
+    b = tgba.tgba_build_basis(w3.L, w3.h_z, [0], w3.max_qp, w3.e_cut)
+    info = tgba.tgba_basis_info(b, 0, w3.max_qp)
+    n = info["n_ns"] + info["n_r"]
+    ev = torch.empty(n, dtype=torch.float64, device="cuda")
+    tgba.tgba_compute_x(b)
+    tgba.tgba_eigvals(b, hx, ev)
+    exact = ev[:20].clone()
+    tau = inputs.SCREEN_TAUS[-1]
+    tgba.tgba_compute_x(b, s, tau, hx)
+    tgba.tgba_eigvals(b, hx, ev)
+    err = ((ev[:20] - exact).abs() / exact.abs()).max().item()
+    _, sc = tgba.tgba_x_stats(b)
+    out["L40_k0_eigen_check"] = {"tau": tau, "screened_fraction": sc / (info["n_ns"] * info["n_r"]),
+                                 "max_rel_err_lowest20": err}
+    tgba.tgba_basis_free(b)
+    tgba.tgba_screen_free(s)
+    return out
+
+
 # ------------------------------------------------------------------ the GPU path
 def run_gb300(args):
     import torch
@@ -307,6 +360,8 @@ def run_gb300(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": n_states * 8 * len(w.h_x)},
             "gpu_launches": launches}
+    if not args.no_screening:
+        line["screening"] = screening_leg(b, tgba, inputs, torch)
     tgba.tgba_basis_free(b)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s = oracle_sample(w, args.cpu_budget_s)

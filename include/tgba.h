@@ -153,11 +153,15 @@ tgba_status tgba_dsf(tgba_basis b, int32_t s, double h_x, double w_min, double w
  * of the basis with E - E_NS,vacuum <= ecut_variants[v] (+1e-9; a negative value keeps all), so
  * variants with growing cutoffs are nested truncations (Method section, Fig. 2: several chi).
  * B(t) = M^T e^{-iEt} M^* c0 with c0 = <phi|Phi0> (Eq. S6), <sigma^x>(t) = B^H X B / ||c0||^2
- * on t_i = i t_max/(n_t - 1).  mx_dev: double [n_variants][n_t]; norm_dev (optional): double
- * [n_variants], ||c0||^2 of each variant; chi_host (optional): int64 [n_variants], the retained
- * basis size of each variant.  Blocks on `stream`. */
+ * on t_i = i t_max/(n_t - 1).  method: 1 diagonalises H_eff (FP64 syevd) and forms B(t) from its
+ * eigenpairs, as Eq. 10 writes it; 2 expands e^{-iH t} c0 = B(t) in Chebyshev polynomials of the
+ * rescaled H_eff with Bessel coefficients (Jacobi-Anger), truncated where J_k(R t_max) < 1e-16,
+ * which needs only products with H_eff and lifts the cubic cost of the diagonalisation; 0 picks 1
+ * up to 4096 retained states and 2 above.  mx_dev: double [n_variants][n_t]; norm_dev (optional):
+ * double [n_variants], ||c0||^2 of each variant; chi_host (optional): int64 [n_variants], the
+ * retained basis size of each variant.  Blocks on `stream`. */
 tgba_status tgba_quench(tgba_basis b, int32_t s, double h_z0, const double* hx_variants,
-                        const double* ecut_variants, int32_t n_variants, double t_max, int32_t n_t,
+                        const double* ecut_variants, int32_t n_variants, double t_max, int32_t n_t, int32_t method,
                         double* mx_dev, double* norm_dev, int64_t* chi_host, void* stream);
 
 /* ---------------------------------------------------------------- learned pair screener

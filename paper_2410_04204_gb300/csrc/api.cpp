@@ -126,7 +126,7 @@ static tgba_status build(const tgba_model* model, const int32_t* sectors, int32_
   if ((r = upload(&b->d_nlab, nl.data(), nl.size(), &b->upload_bytes)) != TGBA_OK) return r;
   TGBA_CUDA(cudaMalloc((void**)&b->d_table, sizeof(double) * 4 * L * L));
   TGBA_CUDA(cudaMalloc((void**)&b->d_c0, sizeof(double) * 4));
-  TGBA_CUDA(cudaMalloc((void**)&b->d_work, sizeof(double) * 2 * 16 * L * L));
+  TGBA_CUDA(cudaMalloc((void**)&b->d_work, sizeof(double) * 2 * (16 * L * L + 4 * L + 1)));
   TGBA_CUDA(cudaMalloc((void**)&b->d_P, sizeof(double) * std::max<int64_t>(1, b->n_elements)));
   TGBA_CUDA(cudaMalloc((void**)&b->d_status, sizeof(unsigned)));
   TGBA_CUDA(cudaMemset(b->d_status, 0, sizeof(unsigned)));
@@ -422,7 +422,7 @@ tgba_status tgba_dsf(tgba_basis h, int32_t s, double h_x, double w_min, double w
 }
 
 tgba_status tgba_quench(tgba_basis h, int32_t s, double h_z0, const double* hx_variants, const double* ecut_variants,
-                        int32_t n_variants, double t_max, int32_t n_t, double* mx_dev, double* norm_dev,
+                        int32_t n_variants, double t_max, int32_t n_t, int32_t method, double* mx_dev, double* norm_dev,
                         int64_t* chi_host, void* stream) {
   Basis* b = (Basis*)h;
   BASIS_OK(b);
@@ -431,10 +431,11 @@ tgba_status tgba_quench(tgba_basis h, int32_t s, double h_z0, const double* hx_v
   if (n_variants < 1 || !hx_variants || !ecut_variants || !mx_dev || n_t < 1)
     return fail(TGBA_EINVAL, "need variants, n_t >= 1 and an output buffer");
   if (!(h_z0 > 0) || !std::isfinite(t_max) || t_max < 0) return fail(TGBA_EINVAL, "need h_z0 > 0 and t_max >= 0");
+  if (method < 0 || method > 2) return fail(TGBA_EINVAL, "method must be 0 (automatic), 1 (eigen) or 2 (Chebyshev)");
   if (!b->x_valid) return fail(TGBA_EINVAL, "no X computed yet: call tgba_compute_x");
   tgba_status r = ensure_c0_host(*b, (cudaStream_t)stream);
   if (r != TGBA_OK) return r;
-  return quench(*b, s, h_z0, hx_variants, ecut_variants, n_variants, t_max, n_t, mx_dev, norm_dev, chi_host,
+  return quench(*b, s, h_z0, hx_variants, ecut_variants, n_variants, t_max, n_t, method, mx_dev, norm_dev, chi_host,
                 (cudaStream_t)stream);
 }
 

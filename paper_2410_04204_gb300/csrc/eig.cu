@@ -83,28 +83,46 @@ __global__ void heff_real_padded(int64_t kn, int64_t kr, int64_t n_max, int64_t 
   }
 }
 
-// Gershgorin upper bound of the spectrum of the n x n corner, then the padding diagonal
-// entries set just above it, so the n true eigenvalues are the n smallest of the slot.
-__global__ void pad_kernel(int64_t n, int64_t n_max, double* __restrict__ A) {
+// Order-preserving map of doubles onto unsigned integers (and back), for atomicMax.
+__device__ __forceinline__ unsigned long long ordered(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double unordered(unsigned long long k) {
+  return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+
+// Gershgorin upper bound of each slot's spectrum: thread = row of the n x n corner
+// (column-major reads are coalesced across the warp), block maximum, atomicMax per slot.
+__global__ void gershgorin_kernel(const int64_t* __restrict__ nq, int64_t n_max, const double* __restrict__ A,
+                                  unsigned long long* __restrict__ bound) {
   __shared__ double red[32];
-  double best = -1e300;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    double r = A[i * n_max + i];
+  const int64_t q = blockIdx.y, n = nq[q];
+  const double* Aq = A + q * n_max * n_max;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double r = -1e300;
+  if (i < n) {
+    r = Aq[i * n_max + i];
     for (int64_t j = 0; j < n; ++j)
-      if (j != i) r += fabs(A[j * n_max + i]);
-    best = fmax(best, r);
+      if (j != i) r += fabs(Aq[j * n_max + i]);
   }
-  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    best = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : -1e300;
-    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if (threadIdx.x == 0) red[0] = best;
+  if (threadIdx.x == 0) {
+    double m = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+    atomicMax(bound + q, ordered(m));
   }
-  __syncthreads();
-  const double pad = red[0] + 1.0;
-  for (int64_t i = n + threadIdx.x; i < n_max; i += blockDim.x) A[i * n_max + i] = pad;
+}
+
+// Padding diagonal entries just above the bound, so the n true eigenvalues are the n smallest.
+__global__ void pad_kernel(const int64_t* __restrict__ nq, int64_t n_max, const unsigned long long* __restrict__ bound,
+                           double* __restrict__ A) {
+  const int64_t q = blockIdx.y, n = nq[q];
+  const double pad = unordered(bound[q]) + 1.0;
+  for (int64_t i = n + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_max; i += (int64_t)gridDim.x * blockDim.x)
+    A[q * n_max * n_max + i * n_max + i] = pad;
 }
 
 }  // namespace
@@ -122,10 +140,16 @@ tgba_status eig_all_sectors(Basis& b, const double* hx, int n_hx, double* evals,
   if (slots.empty()) return TGBA_OK;
   const int64_t B = (int64_t)slots.size();
   double* A;
-  tgba_status r = scratch(b, B * n_max * n_max + B * n_max + B, &A);
+  tgba_status r = scratch(b, B * n_max * n_max + B * n_max + 3 * B + 2, &A);
   if (r != TGBA_OK) return r;
   double* W = A + B * n_max * n_max;
-  int* info = (int*)(W + B * n_max);
+  int64_t* nq = (int64_t*)(W + B * n_max);
+  unsigned long long* bound = (unsigned long long*)(nq + B);
+  int* info = (int*)(bound + B);
+  std::vector<int64_t> hn(B);
+  for (int64_t q = 0; q < B; ++q) hn[q] = b.sectors[slots[q].second].n_ns + b.sectors[slots[q].second].n_r;
+  TGBA_CUDA(cudaMemcpyAsync(nq, hn.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  TGBA_CUDA(cudaMemsetAsync(bound, 0, B * sizeof(unsigned long long), st));
   for (int64_t q = 0; q < B; ++q) {
     const Sector& sec = b.sectors[slots[q].second];
     double* Aq = A + q * n_max * n_max;
@@ -133,10 +157,13 @@ tgba_status eig_all_sectors(Basis& b, const double* hx, int n_hx, double* evals,
     const int grid = (int)std::min<int64_t>((work + 255) / 256, 152 * 32);
     heff_real_padded<<<grid, 256, 0, st>>>(sec.n_ns, sec.n_r, n_max, sec.n_r, b.d_E_ns + sec.ns_off,
                                           b.d_E_r + sec.r_off, b.d_P + sec.x_off, b.d_c0, -b.L * hx[slots[q].first], Aq);
-    pad_kernel<<<1, 1024, 0, st>>>(sec.n_ns + sec.n_r, n_max, Aq);
     TGBA_CUDA(cudaGetLastError());
-    b.launches += 2;
+    ++b.launches;
   }
+  gershgorin_kernel<<<dim3((unsigned)((n_max + 255) / 256), (unsigned)B), 256, 0, st>>>(nq, n_max, A, bound);
+  pad_kernel<<<dim3(4, (unsigned)B), 256, 0, st>>>(nq, n_max, bound, A);
+  TGBA_CUDA(cudaGetLastError());
+  b.launches += 2;
   cusolverDnHandle_t h = (cusolverDnHandle_t)b.solver;
   if (h == nullptr) {
     cusolverStatus_t cs = cusolverDnCreate(&h);

@@ -18,6 +18,7 @@
 // and records max |Im| of the rotated entries so a violation is reported, never dropped.
 //
 // The sums over sites j = 1..L are closed-form geometric series of plane waves.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -204,16 +205,124 @@ __global__ void table_check(const double* c0, unsigned* status) {
   if (!(c0[2] <= 1e-9 * c0[3])) atomicOr(status, kStTableImag);
 }
 
+// ---- the same elimination spread over the GPU: one launch per step (used by build_table)
+__global__ void fill_kernel(int L, const int* nlab, const double* theta, cd* A) {
+  const int n4 = 4 * L;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n4 * n4; idx += gridDim.x * blockDim.x) {
+    const int g = idx / n4, h = idx % n4;
+    if (g > h) continue;
+    cd val = mk(0, 0);
+    if (g != h) {
+      Op a = op_of(g, L, nlab, theta), b = op_of(h, L, nlab, theta);
+      val = (a.pos < b.pos) ? contract(a, b, L) : scal(contract(b, a, L), -1.0);
+    }
+    A[(size_t)g * n4 + h] = val;
+    A[(size_t)h * n4 + g] = scal(val, -1.0);
+  }
+}
+
+// step k: pivot inside F (rows k+1 .. 2L-1 of column k), exchange, running Pf, Gauss vector
+__global__ void __launch_bounds__(256) pivot_kernel(int L, int k, cd* A, cd* tau, cd* pf) {
+  const int n4 = 4 * L, n2 = 2 * L, r = k + 1;
+  __shared__ int s_piv;
+  if (threadIdx.x < 32) {
+    double best = -1; int bi = r;
+    for (int i = r + threadIdx.x; i < n2; i += 32) {
+      double v = abs2(A[(size_t)i * n4 + k]);
+      if (v > best) { best = v; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (threadIdx.x == 0) s_piv = bi;
+  }
+  __syncthreads();
+  const int p = s_piv;
+  if (p != r) {
+    for (int j = threadIdx.x; j < n4; j += blockDim.x) {
+      cd t = A[(size_t)r * n4 + j]; A[(size_t)r * n4 + j] = A[(size_t)p * n4 + j]; A[(size_t)p * n4 + j] = t;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+      cd t = A[(size_t)i * n4 + r]; A[(size_t)i * n4 + r] = A[(size_t)i * n4 + p]; A[(size_t)i * n4 + p] = t;
+    }
+    __syncthreads();
+  }
+  const cd a = A[(size_t)k * n4 + r];
+  if (threadIdx.x == 0) {
+    cd v = mul(*pf, a);
+    *pf = (p != r) ? scal(v, -1.0) : v;
+  }
+  const cd ia = inv(a);
+  for (int j = k + 2 + threadIdx.x; j < n4; j += blockDim.x) tau[j] = mul(A[(size_t)k * n4 + j], ia);
+}
+
+// step k: A_ij += A[k+1][i] tau_j - tau_i A[k+1][j] on the trailing upper triangle (mirrored)
+__global__ void update_kernel(int L, int k, cd* A, const cd* tau) {
+  const int n4 = 4 * L, r = k + 1, m = n4 - (k + 2);
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < m * m; idx += gridDim.x * blockDim.x) {
+    const int i = k + 2 + idx / m, j = k + 2 + idx % m;
+    if (i >= j) continue;
+    cd v = add(A[(size_t)i * n4 + j], sub(mul(A[(size_t)r * n4 + i], tau[j]), mul(tau[i], A[(size_t)r * n4 + j])));
+    A[(size_t)i * n4 + j] = v;
+    A[(size_t)j * n4 + i] = scal(v, -1.0);
+  }
+}
+
+// gauge rotation of the Schur complement to the real table, C0 and the realness record
+__global__ void finalize_kernel(int L, const int* nlab, double vac_norm, const cd* A, const cd* pf, double* R,
+                                double* c0, unsigned* status) {
+  const int n4 = 4 * L, n2 = 2 * L;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n2 * n2; idx += gridDim.x * blockDim.x) {
+    int a = idx / n2, b = idx % n2;
+    double val = 0;
+    if (a != b) {
+      cd s = A[(size_t)(n2 + a) * n4 + (n2 + b)];
+      int ia = a < L ? (L - 1 - a) : (L + (a - L)), ib = b < L ? (L - 1 - b) : (L + (b - L));
+      int sa = a < L ? 1 : -1, sb = b < L ? 1 : -1;
+      cd rot = mul(mk(0, 1), expi(M_PI * (double)(sa * nlab[ia] + sb * nlab[ib]) / L));
+      cd v = mul(rot, s);
+      val = v.x;
+      atomic_max_pos(c0 + 2, fabs(v.y));
+      atomic_max_pos(c0 + 3, fabs(v.x));
+    }
+    R[idx] = val;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const cd p = *pf;
+    c0[0] = p.x * vac_norm;
+    c0[1] = p.y * vac_norm;
+    if (!(abs2(p) > 1e-200) || !isfinite(p.x) || !isfinite(p.y)) atomicOr(status, kStTableSingular);
+  }
+}
+
+__global__ void pf_init(cd* pf) { *pf = mk(1, 0); }
+
 }  // namespace
 
 tgba_status build_table(Basis& b, cudaStream_t st) {
-  const int L = b.L;
+  const int L = b.L, n4 = 4 * L;
+  cd* A = (cd*)b.d_work;
+  cd* tau = A + (size_t)n4 * n4;       // the work area holds A, the Gauss vector and Pf(A_FF)
+  cd* pf = tau + n4;
+  int sms = 0;
+  TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
+  auto grid = [&](int64_t work) { return (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, (int64_t)sms * 4)); };
   TGBA_CUDA(cudaMemsetAsync(b.d_c0, 0, 4 * sizeof(double), st));
-  table_kernel<<<1, 1024, 0, st>>>(L, b.d_nlab, b.d_theta, b.vac_norm, (cd*)b.d_work, b.d_table, b.d_c0, b.d_status);
-  TGBA_CUDA(cudaGetLastError());
+  fill_kernel<<<grid((int64_t)n4 * n4), 256, 0, st>>>(L, b.d_nlab, b.d_theta, A);
+  pf_init<<<1, 1, 0, st>>>(pf);
+  for (int k = 0; k < 2 * L; k += 2) {
+    pivot_kernel<<<1, 256, 0, st>>>(L, k, A, tau, pf);
+    const int64_t m = n4 - (k + 2);
+    update_kernel<<<grid(m * m), 256, 0, st>>>(L, k, A, tau);
+  }
+  finalize_kernel<<<grid((int64_t)4 * L * L), 256, 0, st>>>(L, b.d_nlab, b.vac_norm, A, pf, b.d_table, b.d_c0,
+                                                           b.d_status);
   table_check<<<1, 1, 0, st>>>(b.d_c0, b.d_status);
   TGBA_CUDA(cudaGetLastError());
-  b.launches += 2;
+  b.launches += 4 + 2 * L;
   b.table_valid = true;
   return TGBA_OK;
 }

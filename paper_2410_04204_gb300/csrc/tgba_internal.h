@@ -187,7 +187,7 @@ tgba_status dsf(Basis& b, int s, double h_x, double w_min, double w_max, int n_w
 
 // quench.cu
 tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* ecut, int nv, double t_max,
-                   int n_t, double* mx, double* norm, int64_t* chi, cudaStream_t st);
+                   int n_t, int method, double* mx, double* norm, int64_t* chi, cudaStream_t st);
 
 // screen.cu
 struct Screen;

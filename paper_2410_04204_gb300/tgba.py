@@ -71,7 +71,7 @@ def lib():
             "tgba_assemble_heff": (_I32, [_VP, _D, _VP, _D, _VP, _VP]),
             "tgba_eigvals": (_I32, [_VP, _VP, _I32, _VP, _VP]),
             "tgba_dsf": (_I32, [_VP, _I32, _D, _D, _D, _I32, _D, _VP, _VP, _I32, _VP, _VP, _VP]),
-            "tgba_quench": (_I32, [_VP, _I32, _D, _VP, _VP, _I32, _D, _I32, _VP, _VP, _VP, _VP]),
+            "tgba_quench": (_I32, [_VP, _I32, _D, _VP, _VP, _I32, _D, _I32, _I32, _VP, _VP, _VP, _VP]),
             "tgba_screen_create": (_I32, [_I32, _VP, ctypes.c_uint64, _P(_VP)]),
             "tgba_screen_nparams": (_I32, [_VP, _P(_I64)]),
             "tgba_screen_params": (_I32, [_VP, _VP]),
@@ -215,8 +215,8 @@ def tgba_dsf(b, s, h_x, w_min, w_max, n_w, eta, S_out, evals_out=None, n_ev=0, w
                           _ptr(evals_out), int(n_ev), _ptr(weights_out), _ptr(dE_out), _stream(stream)))
 
 
-def tgba_quench(b, s, h_z0, hx_variants, ecut_variants, t_max, n_t, mx_out, norm_out=None, stream=None):
-    """Returns the retained basis size of each variant."""
+def tgba_quench(b, s, h_z0, hx_variants, ecut_variants, t_max, n_t, mx_out, norm_out=None, method=0, stream=None):
+    """Returns the retained basis size of each variant (method: 0 automatic, 1 eigen, 2 Chebyshev)."""
     import torch
     hx = np.ascontiguousarray(np.asarray(hx_variants, np.float64))
     ec = np.ascontiguousarray(np.asarray(ecut_variants, np.float64))
@@ -226,7 +226,7 @@ def tgba_quench(b, s, h_z0, hx_variants, ecut_variants, t_max, n_t, mx_out, norm
     _cuda_tensor(norm_out, torch.float64, len(hx), name="norm_out")
     chi = np.zeros(len(hx), np.int64)
     _check(lib().tgba_quench(b, s, float(h_z0), hx.ctypes.data, ec.ctypes.data, len(hx), float(t_max), int(n_t),
-                             _ptr(mx_out), _ptr(norm_out), chi.ctypes.data, _stream(stream)))
+                             int(method), _ptr(mx_out), _ptr(norm_out), chi.ctypes.data, _stream(stream)))
     return chi
 
 

@@ -103,7 +103,9 @@ def test_dsf_config1(wl):
         tgba.tgba_basis_free(b)
 
 
-def test_quench_small():
+@pytest.mark.parametrize("method", [1, 2])
+def test_quench_small(method):
+    """Both propagators (1: eigendecomposition, 2: Chebyshev expansion) against the oracle."""
     L, h, h0, hx = 12, 1.0, 0.5, 0.1
     for mq, cuts in ((12, [-1.0]), (4, [-1.0, 6.0])):
         b = tgba.tgba_build_basis(L, h, [0], mq)
@@ -112,7 +114,7 @@ def test_quench_small():
             n_t, t_max = 41, 20.0
             mx = torch.empty(len(cuts) * n_t, dtype=torch.float64, device="cuda")
             nrm = torch.empty(len(cuts), dtype=torch.float64, device="cuda")
-            chi = tgba.tgba_quench(b, 0, h0, [hx] * len(cuts), cuts, t_max, n_t, mx, nrm)
+            chi = tgba.tgba_quench(b, 0, h0, [hx] * len(cuts), cuts, t_max, n_t, mx, nrm, method=method)
             mxg = mx.cpu().numpy().reshape(len(cuts), n_t)
             for v, cut in enumerate(cuts):
                 t, mo, c0 = otgba.quench(L, h, h0, hx, mq, None if cut < 0 else cut, t_max, n_t)

@@ -83,6 +83,10 @@ def test_quench_L80():
         assert chi[0] == len(c0)
         assert abs(c2[0] - np.vdot(c0, c0).real) < 1e-12
         assert np.abs(m[0] - mo).max() < 1e-9
+        # the Chebyshev propagator on the same variants agrees with the eigendecomposition
+        mx2 = torch.empty(len(cuts) * n_t, dtype=torch.float64, device="cuda")
+        tgba.tgba_quench(b, 0, h0, [0.1] * len(cuts), cuts, t_max, n_t, mx2, None, method=2)
+        assert np.abs(mx2.cpu().numpy().reshape(len(cuts), n_t) - m).max() < 1e-9
     finally:
         tgba.tgba_basis_free(b)
 
