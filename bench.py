@@ -256,6 +256,23 @@ def screening_leg(b24, tgba, inputs, torch):
     return out
 
 
+def eigen_solver_leg(b, w, evs, tgba, torch):
+    """Outside the timed steps: the native eigen-solver against cuSOLVER's batched one on the
+    same matrices (time of one call each, and the largest eigenvalue difference)."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out, res = {}, {}
+    for name, method in (("cusolver_batched_ms", 2), ("native_ms", 1)):
+        torch.cuda.synchronize()
+        e0.record()
+        tgba.tgba_eigvals(b, list(w.h_x), evs, method=method)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = round(e0.elapsed_time(e1), 2)
+        res[method] = evs.clone()
+    out["max_abs_diff"] = (res[1] - res[2]).abs().max().item()
+    return out
+
+
 # ------------------------------------------------------------------ the GPU path
 def run_gb300(args):
     import torch
@@ -294,7 +311,7 @@ def run_gb300(args):
         step()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    step_ms, pf_ms, tab_ms = [], [], []
+    step_ms, pf_ms, tab_ms, tri_ms, bis_ms = [], [], [], [], []
     launches0 = tgba.tgba_profile(b)["kernel_launches"]
     clocks = Clocks(local_rank)
     if dist:
@@ -309,6 +326,8 @@ def run_gb300(args):
         prof = tgba.tgba_profile(b)
         pf_ms.append(prof["pfaffian_ms"])
         tab_ms.append(prof["table_ms"])
+        tri_ms.append(prof["tridiag_ms"])
+        bis_ms.append(prof["bisect_ms"])
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -317,8 +336,26 @@ def run_gb300(args):
     step_ms = [a.elapsed_time(c) for a, c in ev]
     ms, value = aggregate(statistics.mean(step_ms), n_el, world, dist, "cuda")
     prof = tgba.tgba_profile(b)
-    pf_mean = statistics.mean(pf_ms)
-    achieved = prof["pfaffian_flops"] / (pf_mean * 1e-3) / 1e9
+    pf_mean, tab_mean = statistics.mean(pf_ms), statistics.mean(tab_ms)
+    tri_mean, bis_mean = statistics.mean(tri_ms), statistics.mean(bis_ms)
+    pf_gflops = prof["pfaffian_flops"] / (pf_mean * 1e-3) / 1e9
+    peak_src = "live FP64 DFMA-chain kernel (tgba_fp64_peak); MEASURED_PEAKS.json has no FP64 entry"
+    pf_roof = {"bound": "alu", "kernel": "pf_reg_queue / pf_tiles (FP64 Parlett-Reid Pfaffians)",
+               "achieved": pf_gflops, "peak": peak_gflops, "unit": "GFLOP/s", "frac": pf_gflops / peak_gflops,
+               "traffic": None, "peak_source": peak_src, "flops_per_launch": prof["pfaffian_flops"],
+               "ms": pf_mean, "launches_per_stage": prof["pfaffian_launches"],
+               "autotune": {"mode": prof["tune_mode"], "threads": prof["tune_threads"],
+                            "candidates_ms": [round(x, 3) for x in prof["tune_ms"]]}}
+    if tri_mean > pf_mean:
+        # the dominant kernel of the step: the cluster tridiagonalisation of the native solver
+        tri_gflops = prof["tridiag_flops"] / (tri_mean * 1e-3) / 1e9
+        roofline = {"bound": "alu", "kernel": "sytrd_cluster (FP64 Householder tridiagonalisation)",
+                    "achieved": tri_gflops, "peak": peak_gflops, "unit": "GFLOP/s",
+                    "frac": tri_gflops / peak_gflops, "traffic": None, "peak_source": peak_src,
+                    "flops_per_launch": prof["tridiag_flops"], "ms": tri_mean,
+                    "matrices": prof["eig_matrices"], "ctas_per_matrix": prof["eig_cluster"]}
+    else:
+        roofline = pf_roof
 
     # end to end through the public API with host buffers: host enumeration and upload of the
     # state tables, the step, and the eigenvalues read back to pinned host memory
@@ -344,22 +381,16 @@ def run_gb300(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(workload_config(w, n_el, n_states),
                            l2="256 MiB buffer written between steps, outside the step events"),
-            "roofline": {"bound": "alu", "kernel": "pf_tiles (FP64 Parlett-Reid Pfaffians)",
-                         "achieved": achieved, "peak": peak_gflops, "unit": "GFLOP/s",
-                         "frac": achieved / peak_gflops, "traffic": None,
-                         "peak_source": "live FP64 DFMA-chain kernel (tgba_fp64_peak); MEASURED_PEAKS.json has no FP64 entry",
-                         "flops_per_launch": prof["pfaffian_flops"], "pfaffian_ms": pf_mean,
-                         "launches_per_stage": prof["pfaffian_launches"],
-                         "autotune": {"mode": prof["tune_mode"], "threads": prof["tune_threads"],
-                                      "candidates_ms": [round(x, 3) for x in prof["tune_ms"]]}},
-            "stages_ms": {"table": statistics.mean(tab_ms), "pfaffian": pf_mean,
-                          "heff_and_eigvals": ms - statistics.mean(tab_ms) - pf_mean},
-            "pfaffian_stage": {"elements_per_s": n_el / (pf_mean * 1e-3),
-                               "elements_per_s_with_table": n_el / ((pf_mean + statistics.mean(tab_ms)) * 1e-3)},
+            "roofline": roofline,
+            "stages_ms": {"table": tab_mean, "pfaffian": pf_mean, "tridiag": tri_mean, "bisect": bis_mean,
+                          "heff_fill_and_other": ms - tab_mean - pf_mean - tri_mean - bis_mean},
+            "pfaffian_stage": dict(pf_roof, elements_per_s=n_el / (pf_mean * 1e-3),
+                                   elements_per_s_with_table=n_el / ((pf_mean + tab_mean) * 1e-3)),
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": n_states * 8 * len(w.h_x)},
             "gpu_launches": launches}
+    line["eigen_solver"] = eigen_solver_leg(b, w, evs, tgba, torch)
     if not args.no_screening:
         line["screening"] = screening_leg(b, tgba, inputs, torch)
     tgba.tgba_basis_free(b)

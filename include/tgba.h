@@ -130,10 +130,17 @@ tgba_status tgba_assemble_heff(tgba_basis b, double h_x, tgba_screen screen, dou
  * [n_hx][n_states] (n_states = sum over sectors of n_ns + n_r); field i, sector s starts at
  * i * n_states + (sum of the sizes of sectors before s).  The sector matrices are real
  * symmetric after a diagonal change of phase of the basis states, so every (field, sector)
- * matrix goes into one batched FP64 real symmetric solve (cuSOLVER XsyevBatched), each padded
- * to the largest sector size with decoupled diagonal entries above its Gershgorin bound.
- * Blocks on `stream`. */
+ * matrix goes into one batched FP64 real symmetric solve.  method (tgba_eigvals_ex):
+ *   0  automatic: 1 when every sector has at most 6400 states (rounded up to a multiple of
+ *      32), else 2;
+ *   1  native: Householder tridiagonalisation, one thread-block cluster per matrix, then
+ *      bisection on Sturm counts (TGBA_EINVAL if a sector is too large);
+ *   2  cuSOLVER XsyevBatched, each matrix padded to the largest sector size with decoupled
+ *      diagonal entries above its Gershgorin bound.
+ * A non-finite matrix entry gives TGBA_ENUMERIC.  tgba_eigvals is method 0.  Blocks on `stream`. */
 tgba_status tgba_eigvals(tgba_basis b, const double* h_x, int32_t n_hx, double* evals_dev, void* stream);
+tgba_status tgba_eigvals_ex(tgba_basis b, const double* h_x, int32_t n_hx, int32_t method, double* evals_dev,
+                            void* stream);
 
 /* ---------------------------------------------------------------- S(k=0, w) (Eq. 8-9)
  * Dynamic structure factor of sector index s (which must be the k = 0 sector, m = 0):
@@ -223,12 +230,20 @@ tgba_status tgba_table_noalloc(int32_t L, double J, double h_z, double* table_de
  * shape the autotuner chose for the register-resident sizes (0: one launch per size, 1: one
  * persistent queue launch, 3: the queue with a register cap for occupancy; threads per block),
  * tune_ms: its measured stage time (ms) for each candidate in the order {0,64}, {0,128},
- * {0,256}, {1,64}, {1,128}, {1,256}, {3,128} (0 where not measured). */
+ * {0,256}, {1,64}, {1,128}, {1,256}, {3,128} (0 where not measured).
+ * tridiag_ms / bisect_ms: device time of the tridiagonalisation and of the bisection kernel of
+ * the last native tgba_eigvals (0 if none ran); tridiag_flops: its algorithmic FP64 flops,
+ * sum over matrices of sum_{m=1}^{n-1} 4 m (m + 1) (two FMAs of the rank-2 update and two of
+ * the symmetric product per element of the trailing lower triangle, ~4n^3/3); eig_matrices:
+ * matrices in that batch; eig_cluster: CTAs per matrix. */
 typedef struct {
   double table_ms, pfaffian_ms, pfaffian_flops;
   int64_t pfaffian_launches, kernel_launches, upload_bytes, evaluated;
   int32_t tune_mode, tune_threads;
   double tune_ms[8];
+  double tridiag_ms, bisect_ms, tridiag_flops;
+  int64_t eig_matrices;
+  int32_t eig_cluster, pad_;
 } tgba_prof;
 tgba_status tgba_profile(tgba_basis b, tgba_prof* out);
 

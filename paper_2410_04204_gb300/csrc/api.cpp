@@ -34,6 +34,7 @@ tgba_status check_status(Basis& b, cudaStream_t st) {
   TGBA_CUDA(cudaStreamSynchronize(st));
   if (w & kStTimeout) return fail(TGBA_ETIMEOUT, "a bounded device wait gave up");
   if (w & kStBadIndex) return fail(TGBA_EINVAL, "a pair index was outside the sector");
+  if (w & kStEigen) return fail(TGBA_ENUMERIC, "the eigen-solver met a non-finite matrix entry");
   if (w & kStTableSingular) return fail(TGBA_ENUMERIC, "the vacuum block of the contraction matrix is singular");
   if (w & kStTableImag) return fail(TGBA_ENUMERIC, "the gauge-rotated contraction table is not real");
   return fail(TGBA_ENUMERIC, "a Pfaffian produced NaN or Inf");
@@ -59,8 +60,10 @@ static void release(Basis* b) {
                   b->d_reg_rects, b->d_counter};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  for (int e = 0; e < 3; ++e)
+  for (int e = 0; e < 3; ++e) {
     if (b->ev[e]) cudaEventDestroy(b->ev[e]);
+    if (b->eig_ev[e]) cudaEventDestroy(b->eig_ev[e]);
+  }
   for (RectList& L : b->rect_lists)
     if (L.d_rects) cudaFree(L.d_rects);
   if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
@@ -394,15 +397,21 @@ tgba_status tgba_assemble_heff(tgba_basis h, double h_x, tgba_screen screen, dou
 }
 
 tgba_status tgba_eigvals(tgba_basis h, const double* h_x, int32_t n_hx, double* evals_dev, void* stream) {
+  return tgba_eigvals_ex(h, h_x, n_hx, 0, evals_dev, stream);
+}
+
+tgba_status tgba_eigvals_ex(tgba_basis h, const double* h_x, int32_t n_hx, int32_t method, double* evals_dev,
+                            void* stream) {
   Basis* b = (Basis*)h;
   BASIS_OK(b);
+  if (method < 0 || method > 2) return fail(TGBA_EINVAL, "method must be 0 (automatic), 1 (native) or 2 (cuSOLVER)");
   if (!h_x || n_hx < 1) return fail(TGBA_EINVAL, "need at least one h_x");
   for (int i = 0; i < n_hx; ++i)
     if (!std::isfinite(h_x[i])) return fail(TGBA_EINVAL, "h_x must be finite");
   if (!b->x_valid) return fail(TGBA_EINVAL, "no X computed yet: call tgba_compute_x");
   if (!evals_dev && b->n_states > 0) return fail(TGBA_EINVAL, "null output");
   cudaStream_t st = (cudaStream_t)stream;
-  tgba_status r = eig_all_sectors(*b, h_x, n_hx, evals_dev, st);
+  tgba_status r = eig_all_sectors(*b, h_x, n_hx, evals_dev, method, st);
   if (r != TGBA_OK) return r;
   return check_status(*b, st);
 }
@@ -516,6 +525,17 @@ tgba_status tgba_profile(tgba_basis h, tgba_prof* out) {
   out->tune_mode = b->tuned ? b->tune_mode : -1;
   out->tune_threads = b->tune_threads;
   for (size_t i = 0; i < b->tune_log.size() && i < 8; ++i) out->tune_ms[i] = b->tune_log[i].ms;
+  if (b->eig_ev_recorded) {
+    float t0 = 0, t1 = 0;
+    TGBA_CUDA(cudaEventSynchronize(b->eig_ev[2]));
+    TGBA_CUDA(cudaEventElapsedTime(&t0, b->eig_ev[0], b->eig_ev[1]));
+    TGBA_CUDA(cudaEventElapsedTime(&t1, b->eig_ev[1], b->eig_ev[2]));
+    out->tridiag_ms = t0;
+    out->bisect_ms = t1;
+  }
+  out->tridiag_flops = b->tridiag_flops;
+  out->eig_matrices = b->eig_matrices;
+  out->eig_cluster = b->eig_cluster;
   return TGBA_OK;
 }
 

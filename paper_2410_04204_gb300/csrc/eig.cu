@@ -1,5 +1,7 @@
 // Dense FP64 eigen-solver of the real-gauge H_eff (row a7; Eq. 1: diagonalising the truncated
-// Hamiltonian gives E_a and M).  Library call: cuSOLVER's 64-bit syevd.
+// Hamiltonian gives E_a and M), library path: cuSOLVER's 64-bit syevd with eigenvectors (DSF,
+// quench) and its batched XsyevBatched for eigenvalues of sectors too large for the native
+// solver in tridiag.cu.
 #include <cusolverDn.h>
 
 #include <algorithm>
@@ -127,7 +129,19 @@ __global__ void pad_kernel(const int64_t* __restrict__ nq, int64_t n_max, const 
 
 }  // namespace
 
-tgba_status eig_all_sectors(Basis& b, const double* hx, int n_hx, double* evals, cudaStream_t st) {
+static tgba_status eig_all_sectors_lib(Basis& b, const double* hx, int n_hx, double* evals, cudaStream_t st);
+
+tgba_status eig_all_sectors(Basis& b, const double* hx, int n_hx, double* evals, int method, cudaStream_t st) {
+  int64_t n_max = 0;
+  for (const Sector& s : b.sectors) n_max = std::max(n_max, s.n_ns + s.n_r);
+  const bool fits = (n_max + 31) / 32 * 32 <= kMaxNativeLd;
+  if (method == 1 && !fits)
+    return fail(TGBA_EINVAL, "the native eigen-solver takes sectors of at most " + std::to_string(kMaxNativeLd) + " states");
+  if (method == 1 || (method == 0 && fits)) return eig_all_sectors_native(b, hx, n_hx, evals, st);
+  return eig_all_sectors_lib(b, hx, n_hx, evals, st);
+}
+
+static tgba_status eig_all_sectors_lib(Basis& b, const double* hx, int n_hx, double* evals, cudaStream_t st) {
   int64_t n_max = 0;
   std::vector<std::pair<int, int>> slots;     // (h index, sector)
   for (int h = 0; h < n_hx; ++h)

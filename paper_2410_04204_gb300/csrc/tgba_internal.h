@@ -18,7 +18,12 @@ constexpr int kMaxN = 2 * kMaxQp; // largest Pfaffian M_a + M_b
 constexpr int kNumClasses = 12;   // Pfaffian size classes (basis.cpp: tile_class)
 
 // Device status word bits (tgba_status is derived from them at the next sync).
-enum : unsigned { kStNan = 1u, kStTableImag = 2u, kStTableSingular = 4u, kStTimeout = 8u, kStBadIndex = 16u };
+enum : unsigned { kStNan = 1u, kStTableImag = 2u, kStTableSingular = 4u, kStTimeout = 8u, kStBadIndex = 16u,
+                  kStEigen = 32u };
+
+// Largest matrix (leading dimension, a multiple of 32) the native eigenvalue solver takes: its
+// four length-ld vectors must fit in one CTA's shared memory.
+constexpr int kMaxNativeLd = 6400;
 
 // A contiguous run of states with the same quasiparticle number.
 struct Group { int M; int64_t begin, end; };
@@ -140,6 +145,12 @@ struct Basis {
   // measurement
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   bool ev_recorded = false;
+  // native eigen-solver: events around its two kernels, work of the last batch
+  cudaEvent_t eig_ev[3] = {nullptr, nullptr, nullptr};
+  bool eig_ev_recorded = false;
+  double tridiag_flops = 0;
+  int64_t eig_matrices = 0;
+  int eig_cluster = 0;
   std::atomic<int64_t> launches{0};
   int64_t upload_bytes = 0, pf_launches = 0;
   double pf_flops = 0;
@@ -178,8 +189,11 @@ void destroy_blas(void* h);
 // eig.cu
 tgba_status eig_sym(Basis& b, int64_t n, double* a, double* w, bool vectors, cudaStream_t st);
 // eigenvalues of every sector's real-gauge H_eff at each of n_hx fields, one batched solve;
-// field h, sector s written at evals + h * n_states + ev_off
-tgba_status eig_all_sectors(Basis& b, const double* hx, int n_hx, double* evals, cudaStream_t st);
+// field h, sector s written at evals + h * n_states + ev_off.  method: 0 = native when every
+// sector fits (n <= kMaxNativeLd), else the library; 1 = native; 2 = cuSOLVER XsyevBatched
+tgba_status eig_all_sectors(Basis& b, const double* hx, int n_hx, double* evals, int method, cudaStream_t st);
+// tridiag.cu: Householder tridiagonalisation by thread-block clusters + Sturm bisection
+tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double* evals, cudaStream_t st);
 
 // dsf.cu
 tgba_status dsf(Basis& b, int s, double h_x, double w_min, double w_max, int n_w, double eta, float* S,

@@ -1,0 +1,511 @@
+// Batched FP64 eigenvalues of the real-gauge H_eff (row a7: Eq. 1, diagonalising the truncated
+// Hamiltonian gives the spectrum E_a of every momentum sector) without a library eigen-solver.
+//
+// Two kernels per batch of (field, sector) matrices:
+//
+// 1. sytrd_cluster: Householder reduction to tridiagonal form, T = Q^T H Q.  A thread-block
+//    cluster of C CTAs (one per SM) owns one matrix and runs all n - 1 reflections in one
+//    launch.  Step j builds the reflector v_j from column j, then makes ONE pass over the
+//    trailing lower triangle that both applies the rank-2 update of step j - 1,
+//        A <- A - v_{j-1} w_{j-1}^T - w_{j-1} v_{j-1}^T,
+//    and accumulates the symmetric product y = A v_j for step j; so every trailing element is
+//    read and written once per step with four FMAs.  The trailing lower triangle is cut into
+//    blocks of 32 rows x 16 columns, numbered column group by column group, and warp w of the
+//    cluster's W warps takes the contiguous blocks [NB w / W, NB (w + 1) / W): equal work for
+//    every warp, whatever the size of the trailing block.  In a block a lane owns one row: its
+//    row sum needs no communication, and its 16 column partial sums stay in registers over the
+//    warp's run of blocks in one column group, then one transpose-reduce (31 adds per lane)
+//    sums them over the warp.  Two block buffers in registers keep the next block's loads in
+//    flight during the current block's arithmetic.  Partials go to global buffers and are
+//    added in a fixed order, so results do not depend on scheduling.  The CTAs of a cluster
+//    meet at two hardware cluster barriers per step (no spin-waits).
+// 2. sturm_bisect: every eigenvalue by bisection on the Sturm count of T - x, one thread per
+//    eigenvalue, with the scaled three-term determinant recurrence (three FP64 operations per
+//    row and no divisions; sign changes counted on the integer bits).
+//
+// FP64 throughput on this GPU is 1/64 of FP32, so the design counts FP64 instructions: the
+// reduction is 4 FMAs per trailing element per step (4n^3/3 flops per matrix); selects, masks,
+// sign tests and rescalings are integer operations, and no double value is selected.
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "tgba_internal.h"
+
+namespace tgba {
+namespace {
+
+constexpr int kWarps = 12;                      // 3 per SM sub-partition
+constexpr int kThreads = kWarps * 32;
+constexpr int kCols = 16;                       // columns of a work block (rows: 32)
+constexpr int kMaxCluster = 8;
+constexpr int kRed = 64;                        // reduction scratch (doubles) after the vectors
+constexpr int kMaxWarpsPerCluster = kWarps * kMaxCluster;
+constexpr int kMaxGroups = kMaxNativeLd / kCols;
+constexpr int kSturmThreads = 128;
+
+struct TriSlot {
+  int64_t a_off;    // matrix, ld x ld column-major, zero beyond n (both triangles, lower one used)
+  int64_t rp_off;   // row sums of the 32 x 16 blocks [ld / 16][ld]
+  int64_t cp_off;   // column sums of each warp's blocks [warps of a cluster][ld]
+  int64_t p_off;    // p = tau A v [ld], then one dot partial per CTA of the cluster [8]
+  int64_t de_off;   // diagonal d [n], off-diagonal e [n]
+  int64_t out_off;  // first eigenvalue in the caller's output
+  int32_t n, ld;
+};
+
+__device__ __forceinline__ double isel(bool s, double y, double x) {   // s ? y : x, integer halves
+  const int lo = s ? __double2loint(y) : __double2loint(x);
+  const int hi = s ? __double2hiint(y) : __double2hiint(x);
+  return __hiloint2double(hi, lo);
+}
+
+__device__ __forceinline__ void cluster_barrier(int C) {
+  if (C == 1) {
+    __syncthreads();
+  } else {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+  }
+}
+
+// Sum over the block in a fixed order (lane 0 of each warp, then warps in order); every thread
+// gets the same value.
+__device__ __forceinline__ double block_sum(double x, double* red) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = x;
+  __syncthreads();
+  double s = red[0];
+#pragma unroll
+  for (int w = 1; w < kWarps; ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+// Work of one step.  Column group g holds columns 16 g .. 16 g + 15; its blocks are the 32-row
+// blocks rb = g / 2 .. LB - 1 (rows 32 rb .. 32 rb + 31, LB = ld / 32), the first on the
+// diagonal.  Groups g0 .. G - 1 are numbered one after another.
+__device__ __forceinline__ int half_sum(int x) {   // sum over g < x of floor(g / 2)
+  const int p = x >> 1;
+  return (x & 1) ? p * p : p * (p - 1);
+}
+// linear index of the first block of group g0 + q
+__device__ __forceinline__ int group_first(int q, int g0, int LB) { return q * LB - (half_sum(g0 + q) - half_sum(g0)); }
+// the warp whose range holds block b: the last w with s[w] <= b (s non-decreasing, s[0] = 0)
+__device__ __forceinline__ int warp_of(const int* __restrict__ s, int W, int b) {
+  int lo = 0, hi = W;                    // s[lo] <= b < s[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (s[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void load_block(double (&a)[kCols], const double* __restrict__ p, int ld) {
+#pragma unroll
+  for (int kk = 0; kk < kCols; ++kk) a[kk] = __ldcg(p + (int64_t)kk * ld);
+}
+
+// One 32 x 16 block held in a[]: row i = 32 rb + lane, columns k0 .. k0 + 15 (p points at
+// row i of column k0).  The rank-2 update of the previous step is applied and stored, the
+// row sum of A_j v_j over the block's columns goes to rp[i], the column sums over its rows
+// accumulate in cs.  DIAG (the group's first block): elements with row < column add nothing
+// and the diagonal element adds only to its row.  Columns left of the trailing block, rows
+// above it and padding rows/columns are processed too: there v_{j-1} and w_{j-1} vanish (the
+// update leaves the value unchanged, except in column j, which is no longer read), v_j
+// vanishes (no row-sum contribution), and the column sums they produce are never read.
+template <bool DIAG>
+__device__ __forceinline__ void sytrd_block(const double (&a)[kCols], double* __restrict__ p, int ld, int i, int k0,
+                                            const double* __restrict__ vp, const double* __restrict__ wp,
+                                            const double* __restrict__ vn, double (&cs)[kCols],
+                                            double* __restrict__ rp) {
+  const double vpi = vp[i], wpi = wp[i], vni = vn[i];
+  double r = 0.0;
+#pragma unroll
+  for (int kk = 0; kk < kCols; ++kk) {
+    const int k = k0 + kk;
+    double x = fma(-vpi, wp[k], a[kk]);
+    x = fma(-wpi, vp[k], x);
+    __stcg(p + (int64_t)kk * ld, x);
+    if (DIAG) {
+      r = fma(x, isel(i >= k, vn[k], 0.0), r);
+      cs[kk] = fma(x, isel(i > k, vni, 0.0), cs[kk]);
+    } else {
+      r = fma(x, vn[k], r);
+      cs[kk] = fma(x, vni, cs[kk]);
+    }
+  }
+  __stcg(rp + i, r);
+}
+
+// Lanes l and l + 16 end with the sum over all 32 lanes of cs[l & 15]: the two half-warps are
+// added first, then a transpose-reduce over 16 lanes (at level s, lanes with bit s set keep
+// the upper half of the values).  31 adds per lane.
+__device__ __forceinline__ double transpose_reduce16(double (&cs)[kCols], int lane) {
+#pragma unroll
+  for (int m = 0; m < kCols; ++m) cs[m] += __shfl_xor_sync(0xffffffffu, cs[m], 16);
+#pragma unroll
+  for (int s = 8; s >= 1; s >>= 1) {
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int m = 0; m < s; ++m) {
+      const double send = isel(up, cs[m], cs[m + s]);
+      const double keep = isel(up, cs[m + s], cs[m]);
+      cs[m] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  return cs[0];
+}
+
+// Row blocks [rb_b, rb_e) of column group g.  Two block buffers in registers: the loads of the
+// next block are in flight while the current one is computed.  Then the warp's column sums of
+// the group go to CP[w].
+__device__ __forceinline__ void sytrd_chunk(double* __restrict__ A, int ld, int g, int rb_b, int rb_e, int lane,
+                                            int w, const double* __restrict__ vp, const double* __restrict__ wp,
+                                            const double* __restrict__ vn, double* __restrict__ RP,
+                                            double* __restrict__ CP) {
+  const int k0 = kCols * g;
+  double* colp = A + (int64_t)k0 * ld + lane;      // + 32 rb: the lane's row of block rb
+  double* rp = RP + (int64_t)g * ld;
+  double cs[kCols], cur[kCols], nxt[kCols];
+#pragma unroll
+  for (int kk = 0; kk < kCols; ++kk) cs[kk] = 0.0;
+  int rb = rb_b;
+  load_block(cur, colp + 32 * rb, ld);
+  if (rb == (g >> 1)) {                            // the diagonal block comes first
+    load_block(nxt, colp + 32 * min(rb + 1, rb_e - 1), ld);
+    sytrd_block<true>(cur, colp + 32 * rb, ld, 32 * rb + lane, k0, vp, wp, vn, cs, rp);
+    ++rb;
+#pragma unroll
+    for (int kk = 0; kk < kCols; ++kk) cur[kk] = nxt[kk];
+  }
+  for (; rb + 1 < rb_e; rb += 2) {
+    load_block(nxt, colp + 32 * (rb + 1), ld);
+    sytrd_block<false>(cur, colp + 32 * rb, ld, 32 * rb + lane, k0, vp, wp, vn, cs, rp);
+    load_block(cur, colp + 32 * min(rb + 2, rb_e - 1), ld);
+    sytrd_block<false>(nxt, colp + 32 * (rb + 1), ld, 32 * (rb + 1) + lane, k0, vp, wp, vn, cs, rp);
+  }
+  if (rb < rb_e) sytrd_block<false>(cur, colp + 32 * rb, ld, 32 * rb + lane, k0, vp, wp, vn, cs, rp);
+  const double colsum = transpose_reduce16(cs, lane);
+  if (lane < kCols) __stcg(CP + (int64_t)w * ld + k0 + lane, colsum);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+sytrd_cluster(const TriSlot* __restrict__ slots, int C, double* __restrict__ ws, unsigned* __restrict__ status) {
+  extern __shared__ double sm[];
+  const int q = blockIdx.x / C, rank = blockIdx.x - q * C;
+  const TriSlot S = slots[q];
+  const int n = S.n, ld = S.ld, LB = ld >> 5, G = ld / kCols;
+  double* A = ws + S.a_off;
+  double* RP = ws + S.rp_off;
+  double* CP = ws + S.cp_off;
+  double* P = ws + S.p_off;
+  double* dots = P + ld;
+  double* D = ws + S.de_off;
+  double* E = D + n;
+  double* vp = sm;
+  double* wp = sm + ld;
+  double* vn = sm + 2 * ld;
+  double* wn = sm + 3 * ld;
+  double* red = sm + 4 * ld;
+  int* sw = (int*)(red + kRed);                   // [W + 1] first block of each warp
+  int* gw = sw + kMaxWarpsPerCluster + 1;         // [2 G] first and last warp meeting each group
+  for (int i = threadIdx.x; i < 4 * ld; i += kThreads) sm[i] = 0.0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int W = kWarps * C, wid = warp * C + rank;
+  bool bad = false;
+  for (int j = 0; j < n; ++j) {
+    // column j of A_j: the stored column (already updated through step j - 2) minus the
+    // rank-2 update of step j - 1; rows j + 2 .. n - 1 go into the norm
+    const double vpj = vp[j], wpj = wp[j];
+    double sig = 0.0;
+    for (int i = j + threadIdx.x; i < n; i += kThreads) {
+      double a = __ldcg(A + (int64_t)j * ld + i);
+      a = fma(-vp[i], wpj, a);
+      a = fma(-wp[i], vpj, a);
+      if (i == j) red[kWarps] = a;
+      else if (i == j + 1) red[kWarps + 1] = a;
+      else sig = fma(a, a, sig);
+      vn[i] = a;
+    }
+    // the step's work split (integer only), published by block_sum's barrier
+    const int g0 = (j + 1) / kCols, NG = G - g0;
+    const int NB = group_first(NG, g0, LB);
+    for (int w = threadIdx.x; w <= W; w += kThreads) sw[w] = (int)((int64_t)NB * w / W);
+    sig = block_sum(sig, red);
+    for (int t = threadIdx.x; t < NG; t += kThreads) {
+      gw[2 * t] = warp_of(sw, W, group_first(t, g0, LB));
+      gw[2 * t + 1] = warp_of(sw, W, group_first(t + 1, g0, LB) - 1);
+    }
+    const double dj = red[kWarps];
+    if (rank == 0 && threadIdx.x == 0) D[j] = dj;
+    if (j + 1 >= n) break;                            // uniform: the last diagonal entry
+    const double alpha = red[kWarps + 1];
+    // Householder reflector H = I - tau v v^T with v_{j+1} = 1 mapping column j to beta e_{j+1}
+    double tau = 0.0, beta = alpha, s = 0.0;
+    if (sig != 0.0) {
+      const double nrm = sqrt(fma(alpha, alpha, sig));
+      beta = alpha >= 0.0 ? -nrm : nrm;
+      tau = (beta - alpha) / beta;
+      s = 1.0 / (alpha - beta);
+    }
+    if (rank == 0 && threadIdx.x == 0) E[j] = beta;
+    if (threadIdx.x == 0 && !(isfinite(dj) && isfinite(beta))) bad = true;
+    for (int i = threadIdx.x; i < ld; i += kThreads) {
+      const double x = vn[i];
+      vn[i] = i == j + 1 ? 1.0 : (i > j + 1 && i < n ? x * s : 0.0);
+    }
+    __syncthreads();
+    // one pass over the trailing lower triangle: update of step j - 1 and y = A_j v_j
+    {
+      int sb = sw[wid];
+      const int se = sw[wid + 1];
+      if (sb < se) {
+        int lo = 0, hi = NG;                          // group_first(lo) <= sb < group_first(hi)
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (group_first(mid, g0, LB) <= sb) lo = mid;
+          else hi = mid;
+        }
+        int gq = lo, b = sb - group_first(gq, g0, LB);
+        while (sb < se) {
+          const int g = g0 + gq, nbg = LB - (g >> 1);
+          const int b1 = min(nbg, b + (se - sb));
+          sytrd_chunk(A, ld, g, (g >> 1) + b, (g >> 1) + b1, lane, wid, vp, wp, vn, RP, CP);
+          sb += b1 - b;
+          ++gq;
+          b = 0;
+        }
+      }
+    }
+    cluster_barrier(C);
+    // rows j + 1 .. n - 1, a slice per CTA: y_i = row sums of the blocks of groups g0 .. i/16
+    // + the column sums of the warps whose ranges met column i's group; p = tau y
+    double dot = 0.0;
+    {
+      const int m = n - (j + 1);
+      const int lo = j + 1 + (int)((int64_t)m * rank / C), hi = j + 1 + (int)((int64_t)m * (rank + 1) / C);
+      for (int i = lo + threadIdx.x; i < hi; i += kThreads) {
+        const int gi = i / kCols;
+        double y = 0.0;
+        for (int g = g0; g <= gi; ++g) y += __ldcg(RP + (int64_t)g * ld + i);
+        const int t = gi - g0;
+        for (int w = gw[2 * t]; w <= gw[2 * t + 1]; ++w)
+          if (sw[w] < sw[w + 1]) y += __ldcg(CP + (int64_t)w * ld + i);
+        const double p = tau * y;
+        __stcg(P + i, p);
+        dot = fma(p, vn[i], dot);
+      }
+    }
+    dot = block_sum(dot, red);
+    if (threadIdx.x == 0) __stcg(dots + rank, dot);
+    cluster_barrier(C);
+    double pv = 0.0;
+    for (int r = 0; r < C; ++r) pv += __ldcg(dots + r);
+    const double Kc = 0.5 * tau * pv;
+    for (int i = threadIdx.x; i < ld; i += kThreads)
+      wn[i] = (i > j && i < n) ? fma(-Kc, vn[i], __ldcg(P + i)) : 0.0;
+    __syncthreads();
+    double* t = vp; vp = vn; vn = t;
+    t = wp; wp = wn; wn = t;
+  }
+  if (bad) atomicOr(status, kStEigen);
+}
+
+// Number of eigenvalues of T below x: sign changes of P_0 = 1, P_1, ..., P_n with
+// P_{i+1} = (d_i - x) P_i - e_{i-1}^2 P_{i-1}.  A zero P_i is replaced by a tiny value of the
+// sign opposite to P_{i-1} (the analogue of a negative pivot floor in the ratio form).  Every
+// 8 rows both terms are rescaled by the power of two that brings the larger to [1, 2).
+__device__ __forceinline__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e2, int n,
+                                           double x) {
+  double pm = 1.0, pc = d[0] - x;
+  if (((unsigned long long)__double_as_longlong(pc) << 1) == 0ull) pc = -0x1p-60;
+  int cnt = (int)((unsigned)__double2hiint(pc) >> 31);
+  int i = 1;
+  for (; i + 8 <= n; i += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      double pn = fma(d[i + u] - x, pc, -e2[i + u - 1] * pm);
+      if (((unsigned long long)__double_as_longlong(pn) << 1) == 0ull) pn = pc * -0x1p-60;
+      cnt += (int)((unsigned)(__double2hiint(pn) ^ __double2hiint(pc)) >> 31);
+      pm = pc;
+      pc = pn;
+    }
+    const int em = max((__double2hiint(pm) >> 20) & 0x7ff, (__double2hiint(pc) >> 20) & 0x7ff);
+    const double sc = __hiloint2double(min(2046, max(1, 2046 - em)) << 20, 0);
+    pm *= sc;
+    pc *= sc;
+  }
+  for (; i < n; ++i) {
+    double pn = fma(d[i] - x, pc, -e2[i - 1] * pm);
+    if (((unsigned long long)__double_as_longlong(pn) << 1) == 0ull) pn = pc * -0x1p-60;
+    cnt += (int)((unsigned)(__double2hiint(pn) ^ __double2hiint(pc)) >> 31);
+    pm = pc;
+    pc = pn;
+  }
+  return cnt;
+}
+
+__global__ void __launch_bounds__(kSturmThreads)
+sturm_bisect(const TriSlot* __restrict__ slots, const double* __restrict__ ws, double* __restrict__ evals,
+             unsigned* __restrict__ status) {
+  extern __shared__ double sm[];
+  __shared__ double red[2 * (kSturmThreads / 32)];
+  const TriSlot S = slots[blockIdx.y];
+  const int n = S.n;
+  if ((int)blockIdx.x * kSturmThreads >= n) return;     // block-uniform
+  const double* D = ws + S.de_off;
+  const double* E = D + n;
+  double* d = sm;
+  double* e2 = sm + n;
+  double lo = 1e300, hi = -1e300;
+  for (int i = threadIdx.x; i < n; i += kSturmThreads) {
+    const double di = D[i];
+    const double el = i > 0 ? fabs(E[i - 1]) : 0.0, er = i + 1 < n ? fabs(E[i]) : 0.0;
+    d[i] = di;
+    e2[i] = i + 1 < n ? E[i] * E[i] : 0.0;
+    lo = fmin(lo, di - el - er);
+    hi = fmax(hi, di + el + er);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { red[warp] = lo; red[kSturmThreads / 32 + warp] = hi; }
+  __syncthreads();
+  lo = red[0];
+  hi = red[kSturmThreads / 32];
+  for (int w = 1; w < kSturmThreads / 32; ++w) { lo = fmin(lo, red[w]); hi = fmax(hi, red[kSturmThreads / 32 + w]); }
+  const int k = blockIdx.x * kSturmThreads + threadIdx.x;
+  if (k >= n) return;
+  if (!(isfinite(lo) && isfinite(hi))) {
+    if (threadIdx.x == 0) atomicOr(status, kStEigen);
+    evals[S.out_off + k] = __longlong_as_double(0x7ff8000000000000ll);
+    return;
+  }
+  const double tnorm = fmax(fabs(lo), fabs(hi));
+  const double eps = 0x1p-53;
+  const double fudge = 4.0 * eps * n * tnorm + 0x1p-1000;   // widen the Gershgorin interval
+  double a = lo - fudge, b = hi + fudge;                    // count(a) <= k < count(b)
+  const double tol = 4.0 * eps * tnorm + 0x1p-1000;
+  for (int it = 0; it < 200 && b - a > tol; ++it) {
+    const double mid = 0.5 * (a + b);
+    if (mid <= a || mid >= b) break;
+    if (sturm_count(d, e2, n, mid) <= k) a = mid;
+    else b = mid;
+  }
+  evals[S.out_off + k] = 0.5 * (a + b);
+}
+
+// Real-gauge H~ of one (field, sector) slot, full symmetric, ld x ld column-major; padding rows
+// and columns n .. ld - 1 are zero.
+__global__ void fill_sym(int64_t kn, int64_t kr, int ld, const double* __restrict__ E_ns,
+                         const double* __restrict__ E_r, const double* __restrict__ Pm,
+                         const double* __restrict__ c0, double scale, double* __restrict__ A) {
+  const int64_t n = kn + kr;
+  const double c = scale * sqrt(c0[0] * c0[0] + c0[1] * c0[1]);
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)ld * ld;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t col = idx / ld, row = idx - col * ld;
+    double v = 0.0;
+    if (row < n && col < n) {
+      if (row == col) v = row < kn ? E_ns[row] : E_r[row - kn];
+      else if (row < kn && col >= kn) v = c * Pm[row * kr + (col - kn)];
+      else if (row >= kn && col < kn) v = c * Pm[col * kr + (row - kn)];
+    }
+    A[idx] = v;
+  }
+}
+
+int64_t round32(int64_t x) { return (x + 31) / 32 * 32; }
+
+}  // namespace
+
+tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double* evals, cudaStream_t st) {
+  std::vector<TriSlot> slots;
+  std::vector<std::pair<int, int>> who;     // (field, sector)
+  int64_t total = 0;
+  int n_max = 0;
+  for (int h = 0; h < n_hx; ++h)
+    for (size_t s = 0; s < b.sectors.size(); ++s) {
+      const int64_t n = b.sectors[s].n_ns + b.sectors[s].n_r;
+      if (n == 0) continue;
+      TriSlot t{};
+      t.n = (int32_t)n;
+      t.ld = (int32_t)round32(n);
+      t.out_off = (int64_t)h * b.n_states + b.sectors[s].ev_off;
+      t.a_off = total;            total += round32((int64_t)t.ld * t.ld);
+      t.rp_off = total;           total += round32((int64_t)(t.ld / kCols) * t.ld);
+      t.cp_off = total;           total += round32((int64_t)kMaxWarpsPerCluster * t.ld);
+      t.p_off = total;            total += round32(t.ld + kMaxCluster);
+      t.de_off = total;           total += round32(2 * n);
+      slots.push_back(t);
+      who.emplace_back(h, (int)s);
+      n_max = std::max(n_max, (int)n);
+    }
+  if (slots.empty()) return TGBA_OK;
+  const int B = (int)slots.size();
+  int ld_max = 0;
+  for (const TriSlot& t : slots) ld_max = std::max(ld_max, t.ld);
+  if (ld_max > kMaxNativeLd) return fail(TGBA_EINVAL, "sector too large for the native eigen-solver");
+  const int64_t slot_doubles = round32(((int64_t)B * sizeof(TriSlot) + 7) / 8);
+  double* ws;
+  tgba_status r = scratch(b, total + slot_doubles, &ws);
+  if (r != TGBA_OK) return r;
+  TriSlot* d_slots = (TriSlot*)(ws + total);
+  TGBA_CUDA(cudaMemcpyAsync(d_slots, slots.data(), B * sizeof(TriSlot), cudaMemcpyHostToDevice, st));
+  for (int q = 0; q < B; ++q) {
+    const Sector& sec = b.sectors[who[q].second];
+    const int64_t work = (int64_t)slots[q].ld * slots[q].ld;
+    const int grid = (int)std::min<int64_t>((work + 255) / 256, 152 * 16);
+    fill_sym<<<grid, 256, 0, st>>>(sec.n_ns, sec.n_r, slots[q].ld, b.d_E_ns + sec.ns_off, b.d_E_r + sec.r_off,
+                                   b.d_P + sec.x_off, b.d_c0, -b.L * hx[who[q].first], ws + slots[q].a_off);
+    TGBA_CUDA(cudaGetLastError());
+    ++b.launches;
+  }
+  int dev = 0, sms = 0;
+  TGBA_CUDA(cudaGetDevice(&dev));
+  TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int C = std::max(1, std::min(kMaxCluster, sms / B));
+  const size_t smem = (size_t)(4 * ld_max + kRed) * sizeof(double) +
+                      (size_t)(kMaxWarpsPerCluster + 1 + 2 * kMaxGroups) * sizeof(int);
+  TGBA_CUDA(cudaFuncSetAttribute(sytrd_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(B * C));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  for (int e = 0; e < 3; ++e)
+    if (b.eig_ev[e] == nullptr) TGBA_CUDA(cudaEventCreate(&b.eig_ev[e]));
+  TGBA_CUDA(cudaEventRecord(b.eig_ev[0], st));
+  TGBA_CUDA(cudaLaunchKernelEx(&cfg, sytrd_cluster, (const TriSlot*)d_slots, C, ws, b.d_status));
+  ++b.launches;
+  TGBA_CUDA(cudaEventRecord(b.eig_ev[1], st));
+  const size_t smem2 = (size_t)2 * n_max * sizeof(double);
+  TGBA_CUDA(cudaFuncSetAttribute(sturm_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+  sturm_bisect<<<dim3((unsigned)((n_max + kSturmThreads - 1) / kSturmThreads), (unsigned)B), kSturmThreads, smem2, st>>>(
+      d_slots, ws, evals, b.d_status);
+  TGBA_CUDA(cudaGetLastError());
+  ++b.launches;
+  TGBA_CUDA(cudaEventRecord(b.eig_ev[2], st));
+  b.eig_ev_recorded = true;
+  double flops = 0;
+  for (const TriSlot& t : slots)
+    for (int64_t m = 1; m < t.n; ++m) flops += 4.0 * m * (m + 1);
+  b.tridiag_flops = flops;
+  b.eig_matrices = B;
+  b.eig_cluster = C;
+  return TGBA_OK;
+}
+
+}  // namespace tgba

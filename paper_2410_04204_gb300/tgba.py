@@ -19,7 +19,7 @@ _NAMES = {0: "TGBA_OK", 1: "TGBA_EINVAL", 2: "TGBA_ENOMEM", 3: "TGBA_ECUDA", 4: 
 # every symbol include/tgba.h declares
 SYMBOLS = ("tgba_last_error", "tgba_device_count", "tgba_build_basis", "tgba_basis_info", "tgba_basis_totals",
            "tgba_basis_free", "tgba_compute_x", "tgba_x_stats", "tgba_x_export", "tgba_x_pairs", "tgba_table",
-           "tgba_assemble_heff", "tgba_eigvals", "tgba_dsf", "tgba_quench", "tgba_screen_create",
+           "tgba_assemble_heff", "tgba_eigvals", "tgba_eigvals_ex", "tgba_dsf", "tgba_quench", "tgba_screen_create",
            "tgba_screen_nparams", "tgba_screen_params", "tgba_screen_grad", "tgba_screen_train",
            "tgba_screen_predict", "tgba_screen_free", "tgba_table_noalloc", "tgba_profile", "tgba_fp64_peak")
 
@@ -42,7 +42,9 @@ class _Prof(ctypes.Structure):
     _fields_ = [("table_ms", ctypes.c_double), ("pfaffian_ms", ctypes.c_double), ("pfaffian_flops", ctypes.c_double),
                 ("pfaffian_launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("upload_bytes", ctypes.c_int64), ("evaluated", ctypes.c_int64),
-                ("tune_mode", ctypes.c_int32), ("tune_threads", ctypes.c_int32), ("tune_ms", ctypes.c_double * 8)]
+                ("tune_mode", ctypes.c_int32), ("tune_threads", ctypes.c_int32), ("tune_ms", ctypes.c_double * 8),
+                ("tridiag_ms", ctypes.c_double), ("bisect_ms", ctypes.c_double), ("tridiag_flops", ctypes.c_double),
+                ("eig_matrices", ctypes.c_int64), ("eig_cluster", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 _lib = None
@@ -70,6 +72,7 @@ def lib():
             "tgba_table": (_I32, [_VP, _VP, _VP, _VP]),
             "tgba_assemble_heff": (_I32, [_VP, _D, _VP, _D, _VP, _VP]),
             "tgba_eigvals": (_I32, [_VP, _VP, _I32, _VP, _VP]),
+            "tgba_eigvals_ex": (_I32, [_VP, _VP, _I32, _I32, _VP, _VP]),
             "tgba_dsf": (_I32, [_VP, _I32, _D, _D, _D, _I32, _D, _VP, _VP, _I32, _VP, _VP, _VP]),
             "tgba_quench": (_I32, [_VP, _I32, _D, _VP, _VP, _I32, _D, _I32, _I32, _VP, _VP, _VP, _VP]),
             "tgba_screen_create": (_I32, [_I32, _VP, ctypes.c_uint64, _P(_VP)]),
@@ -129,11 +132,20 @@ def tgba_build_basis(L, h_z, sectors, max_qp, e_cut=-1.0, max_per_parity=0, J=1.
     h = _VP()
     _check(lib().tgba_build_basis(ctypes.byref(m), sec.ctypes.data_as(_P(_I32)), len(sec), ctypes.byref(t),
                                   ctypes.byref(h)))
+    _MAX_QP[h.value] = int(max_qp)
     return h.value
 
 
-def tgba_basis_info(b, s, max_qp):
-    """Sizes and state tables of sector s (numpy, basis order)."""
+_MAX_QP = {}     # handle -> max_qp, the row length of the modes table tgba_basis_info writes
+
+
+def tgba_basis_info(b, s, max_qp=None):
+    """Sizes and state tables of sector s (numpy, basis order).  The modes table has the basis's
+    max_qp columns; a different max_qp argument is an error."""
+    mq = _MAX_QP.get(b, max_qp)
+    if mq is None or (max_qp is not None and max_qp != mq):
+        raise ValueError("max_qp must be the basis's own (%s)" % mq)
+    max_qp = mq
     n_ns, n_r = _I64(), _I64()
     _check(lib().tgba_basis_info(b, s, ctypes.byref(n_ns), ctypes.byref(n_r), None, None, None, None))
     n = n_ns.value + n_r.value
@@ -146,6 +158,20 @@ def tgba_basis_info(b, s, max_qp):
     return dict(n_ns=n_ns.value, n_r=n_r.value, E0=E, parity=par, nqp=nqp, modes=modes[:, :max_qp])
 
 
+def tgba_sector_sizes(b):
+    """[(n_ns, n_r)] of every sector, in order."""
+    out = []
+    for s in range(tgba_basis_totals(b)[0]):
+        n_ns, n_r = _I64(), _I64()
+        _check(lib().tgba_basis_info(b, s, ctypes.byref(n_ns), ctypes.byref(n_r), None, None, None, None))
+        out.append((n_ns.value, n_r.value))
+    return out
+
+
+def _n_states(b):
+    return sum(a + c for a, c in tgba_sector_sizes(b))
+
+
 def tgba_basis_totals(b):
     ns, ne, nh = _I32(), _I64(), _I64()
     _check(lib().tgba_basis_totals(b, ctypes.byref(ns), ctypes.byref(ne), ctypes.byref(nh)))
@@ -154,6 +180,7 @@ def tgba_basis_totals(b):
 
 def tgba_basis_free(b):
     _check(lib().tgba_basis_free(b))
+    _MAX_QP.pop(b, None)
 
 
 def tgba_compute_x(b, screen=None, screen_tau=0.0, screen_hx=0.0, stream=None):
@@ -197,12 +224,13 @@ def tgba_assemble_heff(b, h_x, heff_out, screen=None, screen_tau=0.0, stream=Non
     _check(lib().tgba_assemble_heff(b, float(h_x), screen, float(screen_tau), _ptr(heff_out), _stream(stream)))
 
 
-def tgba_eigvals(b, h_x, evals_out, stream=None):
-    """h_x: one field or a list; evals_out: float64 CUDA tensor [len(h_x) * n_states]."""
+def tgba_eigvals(b, h_x, evals_out, stream=None, method=0):
+    """h_x: one field or a list; evals_out: float64 CUDA tensor [len(h_x) * n_states].
+    method: 0 automatic, 1 native (tridiagonalisation + bisection), 2 cuSOLVER."""
     import torch
     hx = np.ascontiguousarray(np.atleast_1d(np.asarray(h_x, np.float64)))
-    _cuda_tensor(evals_out, torch.float64, name="evals_out")
-    _check(lib().tgba_eigvals(b, hx.ctypes.data, len(hx), _ptr(evals_out), _stream(stream)))
+    _cuda_tensor(evals_out, torch.float64, len(hx) * _n_states(b), name="evals_out")
+    _check(lib().tgba_eigvals_ex(b, hx.ctypes.data, len(hx), int(method), _ptr(evals_out), _stream(stream)))
 
 
 def tgba_dsf(b, s, h_x, w_min, w_max, n_w, eta, S_out, evals_out=None, n_ev=0, weights_out=None, dE_out=None,
@@ -296,6 +324,7 @@ def tgba_profile(b):
     _check(lib().tgba_profile(b, ctypes.byref(p)))
     out = {k: getattr(p, k) for k, _ in _Prof._fields_}
     out["tune_ms"] = list(p.tune_ms)[:7]
+    out.pop("pad_")
     return out
 
 
