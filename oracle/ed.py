@@ -95,6 +95,22 @@ def dsf_weights(N, h, h_x):
     return E - E[0], np.abs(amp) ** 2
 
 
+def sector_dsf_weights(N, h, h_x, m):
+    """Exact (E_a - E_0, N |<psi_a| sigma^x_1 |psi_0>|^2) for every eigenstate a of momentum
+    sector m, with psi_0 the ground state of the K = 0 sector.  Translation invariance makes
+    this |<psi_a| sigma^x_k |psi_0>|^2 with sigma^x_k = N^{-1/2} sum_j e^{-ikj} sigma^x_j at the
+    momentum k of sector m (the weights of S(k, w), Eq. 8-9); written with sigma^x_1 so that no
+    Fourier sign convention enters."""
+    H = spin_hamiltonian(N, h, h_x)
+    B0 = momentum_basis(N, 0)
+    E0, V0 = np.linalg.eigh(B0.conj().T @ (H @ B0))
+    psi0 = B0 @ V0[:, 0]
+    Bm = momentum_basis(N, m)
+    Em, Vm = np.linalg.eigh(Bm.conj().T @ (H @ Bm))
+    amp = Vm.conj().T @ (Bm.conj().T @ (pauli_x(N, 1) @ psi0))
+    return Em - E0[0], N * np.abs(amp) ** 2
+
+
 def quench_magnetisation(N, h0, h, h_x, t):
     """Exact <sigma^x>(t) from (|GS_Q=+1(h0)> + s|GS_Q=-1(h0)>)/sqrt 2 in the k = 0 sector,
     s chosen to make <sigma^x>(0) > 0, evolved with H(h, h_x)."""

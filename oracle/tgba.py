@@ -64,6 +64,41 @@ def dsf(E, U, Xf, N, w_min, w_max, n_w, eta):
     return 2.0 * math.pi * (lorentzian(om[:, None] - dE[None, :], eta) @ w)
 
 
+def x_cross(X_k0, X_0k):
+    """<phi_mu|sigma^x_1|phi_nu> from the basis of sector k (rows: NS states, then R states) to
+    the basis of the K = 0 sector (columns: NS, then R).  sigma^x_1 flips the fermion parity, so
+    only NS_k x R_0 (X_k0 = X(NS_k, R_0)) and R_k x NS_0 (the adjoint of X_0k = X(NS_0, R_k))
+    are non-zero.  For k = 0 it is x_full(X)."""
+    a, b = X_k0.shape
+    c, d = X_0k.shape
+    Y = np.zeros((a + d, c + b), dtype=np.complex128)
+    Y[:a, c:] = X_k0
+    Y[a:, :c] = np.conj(X_0k).T
+    return Y
+
+
+def dsf_k_weights(E_k, U_k, E_0, u0, Y, N):
+    """Weights of S(k, w) (Eq. 9 with the matrix element sqrt(N) e^{-ik} <psi_a|sigma^x_1|psi_0>
+    that follows it): (E_a - E_0, w_a = N |u_a^H Y u_0|^2) for every eigenstate a of sector k;
+    E_0, u_0: ground-state energy and vector of the K = 0 sector."""
+    amp = np.conj(U_k).T @ (Y @ u0)
+    return E_k - E_0, N * np.abs(amp) ** 2
+
+
+def dsf_k(N, h, h_x, m, max_qp, e_cut, w_min, w_max, n_w, eta, n_threads=0):
+    """S(k, w) = 2 pi sum_a w_a L_eta(w - (E_a - E_0)) at the momentum of sector m.  Returns
+    (E_a - E_0, w_a, S on the w grid)."""
+    ns0, r0, X0 = sector(N, h, 0, max_qp, e_cut, None, n_threads)
+    E0, U0 = eigh(heff(ns0, r0, X0, N, h_x))
+    nsk, rk, Xk = sector(N, h, m, max_qp, e_cut, None, n_threads)
+    Ek, Uk = eigh(heff(nsk, rk, Xk, N, h_x))
+    Y = x_cross(el.x_block(N, h, nsk, r0, n_threads), el.x_block(N, h, ns0, rk, n_threads))
+    dE, w = dsf_k_weights(Ek, Uk, E0[0], U0[:, 0], Y, N)
+    om = omega_grid(w_min, w_max, n_w)
+    S = 2.0 * math.pi * (lorentzian(om[:, None] - dE[None, :], eta) @ w)
+    return dE, w, S
+
+
 def vacuum_phase(N, h0):
     """s with |s| = 1 that makes <Phi0|sigma^x_1|Phi0> = Re(s z) > 0, z = <0_NS|sigma_1|0_R>
     at the initial field (Fig. 2 caption: the superposition with positive magnetisation)."""
