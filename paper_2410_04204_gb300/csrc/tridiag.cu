@@ -25,7 +25,9 @@
 //
 // FP64 throughput on this GPU is 1/64 of FP32, so the design counts FP64 instructions: the
 // reduction is 4 FMAs per trailing element per step (4n^3/3 flops per matrix); selects, masks,
-// sign tests and rescalings are integer operations, and no double value is selected.
+// sign tests and rescalings are integer operations, and no double value is selected.  The
+// matrix is stored in 32 x 16 tiles of 4 KB, so the blocks a warp walks through are sequential
+// in memory.
 #include <algorithm>
 #include <string>
 #include <vector>
@@ -45,7 +47,7 @@ constexpr int kMaxGroups = kMaxNativeLd / kCols;
 constexpr int kSturmThreads = 128;
 
 struct TriSlot {
-  int64_t a_off;    // matrix, ld x ld column-major, zero beyond n (both triangles, lower one used)
+  int64_t a_off;    // matrix, ld x ld in 32 x 16 tiles (blk_off), zero beyond n, lower triangle used
   int64_t rp_off;   // row sums of the 32 x 16 blocks [ld / 16][ld]
   int64_t cp_off;   // column sums of each warp's blocks [warps of a cluster][ld]
   int64_t p_off;    // p = tau A v [ld], then one dot partial per CTA of the cluster [8]
@@ -58,6 +60,20 @@ __device__ __forceinline__ double isel(bool s, double y, double x) {   // s ? y 
   const int lo = s ? __double2loint(y) : __double2loint(x);
   const int hi = s ? __double2hiint(y) : __double2hiint(x);
   return __hiloint2double(hi, lo);
+}
+
+// x if s, else +0.0: the bits ANDed with an all-ones or all-zeros mask (no FP64 instruction)
+__device__ __forceinline__ double keep_if(bool s, double x) {
+  const int m = s ? -1 : 0;
+  return __hiloint2double(__double2hiint(x) & m, __double2loint(x) & m);
+}
+
+// Block-tiled storage of an ld x ld matrix: the 32 x 16 block (row block rb, column group g)
+// occupies 512 consecutive doubles at ((g LB + rb) 512), column-major inside (column kk of
+// the block at + 32 kk), so a warp walking down a column group reads sequential memory.
+__device__ __forceinline__ int64_t blk_off(int g, int rb, int LB) { return ((int64_t)g * LB + rb) * (32 * 16); }
+__device__ __forceinline__ int64_t elem_off(int i, int k, int LB) {
+  return blk_off(k >> 4, i >> 5, LB) + (k & 15) * 32 + (i & 31);
 }
 
 __device__ __forceinline__ void cluster_barrier(int C) {
@@ -102,41 +118,45 @@ __device__ __forceinline__ int warp_of(const int* __restrict__ s, int W, int b) 
   return lo;
 }
 
-__device__ __forceinline__ void load_block(double (&a)[kCols], const double* __restrict__ p, int ld) {
+__device__ __forceinline__ void load_block(double (&a)[kCols], const double* __restrict__ p) {
 #pragma unroll
-  for (int kk = 0; kk < kCols; ++kk) a[kk] = __ldcg(p + (int64_t)kk * ld);
+  for (int kk = 0; kk < kCols; ++kk) a[kk] = __ldcg(p + 32 * kk);
 }
 
-// One 32 x 16 block held in a[]: row i = 32 rb + lane, columns k0 .. k0 + 15 (p points at
-// row i of column k0).  The rank-2 update of the previous step is applied and stored, the
-// row sum of A_j v_j over the block's columns goes to rp[i], the column sums over its rows
-// accumulate in cs.  DIAG (the group's first block): elements with row < column add nothing
-// and the diagonal element adds only to its row.  Columns left of the trailing block, rows
-// above it and padding rows/columns are processed too: there v_{j-1} and w_{j-1} vanish (the
-// update leaves the value unchanged, except in column j, which is no longer read), v_j
-// vanishes (no row-sum contribution), and the column sums they produce are never read.
+// One 32 x 16 block held in a[]: row i = 32 rb + lane, columns k0 .. k0 + 15 (p points at the
+// lane's element of the block's first column).  vwp[k] = (v_{j-1}, w_{j-1})[k], vwn[k].x =
+// v_j[k].  The rank-2 update of the previous step is applied and stored, the row sum of
+// A_j v_j over the block's columns goes to rp[i], the column sums over its rows accumulate in
+// cs.  DIAG (the group's first block): elements with row < column add nothing and the
+// diagonal element adds only to its row.  Columns left of the trailing block, rows above it
+// and padding rows/columns are processed too: there v_{j-1} and w_{j-1} vanish (the update
+// leaves the value unchanged, except in column j, which is no longer read), v_j vanishes (no
+// row-sum contribution), and the column sums they produce are never read.
 template <bool DIAG>
-__device__ __forceinline__ void sytrd_block(const double (&a)[kCols], double* __restrict__ p, int ld, int i, int k0,
-                                            const double* __restrict__ vp, const double* __restrict__ wp,
-                                            const double* __restrict__ vn, double (&cs)[kCols],
-                                            double* __restrict__ rp) {
-  const double vpi = vp[i], wpi = wp[i], vni = vn[i];
-  double r = 0.0;
+__device__ __forceinline__ void sytrd_block(const double (&a)[kCols], double* __restrict__ p, int i, int k0,
+                                            const double2* __restrict__ vwp, const double2* __restrict__ vwn,
+                                            double (&cs)[kCols], double* __restrict__ rp) {
+  const double2 vwi = vwp[i];
+  const double vni = vwn[i].x;
+  double r0 = 0.0, r1 = 0.0;
 #pragma unroll
   for (int kk = 0; kk < kCols; ++kk) {
     const int k = k0 + kk;
-    double x = fma(-vpi, wp[k], a[kk]);
-    x = fma(-wpi, vp[k], x);
-    __stcg(p + (int64_t)kk * ld, x);
+    const double2 vwk = vwp[k];
+    const double vnk = vwn[k].x;
+    double x = fma(-vwi.x, vwk.y, a[kk]);
+    x = fma(-vwi.y, vwk.x, x);
+    __stcg(p + 32 * kk, x);
+    double& r = (kk & 1) ? r1 : r0;
     if (DIAG) {
-      r = fma(x, isel(i >= k, vn[k], 0.0), r);
-      cs[kk] = fma(x, isel(i > k, vni, 0.0), cs[kk]);
+      r = fma(x, keep_if(i >= k, vnk), r);
+      cs[kk] = fma(x, keep_if(i > k, vni), cs[kk]);
     } else {
-      r = fma(x, vn[k], r);
+      r = fma(x, vnk, r);
       cs[kk] = fma(x, vni, cs[kk]);
     }
   }
-  __stcg(rp + i, r);
+  __stcg(rp + i, r0 + r1);
 }
 
 // Lanes l and l + 16 end with the sum over all 32 lanes of cs[l & 15]: the two half-warps are
@@ -161,32 +181,32 @@ __device__ __forceinline__ double transpose_reduce16(double (&cs)[kCols], int la
 // Row blocks [rb_b, rb_e) of column group g.  Two block buffers in registers: the loads of the
 // next block are in flight while the current one is computed.  Then the warp's column sums of
 // the group go to CP[w].
-__device__ __forceinline__ void sytrd_chunk(double* __restrict__ A, int ld, int g, int rb_b, int rb_e, int lane,
-                                            int w, const double* __restrict__ vp, const double* __restrict__ wp,
-                                            const double* __restrict__ vn, double* __restrict__ RP,
+__device__ __forceinline__ void sytrd_chunk(double* __restrict__ A, int ld, int LB, int g, int rb_b, int rb_e,
+                                            int lane, int w, const double2* __restrict__ vwp,
+                                            const double2* __restrict__ vwn, double* __restrict__ RP,
                                             double* __restrict__ CP) {
   const int k0 = kCols * g;
-  double* colp = A + (int64_t)k0 * ld + lane;      // + 32 rb: the lane's row of block rb
+  double* gp = A + blk_off(g, 0, LB) + lane;       // + 512 rb: the lane's row of block rb
   double* rp = RP + (int64_t)g * ld;
   double cs[kCols], cur[kCols], nxt[kCols];
 #pragma unroll
   for (int kk = 0; kk < kCols; ++kk) cs[kk] = 0.0;
   int rb = rb_b;
-  load_block(cur, colp + 32 * rb, ld);
+  load_block(cur, gp + 512 * rb);
   if (rb == (g >> 1)) {                            // the diagonal block comes first
-    load_block(nxt, colp + 32 * min(rb + 1, rb_e - 1), ld);
-    sytrd_block<true>(cur, colp + 32 * rb, ld, 32 * rb + lane, k0, vp, wp, vn, cs, rp);
+    load_block(nxt, gp + 512 * min(rb + 1, rb_e - 1));
+    sytrd_block<true>(cur, gp + 512 * rb, 32 * rb + lane, k0, vwp, vwn, cs, rp);
     ++rb;
 #pragma unroll
     for (int kk = 0; kk < kCols; ++kk) cur[kk] = nxt[kk];
   }
   for (; rb + 1 < rb_e; rb += 2) {
-    load_block(nxt, colp + 32 * (rb + 1), ld);
-    sytrd_block<false>(cur, colp + 32 * rb, ld, 32 * rb + lane, k0, vp, wp, vn, cs, rp);
-    load_block(cur, colp + 32 * min(rb + 2, rb_e - 1), ld);
-    sytrd_block<false>(nxt, colp + 32 * (rb + 1), ld, 32 * (rb + 1) + lane, k0, vp, wp, vn, cs, rp);
+    load_block(nxt, gp + 512 * (rb + 1));
+    sytrd_block<false>(cur, gp + 512 * rb, 32 * rb + lane, k0, vwp, vwn, cs, rp);
+    load_block(cur, gp + 512 * min(rb + 2, rb_e - 1));
+    sytrd_block<false>(nxt, gp + 512 * (rb + 1), 32 * (rb + 1) + lane, k0, vwp, vwn, cs, rp);
   }
-  if (rb < rb_e) sytrd_block<false>(cur, colp + 32 * rb, ld, 32 * rb + lane, k0, vp, wp, vn, cs, rp);
+  if (rb < rb_e) sytrd_block<false>(cur, gp + 512 * rb, 32 * rb + lane, k0, vwp, vwn, cs, rp);
   const double colsum = transpose_reduce16(cs, lane);
   if (lane < kCols) __stcg(CP + (int64_t)w * ld + k0 + lane, colsum);
 }
@@ -204,10 +224,8 @@ sytrd_cluster(const TriSlot* __restrict__ slots, int C, double* __restrict__ ws,
   double* dots = P + ld;
   double* D = ws + S.de_off;
   double* E = D + n;
-  double* vp = sm;
-  double* wp = sm + ld;
-  double* vn = sm + 2 * ld;
-  double* wn = sm + 3 * ld;
+  double2* vwp = (double2*)sm;                   // (v_{j-1}, w_{j-1}) per index
+  double2* vwn = (double2*)(sm + 2 * ld);         // (v_j, w_j)
   double* red = sm + 4 * ld;
   int* sw = (int*)(red + kRed);                   // [W + 1] first block of each warp
   int* gw = sw + kMaxWarpsPerCluster + 1;         // [2 G] first and last warp meeting each group
@@ -219,16 +237,17 @@ sytrd_cluster(const TriSlot* __restrict__ slots, int C, double* __restrict__ ws,
   for (int j = 0; j < n; ++j) {
     // column j of A_j: the stored column (already updated through step j - 2) minus the
     // rank-2 update of step j - 1; rows j + 2 .. n - 1 go into the norm
-    const double vpj = vp[j], wpj = wp[j];
+    const double2 vwj = vwp[j];
     double sig = 0.0;
     for (int i = j + threadIdx.x; i < n; i += kThreads) {
-      double a = __ldcg(A + (int64_t)j * ld + i);
-      a = fma(-vp[i], wpj, a);
-      a = fma(-wp[i], vpj, a);
+      const double2 vwi = vwp[i];
+      double a = __ldcg(A + elem_off(i, j, LB));
+      a = fma(-vwi.x, vwj.y, a);
+      a = fma(-vwi.y, vwj.x, a);
       if (i == j) red[kWarps] = a;
       else if (i == j + 1) red[kWarps + 1] = a;
       else sig = fma(a, a, sig);
-      vn[i] = a;
+      vwn[i].x = a;
     }
     // the step's work split (integer only), published by block_sum's barrier
     const int g0 = (j + 1) / kCols, NG = G - g0;
@@ -254,8 +273,8 @@ sytrd_cluster(const TriSlot* __restrict__ slots, int C, double* __restrict__ ws,
     if (rank == 0 && threadIdx.x == 0) E[j] = beta;
     if (threadIdx.x == 0 && !(isfinite(dj) && isfinite(beta))) bad = true;
     for (int i = threadIdx.x; i < ld; i += kThreads) {
-      const double x = vn[i];
-      vn[i] = i == j + 1 ? 1.0 : (i > j + 1 && i < n ? x * s : 0.0);
+      const double x = vwn[i].x;
+      vwn[i].x = i == j + 1 ? 1.0 : (i > j + 1 && i < n ? x * s : 0.0);
     }
     __syncthreads();
     // one pass over the trailing lower triangle: update of step j - 1 and y = A_j v_j
@@ -273,7 +292,7 @@ sytrd_cluster(const TriSlot* __restrict__ slots, int C, double* __restrict__ ws,
         while (sb < se) {
           const int g = g0 + gq, nbg = LB - (g >> 1);
           const int b1 = min(nbg, b + (se - sb));
-          sytrd_chunk(A, ld, g, (g >> 1) + b, (g >> 1) + b1, lane, wid, vp, wp, vn, RP, CP);
+          sytrd_chunk(A, ld, LB, g, (g >> 1) + b, (g >> 1) + b1, lane, wid, vwp, vwn, RP, CP);
           sb += b1 - b;
           ++gq;
           b = 0;
@@ -296,7 +315,7 @@ sytrd_cluster(const TriSlot* __restrict__ slots, int C, double* __restrict__ ws,
           if (sw[w] < sw[w + 1]) y += __ldcg(CP + (int64_t)w * ld + i);
         const double p = tau * y;
         __stcg(P + i, p);
-        dot = fma(p, vn[i], dot);
+        dot = fma(p, vwn[i].x, dot);
       }
     }
     dot = block_sum(dot, red);
@@ -306,10 +325,9 @@ sytrd_cluster(const TriSlot* __restrict__ slots, int C, double* __restrict__ ws,
     for (int r = 0; r < C; ++r) pv += __ldcg(dots + r);
     const double Kc = 0.5 * tau * pv;
     for (int i = threadIdx.x; i < ld; i += kThreads)
-      wn[i] = (i > j && i < n) ? fma(-Kc, vn[i], __ldcg(P + i)) : 0.0;
+      vwn[i].y = (i > j && i < n) ? fma(-Kc, vwn[i].x, __ldcg(P + i)) : 0.0;
     __syncthreads();
-    double* t = vp; vp = vn; vn = t;
-    t = wp; wp = wn; wn = t;
+    double2* t = vwp; vwp = vwn; vwn = t;
   }
   if (bad) atomicOr(status, kStEigen);
 }
@@ -400,16 +418,20 @@ sturm_bisect(const TriSlot* __restrict__ slots, const double* __restrict__ ws, d
   evals[S.out_off + k] = 0.5 * (a + b);
 }
 
-// Real-gauge H~ of one (field, sector) slot, full symmetric, ld x ld column-major; padding rows
-// and columns n .. ld - 1 are zero.
+// Real-gauge H~ of one (field, sector) slot, full symmetric, ld x ld in 32 x 16 tiles (see
+// blk_off); padding rows and columns n .. ld - 1 are zero.  Consecutive threads write
+// consecutive doubles of the tiled array.
 __global__ void fill_sym(int64_t kn, int64_t kr, int ld, const double* __restrict__ E_ns,
                          const double* __restrict__ E_r, const double* __restrict__ Pm,
                          const double* __restrict__ c0, double scale, double* __restrict__ A) {
   const int64_t n = kn + kr;
+  const int LB = ld >> 5;
   const double c = scale * sqrt(c0[0] * c0[0] + c0[1] * c0[1]);
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)ld * ld;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t col = idx / ld, row = idx - col * ld;
+    const int64_t blk = idx >> 9, in = idx & 511;
+    const int64_t g = blk / LB, rb = blk - g * LB;
+    const int64_t row = rb * 32 + (in & 31), col = g * 16 + (in >> 5);
     double v = 0.0;
     if (row < n && col < n) {
       if (row == col) v = row < kn ? E_ns[row] : E_r[row - kn];
