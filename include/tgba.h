@@ -153,6 +153,19 @@ tgba_status tgba_dsf(tgba_basis b, int32_t s, double h_x, double w_min, double w
                      float* S_dev, double* evals_dev, int32_t n_ev, double* weights_dev, double* dE_dev,
                      void* stream);
 
+/* S(k, w) at the momentum k = 2 pi m / L of sector s (Eq. 8-9 with the matrix element that follows
+   them, <psi_a^k|sigma^x_k|psi_0> = sqrt(L) e^{-ik} <psi_a^k|sigma^x_1|psi_0>): S(w_i) =
+   2 pi sum_a w_a L_eta(w_i - (E_a - E_0)) over the eigenstates a of sector s, w_a =
+   L |<psi_a|sigma^x_1|psi_0>|^2, with psi_0, E_0 the ground state of sector s0, which must be
+   the k = 0 sector of the basis.  sigma^x_1 connects NS states of one sector with R states of the
+   other, and these cross-sector elements are computed here, as Pfaffians of the same contraction
+   table.  Grid, eta, outputs and their layout as in tgba_dsf (evals/weights/dE are those of sector
+   s; dE relative to E_0).  s = s0 gives tgba_dsf's result.  Needs tgba_compute_x first; blocks on
+   `stream`. */
+tgba_status tgba_dsf_k(tgba_basis b, int32_t s, int32_t s0, double h_x, double w_min, double w_max, int32_t n_w,
+                       double eta, float* S_dev, double* evals_dev, int32_t n_ev, double* weights_dev, double* dE_dev,
+                       void* stream);
+
 /* ---------------------------------------------------------------- quench (Eq. 10)
  * <sigma^x>(t) after the quench from Phi0 = (|0_NS(h_z0)> + s|0_R(h_z0)>)/sqrt 2 (ground states
  * of the h_x = 0 chain at h_z0, s making <sigma^x>(0) > 0) to the basis' model with

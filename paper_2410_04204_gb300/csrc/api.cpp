@@ -430,6 +430,24 @@ tgba_status tgba_dsf(tgba_basis h, int32_t s, double h_x, double w_min, double w
   return dsf(*b, s, h_x, w_min, w_max, n_w, eta, S_dev, evals_dev, n_ev, weights_dev, dE_dev, (cudaStream_t)stream);
 }
 
+tgba_status tgba_dsf_k(tgba_basis h, int32_t s, int32_t s0, double h_x, double w_min, double w_max, int32_t n_w,
+                       double eta, float* S_dev, double* evals_dev, int32_t n_ev, double* weights_dev, double* dE_dev,
+                       void* stream) {
+  Basis* b = (Basis*)h;
+  BASIS_OK(b);
+  const int ns = (int)b->sectors.size();
+  if (s < 0 || s >= ns || s0 < 0 || s0 >= ns) return fail(TGBA_EINVAL, "sector index out of range");
+  if (b->sectors[s0].m != 0) return fail(TGBA_EINVAL, "s0 must be the k = 0 sector (it holds the ground state)");
+  if (n_w < 1 || !S_dev) return fail(TGBA_EINVAL, "need n_w >= 1 and an output buffer");
+  if (!(eta > 0) || !std::isfinite(w_min) || !std::isfinite(w_max) || !std::isfinite(h_x))
+    return fail(TGBA_EINVAL, "eta must be positive and the grid finite");
+  if (!b->x_valid) return fail(TGBA_EINVAL, "no X computed yet: call tgba_compute_x");
+  cudaStream_t st = (cudaStream_t)stream;
+  tgba_status r = ensure_table(*b, st);
+  if (r != TGBA_OK) return r;
+  return dsf_k(*b, s, s0, h_x, w_min, w_max, n_w, eta, S_dev, evals_dev, n_ev, weights_dev, dE_dev, st);
+}
+
 tgba_status tgba_quench(tgba_basis h, int32_t s, double h_z0, const double* hx_variants, const double* ecut_variants,
                         int32_t n_variants, double t_max, int32_t n_t, int32_t method, double* mx_dev, double* norm_dev,
                         int64_t* chi_host, void* stream) {

@@ -261,6 +261,35 @@ __global__ void __launch_bounds__(T) pf_pairs(const int32_t* __restrict__ pairs,
   }
 }
 
+// Every pair of a rectangle of NS states (a0 .. a0 + rows - 1, global index) and R states
+// (b0 .. b0 + cols - 1), possibly of different momentum sectors: out[i][j] = P, the real
+// Pfaffian of the contraction-table rows of the pair (X = C0 (-i)^{n/2} P).  One thread per pair.
+template <int NMAX, int T>
+__global__ void __launch_bounds__(T) pf_cross(int64_t rows, int64_t cols, int64_t a0, int64_t b0,
+                                              const double* __restrict__ R, int two_l,
+                                              const uint8_t* __restrict__ sel_ns, const uint8_t* __restrict__ sel_r,
+                                              const uint8_t* __restrict__ m_ns, const uint8_t* __restrict__ m_r,
+                                              int max_qp, double* __restrict__ out, unsigned* status) {
+  extern __shared__ double smem[];
+  double* W = smem + threadIdx.x;
+  for (int64_t q = (int64_t)blockIdx.x * T + threadIdx.x; q < rows * cols; q += (int64_t)gridDim.x * T) {
+    const int64_t a = a0 + q / cols, b = b0 + q % cols;
+    const int ma = m_ns[a], n = ma + m_r[b];
+    const uint8_t* sa = sel_ns + (size_t)a * max_qp;
+    const uint8_t* sb = sel_r + (size_t)b * max_qp;
+    for (int i = 0; i < n - 1; ++i) {
+      const int si = i < ma ? sa[i] : sb[i - ma];
+      for (int j = i + 1; j < n; ++j) {
+        const int sj = j < ma ? sa[j] : sb[j - ma];
+        W[Packed<NMAX>::idx(i, j) * T] = __ldg(R + (size_t)si * two_l + sj);
+      }
+    }
+    const double pf = pfaffian_smem<NMAX, T>(W, n);
+    if (!is_finite_bits(pf)) atomicOr(status, kStNan);
+    out[q] = pf;
+  }
+}
+
 using KernelFn = void (*)(Args);
 
 // kernel of (kind, size, threads); kind 0: static launch of one exact size, 1: queue over all
@@ -423,6 +452,28 @@ tgba_status run_pfaffian_pairs(Basis& b, int s, const int32_t* pairs, int64_t n,
   if (b.max_n <= 12) return go(pf_pairs<12, 128>, 128, 12);
   if (b.max_n <= 20) return go(pf_pairs<20, 64>, 64, 20);
   return go(pf_pairs<32, 32>, 32, 32);
+}
+
+tgba_status run_pfaffian_cross(Basis& b, int s_ns, int s_r, double* out, cudaStream_t st) {
+  const Sector& A = b.sectors[s_ns];
+  const Sector& B = b.sectors[s_r];
+  const int64_t n = A.n_ns * B.n_r;
+  if (n == 0) return TGBA_OK;
+  int sms = 0;
+  TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
+  auto go = [&](auto kern, int T, int nmax) -> tgba_status {
+    const size_t smem = (size_t)(nmax * (nmax - 1) / 2) * T * sizeof(double);
+    TGBA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t blocks = std::min<int64_t>((n + T - 1) / T, (int64_t)sms * 8);
+    kern<<<(int)blocks, T, smem, st>>>(A.n_ns, B.n_r, A.ns_off, B.r_off, b.d_table, 2 * b.L, b.d_sel_ns, b.d_sel_r,
+                                       b.d_M_ns, b.d_M_r, b.max_qp, out, b.d_status);
+    TGBA_CUDA(cudaGetLastError());
+    ++b.launches;
+    return TGBA_OK;
+  };
+  if (b.max_n <= 12) return go(pf_cross<12, 128>, 128, 12);
+  if (b.max_n <= 20) return go(pf_cross<20, 64>, 64, 20);
+  return go(pf_cross<32, 32>, 32, 32);
 }
 
 }  // namespace tgba

@@ -175,6 +175,8 @@ tgba_status plan_pfaffians(Basis& b);
 tgba_status autotune_pfaffians(Basis& b, cudaStream_t st);
 tgba_status run_pfaffians(Basis& b, const uint8_t* d_mask, cudaStream_t st);
 tgba_status run_pfaffian_pairs(Basis& b, int s, const int32_t* pairs, int64_t n, double* out, cudaStream_t st);
+// real P of every (NS state of sector s_ns, R state of sector s_r) pair, out [n_ns][n_r] row-major
+tgba_status run_pfaffian_cross(Basis& b, int s_ns, int s_r, double* out, cudaStream_t st);
 
 // assemble.cu
 tgba_status assemble_heff(Basis& b, double h_x, double* heff, cudaStream_t st);
@@ -198,6 +200,10 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
 // dsf.cu
 tgba_status dsf(Basis& b, int s, double h_x, double w_min, double w_max, int n_w, double eta, float* S,
                 double* evals, int n_ev, double* weights, double* dE, cudaStream_t st);
+
+// S(k, w) at the momentum of sector s, ground state from the K = 0 sector s0
+tgba_status dsf_k(Basis& b, int s, int s0, double h_x, double w_min, double w_max, int n_w, double eta, float* S,
+                  double* evals, int n_ev, double* weights, double* dE, cudaStream_t st);
 
 // quench.cu
 tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* ecut, int nv, double t_max,

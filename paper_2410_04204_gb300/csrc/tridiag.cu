@@ -48,7 +48,7 @@ constexpr int kSturmThreads = 128;
 
 struct TriSlot {
   int64_t a_off;    // matrix, ld x ld in 32 x 16 tiles (blk_off), zero beyond n, lower triangle used
-  int64_t rp_off;   // row sums of the 32 x 16 blocks [ld / 16][ld]
+  int64_t rp_off;   // row sums of the 32 x 16 blocks [ld][ld / 16]: a row's partials contiguous
   int64_t cp_off;   // column sums of each warp's blocks [warps of a cluster][ld]
   int64_t p_off;    // p = tau A v [ld], then one dot partial per CTA of the cluster [8]
   int64_t de_off;   // diagonal d [n], off-diagonal e [n]
@@ -126,7 +126,7 @@ __device__ __forceinline__ void load_block(double (&a)[kCols], const double* __r
 // One 32 x 16 block held in a[]: row i = 32 rb + lane, columns k0 .. k0 + 15 (p points at the
 // lane's element of the block's first column).  vwp[k] = (v_{j-1}, w_{j-1})[k], vwn[k].x =
 // v_j[k].  The rank-2 update of the previous step is applied and stored, the row sum of
-// A_j v_j over the block's columns goes to rp[i], the column sums over its rows accumulate in
+// A_j v_j over the block's columns goes to rp[i G], the column sums over its rows accumulate in
 // cs.  DIAG (the group's first block): elements with row < column add nothing and the
 // diagonal element adds only to its row.  Columns left of the trailing block, rows above it
 // and padding rows/columns are processed too: there v_{j-1} and w_{j-1} vanish (the update
@@ -135,7 +135,7 @@ __device__ __forceinline__ void load_block(double (&a)[kCols], const double* __r
 template <bool DIAG>
 __device__ __forceinline__ void sytrd_block(const double (&a)[kCols], double* __restrict__ p, int i, int k0,
                                             const double2* __restrict__ vwp, const double2* __restrict__ vwn,
-                                            double (&cs)[kCols], double* __restrict__ rp) {
+                                            double (&cs)[kCols], double* __restrict__ rp, int G) {
   const double2 vwi = vwp[i];
   const double vni = vwn[i].x;
   double r0 = 0.0, r1 = 0.0;
@@ -156,7 +156,7 @@ __device__ __forceinline__ void sytrd_block(const double (&a)[kCols], double* __
       cs[kk] = fma(x, vni, cs[kk]);
     }
   }
-  __stcg(rp + i, r0 + r1);
+  __stcg(rp + (int64_t)i * G, r0 + r1);
 }
 
 // Lanes l and l + 16 end with the sum over all 32 lanes of cs[l & 15]: the two half-warps are
@@ -187,7 +187,8 @@ __device__ __forceinline__ void sytrd_chunk(double* __restrict__ A, int ld, int 
                                             double* __restrict__ CP) {
   const int k0 = kCols * g;
   double* gp = A + blk_off(g, 0, LB) + lane;       // + 512 rb: the lane's row of block rb
-  double* rp = RP + (int64_t)g * ld;
+  double* rp = RP + g;                             // row i's sum at rp[i G]
+  const int G = ld / kCols;
   double cs[kCols], cur[kCols], nxt[kCols];
 #pragma unroll
   for (int kk = 0; kk < kCols; ++kk) cs[kk] = 0.0;
@@ -195,18 +196,18 @@ __device__ __forceinline__ void sytrd_chunk(double* __restrict__ A, int ld, int 
   load_block(cur, gp + 512 * rb);
   if (rb == (g >> 1)) {                            // the diagonal block comes first
     load_block(nxt, gp + 512 * min(rb + 1, rb_e - 1));
-    sytrd_block<true>(cur, gp + 512 * rb, 32 * rb + lane, k0, vwp, vwn, cs, rp);
+    sytrd_block<true>(cur, gp + 512 * rb, 32 * rb + lane, k0, vwp, vwn, cs, rp, G);
     ++rb;
 #pragma unroll
     for (int kk = 0; kk < kCols; ++kk) cur[kk] = nxt[kk];
   }
   for (; rb + 1 < rb_e; rb += 2) {
     load_block(nxt, gp + 512 * (rb + 1));
-    sytrd_block<false>(cur, gp + 512 * rb, 32 * rb + lane, k0, vwp, vwn, cs, rp);
+    sytrd_block<false>(cur, gp + 512 * rb, 32 * rb + lane, k0, vwp, vwn, cs, rp, G);
     load_block(cur, gp + 512 * min(rb + 2, rb_e - 1));
-    sytrd_block<false>(nxt, gp + 512 * (rb + 1), 32 * (rb + 1) + lane, k0, vwp, vwn, cs, rp);
+    sytrd_block<false>(nxt, gp + 512 * (rb + 1), 32 * (rb + 1) + lane, k0, vwp, vwn, cs, rp, G);
   }
-  if (rb < rb_e) sytrd_block<false>(cur, gp + 512 * rb, 32 * rb + lane, k0, vwp, vwn, cs, rp);
+  if (rb < rb_e) sytrd_block<false>(cur, gp + 512 * rb, 32 * rb + lane, k0, vwp, vwn, cs, rp, G);
   const double colsum = transpose_reduce16(cs, lane);
   if (lane < kCols) __stcg(CP + (int64_t)w * ld + k0 + lane, colsum);
 }
@@ -300,23 +301,30 @@ sytrd_cluster(const TriSlot* __restrict__ slots, int C, double* __restrict__ ws,
       }
     }
     cluster_barrier(C);
-    // rows j + 1 .. n - 1, a slice per CTA: y_i = row sums of the blocks of groups g0 .. i/16
-    // + the column sums of the warps whose ranges met column i's group; p = tau y
+    // rows j + 1 .. n - 1, interleaved over the cluster's CTAs (row i to CTA i mod C, so the
+    // long rows at the bottom are shared): y_i = row sums of the blocks of groups g0 .. i/16
+    // (contiguous, read with independent loads) + the column sums of the warps whose ranges
+    // met column i's group; p = tau y
     double dot = 0.0;
-    {
-      const int m = n - (j + 1);
-      const int lo = j + 1 + (int)((int64_t)m * rank / C), hi = j + 1 + (int)((int64_t)m * (rank + 1) / C);
-      for (int i = lo + threadIdx.x; i < hi; i += kThreads) {
-        const int gi = i / kCols;
-        double y = 0.0;
-        for (int g = g0; g <= gi; ++g) y += __ldcg(RP + (int64_t)g * ld + i);
-        const int t = gi - g0;
-        for (int w = gw[2 * t]; w <= gw[2 * t + 1]; ++w)
-          if (sw[w] < sw[w + 1]) y += __ldcg(CP + (int64_t)w * ld + i);
-        const double p = tau * y;
-        __stcg(P + i, p);
-        dot = fma(p, vwn[i].x, dot);
+    for (int i = j + 1 + rank + C * threadIdx.x; i < n; i += C * kThreads) {
+      const int gi = i / kCols;
+      const double* rr = RP + (int64_t)i * G;
+      double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
+      int g = g0;
+      for (; g + 4 <= gi + 1; g += 4) {
+        y0 += __ldcg(rr + g);
+        y1 += __ldcg(rr + g + 1);
+        y2 += __ldcg(rr + g + 2);
+        y3 += __ldcg(rr + g + 3);
       }
+      for (; g <= gi; ++g) y0 += __ldcg(rr + g);
+      double y = (y0 + y1) + (y2 + y3);
+      const int t = gi - g0;
+      for (int w = gw[2 * t]; w <= gw[2 * t + 1]; ++w)
+        if (sw[w] < sw[w + 1]) y += __ldcg(CP + (int64_t)w * ld + i);
+      const double p = tau * y;
+      __stcg(P + i, p);
+      dot = fma(p, vwn[i].x, dot);
     }
     dot = block_sum(dot, red);
     if (threadIdx.x == 0) __stcg(dots + rank, dot);

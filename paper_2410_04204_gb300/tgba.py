@@ -19,7 +19,7 @@ _NAMES = {0: "TGBA_OK", 1: "TGBA_EINVAL", 2: "TGBA_ENOMEM", 3: "TGBA_ECUDA", 4: 
 # every symbol include/tgba.h declares
 SYMBOLS = ("tgba_last_error", "tgba_device_count", "tgba_build_basis", "tgba_basis_info", "tgba_basis_totals",
            "tgba_basis_free", "tgba_compute_x", "tgba_x_stats", "tgba_x_export", "tgba_x_pairs", "tgba_table",
-           "tgba_assemble_heff", "tgba_eigvals", "tgba_eigvals_ex", "tgba_dsf", "tgba_quench", "tgba_screen_create",
+           "tgba_assemble_heff", "tgba_eigvals", "tgba_eigvals_ex", "tgba_dsf", "tgba_dsf_k", "tgba_quench", "tgba_screen_create",
            "tgba_screen_nparams", "tgba_screen_params", "tgba_screen_grad", "tgba_screen_train",
            "tgba_screen_predict", "tgba_screen_free", "tgba_table_noalloc", "tgba_profile", "tgba_fp64_peak")
 
@@ -74,6 +74,7 @@ def lib():
             "tgba_eigvals": (_I32, [_VP, _VP, _I32, _VP, _VP]),
             "tgba_eigvals_ex": (_I32, [_VP, _VP, _I32, _I32, _VP, _VP]),
             "tgba_dsf": (_I32, [_VP, _I32, _D, _D, _D, _I32, _D, _VP, _VP, _I32, _VP, _VP, _VP]),
+            "tgba_dsf_k": (_I32, [_VP, _I32, _I32, _D, _D, _D, _I32, _D, _VP, _VP, _I32, _VP, _VP, _VP]),
             "tgba_quench": (_I32, [_VP, _I32, _D, _VP, _VP, _I32, _D, _I32, _I32, _VP, _VP, _VP, _VP]),
             "tgba_screen_create": (_I32, [_I32, _VP, ctypes.c_uint64, _P(_VP)]),
             "tgba_screen_nparams": (_I32, [_VP, _P(_I64)]),
@@ -241,6 +242,21 @@ def tgba_dsf(b, s, h_x, w_min, w_max, n_w, eta, S_out, evals_out=None, n_ev=0, w
         _cuda_tensor(t, torch.float64)
     _check(lib().tgba_dsf(b, s, float(h_x), float(w_min), float(w_max), int(n_w), float(eta), _ptr(S_out),
                           _ptr(evals_out), int(n_ev), _ptr(weights_out), _ptr(dE_out), _stream(stream)))
+
+
+def tgba_dsf_k(b, s, s0, h_x, w_min, w_max, n_w, eta, S_out, evals_out=None, n_ev=0, weights_out=None, dE_out=None,
+               stream=None):
+    """S(k, w) at the momentum of sector s; s0 is the k = 0 sector (ground state)."""
+    import torch
+    _cuda_tensor(S_out, torch.float32, n_w, name="S_out")
+    n = 0
+    if (weights_out is not None or dE_out is not None) and 0 <= s < tgba_basis_totals(b)[0]:
+        n = sum(tgba_sector_sizes(b)[s])
+    _cuda_tensor(evals_out, torch.float64, n_ev, name="evals_out")
+    _cuda_tensor(weights_out, torch.float64, n, name="weights_out")
+    _cuda_tensor(dE_out, torch.float64, n, name="dE_out")
+    _check(lib().tgba_dsf_k(b, int(s), int(s0), float(h_x), float(w_min), float(w_max), int(n_w), float(eta),
+                            _ptr(S_out), _ptr(evals_out), int(n_ev), _ptr(weights_out), _ptr(dE_out), _stream(stream)))
 
 
 def tgba_quench(b, s, h_z0, hx_variants, ecut_variants, t_max, n_t, mx_out, norm_out=None, method=0, stream=None):
