@@ -349,7 +349,7 @@ def run_gb300(args):
     if tri_mean > pf_mean:
         # the dominant kernel of the step: the cluster tridiagonalisation of the native solver
         tri_gflops = prof["tridiag_flops"] / (tri_mean * 1e-3) / 1e9
-        roofline = {"bound": "alu", "kernel": "sytrd_cluster (FP64 Householder tridiagonalisation)",
+        roofline = {"bound": "alu", "kernel": "sytrd_groups (FP64 Householder tridiagonalisation)",
                     "achieved": tri_gflops, "peak": peak_gflops, "unit": "GFLOP/s",
                     "frac": tri_gflops / peak_gflops, "traffic": None, "peak_source": peak_src,
                     "flops_per_launch": prof["tridiag_flops"], "ms": tri_mean,

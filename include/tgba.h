@@ -133,7 +133,8 @@ tgba_status tgba_assemble_heff(tgba_basis b, double h_x, tgba_screen screen, dou
  * matrix goes into one batched FP64 real symmetric solve.  method (tgba_eigvals_ex):
  *   0  automatic: 1 when every sector has at most 6400 states (rounded up to a multiple of
  *      32), else 2;
- *   1  native: Householder tridiagonalisation, one thread-block cluster per matrix, then
+ *   1  native: Householder tridiagonalisation, a group of CTAs per matrix (one cooperative
+ *      launch, SMs shared out by work), then
  *      bisection on Sturm counts (TGBA_EINVAL if a sector is too large);
  *   2  cuSOLVER XsyevBatched, each matrix padded to the largest sector size with decoupled
  *      diagonal entries above its Gershgorin bound.

@@ -3,22 +3,26 @@
 //
 // Two kernels per batch of (field, sector) matrices:
 //
-// 1. sytrd_cluster: Householder reduction to tridiagonal form, T = Q^T H Q.  A thread-block
-//    cluster of C CTAs (one per SM) owns one matrix and runs all n - 1 reflections in one
-//    launch.  Step j builds the reflector v_j from column j, then makes ONE pass over the
+// 1. sytrd_groups: Householder reduction to tridiagonal form, T = Q^T H Q.  One cooperative
+//    launch with one CTA per SM; the SMs are shared out among the matrices in proportion to
+//    their work (n^3), so a group of C CTAs (1 to 16) owns one matrix and runs all n - 1
+//    reflections.  (Hardware thread-block clusters were tried first: their placement left
+//    SMs idle, e.g. at most 46 clusters of 3 or 15 of 8 could be resident, so 48 matrices ran in
+//    two or more waves.)  Step j builds the reflector v_j from column j, then makes ONE pass over the
 //    trailing lower triangle that both applies the rank-2 update of step j - 1,
 //        A <- A - v_{j-1} w_{j-1}^T - w_{j-1} v_{j-1}^T,
 //    and accumulates the symmetric product y = A v_j for step j; so every trailing element is
 //    read and written once per step with four FMAs.  The trailing lower triangle is cut into
 //    blocks of 32 rows x 16 columns, numbered column group by column group, and warp w of the
-//    cluster's W warps takes the contiguous blocks [NB w / W, NB (w + 1) / W): equal work for
+//    group's W warps takes the contiguous blocks [NB w / W, NB (w + 1) / W): equal work for
 //    every warp, whatever the size of the trailing block.  In a block a lane owns one row: its
 //    row sum needs no communication, and its 16 column partial sums stay in registers over the
 //    warp's run of blocks in one column group, then one transpose-reduce (31 adds per lane)
 //    sums them over the warp.  Two block buffers in registers keep the next block's loads in
 //    flight during the current block's arithmetic.  Partials go to global buffers and are
-//    added in a fixed order, so results do not depend on scheduling.  The CTAs of a cluster
-//    meet at two hardware cluster barriers per step (no spin-waits).
+//    added in a fixed order, so results do not depend on scheduling.  The CTAs of a group meet
+//    at two barriers per step: an arrival counter in global memory with a bounded wait (a
+//    timeout sets an error bit and the kernel returns).
 // 2. sturm_bisect: every eigenvalue by bisection on the Sturm count of T - x, one thread per
 //    eigenvalue, with the scaled three-term determinant recurrence (three FP64 operations per
 //    row and no divisions; sign changes counted on the integer bits).
@@ -40,17 +44,18 @@ namespace {
 constexpr int kWarps = 12;                      // 3 per SM sub-partition
 constexpr int kThreads = kWarps * 32;
 constexpr int kCols = 16;                       // columns of a work block (rows: 32)
-constexpr int kMaxCluster = 8;
+constexpr int kMaxGroup = 16;                   // CTAs cooperating on one matrix
+constexpr unsigned kSpinLimit = 1u << 24;       // bounded barrier wait (>= 100 ns per poll: over 1 s)
 constexpr int kRed = 64;                        // reduction scratch (doubles) after the vectors
-constexpr int kMaxWarpsPerCluster = kWarps * kMaxCluster;
+constexpr int kMaxWarpsPerGroup = kWarps * kMaxGroup;
 constexpr int kMaxGroups = kMaxNativeLd / kCols;
 constexpr int kSturmThreads = 128;
 
 struct TriSlot {
   int64_t a_off;    // matrix, ld x ld in 32 x 16 tiles (blk_off), zero beyond n, lower triangle used
   int64_t rp_off;   // row sums of the 32 x 16 blocks [ld][ld / 16]: a row's partials contiguous
-  int64_t cp_off;   // column sums of each warp's blocks [warps of a cluster][ld]
-  int64_t p_off;    // p = tau A v [ld], then one dot partial per CTA of the cluster [8]
+  int64_t cp_off;   // column sums of each warp's blocks [warps of a group][ld]
+  int64_t p_off;    // p = tau A v [ld], then one dot partial per CTA of the group [16]
   int64_t de_off;   // diagonal d [n], off-diagonal e [n]
   int64_t out_off;  // first eigenvalue in the caller's output
   int32_t n, ld;
@@ -76,12 +81,43 @@ __device__ __forceinline__ int64_t elem_off(int i, int k, int LB) {
   return blk_off(k >> 4, i >> 5, LB) + (k & 15) * 32 + (i & 31);
 }
 
-__device__ __forceinline__ void cluster_barrier(int C) {
-  if (C == 1) {
-    __syncthreads();
-  } else {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+// Which CTAs work on which matrix: CTA b takes matrices first, first + stride, ... (each as
+// rank `rank` of a group of C CTAs).
+struct CtaWork {
+  int32_t first, rank, C, stride;
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Barrier of the C CTAs of one matrix (C = 1: the CTA barrier).  The group's counter counts
+// arrivals; the k-th barrier waits until it reaches k C.  Writes before the barrier are
+// published by the CTA barrier plus a GPU-scope fence before the arrival, and read after it
+// through L2.  The wait is bounded: on timeout it records kStTimeout and returns false, and
+// the kernel leaves the matrix (the other CTAs of the group then time out as well).
+__device__ __forceinline__ bool group_barrier(unsigned* cnt, unsigned target, int C, int* flag, unsigned* status) {
+  __syncthreads();
+  if (C == 1) return true;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(cnt, 1u);
+    int ok = 1;
+    for (unsigned it = 0; ld_acquire(cnt) < target; ++it) {
+      if (it > kSpinLimit) {
+        ok = 0;
+        atomicOr(status, kStTimeout);
+        break;
+      }
+      __nanosleep(100);
+    }
+    __threadfence();
+    *flag = ok;
   }
+  __syncthreads();
+  return *flag != 0;
 }
 
 // Sum over the block in a fixed order (lane 0 of each warp, then warps in order); every thread
@@ -212,11 +248,12 @@ __device__ __forceinline__ void sytrd_chunk(double* __restrict__ A, int ld, int 
   if (lane < kCols) __stcg(CP + (int64_t)w * ld + k0 + lane, colsum);
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
-sytrd_cluster(const TriSlot* __restrict__ slots, int C, double* __restrict__ ws, unsigned* __restrict__ status) {
+// All n - 1 reflections of one matrix, as CTA `rank` of its group of C.  Returns false if a
+// group barrier gave up.
+__device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsigned* cnt, double* __restrict__ ws,
+                                          unsigned* __restrict__ status, int* flag) {
   extern __shared__ double sm[];
-  const int q = blockIdx.x / C, rank = blockIdx.x - q * C;
-  const TriSlot S = slots[q];
+  unsigned arrivals = 0;
   const int n = S.n, ld = S.ld, LB = ld >> 5, G = ld / kCols;
   double* A = ws + S.a_off;
   double* RP = ws + S.rp_off;
@@ -229,7 +266,8 @@ sytrd_cluster(const TriSlot* __restrict__ slots, int C, double* __restrict__ ws,
   double2* vwn = (double2*)(sm + 2 * ld);         // (v_j, w_j)
   double* red = sm + 4 * ld;
   int* sw = (int*)(red + kRed);                   // [W + 1] first block of each warp
-  int* gw = sw + kMaxWarpsPerCluster + 1;         // [2 G] first and last warp meeting each group
+  int* gw = sw + kMaxWarpsPerGroup + 1;         // [2 G] first and last warp meeting each group
+  __syncthreads();                                // the previous matrix is done with sm
   for (int i = threadIdx.x; i < 4 * ld; i += kThreads) sm[i] = 0.0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -300,8 +338,9 @@ sytrd_cluster(const TriSlot* __restrict__ slots, int C, double* __restrict__ ws,
         }
       }
     }
-    cluster_barrier(C);
-    // rows j + 1 .. n - 1, interleaved over the cluster's CTAs (row i to CTA i mod C, so the
+    arrivals += C;
+    if (!group_barrier(cnt, arrivals, C, flag, status)) return false;
+    // rows j + 1 .. n - 1, interleaved over the group's CTAs (row i to CTA i mod C, so the
     // long rows at the bottom are shared): y_i = row sums of the blocks of groups g0 .. i/16
     // (contiguous, read with independent loads) + the column sums of the warps whose ranges
     // met column i's group; p = tau y
@@ -328,7 +367,8 @@ sytrd_cluster(const TriSlot* __restrict__ slots, int C, double* __restrict__ ws,
     }
     dot = block_sum(dot, red);
     if (threadIdx.x == 0) __stcg(dots + rank, dot);
-    cluster_barrier(C);
+    arrivals += C;
+    if (!group_barrier(cnt, arrivals, C, flag, status)) return false;
     double pv = 0.0;
     for (int r = 0; r < C; ++r) pv += __ldcg(dots + r);
     const double Kc = 0.5 * tau * pv;
@@ -338,6 +378,17 @@ sytrd_cluster(const TriSlot* __restrict__ slots, int C, double* __restrict__ ws,
     double2* t = vwp; vwp = vwn; vwn = t;
   }
   if (bad) atomicOr(status, kStEigen);
+  return true;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+sytrd_groups(const TriSlot* __restrict__ slots, int B, const CtaWork* __restrict__ work, unsigned* __restrict__ counters,
+             double* __restrict__ ws, unsigned* __restrict__ status) {
+  __shared__ int flag;
+  const CtaWork cw = work[blockIdx.x];
+  const int C = cw.C, rank = cw.rank;
+  for (int q = cw.first; q < B; q += cw.stride)
+    if (!sytrd_matrix(slots[q], C, rank, counters + q, ws, status, &flag)) return;
 }
 
 // Number of eigenvalues of T below x: sign changes of P_0 = 1, P_1, ..., P_n with
@@ -469,8 +520,8 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
       t.out_off = (int64_t)h * b.n_states + b.sectors[s].ev_off;
       t.a_off = total;            total += round32((int64_t)t.ld * t.ld);
       t.rp_off = total;           total += round32((int64_t)(t.ld / kCols) * t.ld);
-      t.cp_off = total;           total += round32((int64_t)kMaxWarpsPerCluster * t.ld);
-      t.p_off = total;            total += round32(t.ld + kMaxCluster);
+      t.cp_off = total;           total += round32((int64_t)kMaxWarpsPerGroup * t.ld);
+      t.p_off = total;            total += round32(t.ld + kMaxGroup);
       t.de_off = total;           total += round32(2 * n);
       slots.push_back(t);
       who.emplace_back(h, (int)s);
@@ -481,44 +532,74 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
   int ld_max = 0;
   for (const TriSlot& t : slots) ld_max = std::max(ld_max, t.ld);
   if (ld_max > kMaxNativeLd) return fail(TGBA_EINVAL, "sector too large for the native eigen-solver");
-  const int64_t slot_doubles = round32(((int64_t)B * sizeof(TriSlot) + 7) / 8);
-  double* ws;
-  tgba_status r = scratch(b, total + slot_doubles, &ws);
-  if (r != TGBA_OK) return r;
-  TriSlot* d_slots = (TriSlot*)(ws + total);
-  TGBA_CUDA(cudaMemcpyAsync(d_slots, slots.data(), B * sizeof(TriSlot), cudaMemcpyHostToDevice, st));
-  for (int q = 0; q < B; ++q) {
-    const Sector& sec = b.sectors[who[q].second];
-    const int64_t work = (int64_t)slots[q].ld * slots[q].ld;
-    const int grid = (int)std::min<int64_t>((work + 255) / 256, 152 * 16);
-    fill_sym<<<grid, 256, 0, st>>>(sec.n_ns, sec.n_r, slots[q].ld, b.d_E_ns + sec.ns_off, b.d_E_r + sec.r_off,
-                                   b.d_P + sec.x_off, b.d_c0, -b.L * hx[who[q].first], ws + slots[q].a_off);
-    TGBA_CUDA(cudaGetLastError());
-    ++b.launches;
-  }
   int dev = 0, sms = 0;
   TGBA_CUDA(cudaGetDevice(&dev));
   TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int C = std::max(1, std::min(kMaxCluster, sms / B));
+  // One CTA per SM.  With no more matrices than SMs, every SM joins one matrix's group: each
+  // matrix starts with one CTA and the remaining CTAs go, one at a time, to the matrix with the
+  // most work (n^3) per CTA, at most 16 per matrix.  With more matrices than SMs, CTA b takes
+  // matrices b, b + SMs, ... alone.
+  std::vector<CtaWork> map;
+  int C_max = 1;
+  if (B <= sms) {
+    std::vector<int> Cq(B, 1);
+    for (int left = sms - B; left > 0; --left) {
+      int best = -1;
+      double best_w = -1.0;
+      for (int q = 0; q < B; ++q) {
+        const double w = (double)slots[q].n * slots[q].n * slots[q].n / Cq[q];
+        if (Cq[q] < kMaxGroup && w > best_w) { best_w = w; best = q; }
+      }
+      if (best < 0) break;
+      ++Cq[best];
+    }
+    for (int q = 0; q < B; ++q) {
+      for (int r = 0; r < Cq[q]; ++r) map.push_back({q, r, Cq[q], B});
+      C_max = std::max(C_max, Cq[q]);
+    }
+  } else {
+    for (int q = 0; q < sms; ++q) map.push_back({q, 0, 1, sms});
+  }
+  const int grid = (int)map.size();
+  const int64_t slot_doubles = round32(((int64_t)B * sizeof(TriSlot) + 7) / 8);
+  const int64_t map_doubles = round32(((int64_t)grid * sizeof(CtaWork) + 7) / 8);
+  const int64_t cnt_doubles = round32((B + 1) / 2);
+  double* ws;
+  tgba_status r = scratch(b, total + slot_doubles + map_doubles + cnt_doubles, &ws);
+  if (r != TGBA_OK) return r;
+  TriSlot* d_slots = (TriSlot*)(ws + total);
+  CtaWork* d_map = (CtaWork*)(ws + total + slot_doubles);
+  unsigned* d_cnt = (unsigned*)(ws + total + slot_doubles + map_doubles);
+  TGBA_CUDA(cudaMemcpyAsync(d_slots, slots.data(), B * sizeof(TriSlot), cudaMemcpyHostToDevice, st));
+  TGBA_CUDA(cudaMemcpyAsync(d_map, map.data(), grid * sizeof(CtaWork), cudaMemcpyHostToDevice, st));
+  TGBA_CUDA(cudaMemsetAsync(d_cnt, 0, B * sizeof(unsigned), st));
+  for (int q = 0; q < B; ++q) {
+    const Sector& sec = b.sectors[who[q].second];
+    const int64_t work = (int64_t)slots[q].ld * slots[q].ld;
+    const int fgrid = (int)std::min<int64_t>((work + 255) / 256, 152 * 16);
+    fill_sym<<<fgrid, 256, 0, st>>>(sec.n_ns, sec.n_r, slots[q].ld, b.d_E_ns + sec.ns_off, b.d_E_r + sec.r_off,
+                                    b.d_P + sec.x_off, b.d_c0, -b.L * hx[who[q].first], ws + slots[q].a_off);
+    TGBA_CUDA(cudaGetLastError());
+    ++b.launches;
+  }
   const size_t smem = (size_t)(4 * ld_max + kRed) * sizeof(double) +
-                      (size_t)(kMaxWarpsPerCluster + 1 + 2 * kMaxGroups) * sizeof(int);
-  TGBA_CUDA(cudaFuncSetAttribute(sytrd_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                      (size_t)(kMaxWarpsPerGroup + 1 + 2 * kMaxGroups) * sizeof(int);
+  TGBA_CUDA(cudaFuncSetAttribute(sytrd_groups, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(B * C));
+  cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)C;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
+  attr[0].id = cudaLaunchAttributeCooperative;   // all CTAs resident at once: the group barriers rely on it
+  attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   for (int e = 0; e < 3; ++e)
     if (b.eig_ev[e] == nullptr) TGBA_CUDA(cudaEventCreate(&b.eig_ev[e]));
   TGBA_CUDA(cudaEventRecord(b.eig_ev[0], st));
-  TGBA_CUDA(cudaLaunchKernelEx(&cfg, sytrd_cluster, (const TriSlot*)d_slots, C, ws, b.d_status));
+  TGBA_CUDA(cudaLaunchKernelEx(&cfg, sytrd_groups, (const TriSlot*)d_slots, B, (const CtaWork*)d_map, d_cnt, ws,
+                               b.d_status));
   ++b.launches;
   TGBA_CUDA(cudaEventRecord(b.eig_ev[1], st));
   const size_t smem2 = (size_t)2 * n_max * sizeof(double);
@@ -534,7 +615,7 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
     for (int64_t m = 1; m < t.n; ++m) flops += 4.0 * m * (m + 1);
   b.tridiag_flops = flops;
   b.eig_matrices = B;
-  b.eig_cluster = C;
+  b.eig_cluster = C_max;
   return TGBA_OK;
 }
 

@@ -1,8 +1,9 @@
 """Native batched eigenvalue solver (Householder tridiagonalisation by thread-block clusters,
 then bisection on Sturm counts) through the C ABI, against exact diagonalisation of the spin
 chain (Eq. 1 on a complete basis), against LAPACK on the same H_eff (Eq. 2) and against the
-library solver.  The batch size decides the cluster size (1 to 8 CTAs per matrix), so the
-cases below cover one, several and all-single-CTA launches."""
+library solver.  The batch size decides how many CTAs share a matrix (up to 16; a single CTA
+looping over matrices when there are more matrices than SMs), so the cases below cover one,
+several and more-than-SMs batches."""
 import numpy as np
 import pytest
 import torch
@@ -65,7 +66,8 @@ def test_native_complete_basis_equals_ed(L, fields):
 
 
 def test_native_single_matrix_and_full_batch_match_library():
-    """One matrix (a cluster of 8 CTAs) and 156 matrices (one CTA each) against cuSOLVER."""
+    """One matrix (a group of 16 CTAs) and 156 matrices (more than the 152 SMs: single CTAs that
+    loop over matrices) against cuSOLVER."""
     L, h = 12, 1.0
     b = tgba.tgba_build_basis(L, h, [0], L)
     try:
