@@ -25,7 +25,8 @@
 //    timeout sets an error bit and the kernel returns).
 // 2. sturm_bisect: every eigenvalue by bisection on the Sturm count of T - x, one thread per
 //    eigenvalue, with the scaled three-term determinant recurrence (three FP64 operations per
-//    row and no divisions; sign changes counted on the integer bits).
+//    row and no divisions; sign changes counted on the integer bits), starting from a
+//    128-point grid of counts shared by the block.
 //
 // FP64 throughput on this GPU is 1/64 of FP32, so the design counts FP64 instructions: the
 // reduction is 4 FMAs per trailing element per step (4n^3/3 flops per matrix); selects, masks,
@@ -392,20 +393,27 @@ sytrd_groups(const TriSlot* __restrict__ slots, int B, const CtaWork* __restrict
 }
 
 // Number of eigenvalues of T below x: sign changes of P_0 = 1, P_1, ..., P_n with
-// P_{i+1} = (d_i - x) P_i - e_{i-1}^2 P_{i-1}.  A zero P_i is replaced by a tiny value of the
-// sign opposite to P_{i-1} (the analogue of a negative pivot floor in the ratio form).  Every
-// 8 rows both terms are rescaled by the power of two that brings the larger to [1, 2).
+// P_{i+1} = (d_i - x) P_i - e_{i-1}^2 P_{i-1}.  A zero P_i is replaced by the smallest normal
+// number with the sign opposite to P_{i-1} (the analogue of a negative pivot floor in the ratio
+// form), built from integer bits so the FP64 pipe sees only the three operations of the
+// recurrence.  Every 8 rows both terms are rescaled by the power of two that brings the larger
+// to [1, 2).
+__device__ __forceinline__ double nonzero_or_flip(double pn, double pc) {
+  const bool z = ((unsigned long long)__double_as_longlong(pn) << 1) == 0ull;
+  const int hi = z ? (int)((~(unsigned)__double2hiint(pc) & 0x80000000u) | 0x00100000u) : __double2hiint(pn);
+  const int lo = z ? 0 : __double2loint(pn);
+  return __hiloint2double(hi, lo);
+}
+
 __device__ __forceinline__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e2, int n,
                                            double x) {
-  double pm = 1.0, pc = d[0] - x;
-  if (((unsigned long long)__double_as_longlong(pc) << 1) == 0ull) pc = -0x1p-60;
+  double pm = 1.0, pc = nonzero_or_flip(d[0] - x, 1.0);
   int cnt = (int)((unsigned)__double2hiint(pc) >> 31);
   int i = 1;
   for (; i + 8 <= n; i += 8) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      double pn = fma(d[i + u] - x, pc, -e2[i + u - 1] * pm);
-      if (((unsigned long long)__double_as_longlong(pn) << 1) == 0ull) pn = pc * -0x1p-60;
+      const double pn = nonzero_or_flip(fma(d[i + u] - x, pc, -e2[i + u - 1] * pm), pc);
       cnt += (int)((unsigned)(__double2hiint(pn) ^ __double2hiint(pc)) >> 31);
       pm = pc;
       pc = pn;
@@ -416,8 +424,7 @@ __device__ __forceinline__ int sturm_count(const double* __restrict__ d, const d
     pc *= sc;
   }
   for (; i < n; ++i) {
-    double pn = fma(d[i] - x, pc, -e2[i - 1] * pm);
-    if (((unsigned long long)__double_as_longlong(pn) << 1) == 0ull) pn = pc * -0x1p-60;
+    const double pn = nonzero_or_flip(fma(d[i] - x, pc, -e2[i - 1] * pm), pc);
     cnt += (int)((unsigned)(__double2hiint(pn) ^ __double2hiint(pc)) >> 31);
     pm = pc;
     pc = pn;
@@ -430,6 +437,7 @@ sturm_bisect(const TriSlot* __restrict__ slots, const double* __restrict__ ws, d
              unsigned* __restrict__ status) {
   extern __shared__ double sm[];
   __shared__ double red[2 * (kSturmThreads / 32)];
+  __shared__ int grid_cnt[kSturmThreads];
   const TriSlot S = slots[blockIdx.y];
   const int n = S.n;
   if ((int)blockIdx.x * kSturmThreads >= n) return;     // block-uniform
@@ -457,16 +465,28 @@ sturm_bisect(const TriSlot* __restrict__ slots, const double* __restrict__ ws, d
   hi = red[kSturmThreads / 32];
   for (int w = 1; w < kSturmThreads / 32; ++w) { lo = fmin(lo, red[w]); hi = fmax(hi, red[kSturmThreads / 32 + w]); }
   const int k = blockIdx.x * kSturmThreads + threadIdx.x;
-  if (k >= n) return;
-  if (!(isfinite(lo) && isfinite(hi))) {
+  if (!(isfinite(lo) && isfinite(hi))) {                    // block-uniform
     if (threadIdx.x == 0) atomicOr(status, kStEigen);
-    evals[S.out_off + k] = __longlong_as_double(0x7ff8000000000000ll);
+    if (k < n) evals[S.out_off + k] = __longlong_as_double(0x7ff8000000000000ll);
     return;
   }
   const double tnorm = fmax(fabs(lo), fabs(hi));
   const double eps = 0x1p-53;
   const double fudge = 4.0 * eps * n * tnorm + 0x1p-1000;   // widen the Gershgorin interval
   double a = lo - fudge, b = hi + fudge;                    // count(a) <= k < count(b)
+  // a shared first level: the block's threads count at kSturmThreads - 1 interior points of
+  // [a, b], and every eigenvalue starts from the grid cell that holds it
+  const double step = (b - a) / kSturmThreads;
+  if (threadIdx.x > 0) grid_cnt[threadIdx.x] = sturm_count(d, e2, n, a + step * threadIdx.x);
+  __syncthreads();
+  {
+    int c = 1;
+    while (c < kSturmThreads && grid_cnt[c] <= k) ++c;   // grid_cnt is non-decreasing in c
+    const double a1 = c > 1 ? a + step * (c - 1) : a, b1 = c < kSturmThreads ? a + step * c : b;
+    a = a1;
+    b = b1;
+  }
+  if (k >= n) return;
   const double tol = 4.0 * eps * tnorm + 0x1p-1000;
   for (int it = 0; it < 200 && b - a > tol; ++it) {
     const double mid = 0.5 * (a + b);
