@@ -149,3 +149,41 @@ def quench(N, h, h0, h_x, max_qp, e_cut, t_max, n_t, max_per_parity=None, n_thre
     t = time_grid(t_max, n_t)
     B = quench_coefficients(E, U, c0, t)
     return t, magnetisation(B, x_full(X), c0), c0
+
+
+def ordered_subspaces(ns, r, c0, order, sizes):
+    """Nested truncated subspaces of one sector (the Quench section's construction).  order 0:
+    states by bare energy; order 1: by |<phi|Phi0>| (largest first), ties by energy.  Returns
+    the state ranking (NS indices 0..len(ns)-1, R indices len(ns)..) and, for each size chi, the
+    first chi states of it."""
+    E = np.array([x.E for x in ns] + [x.E for x in r])
+    key = (E,) if order == 0 else (E, -np.abs(c0))
+    rank = np.lexsort(key)                       # last key is the primary one
+    return rank, [rank[:chi] for chi in sizes]
+
+
+def quench_ordered(N, h, h0, h_x, max_qp, e_cut, order, sizes, t_max, n_t, n_threads=0):
+    """<sigma^x>(t), the retained weight sum |c0|^2 and the convergence metric of Eq. 11,
+    eps(chi', chi) = max_t || Psi^chi(t) - Psi^chi'(t) ||, for successive nested truncations
+    chi_1 < chi_2 < ... of the k = 0 sector (basis: M <= max_qp, E below e_cut), ordered by
+    energy (order 0) or by the overlap with the initial state (order 1).  Returns
+    (t, mx [len(sizes)][n_t], norm2 [len(sizes)], eps [len(sizes) - 1])."""
+    ns, r, X = sector(N, h, 0, max_qp, e_cut, None, n_threads)
+    c0 = initial_overlaps(N, h, h0, ns, r, n_threads)
+    Hf = heff(ns, r, X, N, h_x)
+    Xf = x_full(X)
+    t = time_grid(t_max, n_t)
+    _, subsets = ordered_subspaces(ns, r, c0, order, sizes)
+    mx, nrm, Bs = [], [], []
+    for keep in subsets:
+        E, U = eigh(Hf[np.ix_(keep, keep)])
+        c = c0[keep]
+        B = quench_coefficients(E, U, c, t)
+        mx.append(magnetisation(B, Xf[np.ix_(keep, keep)], c))
+        nrm.append(float(np.vdot(c, c).real))
+        full = np.zeros((len(c0), len(t)), dtype=np.complex128)    # B in the whole candidate basis
+        full[keep] = B
+        Bs.append(full)
+    eps = [float(np.sqrt((np.abs(Bs[v + 1] - Bs[v]) ** 2).sum(axis=0)).max()) for v in range(len(sizes) - 1)]
+    return t, np.array(mx), np.array(nrm), np.array(eps)
+
