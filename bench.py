@@ -42,6 +42,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-budget-s", type=float, default=12.0)
     p.add_argument("--no-screening", action="store_true")
+    p.add_argument("--no-solver-comparison", action="store_true",
+                   help="skip the one-off native vs cuSOLVER eigen-solver timing after the timed steps")
     return p.parse_args()
 
 
@@ -390,7 +392,8 @@ def run_gb300(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": n_states * 8 * len(w.h_x)},
             "gpu_launches": launches}
-    line["eigen_solver"] = eigen_solver_leg(b, w, evs, tgba, torch)
+    if not args.no_solver_comparison:
+        line["eigen_solver"] = eigen_solver_leg(b, w, evs, tgba, torch)
     if not args.no_screening:
         line["screening"] = screening_leg(b, tgba, inputs, torch)
     tgba.tgba_basis_free(b)
