@@ -151,14 +151,25 @@ def quench(N, h, h0, h_x, max_qp, e_cut, t_max, n_t, max_per_parity=None, n_thre
     return t, magnetisation(B, x_full(X), c0), c0
 
 
-def ordered_subspaces(ns, r, c0, order, sizes):
-    """Nested truncated subspaces of one sector (the Quench section's construction).  order 0:
-    states by bare energy; order 1: by |<phi|Phi0>| (largest first), ties by energy.  Returns
-    the state ranking (NS indices 0..len(ns)-1, R indices len(ns)..) and, for each size chi, the
-    first chi states of it."""
-    E = np.array([x.E for x in ns] + [x.E for x in r])
-    key = (E,) if order == 0 else (E, -np.abs(c0))
-    rank = np.lexsort(key)                       # last key is the primary one
+def ranking_key(state, c0_abs, e_ref, order):
+    """Sort key of a basis state for the truncated subspace (the Quench section).  order 1:
+    |<phi|Phi0>| largest first, then energy; order 0: energy.  The values are quantised
+    (|c0| to 1e-10, E - e_ref to 1e-9) so that exact ties (zero overlaps of states whose momenta
+    are not (-k, k) pairs, degenerate energies) do not depend on rounding; they are broken by
+    (parity, M, modes)."""
+    a = int(round(c0_abs * 1e10))
+    e = int(round((state.E - e_ref) * 1e9))
+    tail = (state.parity, state.M, tuple(state.modes))
+    return ((-a, e) if order == 1 else (e,)) + tail
+
+
+def ordered_subspaces(ns, r, c0, order, sizes, e_ref=0.0):
+    """Nested truncated subspaces of one sector.  Returns the state ranking (NS indices
+    0..len(ns)-1, R indices len(ns)..) by ranking_key and, for each size chi, the first chi
+    states of it."""
+    states = list(ns) + list(r)
+    rank = np.array(sorted(range(len(states)), key=lambda i: ranking_key(states[i], abs(c0[i]), e_ref, order)),
+                    dtype=np.int64)
     return rank, [rank[:chi] for chi in sizes]
 
 
@@ -173,7 +184,7 @@ def quench_ordered(N, h, h0, h_x, max_qp, e_cut, order, sizes, t_max, n_t, n_thr
     Hf = heff(ns, r, X, N, h_x)
     Xf = x_full(X)
     t = time_grid(t_max, n_t)
-    _, subsets = ordered_subspaces(ns, r, c0, order, sizes)
+    _, subsets = ordered_subspaces(ns, r, c0, order, sizes, md.vacuum_energy(N, md.NS, h))
     mx, nrm, Bs = [], [], []
     for keep in subsets:
         E, U = eigh(Hf[np.ix_(keep, keep)])

@@ -14,9 +14,10 @@ def test_overlap_order_keeps_the_largest_overlaps_first():
     ns, r, X = otgba.sector(L, h, 0, mq)
     c0 = otgba.initial_overlaps(L, h, h0, ns, r)
     rank, (first,) = otgba.ordered_subspaces(ns, r, c0, 1, [20])
+    a_all = np.abs(c0)
     a = np.abs(c0[rank])
-    assert np.all(np.diff(a) <= 1e-15)                  # non-increasing overlaps
-    assert a[0] > 0.5 and np.abs(c0[first]).min() >= np.abs(c0[rank[20:]]).max() - 1e-15
+    assert np.all(np.diff(a) <= 1e-10)                  # non-increasing overlaps (to the key's quantum)
+    assert a[0] > 0.5 and np.abs(c0[first]).min() >= np.abs(c0[rank[20:]]).max() - 1e-10
 
 
 def test_eps_bounds_at_t0_and_norm():
