@@ -111,6 +111,17 @@ tgba_status tgba_x_export(tgba_basis b, int32_t s, double* x_dev, void* stream);
 tgba_status tgba_x_pairs(tgba_basis b, int32_t s, const int32_t* pairs_dev, int64_t n_pairs,
                          double* out_dev, void* stream);
 
+/* X for explicit pairs, as tgba_x_pairs, but evaluated the paper-literal way (Appendix A,
+   Eq. S1-S2): the vacuum expectation of the whole string of 2L + M_a + M_b Bogoliubov operators
+   (both vacua, the excitations and sigma^x_1, expanded on the lattice sites), one complex
+   Pfaffian of that size per element, a CTA each.  O((2L)^3) per element instead of the
+   reduced form's O((M_a + M_b)^3): a GPU cross-check of tgba_x_pairs and an FP64-dense workload.
+   Needs the dense 2L + 2 max_qp string in shared memory: TGBA_EINVAL when it does not fit
+   (e.g. L = 32 with max_qp = 16 fits, L = 60 does not).  Pair and output layout, index checks
+   as tgba_x_pairs; blocks on `stream`. */
+tgba_status tgba_x_direct(tgba_basis b, int32_t s, const int32_t* pairs_dev, int64_t n_pairs, double* out_dev,
+                          void* stream);
+
 /* Contraction table and vacuum element: c0_host (complex, 2 doubles) receives
    C0 = <0_NS|c_1 + c_1^dag|0_R>; table_dev (optional, 2L x 2L doubles row-major) receives the
    real table R.  Blocks on `stream`. */
@@ -184,6 +195,21 @@ tgba_status tgba_dsf_k(tgba_basis b, int32_t s, int32_t s0, double h_x, double w
 tgba_status tgba_quench(tgba_basis b, int32_t s, double h_z0, const double* hx_variants,
                         const double* ecut_variants, int32_t n_variants, double t_max, int32_t n_t, int32_t method,
                         double* mx_dev, double* norm_dev, int64_t* chi_host, void* stream);
+
+/* The quench with the paper's choice of truncated subspace (the Quench section): the states of
+   the k = 0 sector s are ranked by bare energy (order 0) or by |<phi|Phi0>|, largest first, ties
+   by energy (order 1), and variant v keeps, in this ranking, the states with
+   E - E_NS,vac <= trunc_variants[v] (order 0; a negative value keeps all) or the first
+   trunc_variants[v] states (order 1; a whole number >= 1).  mx_dev, norm_dev, chi_host as in
+   tgba_quench.  eps_dev (optional, device, n_variants - 1 doubles): the convergence metric of
+   Eq. 11, eps(chi_{v+1}, chi_v) = max over the time grid of || Psi^{chi_v}(t) -
+   Psi^{chi_{v+1}}(t) ||; it needs nested variants (non-decreasing trunc_variants, else
+   TGBA_EINVAL) and the eigendecomposition path (method 1, or method 0 with at most 4096 states
+   per variant).  tgba_quench is order 0 without eps.  Blocks on `stream`. */
+tgba_status tgba_quench_ordered(tgba_basis b, int32_t s, double h_z0, const double* hx_variants,
+                                const double* trunc_variants, int32_t n_variants, int32_t order, double t_max,
+                                int32_t n_t, int32_t method, double* mx_dev, double* norm_dev, double* eps_dev,
+                                int64_t* chi_host, void* stream);
 
 /* ---------------------------------------------------------------- learned pair screener
  * Not in the paper (the paper has no counterpart): a 3-layer MLP (width 256, ReLU, FP32

@@ -369,6 +369,22 @@ tgba_status tgba_x_pairs(tgba_basis h, int32_t s, const int32_t* pairs_dev, int6
   return check_status(*b, st);
 }
 
+tgba_status tgba_x_direct(tgba_basis h, int32_t s, const int32_t* pairs_dev, int64_t n_pairs, double* out_dev,
+                          void* stream) {
+  Basis* b = (Basis*)h;
+  BASIS_OK(b);
+  if (s < 0 || s >= (int)b->sectors.size()) return fail(TGBA_EINVAL, "sector index out of range");
+  if (n_pairs < 0 || (n_pairs > 0 && (!pairs_dev || !out_dev))) return fail(TGBA_EINVAL, "bad pair list");
+  int limit = 0;
+  TGBA_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+  if (x_direct_smem(b->L, b->max_qp) + 8192 > (size_t)limit)
+    return fail(TGBA_EINVAL, "the direct Pfaffian of size 2L + 2 max_qp does not fit in shared memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  tgba_status r = x_direct(*b, s, pairs_dev, n_pairs, out_dev, st);
+  if (r != TGBA_OK) return r;
+  return check_status(*b, st);
+}
+
 tgba_status tgba_table(tgba_basis h, double* c0_host, double* table_dev, void* stream) {
   Basis* b = (Basis*)h;
   BASIS_OK(b);
@@ -462,8 +478,39 @@ tgba_status tgba_quench(tgba_basis h, int32_t s, double h_z0, const double* hx_v
   if (!b->x_valid) return fail(TGBA_EINVAL, "no X computed yet: call tgba_compute_x");
   tgba_status r = ensure_c0_host(*b, (cudaStream_t)stream);
   if (r != TGBA_OK) return r;
-  return quench(*b, s, h_z0, hx_variants, ecut_variants, n_variants, t_max, n_t, method, mx_dev, norm_dev, chi_host,
-                (cudaStream_t)stream);
+  return quench(*b, s, h_z0, hx_variants, ecut_variants, n_variants, 0, t_max, n_t, method, mx_dev, norm_dev, nullptr,
+                chi_host, (cudaStream_t)stream);
+}
+
+tgba_status tgba_quench_ordered(tgba_basis h, int32_t s, double h_z0, const double* hx_variants,
+                                const double* trunc_variants, int32_t n_variants, int32_t order, double t_max,
+                                int32_t n_t, int32_t method, double* mx_dev, double* norm_dev, double* eps_dev,
+                                int64_t* chi_host, void* stream) {
+  Basis* b = (Basis*)h;
+  BASIS_OK(b);
+  if (s < 0 || s >= (int)b->sectors.size()) return fail(TGBA_EINVAL, "sector index out of range");
+  if (b->sectors[s].m != 0) return fail(TGBA_EINVAL, "the quench needs the k = 0 sector");
+  if (n_variants < 1 || !hx_variants || !trunc_variants || !mx_dev || n_t < 1)
+    return fail(TGBA_EINVAL, "need variants, n_t >= 1 and an output buffer");
+  if (!(h_z0 > 0) || !std::isfinite(t_max) || t_max < 0) return fail(TGBA_EINVAL, "need h_z0 > 0 and t_max >= 0");
+  if (method < 0 || method > 2) return fail(TGBA_EINVAL, "method must be 0 (automatic), 1 (eigen) or 2 (Chebyshev)");
+  if (order != 0 && order != 1) return fail(TGBA_EINVAL, "order must be 0 (energy) or 1 (overlap)");
+  for (int v = 0; v < n_variants; ++v) {
+    if (!std::isfinite(hx_variants[v]) || !std::isfinite(trunc_variants[v])) return fail(TGBA_EINVAL, "non-finite variant");
+    if (order == 1 && !(trunc_variants[v] >= 1 && trunc_variants[v] == std::floor(trunc_variants[v])))
+      return fail(TGBA_EINVAL, "with order 1 each variant is a whole number of states >= 1");
+  }
+  if (eps_dev)
+    for (int v = 0; v + 1 < n_variants; ++v) {
+      const double a = trunc_variants[v], c = trunc_variants[v + 1];
+      const bool nested = order == 1 ? a <= c : (c < 0 || (a >= 0 && a <= c));
+      if (!nested) return fail(TGBA_EINVAL, "the convergence metric needs nested variants (non-decreasing truncation)");
+    }
+  if (!b->x_valid) return fail(TGBA_EINVAL, "no X computed yet: call tgba_compute_x");
+  tgba_status r = ensure_c0_host(*b, (cudaStream_t)stream);
+  if (r != TGBA_OK) return r;
+  return quench(*b, s, h_z0, hx_variants, trunc_variants, n_variants, order, t_max, n_t, method, mx_dev, norm_dev,
+                eps_dev, chi_host, (cudaStream_t)stream);
 }
 
 tgba_status tgba_screen_create(int32_t width, const float* params_host, uint64_t seed, tgba_screen* out) {

@@ -10,7 +10,9 @@
 //   a = U~^T c~0,  B~(t) = U~ (e^{-iEt} a),  <sigma^x>(t) = B~^H X~ B~ / ||c0||^2,
 // which is Eq. 10's B(t) = M^T e^{-iEt} M^* c0 up to the diagonal change of phase.  The two
 // products per block of times are FP64 GEMMs (cuBLAS); the overlaps, phases and the final
-// quadratic form are kernels of this file.
+// quadratic form are kernels of this file.  The truncated subspace is the first chi states of
+// the sector in energy or in overlap order (the Quench section), and successive nested
+// truncations give the convergence metric of Eq. 11.
 #include <cublas_v2.h>
 
 #include <algorithm>
@@ -144,6 +146,37 @@ __global__ void gersh_cols(int64_t kn, int64_t kr, const double* __restrict__ Q,
   }
 }
 
+// Eq. 11 at each time t: || Psi^chi(t) - Psi^chi'(t) ||^2 = sum over the larger subspace of
+// |B'_a - B_a|^2 (B_a = 0 for states the smaller one lacks).  The smaller subspace's NS and R
+// lists are prefixes of the larger one's (nested truncations in one ranking).  B, B': [Re | Im]
+// blocks of n x n_t, column-major.  The maximum over t goes to *out (bits of a non-negative
+// double, so the integer maximum is the numerical one).
+__global__ void eps_kernel(int n_t, int64_t knp, int64_t krp, int64_t kn, int64_t kr, const double* __restrict__ Bp,
+                           const double* __restrict__ Bc, unsigned long long* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t np = knp + krp, nc = kn + kr;
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n_t;
+       t += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    double acc = 0.0;
+    for (int64_t i = lane; i < nc; i += 32) {
+      double dre = Bc[i + t * nc], dim = Bc[i + (n_t + t) * nc];
+      int64_t ip = -1;
+      if (i < kn) {
+        if (i < knp) ip = i;
+      } else if (i - kn < krp) {
+        ip = knp + (i - kn);
+      }
+      if (ip >= 0) {
+        dre -= Bp[ip + t * np];
+        dim -= Bp[ip + (n_t + t) * np];
+      }
+      acc = fma(dre, dre, fma(dim, dim, acc));
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) atomicMax(out, (unsigned long long)__double_as_longlong(sqrt(acc)));
+  }
+}
+
 __global__ void gather_energy(int64_t kn, int64_t kr, const int32_t* __restrict__ idx_ns, const int32_t* __restrict__ idx_r,
                               const double* __restrict__ E_ns, const double* __restrict__ E_r, double* __restrict__ E) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < kn + kr; i += (int64_t)gridDim.x * blockDim.x)
@@ -256,8 +289,8 @@ static double ord_val_host(unsigned long long k) {
   return d;
 }
 
-tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* ecut, int nv, double t_max, int n_t,
-                   int method, double* mx, double* norm_out, int64_t* chi_out, cudaStream_t st) {
+tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* trunc, int nv, int order, double t_max,
+                   int n_t, int method, double* mx, double* norm_out, double* eps_out, int64_t* chi_out, cudaStream_t st) {
   const Sector& sec = b.sectors[s];
   const int L = b.L;
   // s = conj(z)/|z|, z = <0_NS(h0)|sigma_1|0_R(h0)>: the vacuum element of a table at h0
@@ -313,16 +346,104 @@ tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* e
   cublasSetStream(bh, st);
   const double e_ns = b.e_ns_vac * b.J;
   const double one = 1.0, zero = 0.0;
+  // Ranking of the sector's states (the Quench section's construction of the truncated
+  // subspace): order 0 by bare energy, order 1 by |<phi|Phi0>| (largest first), ties by energy
+  // and then index.  Variant v keeps, in this ranking, the states below its cutoff (order 0) or
+  // its first chi_v states (order 1); nested variants then have NS and R lists that are
+  // prefixes of each other.
+  const int64_t n_all = sec.n_ns + sec.n_r;
+  auto energy = [&](int64_t q) { return q < sec.n_ns ? b.ns.E[sec.ns_off + q] : b.r.E[sec.r_off + q - sec.n_ns]; };
+  std::vector<double> absc(n_all, 0.0);
+  if (order == 1 && n_all > 0) {
+    const int64_t need = 2 * n_all + 8 + 2 * L + (n_all + 2) / 2 + 8;
+    double* sc;
+    tgba_status r = scratch(b, need, &sc);
+    if (r != TGBA_OK) return r;
+    double* c = sc;
+    double* norm2 = c + 2 * n_all;
+    double* dth_dev = norm2 + 8;
+    int32_t* idx = (int32_t*)(dth_dev + 2 * L);
+    std::vector<int32_t> all(n_all);
+    for (int64_t q = 0; q < sec.n_ns; ++q) all[q] = (int32_t)q;
+    for (int64_t q = 0; q < sec.n_r; ++q) all[sec.n_ns + q] = (int32_t)q;
+    TGBA_CUDA(cudaMemcpyAsync(dth_dev, dth.data(), 2 * L * sizeof(double), cudaMemcpyHostToDevice, st));
+    TGBA_CUDA(cudaMemcpyAsync(idx, all.data(), n_all * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    overlap_kernel<<<blocks_for(n_all), 256, 0, st>>>(sec.n_ns, sec.n_r, idx, idx + sec.n_ns, sec.ns_off, sec.r_off,
+                                                     b.d_M_ns, b.d_M_r, b.d_modes_ns, b.d_modes_r, b.max_qp, b.d_nlab,
+                                                     dth_dev, base[0], base[1], s_re, s_im, g_re, g_im, L, c, norm2);
+    TGBA_CUDA(cudaGetLastError());
+    ++b.launches;
+    std::vector<double> ch(2 * n_all);
+    TGBA_CUDA(cudaMemcpyAsync(ch.data(), c, 2 * n_all * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TGBA_CUDA(cudaStreamSynchronize(st));
+    for (int64_t q = 0; q < n_all; ++q) absc[q] = std::hypot(ch[2 * q], ch[2 * q + 1]);
+  }
+  // Sort key: |c0| quantised to 1e-10 (largest first; order 1 only), E - E_NS,vac quantised to
+  // 1e-9, then (parity, M, modes): exact ties (the zero overlaps of states whose momenta are not
+  // (-k, k) pairs, degenerate energies) are broken the same way whatever the rounding.
+  struct Key {
+    long long a, e;
+    int parity, M;
+    const int16_t* modes;
+  };
+  std::vector<Key> keys(n_all);
+  for (int64_t q = 0; q < n_all; ++q) {
+    const bool ns = q < sec.n_ns;
+    const int64_t g = ns ? sec.ns_off + q : sec.r_off + (q - sec.n_ns);
+    const int16_t* md = (ns ? b.ns.modes.data() : b.r.modes.data()) + g * b.max_qp;
+    int M = 0;
+    while (M < b.max_qp && md[M] >= 0) ++M;
+    keys[q] = {order == 1 ? -std::llround(absc[q] * 1e10) : 0, std::llround((energy(q) - e_ns) * 1e9), ns ? 0 : 1, M, md};
+  }
+  std::vector<int64_t> rank(n_all);
+  for (int64_t q = 0; q < n_all; ++q) rank[q] = q;
+  std::sort(rank.begin(), rank.end(), [&](int64_t x, int64_t y) {
+    const Key &p = keys[x], &o = keys[y];
+    if (p.a != o.a) return p.a < o.a;
+    if (p.e != o.e) return p.e < o.e;
+    if (p.parity != o.parity) return p.parity < o.parity;
+    if (p.M != o.M) return p.M < o.M;
+    for (int i = 0; i < p.M; ++i)
+      if (p.modes[i] != o.modes[i]) return p.modes[i] < o.modes[i];
+    return x < y;
+  });
+  std::vector<std::vector<int32_t>> sel_ns(nv), sel_r(nv);
+  int64_t n_max = 0;
   for (int v = 0; v < nv; ++v) {
-    std::vector<int32_t> ins, ir;
-    for (int64_t q = 0; q < sec.n_ns; ++q)
-      if (ecut[v] < 0 || b.ns.E[sec.ns_off + q] <= (e_ns + ecut[v]) + 1e-9) ins.push_back((int32_t)q);
-    for (int64_t q = 0; q < sec.n_r; ++q)
-      if (ecut[v] < 0 || b.r.E[sec.r_off + q] <= (e_ns + ecut[v]) + 1e-9) ir.push_back((int32_t)q);
+    int64_t keep = n_all;
+    if (order == 1) keep = std::min<int64_t>(n_all, (int64_t)trunc[v]);
+    for (int64_t k = 0; k < keep; ++k) {
+      const int64_t q = rank[k];
+      if (order == 0 && trunc[v] >= 0 && energy(q) > (e_ns + trunc[v]) + 1e-9) break;
+      if (q < sec.n_ns) sel_ns[v].push_back((int32_t)q);
+      else sel_r[v].push_back((int32_t)(q - sec.n_ns));
+    }
+    const int64_t n = (int64_t)(sel_ns[v].size() + sel_r[v].size());
+    if (n == 0) return fail(TGBA_EINVAL, "a quench variant keeps no states");
+    if (eps_out && (method == 2 || (method == 0 && n > kEigenMaxStates)))
+      return fail(TGBA_EINVAL, "the convergence metric needs the eigendecomposition method (at most 4096 states "
+                               "with method 0)");
+    n_max = std::max(n_max, n);
+  }
+  double* Bbuf[2] = {nullptr, nullptr};
+  if (eps_out) {
+    TGBA_CUDA(cudaMemsetAsync(eps_out, 0, std::max(0, nv - 1) * sizeof(double), st));
+    TGBA_CUDA(cudaMallocAsync(&Bbuf[0], 2 * sizeof(double) * (size_t)n_max * 2 * n_t, st));
+    Bbuf[1] = Bbuf[0] + (size_t)n_max * 2 * n_t;
+  }
+  struct FreeB {
+    double* p; cudaStream_t s;
+    ~FreeB() { if (p) cudaFreeAsync(p, s); }
+  } free_b{Bbuf[0], st};
+  int64_t knp = 0, krp = 0;
+  for (int v = 0; v < nv; ++v) {
+    const std::vector<int32_t>& ins = sel_ns[v];
+    const std::vector<int32_t>& ir = sel_r[v];
     const int64_t kn = (int64_t)ins.size(), kr = (int64_t)ir.size(), n = kn + kr;
     if (chi_out) chi_out[v] = n;
-    if (n == 0) return fail(TGBA_EINVAL, "a quench variant keeps no states");
     const bool cheb = method == 2 || (method == 0 && n > kEigenMaxStates);
+    double* Bcur = Bbuf[v & 1];
+    double* Bprev = Bbuf[(v + 1) & 1];
     const int nb = std::min(n_t, 256);
     // scratch layout (doubles): shared part, then the eigen-path buffers
     const int64_t shared = n + 2 * n + 2 * n + 8 + kn * kr + 2 * L + (kn + kr + 2) / 2 + 8;
@@ -385,7 +506,20 @@ tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* e
         quad_kernel<<<(cnt * 32 + 255) / 256, 256, 0, st>>>(n, nb, cnt, B, XB, norm2, mx + (int64_t)v * n_t + t0);
         TGBA_CUDA(cudaGetLastError());
         ++b.launches;
+        if (Bcur) {                                   // keep B(t) of this variant for Eq. 11
+          TGBA_CUDA(cudaMemcpyAsync(Bcur + (size_t)t0 * n, B, (size_t)n * cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+          TGBA_CUDA(cudaMemcpyAsync(Bcur + (size_t)(n_t + t0) * n, B + (size_t)n * nb, (size_t)n * cnt * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, st));
+        }
       }
+      if (Bcur && v > 0) {
+        eps_kernel<<<(int)std::min<int64_t>(((int64_t)n_t * 32 + 255) / 256, 152 * 8), 256, 0, st>>>(
+            n_t, knp, krp, kn, kr, Bprev, Bcur, (unsigned long long*)(eps_out + v - 1));
+        TGBA_CUDA(cudaGetLastError());
+        ++b.launches;
+      }
+      knp = kn;
+      krp = kr;
     } else {
       // energies of the kept states and the Gershgorin interval of H~
       gather_energy<<<blocks_for(n), 256, 0, st>>>(kn, kr, idx, idx + kn, b.d_E_ns + sec.ns_off, b.d_E_r + sec.r_off, E);

@@ -175,6 +175,9 @@ tgba_status plan_pfaffians(Basis& b);
 tgba_status autotune_pfaffians(Basis& b, cudaStream_t st);
 tgba_status run_pfaffians(Basis& b, const uint8_t* d_mask, cudaStream_t st);
 tgba_status run_pfaffian_pairs(Basis& b, int s, const int32_t* pairs, int64_t n, double* out, cudaStream_t st);
+// direct.cu: X of explicit pairs by the paper-literal Pfaffian of size 2L + M_a + M_b
+size_t x_direct_smem(int L, int max_qp);
+tgba_status x_direct(Basis& b, int s, const int32_t* pairs, int64_t n, double* out, cudaStream_t st);
 // real P of every (NS state of sector s_ns, R state of sector s_r) pair, out [n_ns][n_r] row-major
 tgba_status run_pfaffian_cross(Basis& b, int s_ns, int s_r, double* out, cudaStream_t st);
 
@@ -206,8 +209,11 @@ tgba_status dsf_k(Basis& b, int s, int s0, double h_x, double w_min, double w_ma
                   double* evals, int n_ev, double* weights, double* dE, cudaStream_t st);
 
 // quench.cu
-tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* ecut, int nv, double t_max,
-                   int n_t, int method, double* mx, double* norm, int64_t* chi, cudaStream_t st);
+// order 0: trunc = energy cutoffs above the NS vacuum (< 0: all); order 1: trunc = numbers of
+// states chi, kept in order of |<phi|Phi0>|.  eps (optional, device, nv - 1): Eq. 11 between
+// successive variants (they must be nested).
+tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* trunc, int nv, int order, double t_max,
+                   int n_t, int method, double* mx, double* norm, double* eps, int64_t* chi, cudaStream_t st);
 
 // screen.cu
 struct Screen;

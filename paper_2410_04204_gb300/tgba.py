@@ -18,8 +18,8 @@ _NAMES = {0: "TGBA_OK", 1: "TGBA_EINVAL", 2: "TGBA_ENOMEM", 3: "TGBA_ECUDA", 4: 
 
 # every symbol include/tgba.h declares
 SYMBOLS = ("tgba_last_error", "tgba_device_count", "tgba_build_basis", "tgba_basis_info", "tgba_basis_totals",
-           "tgba_basis_free", "tgba_compute_x", "tgba_x_stats", "tgba_x_export", "tgba_x_pairs", "tgba_table",
-           "tgba_assemble_heff", "tgba_eigvals", "tgba_eigvals_ex", "tgba_dsf", "tgba_dsf_k", "tgba_quench", "tgba_screen_create",
+           "tgba_basis_free", "tgba_compute_x", "tgba_x_stats", "tgba_x_export", "tgba_x_pairs", "tgba_x_direct", "tgba_table",
+           "tgba_assemble_heff", "tgba_eigvals", "tgba_eigvals_ex", "tgba_dsf", "tgba_dsf_k", "tgba_quench", "tgba_quench_ordered", "tgba_screen_create",
            "tgba_screen_nparams", "tgba_screen_params", "tgba_screen_grad", "tgba_screen_train",
            "tgba_screen_predict", "tgba_screen_free", "tgba_table_noalloc", "tgba_profile", "tgba_fp64_peak")
 
@@ -69,6 +69,7 @@ def lib():
             "tgba_x_stats": (_I32, [_VP, _P(_I64), _P(_I64)]),
             "tgba_x_export": (_I32, [_VP, _I32, _VP, _VP]),
             "tgba_x_pairs": (_I32, [_VP, _I32, _VP, _I64, _VP, _VP]),
+            "tgba_x_direct": (_I32, [_VP, _I32, _VP, _I64, _VP, _VP]),
             "tgba_table": (_I32, [_VP, _VP, _VP, _VP]),
             "tgba_assemble_heff": (_I32, [_VP, _D, _VP, _D, _VP, _VP]),
             "tgba_eigvals": (_I32, [_VP, _VP, _I32, _VP, _VP]),
@@ -76,6 +77,8 @@ def lib():
             "tgba_dsf": (_I32, [_VP, _I32, _D, _D, _D, _I32, _D, _VP, _VP, _I32, _VP, _VP, _VP]),
             "tgba_dsf_k": (_I32, [_VP, _I32, _I32, _D, _D, _D, _I32, _D, _VP, _VP, _I32, _VP, _VP, _VP]),
             "tgba_quench": (_I32, [_VP, _I32, _D, _VP, _VP, _I32, _D, _I32, _I32, _VP, _VP, _VP, _VP]),
+            "tgba_quench_ordered": (_I32, [_VP, _I32, _D, _VP, _VP, _I32, _I32, _D, _I32, _I32, _VP, _VP, _VP, _VP,
+                                           _VP]),
             "tgba_screen_create": (_I32, [_I32, _VP, ctypes.c_uint64, _P(_VP)]),
             "tgba_screen_nparams": (_I32, [_VP, _P(_I64)]),
             "tgba_screen_params": (_I32, [_VP, _VP]),
@@ -209,6 +212,13 @@ def tgba_x_pairs(b, s, pairs, out, stream=None):
     _check(lib().tgba_x_pairs(b, s, _ptr(pairs), pairs.shape[0], _ptr(out), _stream(stream)))
 
 
+def tgba_x_direct(b, s, pairs, out, stream=None):
+    """pairs: int32 CUDA tensor [n, 2] (NS index, R index); out: complex128 CUDA tensor [n]."""
+    import torch
+    _cuda_tensor(pairs, torch.int32, name="pairs")
+    _cuda_tensor(out, torch.complex128, pairs.shape[0], name="out")
+    _check(lib().tgba_x_direct(b, s, _ptr(pairs), pairs.shape[0], _ptr(out), _stream(stream)))
+
 def tgba_table(b, table_out=None, stream=None):
     """Returns C0 (complex); fills table_out (float64 CUDA tensor, 2L x 2L) if given."""
     import torch
@@ -271,6 +281,26 @@ def tgba_quench(b, s, h_z0, hx_variants, ecut_variants, t_max, n_t, mx_out, norm
     chi = np.zeros(len(hx), np.int64)
     _check(lib().tgba_quench(b, s, float(h_z0), hx.ctypes.data, ec.ctypes.data, len(hx), float(t_max), int(n_t),
                              int(method), _ptr(mx_out), _ptr(norm_out), chi.ctypes.data, _stream(stream)))
+    return chi
+
+
+def tgba_quench_ordered(b, s, h_z0, hx_variants, trunc_variants, order, t_max, n_t, mx_out, norm_out=None,
+                        eps_out=None, method=0, stream=None):
+    """Quench with energy- (order 0) or overlap-ordered (order 1) nested truncations; eps_out
+    (float64 CUDA tensor, len - 1) receives the Eq. 11 metric between successive variants.
+    Returns the retained basis size of each variant."""
+    import torch
+    hx = np.ascontiguousarray(np.asarray(hx_variants, np.float64))
+    tr = np.ascontiguousarray(np.asarray(trunc_variants, np.float64))
+    if hx.shape != tr.shape:
+        raise ValueError("one truncation per h_x variant")
+    _cuda_tensor(mx_out, torch.float64, len(hx) * n_t, name="mx_out")
+    _cuda_tensor(norm_out, torch.float64, len(hx), name="norm_out")
+    _cuda_tensor(eps_out, torch.float64, max(0, len(hx) - 1), name="eps_out")
+    chi = np.zeros(len(hx), np.int64)
+    _check(lib().tgba_quench_ordered(b, s, float(h_z0), hx.ctypes.data, tr.ctypes.data, len(hx), int(order),
+                                     float(t_max), int(n_t), int(method), _ptr(mx_out), _ptr(norm_out),
+                                     _ptr(eps_out), chi.ctypes.data, _stream(stream)))
     return chi
 
 
