@@ -1,0 +1,242 @@
+// The paper-literal evaluation of X (Appendix A, Eq. S1-S2), one CTA per element: both states
+// are products of Bogoliubov operators on the Jordan-Wigner vacuum (Eq. S3), so
+//   X_ab = <phi_a^NS| (c_1 + c_1^dag) |phi_b^R> = n_NS n_R Pf(A),   A_uv = <0|o_u o_v|0>  (u < v),
+// over the string of m = 2L + M_a + M_b linear operators o = sum_j (U_j c_j^dag + V_j c_j):
+//   d_k^dag for every NS mode, k ascending          (the bra <0|_NS)
+//   d_p for p in phi_a, descending                  (the bra's excitations)
+//   c_1 + c_1^dag                                   (sigma^x_1 after the Jordan-Wigner map)
+//   d_q^dag for q in phi_b, ascending (c_pi^dag at pi)  (the ket's excitations)
+//   d_k for every R mode k != pi, descending        (the ket |0>_R)
+// with d_k = sin(theta_k/2) c_k - i cos(theta_k/2) c_{-k}^dag, c_k = L^{-1/2} sum_j e^{-ikj} c_j,
+// and <0|c_j c_l^dag|0> = delta_jl, so A_uv = sum_j V_u(j) U_v(j).  The Pfaffian is a complex
+// Parlett-Reid elimination with partial pivoting in shared memory (packed strict upper
+// triangle), the CTA's threads sharing each step's pivot search, exchange and rank-2 update.
+// This is the O(m^3)-per-element form the paper describes; the production path evaluates the
+// same numbers through the contraction table (reduced form, pfaffian.cu), and this kernel
+// checks it on the GPU.
+#include <cuComplex.h>
+
+#include <algorithm>
+
+#include "tgba_internal.h"
+
+namespace tgba {
+namespace {
+
+constexpr int kDirThreads = 128;
+enum OpKind : int { kOpC = 0, kOpCdag = 1, kOpD = 2, kOpDdag = 3, kOpSigma = 4 };
+
+__device__ __forceinline__ int pk(int i, int j, int m) { return i * m - ((i * (i + 1)) >> 1) + (j - i - 1); }
+
+// entry (i, j) of the skew matrix held as its packed strict upper triangle T
+__device__ __forceinline__ double2 get(const double2* T, int i, int j, int m) {
+  if (i < j) return T[pk(i, j, m)];
+  const double2 v = T[pk(j, i, m)];
+  return make_double2(-v.x, -v.y);
+}
+__device__ __forceinline__ void set(double2* T, int i, int j, int m, double2 v) {
+  if (i < j) T[pk(i, j, m)] = v;
+  else T[pk(j, i, m)] = make_double2(-v.x, -v.y);
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+__global__ void __launch_bounds__(kDirThreads)
+x_direct_kernel(const int32_t* __restrict__ pairs, int64_t n_pairs, int64_t ns_off, int64_t r_off, int64_t n_ns,
+                int64_t n_r, int L, const double* __restrict__ theta, const int* __restrict__ nlab,
+                const int16_t* __restrict__ modes_ns, const int16_t* __restrict__ modes_r, int max_qp,
+                double vac_norm, double* __restrict__ out, unsigned* __restrict__ status) {
+  extern __shared__ double smem_d[];
+  __shared__ int kind[4 * 32 + 2 * 16 + 2];
+  __shared__ double kk[4 * 32 + 2 * 16 + 2], th[4 * 32 + 2 * 16 + 2];
+  __shared__ double red_v[kDirThreads];
+  __shared__ int red_i[kDirThreads];
+  __shared__ double2 piv;
+  __shared__ int nops, zero_col;
+  const int mmax = 2 * L + 2 * max_qp;
+  double2* U = (double2*)smem_d;                 // [m][L]
+  double2* V = U + (size_t)mmax * L;             // [m][L]
+  double2* T = V + (size_t)mmax * L;             // packed strict upper triangle, m (m - 1) / 2
+  double2* rowR = T + (size_t)mmax * (mmax - 1) / 2;
+  double2* tau = rowR + mmax;
+  const double pi = 3.14159265358979323846;
+  for (int64_t q = blockIdx.x; q < n_pairs; q += gridDim.x) {
+    const int32_t pa = pairs[2 * q], pb = pairs[2 * q + 1];
+    if (pa < 0 || pa >= n_ns || pb < 0 || pb >= n_r) {      // block-uniform
+      if (threadIdx.x == 0) {
+        atomicOr(status, kStBadIndex);
+        out[2 * q] = out[2 * q + 1] = __longlong_as_double(0x7ff8000000000000ll);
+      }
+      continue;
+    }
+    // the operator string (thread 0: at most 2L + 2 max_qp + 1 entries)
+    if (threadIdx.x == 0) {
+      const int16_t* sa = modes_ns + (ns_off + pa) * max_qp;
+      const int16_t* sb = modes_r + (r_off + pb) * max_qp;
+      int ma = 0, mb = 0;
+      while (ma < max_qp && sa[ma] >= 0) ++ma;
+      while (mb < max_qp && sb[mb] >= 0) ++mb;
+      int c = 0;
+      for (int i = 0; i < L; ++i) {                  // NS vacuum bra: d_k^dag, ascending
+        kind[c] = kOpDdag; kk[c] = pi * nlab[i] / L; th[c] = theta[i]; ++c;
+      }
+      for (int t = ma - 1; t >= 0; --t) {            // bra excitations: d_p, descending
+        const int i = sa[t];
+        kind[c] = kOpD; kk[c] = pi * nlab[i] / L; th[c] = theta[i]; ++c;
+      }
+      kind[c] = kOpSigma; kk[c] = 0.0; th[c] = 0.0; ++c;
+      for (int t = 0; t < mb; ++t) {                 // ket excitations: d_q^dag (c_pi^dag), ascending
+        const int i = sb[t], n = nlab[L + i];
+        if (n == L) { kind[c] = kOpCdag; kk[c] = pi; th[c] = 0.0; }
+        else { kind[c] = kOpDdag; kk[c] = pi * n / L; th[c] = theta[L + i]; }
+        ++c;
+      }
+      for (int i = L - 1; i >= 0; --i) {             // R vacuum ket: d_k (k != pi), descending
+        const int n = nlab[L + i];
+        if (n == L) continue;
+        kind[c] = kOpD; kk[c] = pi * n / L; th[c] = theta[L + i]; ++c;
+      }
+      nops = c;
+    }
+    __syncthreads();
+    const int m = nops;
+    // coefficients of every operator on every site j = 1..L
+    const double rn = rsqrt((double)L);
+    for (int e = threadIdx.x; e < m * L; e += kDirThreads) {
+      const int u = e / L, j = e - u * L + 1;
+      double sn, cs;
+      sincos(kk[u] * j, &sn, &cs);
+      const double2 ep = make_double2(cs * rn, sn * rn), em = make_double2(cs * rn, -sn * rn);
+      double s2, c2;
+      sincos(0.5 * th[u], &s2, &c2);
+      double2 cu = make_double2(0.0, 0.0), cv = make_double2(0.0, 0.0);
+      switch (kind[u]) {
+        case kOpC: cv = em; break;
+        case kOpCdag: cu = ep; break;
+        case kOpD:                                   // s c_k - i c c_{-k}^dag
+          cv = make_double2(s2 * em.x, s2 * em.y);
+          cu = make_double2(c2 * em.y, -c2 * em.x);
+          break;
+        case kOpDdag:                                // s c_k^dag + i c c_{-k}
+          cu = make_double2(s2 * ep.x, s2 * ep.y);
+          cv = make_double2(-c2 * ep.y, c2 * ep.x);
+          break;
+        default:
+          if (j == 1) { cu = make_double2(1.0, 0.0); cv = cu; }
+      }
+      U[(size_t)u * L + (j - 1)] = cu;
+      V[(size_t)u * L + (j - 1)] = cv;
+    }
+    __syncthreads();
+    // A_uv = sum_j V_u(j) U_v(j), u < v (Eq. S2)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = kDirThreads / 32;
+    for (int u = warp; u < m; u += nwarp)               // a warp per row, lanes along it
+      for (int v = u + 1 + lane; v < m; v += 32) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int j = 0; j < L; ++j) {
+          const double2 a = V[(size_t)u * L + j], b = U[(size_t)v * L + j];
+          acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+          acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+        }
+        T[pk(u, v, m)] = acc;
+      }
+    __syncthreads();
+    // complex Parlett-Reid: pivot, exchange, rank-2 update, two indices per step
+    double2 pf = make_double2(1.0, 0.0);
+    for (int k = 0; k + 1 < m; k += 2) {
+      // pivot: the largest |A[k][x]|, x > k (ties: the smallest x)
+      double best = -1.0;
+      int bi = k + 1;
+      for (int x = k + 1 + threadIdx.x; x < m; x += kDirThreads) {
+        const double2 v = T[pk(k, x, m)];
+        const double a2 = fma(v.x, v.x, v.y * v.y);
+        if (a2 > best) { best = a2; bi = x; }
+      }
+      red_v[threadIdx.x] = best;
+      red_i[threadIdx.x] = bi;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int t = 1; t < kDirThreads; ++t)
+          if (red_v[t] > best || (red_v[t] == best && red_i[t] < bi)) { best = red_v[t]; bi = red_i[t]; }
+        red_i[0] = bi;
+        zero_col = !(best > 0.0);
+      }
+      __syncthreads();
+      if (zero_col) { pf = make_double2(0.0, 0.0); break; }       // block-uniform
+      const int R = k + 1, C = red_i[0];
+      if (C != R) {                                   // exchange indices R and C
+        for (int x = threadIdx.x; x < m; x += kDirThreads) {
+          if (x == R || x == C) continue;
+          const double2 a = get(T, R, x, m), b = get(T, C, x, m);
+          set(T, R, x, m, b);
+          set(T, C, x, m, a);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          const double2 v = T[pk(R, C, m)];
+          T[pk(R, C, m)] = make_double2(-v.x, -v.y);
+        }
+        pf = make_double2(-pf.x, -pf.y);
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) piv = T[pk(k, R, m)];
+      __syncthreads();
+      const double2 a = piv;
+      pf = cmul(pf, a);
+      const double den = fma(a.x, a.x, a.y * a.y);
+      const double2 ia = make_double2(a.x / den, -a.y / den);
+      for (int x = k + 2 + threadIdx.x; x < m; x += kDirThreads) {
+        tau[x] = cmul(T[pk(k, x, m)], ia);            // Gauss vector
+        rowR[x] = T[pk(R, x, m)];
+      }
+      __syncthreads();
+      // A_ij += A_Ri tau_j - tau_i A_Rj  for k + 2 <= i < j
+      for (int gi = k + 2 + warp; gi < m; gi += nwarp) {
+        const double2 ri = rowR[gi], ti = tau[gi];
+        double2* rowp = T + pk(gi, gi + 1, m) - (gi + 1);   // rowp[gj] = A[gi][gj]
+        for (int gj = gi + 1 + lane; gj < m; gj += 32) {
+          double2 w = rowp[gj];
+          const double2 p1 = cmul(ri, tau[gj]), p2 = cmul(ti, rowR[gj]);
+          w.x += p1.x - p2.x;
+          w.y += p1.y - p2.y;
+          rowp[gj] = w;
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const double re = vac_norm * pf.x, im = vac_norm * pf.y;
+      if (!(isfinite(re) && isfinite(im))) atomicOr(status, kStNan);
+      out[2 * q] = re;
+      out[2 * q + 1] = im;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+size_t x_direct_smem(int L, int max_qp) {
+  const size_t m = (size_t)(2 * L + 2 * max_qp);
+  return sizeof(double2) * (2 * m * L + m * (m - 1) / 2 + 2 * m);
+}
+
+tgba_status x_direct(Basis& b, int s, const int32_t* pairs, int64_t n, double* out, cudaStream_t st) {
+  if (n == 0) return TGBA_OK;
+  const Sector& sec = b.sectors[s];
+  const size_t smem = x_direct_smem(b.L, b.max_qp);
+  TGBA_CUDA(cudaFuncSetAttribute(x_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int sms = 0;
+  TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
+  const int64_t grid = std::min<int64_t>(n, (int64_t)sms * 8);
+  x_direct_kernel<<<(unsigned)grid, kDirThreads, smem, st>>>(pairs, n, sec.ns_off, sec.r_off, sec.n_ns, sec.n_r, b.L,
+                                                             b.d_theta, b.d_nlab, b.d_modes_ns, b.d_modes_r, b.max_qp,
+                                                             b.vac_norm, out, b.d_status);
+  TGBA_CUDA(cudaGetLastError());
+  ++b.launches;
+  return TGBA_OK;
+}
+
+}  // namespace tgba
