@@ -258,6 +258,12 @@ def screening_leg(b24, tgba, inputs, torch):
     return out
 
 
+# DRAM bytes of one sytrd_groups launch on the L = 24 all-sector workload, measured with ncu
+# (dram__bytes_read.sum 4.980e11 + dram__bytes_write.sum 5.245e11); to be re-measured whenever
+# the kernel changes.
+SYTRD_TRAFFIC = 4.97974480640e11 + 5.24546127104e11
+
+
 def eigen_solver_leg(b, w, evs, tgba, torch):
     """Outside the timed steps: the native eigen-solver against cuSOLVER's batched one on the
     same matrices (time of one call each, and the largest eigenvalue difference)."""
@@ -353,7 +359,10 @@ def run_gb300(args):
         tri_gflops = prof["tridiag_flops"] / (tri_mean * 1e-3) / 1e9
         roofline = {"bound": "alu", "kernel": "sytrd_groups (FP64 Householder tridiagonalisation)",
                     "achieved": tri_gflops, "peak": peak_gflops, "unit": "GFLOP/s",
-                    "frac": tri_gflops / peak_gflops, "traffic": None, "peak_source": peak_src,
+                    "frac": tri_gflops / peak_gflops, "traffic": SYTRD_TRAFFIC, "peak_source": peak_src,
+                    "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of this kernel on this workload "
+                                      "(one ncu capture of the warm-up launch; 1.16x the algorithmic 8 n^3/3 B per "
+                                      "matrix)",
                     "flops_per_launch": prof["tridiag_flops"], "ms": tri_mean,
                     "matrices": prof["eig_matrices"], "ctas_per_matrix": prof["eig_cluster"]}
     else:
