@@ -133,6 +133,34 @@ def quench_magnetisation(N, h0, h, h_x, t):
     return np.einsum("it,ij,jt->t", np.conj(psi), Mx, psi).real
 
 
+def quench_correlators(N, h0, h, h_x, t, j_max):
+    """Exact connected <sigma^x_1 sigma^x_{j+1}>(t) - <sigma^x_1>(t) <sigma^x_{j+1}>(t) for
+    j = 1..j_max after the quench of quench_magnetisation (rows: j; columns: t)."""
+    B = momentum_basis(N, 0)
+    Q = np.ones(1 << N)
+    for j in range(1, N + 1):
+        Q = Q * (2.0 * ((np.arange(1 << N) >> (j - 1)) & 1) - 1.0)
+    Mx = B.conj().T @ (magnetisation_op(N) @ B)
+    H0 = B.conj().T @ (spin_hamiltonian(N, h0, 0.0) @ B)
+    E0, V0 = np.linalg.eigh(H0)
+    qv = np.einsum("ia,i,ia->a", np.conj(B @ V0), Q, B @ V0).real
+    ns = V0[:, np.where(qv > 0.5)[0][0]]
+    r = V0[:, np.where(qv < -0.5)[0][0]]
+    z = np.vdot(ns, Mx @ r)
+    phi0 = (ns + (np.conj(z) / abs(z)) * r) / math.sqrt(2.0)
+    Hk = B.conj().T @ (spin_hamiltonian(N, h, h_x) @ B)
+    E, V = np.linalg.eigh(Hk)
+    psi = B @ (V @ (np.exp(-1j * np.outer(E, t)) * (V.conj().T @ phi0)[:, None]))   # full space
+    s1 = pauli_x(N, 1)
+    m1 = np.einsum("it,it->t", np.conj(psi), s1 @ psi).real
+    out = np.zeros((j_max, len(t)))
+    for j in range(1, j_max + 1):
+        op = s1 @ pauli_x(N, j + 1)
+        mj = np.einsum("it,it->t", np.conj(psi), pauli_x(N, j + 1) @ psi).real
+        out[j - 1] = np.einsum("it,it->t", np.conj(psi), op @ psi).real - m1 * mj
+    return out
+
+
 # ---------------------------------------------------------------- Fock-space brute force
 
 def fermion_c(N, j):

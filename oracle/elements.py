@@ -84,6 +84,41 @@ def x_block(N, h, ns_states, r_states, n_threads=0):
     return x_elements(N, h, pairs, n_threads).reshape(len(ns_states), len(r_states))
 
 
+def sxsx_middle(j):
+    """sigma^x_1 sigma^x_{j+1} after the Jordan-Wigner map: with A_l = c_l^dag + c_l and
+    B_l = c_l^dag - c_l (so 1 - 2 n_l = A_l B_l and sigma^x_1 = A_1),
+    sigma^x_1 sigma^x_{j+1} = A_1 (A_1 B_1)(A_2 B_2)...(A_j B_j) A_{j+1} = B_1 A_2 B_2 ... B_j A_{j+1}."""
+    out = []
+    for l in range(1, j + 1):
+        out.append((nat.OP_MAJ_B, float(l), 0.0))
+        out.append((nat.OP_MAJ_A, float(l + 1), 0.0))
+    return out
+
+
+def z_string(N, h, parity, sel_a, sel_b, j):
+    """<phi_a| sigma^x_1 sigma^x_{j+1} |phi_b> between two states of the same parity: the
+    string of X with the bra and ket vacua of that parity and the 2j Majoranas of
+    sxsx_middle(j) in place of sigma^x_1."""
+    th = md.theta(N, parity, h)
+    return (_bra_vacuum(N, parity, th) + _bra_excitations(N, parity, th, sel_a) + sxsx_middle(j)
+            + _ket_excitations(N, parity, th, sel_b) + _ket_vacuum(N, parity, th))
+
+
+def z_elements(N, h, parity, j, pairs, n_threads=0):
+    """<phi_a|sigma^x_1 sigma^x_{j+1}|phi_b> for a list of (modes_a, modes_b) pairs of one parity."""
+    strings = [z_string(N, h, parity, a, b, j) for a, b in pairs]
+    vals, _ = nat.wick_batch(N, strings, n_threads)
+    return vals * md.vacuum_norm(N, parity, h) ** 2
+
+
+def z_block(N, h, parity, j, states, n_threads=0):
+    """Dense Z[a, b] over one list of basis states of one parity."""
+    pairs = [(a.modes, b.modes) for a in states for b in states]
+    if not pairs:
+        return np.zeros((len(states), len(states)), dtype=np.complex128)
+    return z_elements(N, h, parity, j, pairs, n_threads).reshape(len(states), len(states))
+
+
 def vacuum_sigma(N, h):
     """<0_NS(h)| sigma^x_1 |0_R(h)>."""
     return x_elements(N, h, [((), ())])[0]

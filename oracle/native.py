@@ -68,4 +68,4 @@ def wick_batch(N, strings, n_threads=0):
     return out, used
 
 
-OP_C, OP_CDAG, OP_D, OP_DDAG, OP_SIGMA1 = 0, 1, 2, 3, 4
+OP_C, OP_CDAG, OP_D, OP_DDAG, OP_SIGMA1, OP_MAJ_A, OP_MAJ_B = 0, 1, 2, 3, 4, 5, 6

@@ -198,3 +198,34 @@ def quench_ordered(N, h, h0, h_x, max_qp, e_cut, order, sizes, t_max, n_t, n_thr
     eps = [float(np.sqrt((np.abs(Bs[v + 1] - Bs[v]) ** 2).sum(axis=0)).max()) for v in range(len(sizes) - 1)]
     return t, np.array(mx), np.array(nrm), np.array(eps)
 
+
+def quench_correlators(N, h, h0, h_x, max_qp, e_cut, order, chi, t_max, n_t, j_max, n_threads=0):
+    """Equal-time connected correlators <sigma^x_1(t) sigma^x_{j+1}(t)> - <sigma^x(t)>^2,
+    j = 1..j_max, in the truncated subspace of the first chi states (order as quench_ordered),
+    with the state normalised by its time-independent norm (the Quench section); translation
+    invariance of the k = 0 state makes <sigma^x_{j+1}> = <sigma^x_1>.  The NS-NS and R-R
+    blocks of sigma^x_1 sigma^x_{j+1} are direct Pfaffians (elements.z_block).  Returns
+    (t, mx [n_t], corr [j_max][n_t])."""
+    ns, r, X = sector(N, h, 0, max_qp, e_cut, None, n_threads)
+    c0 = initial_overlaps(N, h, h0, ns, r, n_threads)
+    _, (keep,) = ordered_subspaces(ns, r, c0, order, [chi], md.vacuum_energy(N, md.NS, h))
+    Hf = heff(ns, r, X, N, h_x)
+    E, U = eigh(Hf[np.ix_(keep, keep)])
+    c = c0[keep]
+    t = time_grid(t_max, n_t)
+    B = quench_coefficients(E, U, c, t)
+    nrm = float(np.vdot(c, c).real)
+    mx = magnetisation(B, x_full(X)[np.ix_(keep, keep)], c)
+    kns = [i for i in keep if i < len(ns)]
+    kr = [i - len(ns) for i in keep if i >= len(ns)]
+    pos_ns = [k for k, i in enumerate(keep) if i < len(ns)]
+    pos_r = [k for k, i in enumerate(keep) if i >= len(ns)]
+    corr = np.zeros((j_max, n_t))
+    for j in range(1, j_max + 1):
+        Zn = el.z_block(N, h, md.NS, j, [ns[i] for i in kns], n_threads)
+        Zr = el.z_block(N, h, md.R, j, [r[i] for i in kr], n_threads)
+        Bn, Br = B[pos_ns], B[pos_r]
+        val = (np.einsum("it,ij,jt->t", np.conj(Bn), Zn, Bn) + np.einsum("it,ij,jt->t", np.conj(Br), Zr, Br)).real
+        corr[j - 1] = val / nrm - mx ** 2
+    return t, mx, corr
+

@@ -31,7 +31,8 @@
 
 typedef double _Complex cplx;
 
-enum { OP_C = 0, OP_CDAG = 1, OP_D = 2, OP_DDAG = 3, OP_SIGMA1 = 4 };
+enum { OP_C = 0, OP_CDAG = 1, OP_D = 2, OP_DDAG = 3, OP_SIGMA1 = 4, OP_MAJ_A = 5, OP_MAJ_B = 6 };
+/* OP_MAJ_A / OP_MAJ_B: the Majorana operators c_l^dag + c_l and c_l^dag - c_l of site l = (int)k */
 
 /* Pfaffian of the dense skew-symmetric n x n matrix A (row-major; destroyed). */
 cplx oracle_pfaffian(cplx* A, int n) {
@@ -88,6 +89,8 @@ static void op_coeffs(int N, int kind, double k, double theta, cplx* U, cplx* V)
       case OP_D:      v = s * em; u = -I * c * em; break;    /* c_{-k}^dag carries e^{-ikj} */
       case OP_DDAG:   u = s * ep; v = I * c * ep; break;     /* c_{-k} carries e^{+ikj} */
       case OP_SIGMA1: u = (j == 1) ? 1.0 : 0.0; v = u; break;
+      case OP_MAJ_A: u = (j == (int)k) ? 1.0 : 0.0; v = u; break;
+      case OP_MAJ_B: u = (j == (int)k) ? 1.0 : 0.0; v = -u; break;
     }
     U[j - 1] = u; V[j - 1] = v;
   }
