@@ -211,6 +211,20 @@ tgba_status tgba_quench_ordered(tgba_basis b, int32_t s, double h_z0, const doub
                                 int32_t n_t, int32_t method, double* mx_dev, double* norm_dev, double* eps_dev,
                                 int64_t* chi_host, void* stream);
 
+/* Equal-time connected correlators after the quench (the correlation-function passage of the
+   appendix): C_j(t) = <sigma^x_1(t) sigma^x_{j+1}(t)> - <sigma^x(t)>^2 for j = 1..j_max, in the
+   truncated subspace of one variant (h_x, trunc, order as one variant of tgba_quench_ordered),
+   with expectation values in the normalised state (the k = 0 state is translation invariant,
+   so <sigma^x_{j+1}> = <sigma^x_1>).  After the Jordan-Wigner map sigma^x_1 sigma^x_{j+1} is a
+   string of 2j Majorana operators; its NS-NS and R-R elements are direct Pfaffians of size
+   2L + M_a + M_b + 2j (the tgba_x_direct kernel), so L, max_qp and j_max are bounded by shared
+   memory (TGBA_EINVAL when the string does not fit; 1 <= j_max < L).  Eigendecomposition path.
+   mx_dev: double [n_t]; corr_dev: double [j_max][n_t]; norm_dev (optional): ||c0||^2;
+   chi_host (optional): the kept basis size.  Blocks on `stream`. */
+tgba_status tgba_quench_correlators(tgba_basis b, int32_t s, double h_z0, double h_x, double trunc, int32_t order,
+                                   double t_max, int32_t n_t, int32_t j_max, double* mx_dev, double* corr_dev,
+                                   double* norm_dev, int64_t* chi_host, void* stream);
+
 /* ---------------------------------------------------------------- learned pair screener
  * Not in the paper (the paper has no counterpart): a 3-layer MLP (width 256, ReLU, FP32
  * parameters) that predicts log10|X_ab| from the two quasiparticle momentum sets, trained on

@@ -125,6 +125,8 @@ static tgba_status build(const tgba_model* model, const int32_t* sectors, int32_
     nl[i] = mns.nlab[i]; nl[L + i] = mr.nlab[i];
   }
   b->vac_norm = mns.norm * mr.norm;
+  b->norm_ns = mns.norm;
+  b->norm_r = mr.norm;
   if ((r = upload(&b->d_theta, th.data(), th.size(), &b->upload_bytes)) != TGBA_OK) return r;
   if ((r = upload(&b->d_nlab, nl.data(), nl.size(), &b->upload_bytes)) != TGBA_OK) return r;
   TGBA_CUDA(cudaMalloc((void**)&b->d_table, sizeof(double) * 4 * L * L));
@@ -377,7 +379,7 @@ tgba_status tgba_x_direct(tgba_basis h, int32_t s, const int32_t* pairs_dev, int
   if (n_pairs < 0 || (n_pairs > 0 && (!pairs_dev || !out_dev))) return fail(TGBA_EINVAL, "bad pair list");
   int limit = 0;
   TGBA_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
-  if (x_direct_smem(b->L, b->max_qp) + 8192 > (size_t)limit)
+  if (x_direct_smem(b->L, b->max_qp, -1) + 16384 > (size_t)limit)
     return fail(TGBA_EINVAL, "the direct Pfaffian of size 2L + 2 max_qp does not fit in shared memory");
   cudaStream_t st = (cudaStream_t)stream;
   tgba_status r = x_direct(*b, s, pairs_dev, n_pairs, out_dev, st);
@@ -511,6 +513,31 @@ tgba_status tgba_quench_ordered(tgba_basis h, int32_t s, double h_z0, const doub
   if (r != TGBA_OK) return r;
   return quench(*b, s, h_z0, hx_variants, trunc_variants, n_variants, order, t_max, n_t, method, mx_dev, norm_dev,
                 eps_dev, chi_host, (cudaStream_t)stream);
+}
+
+tgba_status tgba_quench_correlators(tgba_basis h, int32_t s, double h_z0, double h_x, double trunc, int32_t order,
+                                   double t_max, int32_t n_t, int32_t j_max, double* mx_dev, double* corr_dev,
+                                   double* norm_dev, int64_t* chi_host, void* stream) {
+  Basis* b = (Basis*)h;
+  BASIS_OK(b);
+  if (s < 0 || s >= (int)b->sectors.size()) return fail(TGBA_EINVAL, "sector index out of range");
+  if (b->sectors[s].m != 0) return fail(TGBA_EINVAL, "the quench needs the k = 0 sector");
+  if (!mx_dev || !corr_dev || n_t < 1 || j_max < 1 || j_max >= b->L)
+    return fail(TGBA_EINVAL, "need output buffers, n_t >= 1 and 1 <= j_max < L");
+  if (!(h_z0 > 0) || !std::isfinite(t_max) || t_max < 0 || !std::isfinite(h_x) || !std::isfinite(trunc))
+    return fail(TGBA_EINVAL, "need h_z0 > 0, t_max >= 0 and finite fields");
+  if (order != 0 && order != 1) return fail(TGBA_EINVAL, "order must be 0 (energy) or 1 (overlap)");
+  if (order == 1 && !(trunc >= 1 && trunc == std::floor(trunc)))
+    return fail(TGBA_EINVAL, "with order 1 the truncation is a whole number of states >= 1");
+  int limit = 0;
+  TGBA_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+  if (x_direct_smem(b->L, b->max_qp, j_max) + 16384 > (size_t)limit)
+    return fail(TGBA_EINVAL, "the operator string of sigma^x_1 sigma^x_{j_max+1} does not fit in shared memory");
+  if (!b->x_valid) return fail(TGBA_EINVAL, "no X computed yet: call tgba_compute_x");
+  tgba_status r = ensure_c0_host(*b, (cudaStream_t)stream);
+  if (r != TGBA_OK) return r;
+  return quench(*b, s, h_z0, &h_x, &trunc, 1, order, t_max, n_t, 1, mx_dev, norm_dev, nullptr, chi_host,
+                (cudaStream_t)stream, j_max, corr_dev);
 }
 
 tgba_status tgba_screen_create(int32_t width, const float* params_host, uint64_t seed, tgba_screen* out) {

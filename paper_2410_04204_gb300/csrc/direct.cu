@@ -13,7 +13,11 @@
 // triangle), the CTA's threads sharing each step's pivot search, exchange and rank-2 update.
 // This is the O(m^3)-per-element form the paper describes; the production path evaluates the
 // same numbers through the contraction table (reduced form, pfaffian.cu), and this kernel
-// checks it on the GPU.
+// checks it on the GPU.  The same kernel gives the elements of sigma^x_1 sigma^x_{j+1} between
+// two states of one parity (the equal-time correlators after a quench): after the
+// Jordan-Wigner map, with A_l = c_l^dag + c_l and B_l = c_l^dag - c_l (1 - 2 n_l = A_l B_l),
+// sigma^x_1 sigma^x_{j+1} = B_1 A_2 B_2 ... B_j A_{j+1}, a string of 2j Majoranas that takes the
+// place of sigma^x_1, between vacua of the same parity.
 #include <cuComplex.h>
 
 #include <algorithm>
@@ -24,7 +28,8 @@ namespace tgba {
 namespace {
 
 constexpr int kDirThreads = 128;
-enum OpKind : int { kOpC = 0, kOpCdag = 1, kOpD = 2, kOpDdag = 3, kOpSigma = 4 };
+constexpr int kMaxOps = 2 * kMaxL + 2 * kMaxQp + 2 * kMaxL + 2;   // vacua, excitations, middle
+enum OpKind : int { kOpC = 0, kOpCdag = 1, kOpD = 2, kOpDdag = 3, kOpSigma = 4, kOpMajA = 5, kOpMajB = 6 };
 
 __device__ __forceinline__ int pk(int i, int j, int m) { return i * m - ((i * (i + 1)) >> 1) + (j - i - 1); }
 
@@ -44,18 +49,18 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 }
 
 __global__ void __launch_bounds__(kDirThreads)
-x_direct_kernel(const int32_t* __restrict__ pairs, int64_t n_pairs, int64_t ns_off, int64_t r_off, int64_t n_ns,
-                int64_t n_r, int L, const double* __restrict__ theta, const int* __restrict__ nlab,
-                const int16_t* __restrict__ modes_ns, const int16_t* __restrict__ modes_r, int max_qp,
-                double vac_norm, double* __restrict__ out, unsigned* __restrict__ status) {
+x_direct_kernel(const int32_t* __restrict__ pairs, int64_t n_pairs, int pa_par, int pb_par, int jmid, int64_t a_off,
+                int64_t b_off, int64_t n_a, int64_t n_b, int L, const double* __restrict__ theta,
+                const int* __restrict__ nlab, const int16_t* __restrict__ modes_ns, const int16_t* __restrict__ modes_r,
+                int max_qp, double vac_norm, double* __restrict__ out, unsigned* __restrict__ status) {
   extern __shared__ double smem_d[];
-  __shared__ int kind[4 * 32 + 2 * 16 + 2];
-  __shared__ double kk[4 * 32 + 2 * 16 + 2], th[4 * 32 + 2 * 16 + 2];
+  __shared__ int kind[kMaxOps];
+  __shared__ double kk[kMaxOps], th[kMaxOps];
   __shared__ double red_v[kDirThreads];
   __shared__ int red_i[kDirThreads];
   __shared__ double2 piv;
   __shared__ int nops, zero_col;
-  const int mmax = 2 * L + 2 * max_qp;
+  const int mmax = 2 * L + 2 * max_qp + (jmid > 0 ? 2 * jmid : 0);
   double2* U = (double2*)smem_d;                 // [m][L]
   double2* V = U + (size_t)mmax * L;             // [m][L]
   double2* T = V + (size_t)mmax * L;             // packed strict upper triangle, m (m - 1) / 2
@@ -64,39 +69,51 @@ x_direct_kernel(const int32_t* __restrict__ pairs, int64_t n_pairs, int64_t ns_o
   const double pi = 3.14159265358979323846;
   for (int64_t q = blockIdx.x; q < n_pairs; q += gridDim.x) {
     const int32_t pa = pairs[2 * q], pb = pairs[2 * q + 1];
-    if (pa < 0 || pa >= n_ns || pb < 0 || pb >= n_r) {      // block-uniform
+    if (pa < 0 || pa >= n_a || pb < 0 || pb >= n_b) {        // block-uniform
       if (threadIdx.x == 0) {
         atomicOr(status, kStBadIndex);
         out[2 * q] = out[2 * q + 1] = __longlong_as_double(0x7ff8000000000000ll);
       }
       continue;
     }
-    // the operator string (thread 0: at most 2L + 2 max_qp + 1 entries)
+    // the operator string (thread 0)
     if (threadIdx.x == 0) {
-      const int16_t* sa = modes_ns + (ns_off + pa) * max_qp;
-      const int16_t* sb = modes_r + (r_off + pb) * max_qp;
+      const int16_t* sa = (pa_par ? modes_r : modes_ns) + (a_off + pa) * max_qp;
+      const int16_t* sb = (pb_par ? modes_r : modes_ns) + (b_off + pb) * max_qp;
+      const int oa = pa_par * L, ob = pb_par * L;     // mode tables: NS modes, then R modes
       int ma = 0, mb = 0;
       while (ma < max_qp && sa[ma] >= 0) ++ma;
       while (mb < max_qp && sb[mb] >= 0) ++mb;
       int c = 0;
-      for (int i = 0; i < L; ++i) {                  // NS vacuum bra: d_k^dag, ascending
-        kind[c] = kOpDdag; kk[c] = pi * nlab[i] / L; th[c] = theta[i]; ++c;
+      for (int i = 0; i < L; ++i) {                  // bra vacuum: d_k^dag, ascending (k != pi)
+        const int n = nlab[oa + i];
+        if (n == L) continue;
+        kind[c] = kOpDdag; kk[c] = pi * n / L; th[c] = theta[oa + i]; ++c;
       }
-      for (int t = ma - 1; t >= 0; --t) {            // bra excitations: d_p, descending
-        const int i = sa[t];
-        kind[c] = kOpD; kk[c] = pi * nlab[i] / L; th[c] = theta[i]; ++c;
-      }
-      kind[c] = kOpSigma; kk[c] = 0.0; th[c] = 0.0; ++c;
-      for (int t = 0; t < mb; ++t) {                 // ket excitations: d_q^dag (c_pi^dag), ascending
-        const int i = sb[t], n = nlab[L + i];
-        if (n == L) { kind[c] = kOpCdag; kk[c] = pi; th[c] = 0.0; }
-        else { kind[c] = kOpDdag; kk[c] = pi * n / L; th[c] = theta[L + i]; }
+      for (int t = ma - 1; t >= 0; --t) {            // bra excitations: d_p, descending ((c_pi^dag)^dag)
+        const int i = sa[t], n = nlab[oa + i];
+        if (n == L) { kind[c] = kOpC; kk[c] = pi; th[c] = 0.0; }
+        else { kind[c] = kOpD; kk[c] = pi * n / L; th[c] = theta[oa + i]; }
         ++c;
       }
-      for (int i = L - 1; i >= 0; --i) {             // R vacuum ket: d_k (k != pi), descending
-        const int n = nlab[L + i];
+      if (jmid < 0) {                                // sigma^x_1 = c_1 + c_1^dag
+        kind[c] = kOpSigma; kk[c] = 0.0; th[c] = 0.0; ++c;
+      } else {                                       // sigma^x_1 sigma^x_{j+1} = B_1 A_2 B_2 ... B_j A_{j+1}
+        for (int l = 1; l <= jmid; ++l) {
+          kind[c] = kOpMajB; kk[c] = l; th[c] = 0.0; ++c;
+          kind[c] = kOpMajA; kk[c] = l + 1; th[c] = 0.0; ++c;
+        }
+      }
+      for (int t = 0; t < mb; ++t) {                 // ket excitations: d_q^dag (c_pi^dag), ascending
+        const int i = sb[t], n = nlab[ob + i];
+        if (n == L) { kind[c] = kOpCdag; kk[c] = pi; th[c] = 0.0; }
+        else { kind[c] = kOpDdag; kk[c] = pi * n / L; th[c] = theta[ob + i]; }
+        ++c;
+      }
+      for (int i = L - 1; i >= 0; --i) {             // ket vacuum: d_k (k != pi), descending
+        const int n = nlab[ob + i];
         if (n == L) continue;
-        kind[c] = kOpD; kk[c] = pi * n / L; th[c] = theta[L + i]; ++c;
+        kind[c] = kOpD; kk[c] = pi * n / L; th[c] = theta[ob + i]; ++c;
       }
       nops = c;
     }
@@ -122,6 +139,12 @@ x_direct_kernel(const int32_t* __restrict__ pairs, int64_t n_pairs, int64_t ns_o
         case kOpDdag:                                // s c_k^dag + i c c_{-k}
           cu = make_double2(s2 * ep.x, s2 * ep.y);
           cv = make_double2(-c2 * ep.y, c2 * ep.x);
+          break;
+        case kOpMajA:                                // c_l^dag + c_l at site l = kk
+          if (j == (int)kk[u]) { cu = make_double2(1.0, 0.0); cv = cu; }
+          break;
+        case kOpMajB:                                // c_l^dag - c_l
+          if (j == (int)kk[u]) { cu = make_double2(1.0, 0.0); cv = make_double2(-1.0, 0.0); }
           break;
         default:
           if (j == 1) { cu = make_double2(1.0, 0.0); cv = cu; }
@@ -218,25 +241,36 @@ x_direct_kernel(const int32_t* __restrict__ pairs, int64_t n_pairs, int64_t ns_o
 
 }  // namespace
 
-size_t x_direct_smem(int L, int max_qp) {
-  const size_t m = (size_t)(2 * L + 2 * max_qp);
+size_t x_direct_smem(int L, int max_qp, int jmid) {
+  const size_t m = (size_t)(2 * L + 2 * max_qp + (jmid > 0 ? 2 * jmid : 0));
   return sizeof(double2) * (2 * m * L + m * (m - 1) / 2 + 2 * m);
 }
 
-tgba_status x_direct(Basis& b, int s, const int32_t* pairs, int64_t n, double* out, cudaStream_t st) {
+// Elements <phi_a|O|phi_b> for explicit (a, b) pairs of sector s: O = sigma^x_1 between NS bra
+// and R ket (jmid < 0), or sigma^x_1 sigma^x_{jmid+1} between two states of parity `parity`.
+tgba_status direct_elements(Basis& b, int s, int parity, int jmid, const int32_t* pairs, int64_t n, double* out,
+                            cudaStream_t st) {
   if (n == 0) return TGBA_OK;
   const Sector& sec = b.sectors[s];
-  const size_t smem = x_direct_smem(b.L, b.max_qp);
+  const size_t smem = x_direct_smem(b.L, b.max_qp, jmid);
   TGBA_CUDA(cudaFuncSetAttribute(x_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int sms = 0;
   TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
   const int64_t grid = std::min<int64_t>(n, (int64_t)sms * 8);
-  x_direct_kernel<<<(unsigned)grid, kDirThreads, smem, st>>>(pairs, n, sec.ns_off, sec.r_off, sec.n_ns, sec.n_r, b.L,
+  const int pa_par = jmid < 0 ? 0 : parity, pb_par = jmid < 0 ? 1 : parity;
+  const int64_t a_off = pa_par ? sec.r_off : sec.ns_off, b_off = pb_par ? sec.r_off : sec.ns_off;
+  const int64_t n_a = pa_par ? sec.n_r : sec.n_ns, n_b = pb_par ? sec.n_r : sec.n_ns;
+  const double norm = jmid < 0 ? b.vac_norm : (parity ? b.norm_r * b.norm_r : b.norm_ns * b.norm_ns);
+  x_direct_kernel<<<(unsigned)grid, kDirThreads, smem, st>>>(pairs, n, pa_par, pb_par, jmid, a_off, b_off, n_a, n_b, b.L,
                                                              b.d_theta, b.d_nlab, b.d_modes_ns, b.d_modes_r, b.max_qp,
-                                                             b.vac_norm, out, b.d_status);
+                                                             norm, out, b.d_status);
   TGBA_CUDA(cudaGetLastError());
   ++b.launches;
   return TGBA_OK;
+}
+
+tgba_status x_direct(Basis& b, int s, const int32_t* pairs, int64_t n, double* out, cudaStream_t st) {
+  return direct_elements(b, s, 0, -1, pairs, n, out, st);
 }
 
 }  // namespace tgba

@@ -177,6 +177,50 @@ __global__ void eps_kernel(int n_t, int64_t knp, int64_t krp, int64_t kn, int64_
   }
 }
 
+// Z~ = G^H Z G for one parity block of sigma^x_1 sigma^x_{j+1} (Z row-major complex [k][k] over
+// the kept states idx): the real-gauge phase of a state depends only on M, and for two states of
+// one parity it is i^{sgn (M_a - M_b)/2} (sgn = +1 NS, -1 R).  Output: real and imaginary parts.
+__global__ void zgauge_kernel(int64_t k, const int32_t* __restrict__ idx, const uint8_t* __restrict__ M, int64_t off,
+                              int sgn, const double* __restrict__ Zc, double* __restrict__ Zr, double* __restrict__ Zi) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = e / k, c = e - a * k;
+    const int p = (((sgn * ((int)M[off + idx[a]] - (int)M[off + idx[c]])) / 2) % 4 + 4) % 4;
+    const double re = Zc[2 * e], im = Zc[2 * e + 1];
+    double xr = re, xi = im;
+    if (p == 1) { xr = -im; xi = re; }
+    else if (p == 2) { xr = -re; xi = -im; }
+    else if (p == 3) { xr = im; xi = -re; }
+    Zr[e] = xr;
+    Zi[e] = xi;
+  }
+}
+
+// Connected correlator for a block of cnt times: Re(B~^H Z~ B~) / ||c0||^2 - <sigma^x>^2, with
+// Y1 = Z~_re [B_re | B_im] and Y2 = Z~_im [B_re | B_im] per parity block (NS rows 0..kn-1 and R
+// rows kn..n-1 of B~, stored [Re block | Im block] with leading dimension n).
+__global__ void corr_kernel(int64_t n, int64_t kn, int64_t kr, int nb, int cnt, const double* __restrict__ B,
+                            const double* __restrict__ Y1n, const double* __restrict__ Y2n,
+                            const double* __restrict__ Y1r, const double* __restrict__ Y2r,
+                            const double* __restrict__ norm2, const double* __restrict__ mx, double* __restrict__ corr) {
+  const int lane = threadIdx.x & 31;
+  for (int t = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < cnt;
+       t += (int)(((int64_t)gridDim.x * blockDim.x) >> 5)) {
+    double acc = 0.0;
+    for (int64_t a = lane; a < kn; a += 32) {
+      const double br = B[a + (int64_t)t * n], bi = B[a + (int64_t)(nb + t) * n];
+      acc = fma(br, Y1n[a + (int64_t)t * kn] - Y2n[a + (int64_t)(nb + t) * kn],
+                fma(bi, Y1n[a + (int64_t)(nb + t) * kn] + Y2n[a + (int64_t)t * kn], acc));
+    }
+    for (int64_t a = lane; a < kr; a += 32) {
+      const double br = B[kn + a + (int64_t)t * n], bi = B[kn + a + (int64_t)(nb + t) * n];
+      acc = fma(br, Y1r[a + (int64_t)t * kr] - Y2r[a + (int64_t)(nb + t) * kr],
+                fma(bi, Y1r[a + (int64_t)(nb + t) * kr] + Y2r[a + (int64_t)t * kr], acc));
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) corr[t] = acc / norm2[0] - mx[t] * mx[t];
+  }
+}
+
 __global__ void gather_energy(int64_t kn, int64_t kr, const int32_t* __restrict__ idx_ns, const int32_t* __restrict__ idx_r,
                               const double* __restrict__ E_ns, const double* __restrict__ E_r, double* __restrict__ E) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < kn + kr; i += (int64_t)gridDim.x * blockDim.x)
@@ -290,7 +334,8 @@ static double ord_val_host(unsigned long long k) {
 }
 
 tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* trunc, int nv, int order, double t_max,
-                   int n_t, int method, double* mx, double* norm_out, double* eps_out, int64_t* chi_out, cudaStream_t st) {
+                   int n_t, int method, double* mx, double* norm_out, double* eps_out, int64_t* chi_out, cudaStream_t st,
+                   int j_max, double* corr_out) {
   const Sector& sec = b.sectors[s];
   const int L = b.L;
   // s = conj(z)/|z|, z = <0_NS(h0)|sigma_1|0_R(h0)>: the vacuum element of a table at h0
@@ -420,7 +465,7 @@ tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* t
     }
     const int64_t n = (int64_t)(sel_ns[v].size() + sel_r[v].size());
     if (n == 0) return fail(TGBA_EINVAL, "a quench variant keeps no states");
-    if (eps_out && (method == 2 || (method == 0 && n > kEigenMaxStates)))
+    if ((eps_out || j_max > 0) && (method == 2 || (method == 0 && n > kEigenMaxStates)))
       return fail(TGBA_EINVAL, "the convergence metric needs the eigendecomposition method (at most 4096 states "
                                "with method 0)");
     n_max = std::max(n_max, n);
@@ -482,6 +527,46 @@ tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* t
       double* XB = B + 2 * n * nb;
       if ((r = build_real_heff(b, s, hx[v], U, idx, kn, idx + kn, kr, st)) != TGBA_OK) return r;
       if ((r = eig_sym(b, n, U, E, true, st)) != TGBA_OK) return r;
+      // correlators: Z~_j of the kept NS-NS and R-R blocks by direct Pfaffians, before the time loop
+      double* zbuf = nullptr;
+      double *Zr_ns = nullptr, *Zi_ns = nullptr, *Zr_r = nullptr, *Zi_r = nullptr, *Yb = nullptr;
+      struct FreeZ {
+        double** p; cudaStream_t s;
+        ~FreeZ() { if (*p) cudaFreeAsync(*p, s); }
+      } free_z{&zbuf, st};
+      if (j_max > 0) {
+        const int64_t kmax = std::max(kn, kr);
+        const size_t zdoubles = (size_t)j_max * 2 * (kn * kn + kr * kr) + 2 * (size_t)kmax * kmax +
+                                4 * (size_t)kmax * 2 * nb + (size_t)kmax * kmax + 16;
+        TGBA_CUDA(cudaMallocAsync(&zbuf, zdoubles * sizeof(double), st));
+        Zr_ns = zbuf;
+        Zi_ns = Zr_ns + (size_t)j_max * kn * kn;
+        Zr_r = Zi_ns + (size_t)j_max * kn * kn;
+        Zi_r = Zr_r + (size_t)j_max * kr * kr;
+        double* Zc = Zi_r + (size_t)j_max * kr * kr;
+        Yb = Zc + 2 * (size_t)kmax * kmax;
+        int32_t* zp = (int32_t*)(Yb + 4 * (size_t)kmax * 2 * nb);
+        for (int par = 0; par < 2; ++par) {
+          const std::vector<int32_t>& lst = par ? ir : ins;
+          const int64_t k = (int64_t)lst.size();
+          if (k == 0) continue;
+          std::vector<int32_t> hp(2 * (size_t)k * k);
+          for (int64_t x = 0; x < k; ++x)
+            for (int64_t y = 0; y < k; ++y) { hp[2 * (x * k + y)] = lst[x]; hp[2 * (x * k + y) + 1] = lst[y]; }
+          TGBA_CUDA(cudaMemcpyAsync(zp, hp.data(), hp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+          int32_t* didx = (int32_t*)(par ? idx + kn : idx);
+          for (int j = 1; j <= j_max; ++j) {
+            if ((r = direct_elements(b, s, par, j, zp, k * k, Zc, st)) != TGBA_OK) return r;
+            double* zr = (par ? Zr_r : Zr_ns) + (size_t)(j - 1) * k * k;
+            double* zi = (par ? Zi_r : Zi_ns) + (size_t)(j - 1) * k * k;
+            zgauge_kernel<<<blocks_for(k * k), 256, 0, st>>>(k, didx, par ? b.d_M_r : b.d_M_ns, par ? sec.r_off : sec.ns_off,
+                                                             par ? -1 : 1, Zc, zr, zi);
+            TGBA_CUDA(cudaGetLastError());
+            ++b.launches;
+          }
+          TGBA_CUDA(cudaStreamSynchronize(st));      // hp is reused for the other parity
+        }
+      }
       // a = U~^T c~0: two real products (strided complex input)
       cs = cublasDgemv(bh, CUBLAS_OP_T, (int)n, (int)n, &one, U, (int)n, c, 2, &zero, a, 1);
       if (cs == CUBLAS_STATUS_SUCCESS) cs = cublasDgemv(bh, CUBLAS_OP_T, (int)n, (int)n, &one, U, (int)n, c + 1, 2, &zero, a + n, 1);
@@ -506,6 +591,39 @@ tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* t
         quad_kernel<<<(cnt * 32 + 255) / 256, 256, 0, st>>>(n, nb, cnt, B, XB, norm2, mx + (int64_t)v * n_t + t0);
         TGBA_CUDA(cudaGetLastError());
         ++b.launches;
+        if (j_max > 0) {                              // <sigma^x_1 sigma^x_{j+1}>(t), connected
+          double* Y1n = Yb;
+          double* Y2n = Y1n + (size_t)std::max<int64_t>(kn, 1) * 2 * nb;
+          double* Y1r = Y2n + (size_t)std::max<int64_t>(kn, 1) * 2 * nb;
+          double* Y2r = Y1r + (size_t)std::max<int64_t>(kr, 1) * 2 * nb;
+          for (int j = 1; j <= j_max; ++j) {
+            if (kn > 0) {
+              const double* zr = Zr_ns + (size_t)(j - 1) * kn * kn;
+              const double* zi = Zi_ns + (size_t)(j - 1) * kn * kn;
+              cs = cublasDgemm(bh, CUBLAS_OP_T, CUBLAS_OP_N, (int)kn, 2 * nb, (int)kn, &one, zr, (int)kn, B, (int)n, &zero,
+                               Y1n, (int)kn);
+              if (cs == CUBLAS_STATUS_SUCCESS)
+                cs = cublasDgemm(bh, CUBLAS_OP_T, CUBLAS_OP_N, (int)kn, 2 * nb, (int)kn, &one, zi, (int)kn, B, (int)n,
+                                 &zero, Y2n, (int)kn);
+              if (cs != CUBLAS_STATUS_SUCCESS) return blas_fail(cs, "gemm Z B (NS)");
+            }
+            if (kr > 0) {
+              const double* zr = Zr_r + (size_t)(j - 1) * kr * kr;
+              const double* zi = Zi_r + (size_t)(j - 1) * kr * kr;
+              cs = cublasDgemm(bh, CUBLAS_OP_T, CUBLAS_OP_N, (int)kr, 2 * nb, (int)kr, &one, zr, (int)kr, B + kn, (int)n,
+                               &zero, Y1r, (int)kr);
+              if (cs == CUBLAS_STATUS_SUCCESS)
+                cs = cublasDgemm(bh, CUBLAS_OP_T, CUBLAS_OP_N, (int)kr, 2 * nb, (int)kr, &one, zi, (int)kr, B + kn,
+                                 (int)n, &zero, Y2r, (int)kr);
+              if (cs != CUBLAS_STATUS_SUCCESS) return blas_fail(cs, "gemm Z B (R)");
+            }
+            corr_kernel<<<(cnt * 32 + 255) / 256, 256, 0, st>>>(n, kn, kr, nb, cnt, B, Y1n, Y2n, Y1r, Y2r, norm2,
+                                                                mx + (int64_t)v * n_t + t0,
+                                                                corr_out + ((int64_t)v * j_max + (j - 1)) * n_t + t0);
+            TGBA_CUDA(cudaGetLastError());
+            ++b.launches;
+          }
+        }
         if (Bcur) {                                   // keep B(t) of this variant for Eq. 11
           TGBA_CUDA(cudaMemcpyAsync(Bcur + (size_t)t0 * n, B, (size_t)n * cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
           TGBA_CUDA(cudaMemcpyAsync(Bcur + (size_t)(n_t + t0) * n, B + (size_t)n * nb, (size_t)n * cnt * sizeof(double),

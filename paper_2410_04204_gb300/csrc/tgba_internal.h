@@ -113,6 +113,7 @@ struct Basis {
   double* d_theta = nullptr;       // [2L]
   int* d_nlab = nullptr;           // [2L]
   double vac_norm = 1;             // n_NS n_R (Eq. S3)
+  double norm_ns = 1, norm_r = 1;   // n_NS, n_R
   // contraction table
   double* d_table = nullptr;       // R, 2L x 2L row-major
   double* d_c0 = nullptr;          // C0 (re, im), then diagnostics: max |Im| residual, max |R|
@@ -176,8 +177,11 @@ tgba_status autotune_pfaffians(Basis& b, cudaStream_t st);
 tgba_status run_pfaffians(Basis& b, const uint8_t* d_mask, cudaStream_t st);
 tgba_status run_pfaffian_pairs(Basis& b, int s, const int32_t* pairs, int64_t n, double* out, cudaStream_t st);
 // direct.cu: X of explicit pairs by the paper-literal Pfaffian of size 2L + M_a + M_b
-size_t x_direct_smem(int L, int max_qp);
+size_t x_direct_smem(int L, int max_qp, int jmid);
 tgba_status x_direct(Basis& b, int s, const int32_t* pairs, int64_t n, double* out, cudaStream_t st);
+// <phi_a| sigma^x_1 sigma^x_{jmid+1} |phi_b> for pairs of parity `parity` (jmid >= 0), or X (jmid < 0)
+tgba_status direct_elements(Basis& b, int s, int parity, int jmid, const int32_t* pairs, int64_t n, double* out,
+                            cudaStream_t st);
 // real P of every (NS state of sector s_ns, R state of sector s_r) pair, out [n_ns][n_r] row-major
 tgba_status run_pfaffian_cross(Basis& b, int s_ns, int s_r, double* out, cudaStream_t st);
 
@@ -212,8 +216,10 @@ tgba_status dsf_k(Basis& b, int s, int s0, double h_x, double w_min, double w_ma
 // order 0: trunc = energy cutoffs above the NS vacuum (< 0: all); order 1: trunc = numbers of
 // states chi, kept in order of |<phi|Phi0>|.  eps (optional, device, nv - 1): Eq. 11 between
 // successive variants (they must be nested).
+// j_max > 0 (eigen path): corr [nv][j_max][n_t] receives <sigma^x_1 sigma^x_{j+1}>(t) - <sigma^x>(t)^2
 tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* trunc, int nv, int order, double t_max,
-                   int n_t, int method, double* mx, double* norm, double* eps, int64_t* chi, cudaStream_t st);
+                   int n_t, int method, double* mx, double* norm, double* eps, int64_t* chi, cudaStream_t st,
+                   int j_max = 0, double* corr = nullptr);
 
 // screen.cu
 struct Screen;

@@ -19,7 +19,7 @@ _NAMES = {0: "TGBA_OK", 1: "TGBA_EINVAL", 2: "TGBA_ENOMEM", 3: "TGBA_ECUDA", 4: 
 # every symbol include/tgba.h declares
 SYMBOLS = ("tgba_last_error", "tgba_device_count", "tgba_build_basis", "tgba_basis_info", "tgba_basis_totals",
            "tgba_basis_free", "tgba_compute_x", "tgba_x_stats", "tgba_x_export", "tgba_x_pairs", "tgba_x_direct", "tgba_table",
-           "tgba_assemble_heff", "tgba_eigvals", "tgba_eigvals_ex", "tgba_dsf", "tgba_dsf_k", "tgba_quench", "tgba_quench_ordered", "tgba_screen_create",
+           "tgba_assemble_heff", "tgba_eigvals", "tgba_eigvals_ex", "tgba_dsf", "tgba_dsf_k", "tgba_quench", "tgba_quench_ordered", "tgba_quench_correlators", "tgba_screen_create",
            "tgba_screen_nparams", "tgba_screen_params", "tgba_screen_grad", "tgba_screen_train",
            "tgba_screen_predict", "tgba_screen_free", "tgba_table_noalloc", "tgba_profile", "tgba_fp64_peak")
 
@@ -79,6 +79,8 @@ def lib():
             "tgba_quench": (_I32, [_VP, _I32, _D, _VP, _VP, _I32, _D, _I32, _I32, _VP, _VP, _VP, _VP]),
             "tgba_quench_ordered": (_I32, [_VP, _I32, _D, _VP, _VP, _I32, _I32, _D, _I32, _I32, _VP, _VP, _VP, _VP,
                                            _VP]),
+            "tgba_quench_correlators": (_I32, [_VP, _I32, _D, _D, _D, _I32, _D, _I32, _I32, _VP, _VP, _VP, _VP,
+                                               _VP]),
             "tgba_screen_create": (_I32, [_I32, _VP, ctypes.c_uint64, _P(_VP)]),
             "tgba_screen_nparams": (_I32, [_VP, _P(_I64)]),
             "tgba_screen_params": (_I32, [_VP, _VP]),
@@ -302,6 +304,21 @@ def tgba_quench_ordered(b, s, h_z0, hx_variants, trunc_variants, order, t_max, n
                                      float(t_max), int(n_t), int(method), _ptr(mx_out), _ptr(norm_out),
                                      _ptr(eps_out), chi.ctypes.data, _stream(stream)))
     return chi
+
+
+def tgba_quench_correlators(b, s, h_z0, h_x, trunc, order, t_max, n_t, j_max, mx_out, corr_out, norm_out=None,
+                            stream=None):
+    """<sigma^x_1 sigma^x_{j+1}>(t) - <sigma^x>(t)^2, j = 1..j_max, for one truncated quench.
+    Returns the kept basis size."""
+    import torch
+    _cuda_tensor(mx_out, torch.float64, n_t, name="mx_out")
+    _cuda_tensor(corr_out, torch.float64, j_max * n_t, name="corr_out")
+    _cuda_tensor(norm_out, torch.float64, 1, name="norm_out")
+    chi = np.zeros(1, np.int64)
+    _check(lib().tgba_quench_correlators(b, s, float(h_z0), float(h_x), float(trunc), int(order), float(t_max),
+                                         int(n_t), int(j_max), _ptr(mx_out), _ptr(corr_out), _ptr(norm_out),
+                                         chi.ctypes.data, _stream(stream)))
+    return int(chi[0])
 
 
 def tgba_screen_create(width=256, params=None, seed=0):
