@@ -259,9 +259,8 @@ def screening_leg(b24, tgba, inputs, torch):
 
 
 # DRAM bytes of one sytrd_groups launch on the L = 24 all-sector workload, measured with ncu
-# (dram__bytes_read.sum 4.980e11 + dram__bytes_write.sum 5.245e11); to be re-measured whenever
-# the kernel changes.
-SYTRD_TRAFFIC = 4.97974480640e11 + 5.24546127104e11
+# (dram__bytes_read.sum + dram__bytes_write.sum); None until measured for the current kernel.
+SYTRD_TRAFFIC = None
 
 
 def eigen_solver_leg(b, w, evs, tgba, torch):

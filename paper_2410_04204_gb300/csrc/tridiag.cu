@@ -42,8 +42,7 @@
 namespace tgba {
 namespace {
 
-constexpr int kWarps = 12;                      // 3 per SM sub-partition
-constexpr int kThreads = kWarps * 32;
+constexpr int kWarps = 12;                      // warps per CTA at most (two CTAs of 6 per SM, or one of 12)
 constexpr int kCols = 16;                       // columns of a work block (rows: 32)
 constexpr int kMaxGroup = 16;                   // CTAs cooperating on one matrix
 constexpr unsigned kSpinLimit = 1u << 24;       // bounded barrier wait (>= 100 ns per poll: over 1 s)
@@ -123,6 +122,7 @@ __device__ __forceinline__ bool group_barrier(unsigned* cnt, unsigned target, in
 
 // Sum over the block in a fixed order (lane 0 of each warp, then warps in order); every thread
 // gets the same value.
+template <int WARPS>
 __device__ __forceinline__ double block_sum(double x, double* red) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -130,7 +130,7 @@ __device__ __forceinline__ double block_sum(double x, double* red) {
   __syncthreads();
   double s = red[0];
 #pragma unroll
-  for (int w = 1; w < kWarps; ++w) s += red[w];
+  for (int w = 1; w < WARPS; ++w) s += red[w];
   __syncthreads();
   return s;
 }
@@ -251,6 +251,7 @@ __device__ __forceinline__ void sytrd_chunk(double* __restrict__ A, int ld, int 
 
 // All n - 1 reflections of one matrix, as CTA `rank` of its group of C.  Returns false if a
 // group barrier gave up.
+template <int WARPS>
 __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsigned* cnt, double* __restrict__ ws,
                                           unsigned* __restrict__ status, int* flag) {
   extern __shared__ double sm[];
@@ -269,39 +270,39 @@ __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsi
   int* sw = (int*)(red + kRed);                   // [W + 1] first block of each warp
   int* gw = sw + kMaxWarpsPerGroup + 1;         // [2 G] first and last warp meeting each group
   __syncthreads();                                // the previous matrix is done with sm
-  for (int i = threadIdx.x; i < 4 * ld; i += kThreads) sm[i] = 0.0;
+  for (int i = threadIdx.x; i < 4 * ld; i += (WARPS * 32)) sm[i] = 0.0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int W = kWarps * C, wid = warp * C + rank;
+  const int W = WARPS * C, wid = warp * C + rank;
   bool bad = false;
   for (int j = 0; j < n; ++j) {
     // column j of A_j: the stored column (already updated through step j - 2) minus the
     // rank-2 update of step j - 1; rows j + 2 .. n - 1 go into the norm
     const double2 vwj = vwp[j];
     double sig = 0.0;
-    for (int i = j + threadIdx.x; i < n; i += kThreads) {
+    for (int i = j + threadIdx.x; i < n; i += (WARPS * 32)) {
       const double2 vwi = vwp[i];
       double a = __ldcg(A + elem_off(i, j, LB));
       a = fma(-vwi.x, vwj.y, a);
       a = fma(-vwi.y, vwj.x, a);
-      if (i == j) red[kWarps] = a;
-      else if (i == j + 1) red[kWarps + 1] = a;
+      if (i == j) red[WARPS] = a;
+      else if (i == j + 1) red[WARPS + 1] = a;
       else sig = fma(a, a, sig);
       vwn[i].x = a;
     }
     // the step's work split (integer only), published by block_sum's barrier
     const int g0 = (j + 1) / kCols, NG = G - g0;
     const int NB = group_first(NG, g0, LB);
-    for (int w = threadIdx.x; w <= W; w += kThreads) sw[w] = (int)((int64_t)NB * w / W);
-    sig = block_sum(sig, red);
-    for (int t = threadIdx.x; t < NG; t += kThreads) {
+    for (int w = threadIdx.x; w <= W; w += (WARPS * 32)) sw[w] = (int)((int64_t)NB * w / W);
+    sig = block_sum<WARPS>(sig, red);
+    for (int t = threadIdx.x; t < NG; t += (WARPS * 32)) {
       gw[2 * t] = warp_of(sw, W, group_first(t, g0, LB));
       gw[2 * t + 1] = warp_of(sw, W, group_first(t + 1, g0, LB) - 1);
     }
-    const double dj = red[kWarps];
+    const double dj = red[WARPS];
     if (rank == 0 && threadIdx.x == 0) D[j] = dj;
     if (j + 1 >= n) break;                            // uniform: the last diagonal entry
-    const double alpha = red[kWarps + 1];
+    const double alpha = red[WARPS + 1];
     // Householder reflector H = I - tau v v^T with v_{j+1} = 1 mapping column j to beta e_{j+1}
     double tau = 0.0, beta = alpha, s = 0.0;
     if (sig != 0.0) {
@@ -312,7 +313,7 @@ __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsi
     }
     if (rank == 0 && threadIdx.x == 0) E[j] = beta;
     if (threadIdx.x == 0 && !(isfinite(dj) && isfinite(beta))) bad = true;
-    for (int i = threadIdx.x; i < ld; i += kThreads) {
+    for (int i = threadIdx.x; i < ld; i += (WARPS * 32)) {
       const double x = vwn[i].x;
       vwn[i].x = i == j + 1 ? 1.0 : (i > j + 1 && i < n ? x * s : 0.0);
     }
@@ -346,7 +347,7 @@ __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsi
     // (contiguous, read with independent loads) + the column sums of the warps whose ranges
     // met column i's group; p = tau y
     double dot = 0.0;
-    for (int i = j + 1 + rank + C * threadIdx.x; i < n; i += C * kThreads) {
+    for (int i = j + 1 + rank + C * threadIdx.x; i < n; i += C * (WARPS * 32)) {
       const int gi = i / kCols;
       const double* rr = RP + (int64_t)i * G;
       double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
@@ -366,14 +367,14 @@ __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsi
       __stcg(P + i, p);
       dot = fma(p, vwn[i].x, dot);
     }
-    dot = block_sum(dot, red);
+    dot = block_sum<WARPS>(dot, red);
     if (threadIdx.x == 0) __stcg(dots + rank, dot);
     arrivals += C;
     if (!group_barrier(cnt, arrivals, C, flag, status)) return false;
     double pv = 0.0;
     for (int r = 0; r < C; ++r) pv += __ldcg(dots + r);
     const double Kc = 0.5 * tau * pv;
-    for (int i = threadIdx.x; i < ld; i += kThreads)
+    for (int i = threadIdx.x; i < ld; i += (WARPS * 32))
       vwn[i].y = (i > j && i < n) ? fma(-Kc, vwn[i].x, __ldcg(P + i)) : 0.0;
     __syncthreads();
     double2* t = vwp; vwp = vwn; vwn = t;
@@ -382,14 +383,15 @@ __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsi
   return true;
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 12 / WARPS)
 sytrd_groups(const TriSlot* __restrict__ slots, int B, const CtaWork* __restrict__ work, unsigned* __restrict__ counters,
              double* __restrict__ ws, unsigned* __restrict__ status) {
   __shared__ int flag;
   const CtaWork cw = work[blockIdx.x];
   const int C = cw.C, rank = cw.rank;
   for (int q = cw.first; q < B; q += cw.stride)
-    if (!sytrd_matrix(slots[q], C, rank, counters + q, ws, status, &flag)) return;
+    if (!sytrd_matrix<WARPS>(slots[q], C, rank, counters + q, ws, status, &flag)) return;
 }
 
 // Number of eigenvalues of T below x: sign changes of P_0 = 1, P_1, ..., P_n with
@@ -555,15 +557,30 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
   int dev = 0, sms = 0;
   TGBA_CUDA(cudaGetDevice(&dev));
   TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  // One CTA per SM.  With no more matrices than SMs, every SM joins one matrix's group: each
-  // matrix starts with one CTA and the remaining CTAs go, one at a time, to the matrix with the
-  // most work (n^3) per CTA, at most 16 per matrix.  With more matrices than SMs, CTA b takes
-  // matrices b, b + SMs, ... alone.
+  // One or two CTAs per SM: two of 6 warps when their shared memory fits (each SM then runs
+  // parts of two matrices, and one's barrier waits and serial phases are filled by the other's
+  // arithmetic), else one of 12 warps.  With no more matrices than CTAs, every CTA joins one
+  // matrix's group: each matrix starts with one CTA and the remaining CTAs go, one at a time,
+  // to the matrix with the most work (n^3) per CTA, at most 16 per matrix.  With more matrices
+  // than CTAs, CTA b takes matrices b, b + CTAs, ... alone.
+  const size_t smem = (size_t)(4 * ld_max + kRed) * sizeof(double) +
+                      (size_t)(kMaxWarpsPerGroup + 1 + 2 * kMaxGroups) * sizeof(int);
+  TGBA_CUDA(cudaFuncSetAttribute(sytrd_groups<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TGBA_CUDA(cudaFuncSetAttribute(sytrd_groups<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  TGBA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sytrd_groups<6>, 6 * 32, smem));
+  per_sm = per_sm >= 2 ? 2 : 1;
+  if (per_sm == 1) {
+    int one = 0;
+    TGBA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&one, sytrd_groups<12>, 12 * 32, smem));
+    if (one < 1) return fail(TGBA_EINVAL, "the tridiagonalisation's shared memory does not fit on an SM");
+  }
+  const int ctas = per_sm * sms;
   std::vector<CtaWork> map;
   int C_max = 1;
-  if (B <= sms) {
+  if (B <= ctas) {
     std::vector<int> Cq(B, 1);
-    for (int left = sms - B; left > 0; --left) {
+    for (int left = ctas - B; left > 0; --left) {
       int best = -1;
       double best_w = -1.0;
       for (int q = 0; q < B; ++q) {
@@ -578,7 +595,7 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
       C_max = std::max(C_max, Cq[q]);
     }
   } else {
-    for (int q = 0; q < sms; ++q) map.push_back({q, 0, 1, sms});
+    for (int q = 0; q < ctas; ++q) map.push_back({q, 0, 1, ctas});
   }
   const int grid = (int)map.size();
   const int64_t slot_doubles = round32(((int64_t)B * sizeof(TriSlot) + 7) / 8);
@@ -602,12 +619,9 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
     TGBA_CUDA(cudaGetLastError());
     ++b.launches;
   }
-  const size_t smem = (size_t)(4 * ld_max + kRed) * sizeof(double) +
-                      (size_t)(kMaxWarpsPerGroup + 1 + 2 * kMaxGroups) * sizeof(int);
-  TGBA_CUDA(cudaFuncSetAttribute(sytrd_groups, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(per_sm == 2 ? 6 * 32 : 12 * 32);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -618,8 +632,12 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
   for (int e = 0; e < 3; ++e)
     if (b.eig_ev[e] == nullptr) TGBA_CUDA(cudaEventCreate(&b.eig_ev[e]));
   TGBA_CUDA(cudaEventRecord(b.eig_ev[0], st));
-  TGBA_CUDA(cudaLaunchKernelEx(&cfg, sytrd_groups, (const TriSlot*)d_slots, B, (const CtaWork*)d_map, d_cnt, ws,
-                               b.d_status));
+  if (per_sm == 2)
+    TGBA_CUDA(cudaLaunchKernelEx(&cfg, sytrd_groups<6>, (const TriSlot*)d_slots, B, (const CtaWork*)d_map, d_cnt, ws,
+                                 b.d_status));
+  else
+    TGBA_CUDA(cudaLaunchKernelEx(&cfg, sytrd_groups<12>, (const TriSlot*)d_slots, B, (const CtaWork*)d_map, d_cnt, ws,
+                                 b.d_status));
   ++b.launches;
   TGBA_CUDA(cudaEventRecord(b.eig_ev[1], st));
   const size_t smem2 = (size_t)2 * n_max * sizeof(double);

@@ -3,7 +3,7 @@ then bisection on Sturm counts) through the C ABI, against exact diagonalisation
 chain (Eq. 1 on a complete basis), against LAPACK on the same H_eff (Eq. 2) and against the
 library solver.  The batch size decides how many CTAs share a matrix (up to 16; a single CTA
 looping over matrices when there are more matrices than SMs), so the cases below cover one,
-several and more-than-SMs batches."""
+several and more-than-CTAs batches."""
 import numpy as np
 import pytest
 import torch
@@ -66,8 +66,8 @@ def test_native_complete_basis_equals_ed(L, fields):
 
 
 def test_native_single_matrix_and_full_batch_match_library():
-    """One matrix (a group of 16 CTAs) and 156 matrices (more than the 152 SMs: single CTAs that
-    loop over matrices) against cuSOLVER."""
+    """One matrix (a group of 16 CTAs) and 312 matrices (more than the 304 CTAs of two per SM:
+    single CTAs that loop over matrices) against cuSOLVER."""
     L, h = 12, 1.0
     b = tgba.tgba_build_basis(L, h, [0], L)
     try:
@@ -81,7 +81,7 @@ def test_native_single_matrix_and_full_batch_match_library():
     b = tgba.tgba_build_basis(L, h, list(range(L)), L)
     try:
         tgba.tgba_compute_x(b)
-        fields = list(np.linspace(0.02, 0.5, 13))          # 13 x 12 = 156 matrices
+        fields = list(np.linspace(0.02, 0.5, 26))          # 26 x 12 = 312 matrices, more than the CTAs
         e1, e2 = _evals(b, fields, 1), _evals(b, fields, 2)
         assert np.abs(e1 - e2).max() < 1e-10 * np.abs(e2).max()
     finally:
