@@ -4,7 +4,7 @@
 // Two kernels per batch of (field, sector) matrices:
 //
 // 1. sytrd_groups: Householder reduction to tridiagonal form, T = Q^T H Q.  One cooperative
-//    launch with one CTA per SM; the SMs are shared out among the matrices in proportion to
+//    launch with two CTAs of 6 warps per SM (one of 12 if two do not fit); the CTAs are shared out among the matrices in proportion to
 //    their work (n^3), so a group of C CTAs (1 to 16) owns one matrix and runs all n - 1
 //    reflections.  (Hardware thread-block clusters were tried first: their placement left
 //    SMs idle, e.g. at most 46 clusters of 3 or 15 of 8 could be resident, so 48 matrices ran in
@@ -22,7 +22,9 @@
 //    flight during the current block's arithmetic.  Partials go to global buffers and are
 //    added in a fixed order, so results do not depend on scheduling.  The CTAs of a group meet
 //    at two barriers per step: an arrival counter in global memory with a bounded wait (a
-//    timeout sets an error bit and the kernel returns).
+//    timeout sets an error bit and the kernel returns).  The pass rewrites column j, which the
+//    other CTAs read in the same step to build v_j, so a second counter records that each CTA
+//    has read it, and only the warps whose blocks hold column j wait for it (bounded too).
 // 2. sturm_bisect: every eigenvalue by bisection on the Sturm count of T - x, one thread per
 //    eigenvalue, with the scaled three-term determinant recurrence (three FP64 operations per
 //    row and no divisions; sign changes counted on the integer bits), starting from a
@@ -118,6 +120,19 @@ __device__ __forceinline__ bool group_barrier(unsigned* cnt, unsigned target, in
   }
   __syncthreads();
   return *flag != 0;
+}
+
+// One warp waits (every lane acquiring for itself, bounded like group_barrier) until the
+// counter reaches target; on timeout it records kStTimeout and goes on (the result is then
+// reported as failed).
+__device__ __forceinline__ void warp_wait(const unsigned* cnt, unsigned target, unsigned* status) {
+  for (unsigned it = 0; ld_acquire(cnt) < target; ++it) {
+    if (it > kSpinLimit) {
+      if ((threadIdx.x & 31) == 0) atomicOr(status, kStTimeout);
+      return;
+    }
+    __nanosleep(64);
+  }
 }
 
 // Sum over the block in a fixed order (lane 0 of each warp, then warps in order); every thread
@@ -252,10 +267,11 @@ __device__ __forceinline__ void sytrd_chunk(double* __restrict__ A, int ld, int 
 // All n - 1 reflections of one matrix, as CTA `rank` of its group of C.  Returns false if a
 // group barrier gave up.
 template <int WARPS>
-__device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsigned* cnt, double* __restrict__ ws,
+__device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsigned* cnt, unsigned* ccnt,
+                                          double* __restrict__ ws,
                                           unsigned* __restrict__ status, int* flag) {
   extern __shared__ double sm[];
-  unsigned arrivals = 0;
+  unsigned arrivals = 0, col_arrivals = 0;
   const int n = S.n, ld = S.ld, LB = ld >> 5, G = ld / kCols;
   double* A = ws + S.a_off;
   double* RP = ws + S.rp_off;
@@ -295,6 +311,13 @@ __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsi
     const int NB = group_first(NG, g0, LB);
     for (int w = threadIdx.x; w <= W; w += (WARPS * 32)) sw[w] = (int)((int64_t)NB * w / W);
     sig = block_sum<WARPS>(sig, red);
+    // this CTA has read column j (block_sum's barrier): the pass below rewrites it, so its
+    // warps that store column j wait until every CTA of the group has arrived here
+    if (C > 1 && threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(ccnt, 1u);
+    }
+    col_arrivals += C;
     for (int t = threadIdx.x; t < NG; t += (WARPS * 32)) {
       gw[2 * t] = warp_of(sw, W, group_first(t, g0, LB));
       gw[2 * t + 1] = warp_of(sw, W, group_first(t + 1, g0, LB) - 1);
@@ -333,6 +356,7 @@ __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsi
         while (sb < se) {
           const int g = g0 + gq, nbg = LB - (g >> 1);
           const int b1 = min(nbg, b + (se - sb));
+          if (C > 1 && gq == 0 && (j + 1) % kCols != 0) warp_wait(ccnt, col_arrivals, status);
           sytrd_chunk(A, ld, LB, g, (g >> 1) + b, (g >> 1) + b1, lane, wid, vwp, vwn, RP, CP);
           sb += b1 - b;
           ++gq;
@@ -391,7 +415,7 @@ sytrd_groups(const TriSlot* __restrict__ slots, int B, const CtaWork* __restrict
   const CtaWork cw = work[blockIdx.x];
   const int C = cw.C, rank = cw.rank;
   for (int q = cw.first; q < B; q += cw.stride)
-    if (!sytrd_matrix<WARPS>(slots[q], C, rank, counters + q, ws, status, &flag)) return;
+    if (!sytrd_matrix<WARPS>(slots[q], C, rank, counters + q, counters + B + q, ws, status, &flag)) return;
 }
 
 // Number of eigenvalues of T below x: sign changes of P_0 = 1, P_1, ..., P_n with
@@ -600,7 +624,7 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
   const int grid = (int)map.size();
   const int64_t slot_doubles = round32(((int64_t)B * sizeof(TriSlot) + 7) / 8);
   const int64_t map_doubles = round32(((int64_t)grid * sizeof(CtaWork) + 7) / 8);
-  const int64_t cnt_doubles = round32((B + 1) / 2);
+  const int64_t cnt_doubles = round32(B);                      // 2 B counters: barriers, column reads
   double* ws;
   tgba_status r = scratch(b, total + slot_doubles + map_doubles + cnt_doubles, &ws);
   if (r != TGBA_OK) return r;
@@ -609,7 +633,7 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
   unsigned* d_cnt = (unsigned*)(ws + total + slot_doubles + map_doubles);
   TGBA_CUDA(cudaMemcpyAsync(d_slots, slots.data(), B * sizeof(TriSlot), cudaMemcpyHostToDevice, st));
   TGBA_CUDA(cudaMemcpyAsync(d_map, map.data(), grid * sizeof(CtaWork), cudaMemcpyHostToDevice, st));
-  TGBA_CUDA(cudaMemsetAsync(d_cnt, 0, B * sizeof(unsigned), st));
+  TGBA_CUDA(cudaMemsetAsync(d_cnt, 0, 2 * B * sizeof(unsigned), st));
   for (int q = 0; q < B; ++q) {
     const Sector& sec = b.sectors[who[q].second];
     const int64_t work = (int64_t)slots[q].ld * slots[q].ld;
