@@ -4,27 +4,31 @@
 // Two kernels per batch of (field, sector) matrices:
 //
 // 1. sytrd_groups: Householder reduction to tridiagonal form, T = Q^T H Q.  One cooperative
-//    launch with two CTAs of 6 warps per SM (one of 12 if two do not fit); the CTAs are shared out among the matrices in proportion to
-//    their work (n^3), so a group of C CTAs (1 to 16) owns one matrix and runs all n - 1
-//    reflections.  (Hardware thread-block clusters were tried first: their placement left
-//    SMs idle, e.g. at most 46 clusters of 3 or 15 of 8 could be resident, so 48 matrices ran in
-//    two or more waves.)  Step j builds the reflector v_j from column j, then makes ONE pass over the
-//    trailing lower triangle that both applies the rank-2 update of step j - 1,
+//    launch with two CTAs of 6 warps per SM (one of 12 if two do not fit); the CTAs are shared
+//    out among the matrices in proportion to their work (n^3), so a group of C CTAs (1 to 16)
+//    owns one matrix and runs all n - 1 reflections, and each SM's two CTAs come from different
+//    matrices with even loads (cta_role).  (Hardware thread-block clusters were tried first:
+//    their placement left SMs idle, e.g. at most 46 clusters of 3 or 15 of 8 could be resident,
+//    so 48 matrices ran in two or more waves.)  Step j builds the reflector v_j from column j,
+//    then makes ONE pass over the trailing lower triangle that both applies the rank-2 update
+//    of step j - 1,
 //        A <- A - v_{j-1} w_{j-1}^T - w_{j-1} v_{j-1}^T,
 //    and accumulates the symmetric product y = A v_j for step j; so every trailing element is
 //    read and written once per step with four FMAs.  The trailing lower triangle is cut into
-//    blocks of 32 rows x 16 columns, numbered column group by column group, and warp w of the
-//    group's W warps takes the contiguous blocks [NB w / W, NB (w + 1) / W): equal work for
-//    every warp, whatever the size of the trailing block.  In a block a lane owns one row: its
-//    row sum needs no communication, and its 16 column partial sums stay in registers over the
-//    warp's run of blocks in one column group, then one transpose-reduce (31 adds per lane)
-//    sums them over the warp.  Two block buffers in registers keep the next block's loads in
-//    flight during the current block's arithmetic.  Partials go to global buffers and are
-//    added in a fixed order, so results do not depend on scheduling.  The CTAs of a group meet
-//    at two barriers per step: an arrival counter in global memory with a bounded wait (a
-//    timeout sets an error bit and the kernel returns).  The pass rewrites column j, which the
-//    other CTAs read in the same step to build v_j, so a second counter records that each CTA
-//    has read it, and only the warps whose blocks hold column j wait for it (bounded too).
+//    blocks of 32 rows x 16 columns, and each column group's blocks into chunks of up to
+//    kChunk consecutive blocks.  Warps draw chunks from a per-step ticket counter of the
+//    group, so warps and CTAs that run faster (a less busy co-resident CTA, a less crowded
+//    SM sub-partition) take more of them.  In a block a lane owns one row: its row sum needs
+//    no communication, and its 16 column partial sums stay in registers over the chunk, then
+//    one transpose-reduce (16 adds per lane) sums them over the warp.  Two block buffers in
+//    registers keep the next block's loads in flight during the current block's arithmetic.
+//    Row sums go to a slot per (row, column group) and column sums to a slot per chunk, added
+//    in a fixed order, so results do not depend on which warp took which chunk.  The CTAs of
+//    a group meet at two barriers per step: an arrival counter in global memory with a
+//    bounded wait (a timeout sets an error bit and the kernel returns).  The pass rewrites
+//    column j, which the other CTAs read in the same step to build v_j, so a second counter
+//    records that each CTA has read it, and a warp waits for it (bounded too) before its
+//    first chunk of the group that holds column j.
 // 2. sturm_bisect: every eigenvalue by bisection on the Sturm count of T - x, one thread per
 //    eigenvalue, with the scaled three-term determinant recurrence (three FP64 operations per
 //    row and no divisions; sign changes counted on the integer bits), starting from a
@@ -44,19 +48,20 @@
 namespace tgba {
 namespace {
 
-constexpr int kWarps = 12;                      // warps per CTA at most (two CTAs of 6 per SM, or one of 12)
 constexpr int kCols = 16;                       // columns of a work block (rows: 32)
 constexpr int kMaxGroup = 16;                   // CTAs cooperating on one matrix
 constexpr unsigned kSpinLimit = 1u << 24;       // bounded barrier wait (>= 100 ns per poll: over 1 s)
 constexpr int kRed = 64;                        // reduction scratch (doubles) after the vectors
-constexpr int kMaxWarpsPerGroup = kWarps * kMaxGroup;
+constexpr int kChunk = 8;                       // row blocks per chunk of the pass
+constexpr int kMaxSmId = 1024;                  // SM ids registered by cta_role
 constexpr int kMaxGroups = kMaxNativeLd / kCols;
 constexpr int kSturmThreads = 128;
 
 struct TriSlot {
   int64_t a_off;    // matrix, ld x ld in 32 x 16 tiles (blk_off), zero beyond n, lower triangle used
   int64_t rp_off;   // row sums of the 32 x 16 blocks [ld][ld / 16]: a row's partials contiguous
-  int64_t cp_off;   // column sums of each warp's blocks [warps of a group][ld]
+  int64_t cp_off;   // column sums of each chunk of a step [chunks][16]
+  int64_t tk_off;   // the matrix's step tickets (one counter per step) in the counter array
   int64_t p_off;    // p = tau A v [ld], then one dot partial per CTA of the group [16]
   int64_t de_off;   // diagonal d [n], off-diagonal e [n]
   int64_t out_off;  // first eigenvalue in the caller's output
@@ -152,23 +157,9 @@ __device__ __forceinline__ double block_sum(double x, double* red) {
 
 // Work of one step.  Column group g holds columns 16 g .. 16 g + 15; its blocks are the 32-row
 // blocks rb = g / 2 .. LB - 1 (rows 32 rb .. 32 rb + 31, LB = ld / 32), the first on the
-// diagonal.  Groups g0 .. G - 1 are numbered one after another.
-__device__ __forceinline__ int half_sum(int x) {   // sum over g < x of floor(g / 2)
-  const int p = x >> 1;
-  return (x & 1) ? p * p : p * (p - 1);
-}
-// linear index of the first block of group g0 + q
-__device__ __forceinline__ int group_first(int q, int g0, int LB) { return q * LB - (half_sum(g0 + q) - half_sum(g0)); }
-// the warp whose range holds block b: the last w with s[w] <= b (s non-decreasing, s[0] = 0)
-__device__ __forceinline__ int warp_of(const int* __restrict__ s, int W, int b) {
-  int lo = 0, hi = W;                    // s[lo] <= b < s[hi]
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (s[mid] <= b) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
+// diagonal.  A chunk is up to kChunk consecutive blocks of one group; the chunks of groups
+// g0 .. G - 1 are numbered group by group, cf[t] being the first chunk of group g0 + t.
+__device__ __forceinline__ int group_chunks(int g, int LB) { return (LB - (g >> 1) + kChunk - 1) / kChunk; }
 
 __device__ __forceinline__ void load_block(double (&a)[kCols], const double* __restrict__ p) {
 #pragma unroll
@@ -211,30 +202,30 @@ __device__ __forceinline__ void sytrd_block(const double (&a)[kCols], double* __
   __stcg(rp + (int64_t)i * G, r0 + r1);
 }
 
-// Lanes l and l + 16 end with the sum over all 32 lanes of cs[l & 15]: the two half-warps are
-// added first, then a transpose-reduce over 16 lanes (at level s, lanes with bit s set keep
-// the upper half of the values).  31 adds per lane.
+// Column sums of a warp's run of blocks: cs[m] holds the lane's partial sum of column m.  At
+// levels s = 16, 8, 4, 2 a lane keeps half of its values (the upper half if it has bit s set)
+// and adds its partner's copy of them, so the values a lane holds halve at every level; a last
+// exchange with lane l ^ 1 completes the sum.  Lane l ends with the total of column l >> 1,
+// after 16 adds.
 __device__ __forceinline__ double transpose_reduce16(double (&cs)[kCols], int lane) {
 #pragma unroll
-  for (int m = 0; m < kCols; ++m) cs[m] += __shfl_xor_sync(0xffffffffu, cs[m], 16);
-#pragma unroll
-  for (int s = 8; s >= 1; s >>= 1) {
+  for (int h = kCols / 2, s = 16; h >= 1; h >>= 1, s >>= 1) {
     const bool up = (lane & s) != 0;
 #pragma unroll
-    for (int m = 0; m < s; ++m) {
-      const double send = isel(up, cs[m], cs[m + s]);
-      const double keep = isel(up, cs[m + s], cs[m]);
+    for (int m = 0; m < h; ++m) {
+      const double send = isel(up, cs[m], cs[m + h]);
+      const double keep = isel(up, cs[m + h], cs[m]);
       cs[m] = keep + __shfl_xor_sync(0xffffffffu, send, s);
     }
   }
-  return cs[0];
+  return cs[0] + __shfl_xor_sync(0xffffffffu, cs[0], 1);
 }
 
-// Row blocks [rb_b, rb_e) of column group g.  Two block buffers in registers: the loads of the
-// next block are in flight while the current one is computed.  Then the warp's column sums of
-// the group go to CP[w].
+// Chunk c of the step: row blocks [rb_b, rb_e) of column group g.  Two block buffers in
+// registers: the loads of the next block are in flight while the current one is computed.
+// The chunk's 16 column sums go to CP[16 c ..].
 __device__ __forceinline__ void sytrd_chunk(double* __restrict__ A, int ld, int LB, int g, int rb_b, int rb_e,
-                                            int lane, int w, const double2* __restrict__ vwp,
+                                            int lane, int c, const double2* __restrict__ vwp,
                                             const double2* __restrict__ vwn, double* __restrict__ RP,
                                             double* __restrict__ CP) {
   const int k0 = kCols * g;
@@ -261,15 +252,15 @@ __device__ __forceinline__ void sytrd_chunk(double* __restrict__ A, int ld, int 
   }
   if (rb < rb_e) sytrd_block<false>(cur, gp + 512 * rb, 32 * rb + lane, k0, vwp, vwn, cs, rp, G);
   const double colsum = transpose_reduce16(cs, lane);
-  if (lane < kCols) __stcg(CP + (int64_t)w * ld + k0 + lane, colsum);
+  if ((lane & 1) == 0) __stcg(CP + (int64_t)c * kCols + (lane >> 1), colsum);
 }
 
 // All n - 1 reflections of one matrix, as CTA `rank` of its group of C.  Returns false if a
 // group barrier gave up.
 template <int WARPS>
 __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsigned* cnt, unsigned* ccnt,
-                                          double* __restrict__ ws,
-                                          unsigned* __restrict__ status, int* flag) {
+                                          unsigned* tk, double* __restrict__ ws, unsigned* __restrict__ status,
+                                          int* flag) {
   extern __shared__ double sm[];
   unsigned arrivals = 0, col_arrivals = 0;
   const int n = S.n, ld = S.ld, LB = ld >> 5, G = ld / kCols;
@@ -283,13 +274,11 @@ __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsi
   double2* vwp = (double2*)sm;                   // (v_{j-1}, w_{j-1}) per index
   double2* vwn = (double2*)(sm + 2 * ld);         // (v_j, w_j)
   double* red = sm + 4 * ld;
-  int* sw = (int*)(red + kRed);                   // [W + 1] first block of each warp
-  int* gw = sw + kMaxWarpsPerGroup + 1;         // [2 G] first and last warp meeting each group
+  int* cf = (int*)(red + kRed);                   // [NG + 1] first chunk of each group
   __syncthreads();                                // the previous matrix is done with sm
   for (int i = threadIdx.x; i < 4 * ld; i += (WARPS * 32)) sm[i] = 0.0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int W = WARPS * C, wid = warp * C + rank;
   bool bad = false;
   for (int j = 0; j < n; ++j) {
     // column j of A_j: the stored column (already updated through step j - 2) minus the
@@ -306,33 +295,49 @@ __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsi
       else sig = fma(a, a, sig);
       vwn[i].x = a;
     }
-    // the step's work split (integer only), published by block_sum's barrier
+    // the step's chunk table (a scan by warp 0 over groups g0 .. G - 1), published by
+    // block_sum's barrier
     const int g0 = (j + 1) / kCols, NG = G - g0;
-    const int NB = group_first(NG, g0, LB);
-    for (int w = threadIdx.x; w <= W; w += (WARPS * 32)) sw[w] = (int)((int64_t)NB * w / W);
+    if (warp == 0) {
+      const int per = (NG + 31) >> 5, t0 = min(NG, lane * per), t1 = min(NG, t0 + per);
+      int own = 0;
+      for (int t = t0; t < t1; ++t) own += group_chunks(g0 + t, LB);
+      int incl = own;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      int run = incl - own;
+      for (int t = t0; t < t1; ++t) {
+        cf[t] = run;
+        run += group_chunks(g0 + t, LB);
+      }
+      if (lane == 31) cf[NG] = incl;
+    }
     sig = block_sum<WARPS>(sig, red);
-    // this CTA has read column j (block_sum's barrier): the pass below rewrites it, so its
+    // this CTA has read column j (block_sum's barrier): the pass below rewrites it, so the
     // warps that store column j wait until every CTA of the group has arrived here
     if (C > 1 && threadIdx.x == 0) {
       __threadfence();
       atomicAdd(ccnt, 1u);
     }
     col_arrivals += C;
-    for (int t = threadIdx.x; t < NG; t += (WARPS * 32)) {
-      gw[2 * t] = warp_of(sw, W, group_first(t, g0, LB));
-      gw[2 * t + 1] = warp_of(sw, W, group_first(t + 1, g0, LB) - 1);
-    }
     const double dj = red[WARPS];
     if (rank == 0 && threadIdx.x == 0) D[j] = dj;
     if (j + 1 >= n) break;                            // uniform: the last diagonal entry
     const double alpha = red[WARPS + 1];
     // Householder reflector H = I - tau v v^T with v_{j+1} = 1 mapping column j to beta e_{j+1}
-    double tau = 0.0, beta = alpha, s = 0.0;
-    if (sig != 0.0) {
-      const double nrm = sqrt(fma(alpha, alpha, sig));
-      beta = alpha >= 0.0 ? -nrm : nrm;
-      tau = (beta - alpha) / beta;
-      s = 1.0 / (alpha - beta);
+    double beta = alpha, s = 0.0;
+    {
+      double tau = 0.0;
+      if (sig != 0.0) {
+        const double nrm = sqrt(fma(alpha, alpha, sig));
+        beta = alpha >= 0.0 ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+        s = 1.0 / (alpha - beta);
+      }
+      if (threadIdx.x == 0) red[WARPS + 2] = tau;     // read back after the pass
     }
     if (rank == 0 && threadIdx.x == 0) E[j] = beta;
     if (threadIdx.x == 0 && !(isfinite(dj) && isfinite(beta))) bad = true;
@@ -341,36 +346,41 @@ __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsi
       vwn[i].x = i == j + 1 ? 1.0 : (i > j + 1 && i < n ? x * s : 0.0);
     }
     __syncthreads();
-    // one pass over the trailing lower triangle: update of step j - 1 and y = A_j v_j
+    // one pass over the trailing lower triangle: update of step j - 1 and y = A_j v_j.  The
+    // chunks go out one at a time from the step's ticket counter (the next ticket is drawn
+    // while a chunk is computed), so warps and CTAs that run faster take more of them.
     {
-      int sb = sw[wid];
-      const int se = sw[wid + 1];
-      if (sb < se) {
-        int lo = 0, hi = NG;                          // group_first(lo) <= sb < group_first(hi)
+      const int NCH = cf[NG];
+      bool waited = !(C > 1 && (j + 1) % kCols != 0);   // column j lies in group g0
+      unsigned c = 0;
+      if (lane == 0) c = atomicAdd(tk + j, 1u);
+      c = __shfl_sync(0xffffffffu, c, 0);
+      while ((int)c < NCH) {
+        unsigned cn = 0;
+        if (lane == 0) cn = atomicAdd(tk + j, 1u);
+        int lo = 0, hi = NG;                          // cf[lo] <= c < cf[hi]
         while (hi - lo > 1) {
           const int mid = (lo + hi) >> 1;
-          if (group_first(mid, g0, LB) <= sb) lo = mid;
+          if (cf[mid] <= (int)c) lo = mid;
           else hi = mid;
         }
-        int gq = lo, b = sb - group_first(gq, g0, LB);
-        while (sb < se) {
-          const int g = g0 + gq, nbg = LB - (g >> 1);
-          const int b1 = min(nbg, b + (se - sb));
-          if (C > 1 && gq == 0 && (j + 1) % kCols != 0) warp_wait(ccnt, col_arrivals, status);
-          sytrd_chunk(A, ld, LB, g, (g >> 1) + b, (g >> 1) + b1, lane, wid, vwp, vwn, RP, CP);
-          sb += b1 - b;
-          ++gq;
-          b = 0;
+        const int g = g0 + lo, rb = (g >> 1) + ((int)c - cf[lo]) * kChunk;
+        if (lo == 0 && !waited) {
+          warp_wait(ccnt, col_arrivals, status);
+          waited = true;
         }
+        sytrd_chunk(A, ld, LB, g, rb, min(rb + kChunk, LB), lane, (int)c, vwp, vwn, RP, CP);
+        c = __shfl_sync(0xffffffffu, cn, 0);
       }
     }
     arrivals += C;
     if (!group_barrier(cnt, arrivals, C, flag, status)) return false;
     // rows j + 1 .. n - 1, interleaved over the group's CTAs (row i to CTA i mod C, so the
     // long rows at the bottom are shared): y_i = row sums of the blocks of groups g0 .. i/16
-    // (contiguous, read with independent loads) + the column sums of the warps whose ranges
-    // met column i's group; p = tau y
+    // (contiguous, read with independent loads) + the column sums of the chunks of column
+    // i's group, in chunk order; p = tau y
     double dot = 0.0;
+    const double tau = red[WARPS + 2];
     for (int i = j + 1 + rank + C * threadIdx.x; i < n; i += C * (WARPS * 32)) {
       const int gi = i / kCols;
       const double* rr = RP + (int64_t)i * G;
@@ -385,8 +395,7 @@ __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsi
       for (; g <= gi; ++g) y0 += __ldcg(rr + g);
       double y = (y0 + y1) + (y2 + y3);
       const int t = gi - g0;
-      for (int w = gw[2 * t]; w <= gw[2 * t + 1]; ++w)
-        if (sw[w] < sw[w + 1]) y += __ldcg(CP + (int64_t)w * ld + i);
+      for (int c = cf[t]; c < cf[t + 1]; ++c) y += __ldcg(CP + (int64_t)c * kCols + (i & (kCols - 1)));
       const double p = tau * y;
       __stcg(P + i, p);
       dot = fma(p, vwn[i].x, dot);
@@ -407,15 +416,82 @@ __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsi
   return true;
 }
 
+// Which CTA plays which role.  A cooperative launch of per_sm CTAs on each of the sms SMs fills
+// every SM, but which blockIdx lands on which SM is the hardware's choice, and it can put two
+// CTAs of one matrix on one SM (their serial phases then coincide) or two heavy ones together.
+// With work_sm given, each CTA registers its SM id (reg[id] counts arrivals per SM, then the
+// total and an error flag), and once all have registered takes work_sm[d per_sm + slot], where
+// d is the SM's rank among the occupied SM ids and slot its arrival order there; the host
+// builds work_sm so that an SM's CTAs come from different matrices and the SMs' loads are even.
+// Unless every SM holds exactly per_sm CTAs, all CTAs take work_blk[blockIdx] instead (the
+// registration ends the same way for every CTA, so they all decide alike).
+__device__ bool cta_role(const CtaWork* __restrict__ work_blk, const CtaWork* __restrict__ work_sm, int per_sm,
+                         int sms, unsigned* reg, unsigned* status, CtaWork* out) {
+  __shared__ unsigned s_smid, s_slot;
+  __shared__ int s_state, s_occ, s_below;
+  if (threadIdx.x == 0) {
+    s_state = 1;
+    s_occ = 0;
+    s_below = 0;
+    if (work_sm != nullptr) {
+      unsigned smid;
+      asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+      unsigned slot = 0;
+      if (smid < kMaxSmId) slot = atomicAdd(reg + smid, 1u);
+      if (smid >= kMaxSmId || slot >= (unsigned)per_sm) atomicOr(reg + kMaxSmId + 1, 1u);
+      __threadfence();
+      atomicAdd(reg + kMaxSmId, 1u);
+      unsigned it = 0;
+      while (ld_acquire(reg + kMaxSmId) < gridDim.x && it <= kSpinLimit) {
+        __nanosleep(100);
+        ++it;
+      }
+      if (it > kSpinLimit) {
+        atomicOr(status, kStTimeout);
+        s_state = 0;
+      } else {
+        s_state = ld_acquire(reg + kMaxSmId + 1) == 0 ? 2 : 1;
+      }
+      s_smid = smid;
+      s_slot = slot;
+    }
+  }
+  __syncthreads();
+  const int state = s_state;
+  if (state == 0) return false;
+  if (state == 2) {
+    int occ = 0, below = 0;
+    for (int id = threadIdx.x; id < kMaxSmId; id += blockDim.x)
+      if (__ldcg(reg + id) != 0u) {
+        ++occ;
+        below += id < (int)s_smid;
+      }
+    atomicAdd(&s_occ, occ);
+    atomicAdd(&s_below, below);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    *out = (state == 2 && s_occ == sms) ? work_sm[s_below * per_sm + (int)s_slot] : work_blk[blockIdx.x];
+  __syncthreads();
+  return true;
+}
+
+// counters: [B] barrier arrivals, [B] column-j reads, then each matrix's step tickets
+// (at 2 B + tk_off, one per step); reg: the SM registration of cta_role.
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 12 / WARPS)
-sytrd_groups(const TriSlot* __restrict__ slots, int B, const CtaWork* __restrict__ work, unsigned* __restrict__ counters,
-             double* __restrict__ ws, unsigned* __restrict__ status) {
+sytrd_groups(const TriSlot* __restrict__ slots, int B, const CtaWork* __restrict__ work_blk,
+             const CtaWork* __restrict__ work_sm, int per_sm, int sms, unsigned* __restrict__ reg,
+             unsigned* __restrict__ counters, double* __restrict__ ws, unsigned* __restrict__ status) {
   __shared__ int flag;
-  const CtaWork cw = work[blockIdx.x];
+  __shared__ CtaWork cw_s;
+  if (!cta_role(work_blk, work_sm, per_sm, sms, reg, status, &cw_s)) return;
+  const CtaWork cw = cw_s;
   const int C = cw.C, rank = cw.rank;
   for (int q = cw.first; q < B; q += cw.stride)
-    if (!sytrd_matrix<WARPS>(slots[q], C, rank, counters + q, counters + B + q, ws, status, &flag)) return;
+    if (!sytrd_matrix<WARPS>(slots[q], C, rank, counters + q, counters + B + q, counters + 2 * B + slots[q].tk_off,
+                             ws, status, &flag))
+      return;
 }
 
 // Number of eigenvalues of T below x: sign changes of P_0 = 1, P_1, ..., P_n with
@@ -549,12 +625,20 @@ __global__ void fill_sym(int64_t kn, int64_t kr, int ld, const double* __restric
 
 int64_t round32(int64_t x) { return (x + 31) / 32 * 32; }
 
+// Chunks of the first step (g0 = 0), the most of any step.
+int64_t max_chunks(int ld) {
+  const int LB = ld >> 5;
+  int64_t c = 0;
+  for (int g = 0; g < ld / kCols; ++g) c += (LB - (g >> 1) + kChunk - 1) / kChunk;
+  return c;
+}
+
 }  // namespace
 
 tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double* evals, cudaStream_t st) {
   std::vector<TriSlot> slots;
   std::vector<std::pair<int, int>> who;     // (field, sector)
-  int64_t total = 0;
+  int64_t total = 0, tk_total = 0;
   int n_max = 0;
   for (int h = 0; h < n_hx; ++h)
     for (size_t s = 0; s < b.sectors.size(); ++s) {
@@ -566,7 +650,8 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
       t.out_off = (int64_t)h * b.n_states + b.sectors[s].ev_off;
       t.a_off = total;            total += round32((int64_t)t.ld * t.ld);
       t.rp_off = total;           total += round32((int64_t)(t.ld / kCols) * t.ld);
-      t.cp_off = total;           total += round32((int64_t)kMaxWarpsPerGroup * t.ld);
+      t.cp_off = total;           total += round32((int64_t)kCols * max_chunks(t.ld));
+      t.tk_off = tk_total;        tk_total += t.ld;
       t.p_off = total;            total += round32(t.ld + kMaxGroup);
       t.de_off = total;           total += round32(2 * n);
       slots.push_back(t);
@@ -588,7 +673,7 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
   // to the matrix with the most work (n^3) per CTA, at most 16 per matrix.  With more matrices
   // than CTAs, CTA b takes matrices b, b + CTAs, ... alone.
   const size_t smem = (size_t)(4 * ld_max + kRed) * sizeof(double) +
-                      (size_t)(kMaxWarpsPerGroup + 1 + 2 * kMaxGroups) * sizeof(int);
+                      (size_t)(kMaxGroups + 1) * sizeof(int);
   TGBA_CUDA(cudaFuncSetAttribute(sytrd_groups<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   TGBA_CUDA(cudaFuncSetAttribute(sytrd_groups<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
@@ -622,9 +707,32 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
     for (int q = 0; q < ctas; ++q) map.push_back({q, 0, 1, ctas});
   }
   const int grid = (int)map.size();
+  // The SMs' pairs when every SM holds two CTAs: the CTAs sorted by their work n^3 / C, the
+  // k-th heaviest shares an SM with the k-th lightest (even loads), and pairs from one matrix
+  // are broken up by exchanging partners with another SM.
+  std::vector<CtaWork> sm_map;
+  if (per_sm == 2 && grid == ctas) {
+    std::vector<int> ord(grid);
+    for (int c = 0; c < grid; ++c) ord[c] = c;
+    auto wt = [&](int c) { const double n = slots[map[c].first].n; return n * n * n / map[c].C; };
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return wt(x) > wt(y); });
+    std::vector<int> lo(sms), hi(sms);
+    for (int d = 0; d < sms; ++d) { hi[d] = ord[d]; lo[d] = ord[grid - 1 - d]; }
+    for (int d = 0; d < sms; ++d) {
+      if (map[hi[d]].first != map[lo[d]].first) continue;
+      for (int e = 0; e < sms; ++e)
+        if (map[lo[e]].first != map[hi[d]].first && map[hi[e]].first != map[lo[d]].first) {
+          std::swap(lo[d], lo[e]);
+          break;
+        }
+    }
+    sm_map.resize(grid);
+    for (int d = 0; d < sms; ++d) { sm_map[2 * d] = map[hi[d]]; sm_map[2 * d + 1] = map[lo[d]]; }
+  }
   const int64_t slot_doubles = round32(((int64_t)B * sizeof(TriSlot) + 7) / 8);
-  const int64_t map_doubles = round32(((int64_t)grid * sizeof(CtaWork) + 7) / 8);
-  const int64_t cnt_doubles = round32(B);                      // 2 B counters: barriers, column reads
+  const int64_t map_doubles = round32(((int64_t)2 * grid * sizeof(CtaWork) + 7) / 8);   // by block, by SM
+  const int64_t n_cnt = 2 * (int64_t)B + tk_total + kMaxSmId + 2;   // barriers, column reads, tickets, SMs
+  const int64_t cnt_doubles = round32((n_cnt + 1) / 2);
   double* ws;
   tgba_status r = scratch(b, total + slot_doubles + map_doubles + cnt_doubles, &ws);
   if (r != TGBA_OK) return r;
@@ -633,7 +741,13 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
   unsigned* d_cnt = (unsigned*)(ws + total + slot_doubles + map_doubles);
   TGBA_CUDA(cudaMemcpyAsync(d_slots, slots.data(), B * sizeof(TriSlot), cudaMemcpyHostToDevice, st));
   TGBA_CUDA(cudaMemcpyAsync(d_map, map.data(), grid * sizeof(CtaWork), cudaMemcpyHostToDevice, st));
-  TGBA_CUDA(cudaMemsetAsync(d_cnt, 0, 2 * B * sizeof(unsigned), st));
+  CtaWork* d_sm_map = nullptr;
+  if (!sm_map.empty()) {
+    d_sm_map = d_map + grid;
+    TGBA_CUDA(cudaMemcpyAsync(d_sm_map, sm_map.data(), grid * sizeof(CtaWork), cudaMemcpyHostToDevice, st));
+  }
+  unsigned* d_reg = d_cnt + 2 * B + tk_total;
+  TGBA_CUDA(cudaMemsetAsync(d_cnt, 0, n_cnt * sizeof(unsigned), st));
   for (int q = 0; q < B; ++q) {
     const Sector& sec = b.sectors[who[q].second];
     const int64_t work = (int64_t)slots[q].ld * slots[q].ld;
@@ -657,11 +771,11 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
     if (b.eig_ev[e] == nullptr) TGBA_CUDA(cudaEventCreate(&b.eig_ev[e]));
   TGBA_CUDA(cudaEventRecord(b.eig_ev[0], st));
   if (per_sm == 2)
-    TGBA_CUDA(cudaLaunchKernelEx(&cfg, sytrd_groups<6>, (const TriSlot*)d_slots, B, (const CtaWork*)d_map, d_cnt, ws,
-                                 b.d_status));
+    TGBA_CUDA(cudaLaunchKernelEx(&cfg, sytrd_groups<6>, (const TriSlot*)d_slots, B, (const CtaWork*)d_map,
+                                 (const CtaWork*)d_sm_map, per_sm, sms, d_reg, d_cnt, ws, b.d_status));
   else
-    TGBA_CUDA(cudaLaunchKernelEx(&cfg, sytrd_groups<12>, (const TriSlot*)d_slots, B, (const CtaWork*)d_map, d_cnt, ws,
-                                 b.d_status));
+    TGBA_CUDA(cudaLaunchKernelEx(&cfg, sytrd_groups<12>, (const TriSlot*)d_slots, B, (const CtaWork*)d_map,
+                                 (const CtaWork*)d_sm_map, per_sm, sms, d_reg, d_cnt, ws, b.d_status));
   ++b.launches;
   TGBA_CUDA(cudaEventRecord(b.eig_ev[1], st));
   const size_t smem2 = (size_t)2 * n_max * sizeof(double);
