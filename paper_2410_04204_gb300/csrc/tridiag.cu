@@ -31,8 +31,10 @@
 //    first chunk of the group that holds column j.
 // 2. sturm_bisect: every eigenvalue by bisection on the Sturm count of T - x, one thread per
 //    eigenvalue, with the scaled three-term determinant recurrence (three FP64 operations per
-//    row and no divisions; sign changes counted on the integer bits), starting from a
-//    128-point grid of counts shared by the block.
+//    row and no divisions; sign changes counted on the integer bits): a grid of counts shared
+//    by the block and the first bisection steps in single precision, within a proven error
+//    bound, then the last steps in FP64.  Persistent blocks draw items of 64 eigenvalues from
+//    a queue.
 //
 // FP64 throughput on this GPU is 1/64 of FP32, so the design counts FP64 instructions: the
 // reduction is 4 FMAs per trailing element per step (4n^3/3 flops per matrix); selects, masks,
@@ -55,7 +57,7 @@ constexpr int kRed = 64;                        // reduction scratch (doubles) a
 constexpr int kChunk = 8;                       // row blocks per chunk of the pass
 constexpr int kMaxSmId = 1024;                  // SM ids registered by cta_role
 constexpr int kMaxGroups = kMaxNativeLd / kCols;
-constexpr int kSturmThreads = 128;
+constexpr int kSturmThreads = 64;                // bisection block: one item of 64 eigenvalues
 
 struct TriSlot {
   int64_t a_off;    // matrix, ld x ld in 32 x 16 tiles (blk_off), zero beyond n, lower triangle used
@@ -375,30 +377,43 @@ __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsi
     }
     arrivals += C;
     if (!group_barrier(cnt, arrivals, C, flag, status)) return false;
-    // rows j + 1 .. n - 1, interleaved over the group's CTAs (row i to CTA i mod C, so the
-    // long rows at the bottom are shared): y_i = row sums of the blocks of groups g0 .. i/16
-    // (contiguous, read with independent loads) + the column sums of the chunks of column
-    // i's group, in chunk order; p = tau y
+    // rows j + 1 .. n - 1, interleaved over the group's CTAs and, within a CTA, over quads of
+    // lanes (row i to CTA i mod C; the long rows at the bottom are shared out): y_i = row sums
+    // of the blocks of groups g0 .. i/16 + the column sums of the chunks of column i's group.
+    // Lane q of the quad adds the partials with index = q mod 4 (four loads in flight each),
+    // then the quad adds its four sums in a fixed order; p = tau y
     double dot = 0.0;
     const double tau = red[WARPS + 2];
-    for (int i = j + 1 + rank + C * threadIdx.x; i < n; i += C * (WARPS * 32)) {
-      const int gi = i / kCols;
-      const double* rr = RP + (int64_t)i * G;
-      double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
-      int g = g0;
-      for (; g + 4 <= gi + 1; g += 4) {
-        y0 += __ldcg(rr + g);
-        y1 += __ldcg(rr + g + 1);
-        y2 += __ldcg(rr + g + 2);
-        y3 += __ldcg(rr + g + 3);
+    {
+      const int q4 = lane & 3;
+      const int quad = threadIdx.x >> 2, QS = C * (WARPS * 8);      // quads of the group
+      const int i_first = j + 1 + rank + C * (threadIdx.x >> 5) * 8;  // the warp's first row
+      for (int base = 0; i_first + base < n; base += QS) {
+        const int i = j + 1 + rank + C * quad + base;
+        double y = 0.0;
+        if (i < n) {
+          const int gi = i / kCols, t = gi - g0;
+          const double* rr = RP + (int64_t)i * G;
+          double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
+          int g = g0 + q4;
+          for (; g + 12 <= gi; g += 16) {
+            y0 += __ldcg(rr + g);
+            y1 += __ldcg(rr + g + 4);
+            y2 += __ldcg(rr + g + 8);
+            y3 += __ldcg(rr + g + 12);
+          }
+          for (; g <= gi; g += 4) y0 += __ldcg(rr + g);
+          for (int c = cf[t] + q4; c < cf[t + 1]; c += 4) y1 += __ldcg(CP + (int64_t)c * kCols + (i & (kCols - 1)));
+          y = (y0 + y1) + (y2 + y3);
+        }
+        y += __shfl_xor_sync(0xffffffffu, y, 1);
+        y += __shfl_xor_sync(0xffffffffu, y, 2);
+        if (i < n && q4 == 0) {
+          const double p = tau * y;
+          __stcg(P + i, p);
+          dot = fma(p, vwn[i].x, dot);
+        }
       }
-      for (; g <= gi; ++g) y0 += __ldcg(rr + g);
-      double y = (y0 + y1) + (y2 + y3);
-      const int t = gi - g0;
-      for (int c = cf[t]; c < cf[t + 1]; ++c) y += __ldcg(CP + (int64_t)c * kCols + (i & (kCols - 1)));
-      const double p = tau * y;
-      __stcg(P + i, p);
-      dot = fma(p, vwn[i].x, dot);
     }
     dot = block_sum<WARPS>(dot, red);
     if (threadIdx.x == 0) __stcg(dots + rank, dot);
@@ -534,69 +549,150 @@ __device__ __forceinline__ int sturm_count(const double* __restrict__ d, const d
   return cnt;
 }
 
+// The same count in single precision on T scaled to norm below 1 (d and e^2 as floats).  It
+// is the exact count of a matrix T'(x) with |d'_i - d_i| <= u (2 |d_i| + |x|) and
+// |e'_i - e_i| <= 2 u |e_i| (u = 2^-24): the rounding of d - x perturbs d_i, and the roundings
+// of e^2 P_{i-2} and of the fused update rescale the terms, which moves into e^2 (the same
+// argument as for the ratio form of the recurrence).  So by Weyl's inequality its eigenvalues
+// are within 5 u ||T||_inf of T's, and a bracket it finds, widened by 8 u ||T||_inf on each
+// side, holds the eigenvalue.  Zero terms take the smallest normal float, as above.
+__device__ __forceinline__ float nonzero_or_flip32(float pn, float pc) {
+  const unsigned b = __float_as_uint(pn);
+  return (b << 1) == 0u ? __uint_as_float((~__float_as_uint(pc) & 0x80000000u) | 0x00800000u) : pn;
+}
+
+__device__ __forceinline__ int sturm_count32(const float* __restrict__ d, const float* __restrict__ e2, int n,
+                                             float x) {
+  float pm = 1.0f, pc = nonzero_or_flip32(d[0] - x, 1.0f);
+  int cnt = (int)(__float_as_uint(pc) >> 31);
+  int i = 1;
+  for (; i + 8 <= n; i += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float pn = nonzero_or_flip32(fmaf(d[i + u] - x, pc, -e2[i + u - 1] * pm), pc);
+      cnt += (int)((__float_as_uint(pn) ^ __float_as_uint(pc)) >> 31);
+      pm = pc;
+      pc = pn;
+    }
+    const int em = max((int)((__float_as_uint(pm) >> 23) & 0xff), (int)((__float_as_uint(pc) >> 23) & 0xff));
+    const float sc = __uint_as_float((unsigned)min(254, max(1, 254 - em)) << 23);
+    pm *= sc;
+    pc *= sc;
+  }
+  for (; i < n; ++i) {
+    const float pn = nonzero_or_flip32(fmaf(d[i] - x, pc, -e2[i - 1] * pm), pc);
+    cnt += (int)((__float_as_uint(pn) ^ __float_as_uint(pc)) >> 31);
+    pm = pc;
+    pc = pn;
+  }
+  return cnt;
+}
+
+// Eigenvalues of the tridiagonal matrices by bisection, one thread per eigenvalue.  The grid
+// is persistent: a block takes items (a matrix and item_len <= 64 consecutive eigenvalue indices) from
+// the queue until none is left, so the SMs stay evenly loaded.  Per item: Gershgorin bounds
+// [lo, hi] and ||T||; a 64-point grid of single-precision counts shared by the block, then
+// single-precision bisection down to a bracket of 2^-21 ||T|| (FP32 runs at 64 times the FP64
+// rate on this GPU); the bracket widened by the FP32 count's error bound is checked with two
+// FP64 counts (if the check fails the FP64 bisection restarts from the Gershgorin interval),
+// then FP64 bisection to 4 eps ||T||.
 __global__ void __launch_bounds__(kSturmThreads)
-sturm_bisect(const TriSlot* __restrict__ slots, const double* __restrict__ ws, double* __restrict__ evals,
+sturm_bisect(const TriSlot* __restrict__ slots, const int2* __restrict__ items, int n_items, int item_len,
+             unsigned* __restrict__ queue, const double* __restrict__ ws, double* __restrict__ evals,
              unsigned* __restrict__ status) {
   extern __shared__ double sm[];
   __shared__ double red[2 * (kSturmThreads / 32)];
   __shared__ int grid_cnt[kSturmThreads];
-  const TriSlot S = slots[blockIdx.y];
-  const int n = S.n;
-  if ((int)blockIdx.x * kSturmThreads >= n) return;     // block-uniform
-  const double* D = ws + S.de_off;
-  const double* E = D + n;
-  double* d = sm;
-  double* e2 = sm + n;
-  double lo = 1e300, hi = -1e300;
-  for (int i = threadIdx.x; i < n; i += kSturmThreads) {
-    const double di = D[i];
-    const double el = i > 0 ? fabs(E[i - 1]) : 0.0, er = i + 1 < n ? fabs(E[i]) : 0.0;
-    d[i] = di;
-    e2[i] = i + 1 < n ? E[i] * E[i] : 0.0;
-    lo = fmin(lo, di - el - er);
-    hi = fmax(hi, di + el + er);
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-  }
+  __shared__ int item_s;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) { red[warp] = lo; red[kSturmThreads / 32 + warp] = hi; }
-  __syncthreads();
-  lo = red[0];
-  hi = red[kSturmThreads / 32];
-  for (int w = 1; w < kSturmThreads / 32; ++w) { lo = fmin(lo, red[w]); hi = fmax(hi, red[kSturmThreads / 32 + w]); }
-  const int k = blockIdx.x * kSturmThreads + threadIdx.x;
-  if (!(isfinite(lo) && isfinite(hi))) {                    // block-uniform
-    if (threadIdx.x == 0) atomicOr(status, kStEigen);
-    if (k < n) evals[S.out_off + k] = __longlong_as_double(0x7ff8000000000000ll);
-    return;
+  for (;;) {
+    __syncthreads();                                          // the previous item is done with sm
+    if (threadIdx.x == 0) item_s = (int)atomicAdd(queue, 1u);
+    __syncthreads();
+    const int it = item_s;
+    if (it >= n_items) return;                                // block-uniform
+    const int2 wk = items[it];
+    const TriSlot S = slots[wk.x];
+    const int n = S.n;
+    const double* D = ws + S.de_off;
+    const double* E = D + n;
+    double* d = sm;
+    double* e2 = sm + n;
+    float* d32 = (float*)(sm + 2 * n);
+    float* e32 = d32 + n;
+    double lo = 1e300, hi = -1e300;
+    for (int i = threadIdx.x; i < n; i += kSturmThreads) {
+      const double di = D[i];
+      const double el = i > 0 ? fabs(E[i - 1]) : 0.0, er = i + 1 < n ? fabs(E[i]) : 0.0;
+      d[i] = di;
+      e2[i] = i + 1 < n ? E[i] * E[i] : 0.0;
+      lo = fmin(lo, di - el - er);
+      hi = fmax(hi, di + el + er);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) { red[warp] = lo; red[kSturmThreads / 32 + warp] = hi; }
+    __syncthreads();
+    lo = red[0];
+    hi = red[kSturmThreads / 32];
+    for (int w = 1; w < kSturmThreads / 32; ++w) { lo = fmin(lo, red[w]); hi = fmax(hi, red[kSturmThreads / 32 + w]); }
+    const int k = wk.y + threadIdx.x;
+    if (!(isfinite(lo) && isfinite(hi))) {                    // block-uniform
+      if (threadIdx.x == 0) atomicOr(status, kStEigen);
+      if (k < n && (int)threadIdx.x < item_len) evals[S.out_off + k] = __longlong_as_double(0x7ff8000000000000ll);
+      continue;
+    }
+    const double tnorm = fmax(fabs(lo), fabs(hi));
+    // T scaled by a power of two to norm in [0.5, 1): exact in FP64, then rounded to floats
+    int ex = 0;
+    frexp(tnorm, &ex);
+    const double sig = ldexp(1.0, -ex);
+    for (int i = threadIdx.x; i < n; i += kSturmThreads) {
+      d32[i] = (float)(d[i] * sig);
+      e32[i] = (float)(e2[i] * sig * sig);
+    }
+    __syncthreads();
+    const double eps = 0x1p-53;
+    const double fudge = 4.0 * eps * n * tnorm + 0x1p-1000;  // widen the Gershgorin interval
+    const float dl32 = 0x1p-21f * (float)(tnorm * sig);       // 8 u ||T|| (scaled): FP32 count error bound
+    // FP32 bracket of the scaled Gershgorin interval, widened by the bound
+    const float a0 = __double2float_rd((lo - fudge) * sig) - 2.0f * dl32;
+    const float b0 = __double2float_ru((hi + fudge) * sig) + 2.0f * dl32;
+    const float step = (b0 - a0) * (1.0f / kSturmThreads);
+    if (threadIdx.x > 0) grid_cnt[threadIdx.x] = sturm_count32(d32, e32, n, fmaf(step, (float)threadIdx.x, a0));
+    __syncthreads();
+    if (k >= n || (int)threadIdx.x >= item_len) continue;
+    float a32 = a0, b32 = b0;                                 // count32(a32) <= k < count32(b32)
+    {
+      int c = 1;
+      while (c < kSturmThreads && grid_cnt[c] <= k) ++c;      // grid_cnt is non-decreasing in c
+      if (c > 1) a32 = fmaf(step, (float)(c - 1), a0);
+      if (c < kSturmThreads) b32 = fmaf(step, (float)c, a0);
+    }
+    for (int i2 = 0; i2 < 64 && b32 - a32 > dl32; ++i2) {
+      const float mid = 0.5f * (a32 + b32);
+      if (mid <= a32 || mid >= b32) break;
+      if (sturm_count32(d32, e32, n, mid) <= k) a32 = mid;
+      else b32 = mid;
+    }
+    // FP64: the FP32 bracket widened by the bound, checked; else the Gershgorin interval
+    const double dl = (double)dl32 / sig;
+    double a = (double)a32 / sig - dl, b = (double)b32 / sig + dl;
+    if (!(sturm_count(d, e2, n, a) <= k && sturm_count(d, e2, n, b) > k)) {
+      a = lo - fudge;
+      b = hi + fudge;
+    }
+    const double tol = 4.0 * eps * tnorm + 0x1p-1000;
+    for (int i2 = 0; i2 < 200 && b - a > tol; ++i2) {
+      const double mid = 0.5 * (a + b);
+      if (mid <= a || mid >= b) break;
+      if (sturm_count(d, e2, n, mid) <= k) a = mid;
+      else b = mid;
+    }
+    evals[S.out_off + k] = 0.5 * (a + b);
   }
-  const double tnorm = fmax(fabs(lo), fabs(hi));
-  const double eps = 0x1p-53;
-  const double fudge = 4.0 * eps * n * tnorm + 0x1p-1000;   // widen the Gershgorin interval
-  double a = lo - fudge, b = hi + fudge;                    // count(a) <= k < count(b)
-  // a shared first level: the block's threads count at kSturmThreads - 1 interior points of
-  // [a, b], and every eigenvalue starts from the grid cell that holds it
-  const double step = (b - a) / kSturmThreads;
-  if (threadIdx.x > 0) grid_cnt[threadIdx.x] = sturm_count(d, e2, n, a + step * threadIdx.x);
-  __syncthreads();
-  {
-    int c = 1;
-    while (c < kSturmThreads && grid_cnt[c] <= k) ++c;   // grid_cnt is non-decreasing in c
-    const double a1 = c > 1 ? a + step * (c - 1) : a, b1 = c < kSturmThreads ? a + step * c : b;
-    a = a1;
-    b = b1;
-  }
-  if (k >= n) return;
-  const double tol = 4.0 * eps * tnorm + 0x1p-1000;
-  for (int it = 0; it < 200 && b - a > tol; ++it) {
-    const double mid = 0.5 * (a + b);
-    if (mid <= a || mid >= b) break;
-    if (sturm_count(d, e2, n, mid) <= k) a = mid;
-    else b = mid;
-  }
-  evals[S.out_off + k] = 0.5 * (a + b);
 }
 
 // Real-gauge H~ of one (field, sector) slot, full symmetric, ld x ld in 32 x 16 tiles (see
@@ -731,10 +827,30 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
   }
   const int64_t slot_doubles = round32(((int64_t)B * sizeof(TriSlot) + 7) / 8);
   const int64_t map_doubles = round32(((int64_t)2 * grid * sizeof(CtaWork) + 7) / 8);   // by block, by SM
-  const int64_t n_cnt = 2 * (int64_t)B + tk_total + kMaxSmId + 2;   // barriers, column reads, tickets, SMs
+  // bisection items: item_len consecutive eigenvalue indices of one matrix, 64 (a block's
+  // threads) unless that gives the persistent blocks fewer than two items each, then 32
+  const size_t smem2 = (size_t)2 * n_max * (sizeof(double) + sizeof(float));   // d, e^2 in FP64 and FP32
+  TGBA_CUDA(cudaFuncSetAttribute(sturm_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+  int bis_per_sm = 0;
+  TGBA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bis_per_sm, sturm_bisect, kSturmThreads, smem2));
+  if (bis_per_sm < 1) return fail(TGBA_EINVAL, "the bisection's shared memory does not fit on an SM");
+  int item_len = kSturmThreads;
+  auto count_items = [&](int len) {
+    int64_t c = 0;
+    for (const TriSlot& t : slots) c += (t.n + len - 1) / len;
+    return c;
+  };
+  if (count_items(item_len) < 2 * (int64_t)bis_per_sm * sms) item_len = kSturmThreads / 2;
+  std::vector<int2> items;
+  for (int q = 0; q < B; ++q)
+    for (int k0 = 0; k0 < slots[q].n; k0 += item_len) items.push_back(make_int2(q, k0));
+  const int n_items = (int)items.size();
+  const int64_t item_doubles = round32(n_items);
+  // counters: barriers, column reads, tickets, SM registration, the bisection queue
+  const int64_t n_cnt = 2 * (int64_t)B + tk_total + kMaxSmId + 2 + 1;
   const int64_t cnt_doubles = round32((n_cnt + 1) / 2);
   double* ws;
-  tgba_status r = scratch(b, total + slot_doubles + map_doubles + cnt_doubles, &ws);
+  tgba_status r = scratch(b, total + slot_doubles + map_doubles + cnt_doubles + item_doubles, &ws);
   if (r != TGBA_OK) return r;
   TriSlot* d_slots = (TriSlot*)(ws + total);
   CtaWork* d_map = (CtaWork*)(ws + total + slot_doubles);
@@ -747,6 +863,9 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
     TGBA_CUDA(cudaMemcpyAsync(d_sm_map, sm_map.data(), grid * sizeof(CtaWork), cudaMemcpyHostToDevice, st));
   }
   unsigned* d_reg = d_cnt + 2 * B + tk_total;
+  unsigned* d_queue = d_reg + kMaxSmId + 2;
+  int2* d_items = (int2*)(ws + total + slot_doubles + map_doubles + cnt_doubles);
+  TGBA_CUDA(cudaMemcpyAsync(d_items, items.data(), n_items * sizeof(int2), cudaMemcpyHostToDevice, st));
   TGBA_CUDA(cudaMemsetAsync(d_cnt, 0, n_cnt * sizeof(unsigned), st));
   for (int q = 0; q < B; ++q) {
     const Sector& sec = b.sectors[who[q].second];
@@ -778,10 +897,9 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
                                  (const CtaWork*)d_sm_map, per_sm, sms, d_reg, d_cnt, ws, b.d_status));
   ++b.launches;
   TGBA_CUDA(cudaEventRecord(b.eig_ev[1], st));
-  const size_t smem2 = (size_t)2 * n_max * sizeof(double);
-  TGBA_CUDA(cudaFuncSetAttribute(sturm_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
-  sturm_bisect<<<dim3((unsigned)((n_max + kSturmThreads - 1) / kSturmThreads), (unsigned)B), kSturmThreads, smem2, st>>>(
-      d_slots, ws, evals, b.d_status);
+  const int bis_grid = std::min(n_items, bis_per_sm * sms);
+  sturm_bisect<<<bis_grid, kSturmThreads, smem2, st>>>(d_slots, d_items, n_items, item_len, d_queue, ws, evals,
+                                                       b.d_status);
   TGBA_CUDA(cudaGetLastError());
   ++b.launches;
   TGBA_CUDA(cudaEventRecord(b.eig_ev[2], st));
