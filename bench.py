@@ -260,7 +260,7 @@ def screening_leg(b24, tgba, inputs, torch):
 
 # DRAM bytes of one sytrd_groups launch on the L = 24 all-sector workload, measured with ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum); None until measured for the current kernel.
-SYTRD_TRAFFIC = None
+SYTRD_TRAFFIC = 488574034944 + 494296249088
 
 
 def eigen_solver_leg(b, w, evs, tgba, torch):
@@ -360,7 +360,7 @@ def run_gb300(args):
                     "achieved": tri_gflops, "peak": peak_gflops, "unit": "GFLOP/s",
                     "frac": tri_gflops / peak_gflops, "traffic": SYTRD_TRAFFIC, "peak_source": peak_src,
                     "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of this kernel on this workload "
-                                      "(one ncu capture of the warm-up launch; 1.17x the algorithmic 8 n^3/3 B per "
+                                      "(one ncu capture of the warm-up launch; 1.11x the algorithmic 8 n^3/3 B per "
                                       "matrix)",
                     "flops_per_launch": prof["tridiag_flops"], "ms": tri_mean,
                     "matrices": prof["eig_matrices"], "ctas_per_matrix": prof["eig_cluster"]}
