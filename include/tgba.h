@@ -122,6 +122,20 @@ tgba_status tgba_x_pairs(tgba_basis b, int32_t s, const int32_t* pairs_dev, int6
 tgba_status tgba_x_direct(tgba_basis b, int32_t s, const int32_t* pairs_dev, int64_t n_pairs, double* out_dev,
                           void* stream);
 
+/* Elements Z_ab = <phi_a| sigma^x_1 sigma^x_{j+1} |phi_b> between two states of parity `parity`
+   (0 = NS, 1 = R) of sector s, 0 <= j < L (j = 0: the overlap <phi_a|phi_b>).  After the
+   Jordan-Wigner map the operator is the string B_1 A_2 B_2 ... B_j A_{j+1} of 2j Majoranas
+   (A_l = c_l^dag + c_l, B_l = c_l^dag - c_l) between vacua of one parity, the structure of
+   Eq. S1-S2 with the string in place of sigma^x_1.  Reduced form: the two vacua are contracted
+   once (a Schur complement whose pivot block has the vacuum norm as Pfaffian), leaving a table
+   over the excitation operators and the string, and each element is a Pfaffian of size
+   M_a + 2j + M_b (shared memory bounds max_qp and j: TGBA_EINVAL when it does not fit).
+   pairs_dev: int32 [n_pairs][2] state indices within the sector's states of that parity;
+   out_dev: complex (re, im) [n_pairs]; TGBA_EINVAL on an out-of-range index (output NaN).
+   Blocks on `stream`. */
+tgba_status tgba_z_elements(tgba_basis b, int32_t s, int32_t parity, int32_t j, const int32_t* pairs_dev,
+                            int64_t n_pairs, double* out_dev, void* stream);
+
 /* Contraction table and vacuum element: c0_host (complex, 2 doubles) receives
    C0 = <0_NS|c_1 + c_1^dag|0_R>; table_dev (optional, 2L x 2L doubles row-major) receives the
    real table R.  Blocks on `stream`. */
@@ -216,9 +230,9 @@ tgba_status tgba_quench_ordered(tgba_basis b, int32_t s, double h_z0, const doub
    truncated subspace of one variant (h_x, trunc, order as one variant of tgba_quench_ordered),
    with expectation values in the normalised state (the k = 0 state is translation invariant,
    so <sigma^x_{j+1}> = <sigma^x_1>).  After the Jordan-Wigner map sigma^x_1 sigma^x_{j+1} is a
-   string of 2j Majorana operators; its NS-NS and R-R elements are direct Pfaffians of size
-   2L + M_a + M_b + 2j (the tgba_x_direct kernel), so L, max_qp and j_max are bounded by shared
-   memory (TGBA_EINVAL when the string does not fit; 1 <= j_max < L).  Eigendecomposition path.
+   string of 2j Majorana operators; its NS-NS and R-R elements are those of tgba_z_elements
+   (reduced-form Pfaffians of size M_a + M_b + 2j, so max_qp and j_max are bounded by shared
+   memory: TGBA_EINVAL when they do not fit; 1 <= j_max < L).  Eigendecomposition path.
    mx_dev: double [n_t]; corr_dev: double [j_max][n_t]; norm_dev (optional): ||c0||^2;
    chi_host (optional): the kept basis size.  Blocks on `stream`. */
 tgba_status tgba_quench_correlators(tgba_basis b, int32_t s, double h_z0, double h_x, double trunc, int32_t order,

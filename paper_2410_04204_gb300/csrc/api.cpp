@@ -387,6 +387,30 @@ tgba_status tgba_x_direct(tgba_basis h, int32_t s, const int32_t* pairs_dev, int
   return check_status(*b, st);
 }
 
+tgba_status tgba_z_elements(tgba_basis h, int32_t s, int32_t parity, int32_t j, const int32_t* pairs_dev,
+                            int64_t n_pairs, double* out_dev, void* stream) {
+  Basis* b = (Basis*)h;
+  BASIS_OK(b);
+  if (s < 0 || s >= (int)b->sectors.size()) return fail(TGBA_EINVAL, "sector index out of range");
+  if (parity != 0 && parity != 1) return fail(TGBA_EINVAL, "parity must be 0 (NS) or 1 (R)");
+  if (j < 0 || j >= b->L) return fail(TGBA_EINVAL, "need 0 <= j < L");
+  if (n_pairs < 0 || (n_pairs > 0 && (!pairs_dev || !out_dev))) return fail(TGBA_EINVAL, "bad pair list");
+  int limit = 0;
+  TGBA_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+  if (z_reduced_smem(b->max_qp, j) + 16384 > (size_t)limit)
+    return fail(TGBA_EINVAL, "the Pfaffian of size 2 max_qp + 2j does not fit in shared memory");
+  if (n_pairs == 0) return TGBA_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t nE = 2 * (int64_t)b->L + 2 * j;
+  double* tab = nullptr;
+  TGBA_CUDA(cudaMallocAsync((void**)&tab, (2 * nE * nE + 4) * sizeof(double), st));
+  tgba_status r = z_table(*b, parity, j, tab, tab + 2 * nE * nE, st);
+  if (r == TGBA_OK) r = z_reduced_elements(*b, s, parity, j, j, tab, tab + 2 * nE * nE, pairs_dev, n_pairs, out_dev, st);
+  cudaFreeAsync(tab, st);
+  if (r != TGBA_OK) return r;
+  return check_status(*b, st);
+}
+
 tgba_status tgba_table(tgba_basis h, double* c0_host, double* table_dev, void* stream) {
   Basis* b = (Basis*)h;
   BASIS_OK(b);
@@ -531,8 +555,8 @@ tgba_status tgba_quench_correlators(tgba_basis h, int32_t s, double h_z0, double
     return fail(TGBA_EINVAL, "with order 1 the truncation is a whole number of states >= 1");
   int limit = 0;
   TGBA_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
-  if (x_direct_smem(b->L, b->max_qp, j_max) + 16384 > (size_t)limit)
-    return fail(TGBA_EINVAL, "the operator string of sigma^x_1 sigma^x_{j_max+1} does not fit in shared memory");
+  if (z_reduced_smem(b->max_qp, j_max) + 16384 > (size_t)limit)
+    return fail(TGBA_EINVAL, "the Pfaffian of size 2 max_qp + 2 j_max does not fit in shared memory");
   if (!b->x_valid) return fail(TGBA_EINVAL, "no X computed yet: call tgba_compute_x");
   tgba_status r = ensure_c0_host(*b, (cudaStream_t)stream);
   if (r != TGBA_OK) return r;

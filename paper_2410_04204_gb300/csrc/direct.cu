@@ -48,6 +48,81 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
 
+// Pfaffian of the m x m skew matrix held as its packed strict upper triangle T (destroyed):
+// complex Parlett-Reid with partial pivoting, two indices per step, the CTA's kDirThreads
+// threads sharing each step's pivot search, exchange and rank-2 update.  Every thread of the
+// CTA calls it and gets the result.  rowR, tau: m entries of scratch.
+__device__ double2 pf_packed(double2* T, int m, double2* rowR, double2* tau) {
+  __shared__ double red_v[kDirThreads];
+  __shared__ int red_i[kDirThreads];
+  __shared__ double2 piv;
+  __shared__ int zero_col;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = kDirThreads / 32;
+  double2 pf = make_double2(1.0, 0.0);
+  for (int k = 0; k + 1 < m; k += 2) {
+    // pivot: the largest |A[k][x]|, x > k (ties: the smallest x)
+    double best = -1.0;
+    int bi = k + 1;
+    for (int x = k + 1 + threadIdx.x; x < m; x += kDirThreads) {
+      const double2 v = T[pk(k, x, m)];
+      const double a2 = fma(v.x, v.x, v.y * v.y);
+      if (a2 > best) { best = a2; bi = x; }
+    }
+    red_v[threadIdx.x] = best;
+    red_i[threadIdx.x] = bi;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int t = 1; t < kDirThreads; ++t)
+        if (red_v[t] > best || (red_v[t] == best && red_i[t] < bi)) { best = red_v[t]; bi = red_i[t]; }
+      red_i[0] = bi;
+      zero_col = !(best > 0.0);
+    }
+    __syncthreads();
+    if (zero_col) { pf = make_double2(0.0, 0.0); break; }       // block-uniform
+    const int R = k + 1, C = red_i[0];
+    if (C != R) {                                   // exchange indices R and C
+      for (int x = threadIdx.x; x < m; x += kDirThreads) {
+        if (x == R || x == C) continue;
+        const double2 a = get(T, R, x, m), b = get(T, C, x, m);
+        set(T, R, x, m, b);
+        set(T, C, x, m, a);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const double2 v = T[pk(R, C, m)];
+        T[pk(R, C, m)] = make_double2(-v.x, -v.y);
+      }
+      pf = make_double2(-pf.x, -pf.y);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) piv = T[pk(k, R, m)];
+    __syncthreads();
+    const double2 a = piv;
+    pf = cmul(pf, a);
+    const double den = fma(a.x, a.x, a.y * a.y);
+    const double2 ia = make_double2(a.x / den, -a.y / den);
+    for (int x = k + 2 + threadIdx.x; x < m; x += kDirThreads) {
+      tau[x] = cmul(T[pk(k, x, m)], ia);            // Gauss vector
+      rowR[x] = T[pk(R, x, m)];
+    }
+    __syncthreads();
+    // A_ij += A_Ri tau_j - tau_i A_Rj  for k + 2 <= i < j
+    for (int gi = k + 2 + warp; gi < m; gi += nwarp) {
+      const double2 ri = rowR[gi], ti = tau[gi];
+      double2* rowp = T + pk(gi, gi + 1, m) - (gi + 1);   // rowp[gj] = A[gi][gj]
+      for (int gj = gi + 1 + lane; gj < m; gj += 32) {
+        double2 w = rowp[gj];
+        const double2 p1 = cmul(ri, tau[gj]), p2 = cmul(ti, rowR[gj]);
+        w.x += p1.x - p2.x;
+        w.y += p1.y - p2.y;
+        rowp[gj] = w;
+      }
+    }
+    __syncthreads();
+  }
+  return pf;
+}
+
 __global__ void __launch_bounds__(kDirThreads)
 x_direct_kernel(const int32_t* __restrict__ pairs, int64_t n_pairs, int pa_par, int pb_par, int jmid, int64_t a_off,
                 int64_t b_off, int64_t n_a, int64_t n_b, int L, const double* __restrict__ theta,
@@ -56,10 +131,7 @@ x_direct_kernel(const int32_t* __restrict__ pairs, int64_t n_pairs, int pa_par, 
   extern __shared__ double smem_d[];
   __shared__ int kind[kMaxOps];
   __shared__ double kk[kMaxOps], th[kMaxOps];
-  __shared__ double red_v[kDirThreads];
-  __shared__ int red_i[kDirThreads];
-  __shared__ double2 piv;
-  __shared__ int nops, zero_col;
+  __shared__ int nops;
   const int mmax = 2 * L + 2 * max_qp + (jmid > 0 ? 2 * jmid : 0);
   double2* U = (double2*)smem_d;                 // [m][L]
   double2* V = U + (size_t)mmax * L;             // [m][L]
@@ -166,69 +238,7 @@ x_direct_kernel(const int32_t* __restrict__ pairs, int64_t n_pairs, int pa_par, 
         T[pk(u, v, m)] = acc;
       }
     __syncthreads();
-    // complex Parlett-Reid: pivot, exchange, rank-2 update, two indices per step
-    double2 pf = make_double2(1.0, 0.0);
-    for (int k = 0; k + 1 < m; k += 2) {
-      // pivot: the largest |A[k][x]|, x > k (ties: the smallest x)
-      double best = -1.0;
-      int bi = k + 1;
-      for (int x = k + 1 + threadIdx.x; x < m; x += kDirThreads) {
-        const double2 v = T[pk(k, x, m)];
-        const double a2 = fma(v.x, v.x, v.y * v.y);
-        if (a2 > best) { best = a2; bi = x; }
-      }
-      red_v[threadIdx.x] = best;
-      red_i[threadIdx.x] = bi;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        for (int t = 1; t < kDirThreads; ++t)
-          if (red_v[t] > best || (red_v[t] == best && red_i[t] < bi)) { best = red_v[t]; bi = red_i[t]; }
-        red_i[0] = bi;
-        zero_col = !(best > 0.0);
-      }
-      __syncthreads();
-      if (zero_col) { pf = make_double2(0.0, 0.0); break; }       // block-uniform
-      const int R = k + 1, C = red_i[0];
-      if (C != R) {                                   // exchange indices R and C
-        for (int x = threadIdx.x; x < m; x += kDirThreads) {
-          if (x == R || x == C) continue;
-          const double2 a = get(T, R, x, m), b = get(T, C, x, m);
-          set(T, R, x, m, b);
-          set(T, C, x, m, a);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          const double2 v = T[pk(R, C, m)];
-          T[pk(R, C, m)] = make_double2(-v.x, -v.y);
-        }
-        pf = make_double2(-pf.x, -pf.y);
-        __syncthreads();
-      }
-      if (threadIdx.x == 0) piv = T[pk(k, R, m)];
-      __syncthreads();
-      const double2 a = piv;
-      pf = cmul(pf, a);
-      const double den = fma(a.x, a.x, a.y * a.y);
-      const double2 ia = make_double2(a.x / den, -a.y / den);
-      for (int x = k + 2 + threadIdx.x; x < m; x += kDirThreads) {
-        tau[x] = cmul(T[pk(k, x, m)], ia);            // Gauss vector
-        rowR[x] = T[pk(R, x, m)];
-      }
-      __syncthreads();
-      // A_ij += A_Ri tau_j - tau_i A_Rj  for k + 2 <= i < j
-      for (int gi = k + 2 + warp; gi < m; gi += nwarp) {
-        const double2 ri = rowR[gi], ti = tau[gi];
-        double2* rowp = T + pk(gi, gi + 1, m) - (gi + 1);   // rowp[gj] = A[gi][gj]
-        for (int gj = gi + 1 + lane; gj < m; gj += 32) {
-          double2 w = rowp[gj];
-          const double2 p1 = cmul(ri, tau[gj]), p2 = cmul(ti, rowR[gj]);
-          w.x += p1.x - p2.x;
-          w.y += p1.y - p2.y;
-          rowp[gj] = w;
-        }
-      }
-      __syncthreads();
-    }
+    const double2 pf = pf_packed(T, m, rowR, tau);
     if (threadIdx.x == 0) {
       const double re = vac_norm * pf.x, im = vac_norm * pf.y;
       if (!(isfinite(re) && isfinite(im))) atomicOr(status, kStNan);
@@ -239,7 +249,86 @@ x_direct_kernel(const int32_t* __restrict__ pairs, int64_t n_pairs, int pa_par, 
   }
 }
 
+// <phi_a| B_1 A_2 ... B_j A_{j+1} |phi_b> for pairs of states of one parity from the
+// contraction table S of z_table (nE = 2L + 2J operators): the Pfaffian of S over the element's
+// operators, m = M_a + 2j + M_b, times c0z = n_P^2 Pf(A_FF).
+__global__ void __launch_bounds__(kDirThreads)
+z_reduced_kernel(const int32_t* __restrict__ pairs, int64_t n_pairs, int j, int J, int64_t off, int64_t n_states, int L,
+                 const double2* __restrict__ S, const double2* __restrict__ c0z, const int16_t* __restrict__ modes,
+                 int max_qp, double* __restrict__ out, unsigned* __restrict__ status) {
+  extern __shared__ double smem_d[];
+  __shared__ int sel[2 * kMaxQp + 2 * kMaxL];
+  __shared__ int nsel;
+  const int nE = 2 * L + 2 * J;
+  const int mmax = 2 * max_qp + 2 * j;
+  double2* T = (double2*)smem_d;                 // packed strict upper triangle, m (m - 1) / 2
+  double2* rowR = T + (size_t)mmax * (mmax - 1) / 2;
+  double2* tau = rowR + mmax;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = kDirThreads / 32;
+  for (int64_t q = blockIdx.x; q < n_pairs; q += gridDim.x) {
+    const int32_t pa = pairs[2 * q], pb = pairs[2 * q + 1];
+    if (pa < 0 || pa >= n_states || pb < 0 || pb >= n_states) {   // block-uniform
+      if (threadIdx.x == 0) {
+        atomicOr(status, kStBadIndex);
+        out[2 * q] = out[2 * q + 1] = __longlong_as_double(0x7ff8000000000000ll);
+      }
+      continue;
+    }
+    if (threadIdx.x == 0) {
+      const int16_t* sa = modes + (off + pa) * max_qp;
+      const int16_t* sb = modes + (off + pb) * max_qp;
+      int ma = 0, mb = 0;
+      while (ma < max_qp && sa[ma] >= 0) ++ma;
+      while (mb < max_qp && sb[mb] >= 0) ++mb;
+      int c = 0;
+      for (int t = ma - 1; t >= 0; --t) sel[c++] = L - 1 - sa[t];   // bra excitations, descending
+      for (int x = 0; x < 2 * j; ++x) sel[c++] = L + x;            // B_1 A_2 ... B_j A_{j+1}
+      for (int t = 0; t < mb; ++t) sel[c++] = L + 2 * J + sb[t];    // ket excitations, ascending
+      nsel = c;
+    }
+    __syncthreads();
+    const int m = nsel;
+    for (int u = warp; u < m; u += nwarp) {          // a warp per row, lanes along it
+      const double2* srow = S + (size_t)sel[u] * nE;
+      for (int v = u + 1 + lane; v < m; v += 32) T[pk(u, v, m)] = srow[sel[v]];
+    }
+    __syncthreads();
+    const double2 pf = pf_packed(T, m, rowR, tau);
+    if (threadIdx.x == 0) {
+      const double2 z = cmul(*c0z, pf);
+      if (!(isfinite(z.x) && isfinite(z.y))) atomicOr(status, kStNan);
+      out[2 * q] = z.x;
+      out[2 * q + 1] = z.y;
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+size_t z_reduced_smem(int max_qp, int j) {
+  const size_t m = (size_t)(2 * max_qp + 2 * j);
+  return sizeof(double2) * (m * (m > 0 ? m - 1 : 0) / 2 + 2 * m + 2);
+}
+
+// Z elements of explicit pairs of parity `parity` of sector s, 0 <= j <= J, from the table of
+// z_table(b, parity, J, S, c0z).  out: complex, interleaved.
+tgba_status z_reduced_elements(Basis& b, int s, int parity, int j, int J, const double* S, const double* c0z,
+                               const int32_t* pairs, int64_t n, double* out, cudaStream_t st) {
+  if (n == 0) return TGBA_OK;
+  const Sector& sec = b.sectors[s];
+  const size_t smem = z_reduced_smem(b.max_qp, j);
+  TGBA_CUDA(cudaFuncSetAttribute(z_reduced_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int sms = 0;
+  TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
+  const int64_t grid = std::min<int64_t>(n, (int64_t)sms * 16);
+  z_reduced_kernel<<<(unsigned)grid, kDirThreads, smem, st>>>(
+      pairs, n, j, J, parity ? sec.r_off : sec.ns_off, parity ? sec.n_r : sec.n_ns, b.L, (const double2*)S,
+      (const double2*)c0z, parity ? b.d_modes_r : b.d_modes_ns, b.max_qp, out, b.d_status);
+  TGBA_CUDA(cudaGetLastError());
+  ++b.launches;
+  return TGBA_OK;
+}
 
 size_t x_direct_smem(int L, int max_qp, int jmid) {
   const size_t m = (size_t)(2 * L + 2 * max_qp + (jmid > 0 ? 2 * jmid : 0));

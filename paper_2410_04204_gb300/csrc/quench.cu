@@ -527,7 +527,7 @@ tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* t
       double* XB = B + 2 * n * nb;
       if ((r = build_real_heff(b, s, hx[v], U, idx, kn, idx + kn, kr, st)) != TGBA_OK) return r;
       if ((r = eig_sym(b, n, U, E, true, st)) != TGBA_OK) return r;
-      // correlators: Z~_j of the kept NS-NS and R-R blocks by direct Pfaffians, before the time loop
+      // correlators: Z~_j of the kept NS-NS and R-R blocks (reduced-form Pfaffians), before the time loop
       double* zbuf = nullptr;
       double *Zr_ns = nullptr, *Zi_ns = nullptr, *Zr_r = nullptr, *Zi_r = nullptr, *Yb = nullptr;
       struct FreeZ {
@@ -555,8 +555,18 @@ tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* t
             for (int64_t y = 0; y < k; ++y) { hp[2 * (x * k + y)] = lst[x]; hp[2 * (x * k + y) + 1] = lst[y]; }
           TGBA_CUDA(cudaMemcpyAsync(zp, hp.data(), hp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
           int32_t* didx = (int32_t*)(par ? idx + kn : idx);
+          // the parity's contraction table of the string up to j_max (reduced form)
+          const int64_t nE = 2 * (int64_t)L + 2 * j_max;
+          double* ztab = nullptr;
+          TGBA_CUDA(cudaMallocAsync((void**)&ztab, (2 * nE * nE + 4) * sizeof(double), st));
+          struct FreeT {
+            double* p; cudaStream_t s;
+            ~FreeT() { cudaFreeAsync(p, s); }
+          } free_t{ztab, st};
+          double* c0z = ztab + 2 * nE * nE;
+          if ((r = z_table(b, par, j_max, ztab, c0z, st)) != TGBA_OK) return r;
           for (int j = 1; j <= j_max; ++j) {
-            if ((r = direct_elements(b, s, par, j, zp, k * k, Zc, st)) != TGBA_OK) return r;
+            if ((r = z_reduced_elements(b, s, par, j, j_max, ztab, c0z, zp, k * k, Zc, st)) != TGBA_OK) return r;
             double* zr = (par ? Zr_r : Zr_ns) + (size_t)(j - 1) * k * k;
             double* zi = (par ? Zi_r : Zi_ns) + (size_t)(j - 1) * k * k;
             zgauge_kernel<<<blocks_for(k * k), 256, 0, st>>>(k, didx, par ? b.d_M_r : b.d_M_ns, par ? sec.r_off : sec.ns_off,

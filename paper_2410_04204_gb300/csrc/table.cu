@@ -27,7 +27,7 @@
 namespace tgba {
 namespace {
 
-enum { K_C = 0, K_CDAG = 1, K_D = 2, K_DDAG = 3, K_SIGMA = 4 };
+enum { K_C = 0, K_CDAG = 1, K_D = 2, K_DDAG = 3, K_SIGMA = 4, K_MAJA = 5, K_MAJB = 6 };   // Majoranas: n = site
 
 struct Op {
   int kind, n, pos;   // kind, momentum label (k = pi n / L), position in the operator string
@@ -222,8 +222,9 @@ __global__ void fill_kernel(int L, const int* nlab, const double* theta, cd* A) 
 }
 
 // step k: pivot inside F (rows k+1 .. 2L-1 of column k), exchange, running Pf, Gauss vector
-__global__ void __launch_bounds__(256) pivot_kernel(int L, int k, cd* A, cd* tau, cd* pf) {
-  const int n4 = 4 * L, n2 = 2 * L, r = k + 1;
+// (n4 operators, the first n2 of them the block F that is eliminated)
+__global__ void __launch_bounds__(256) pivot_kernel(int n4, int n2, int k, cd* A, cd* tau, cd* pf) {
+  const int r = k + 1;
   __shared__ int s_piv;
   if (threadIdx.x < 32) {
     double best = -1; int bi = r;
@@ -260,8 +261,8 @@ __global__ void __launch_bounds__(256) pivot_kernel(int L, int k, cd* A, cd* tau
 }
 
 // step k: A_ij += A[k+1][i] tau_j - tau_i A[k+1][j] on the trailing upper triangle (mirrored)
-__global__ void update_kernel(int L, int k, cd* A, const cd* tau) {
-  const int n4 = 4 * L, r = k + 1, m = n4 - (k + 2);
+__global__ void update_kernel(int n4, int k, cd* A, const cd* tau) {
+  const int r = k + 1, m = n4 - (k + 2);
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < m * m; idx += gridDim.x * blockDim.x) {
     const int i = k + 2 + idx / m, j = k + 2 + idx % m;
     if (i >= j) continue;
@@ -300,7 +301,135 @@ __global__ void finalize_kernel(int L, const int* nlab, double vac_norm, const c
 
 __global__ void pf_init(cd* pf) { *pf = mk(1, 0); }
 
+// ---- the contraction table of sigma^x_1 sigma^x_{j+1} between two states of one parity
+// (U(j), V(j)): the coefficients of c_j^dag and c_j in an operator at site j
+__device__ void at_site(const Op& o, int j, int L, cd& U, cd& V) {
+  if (o.kind == K_MAJA || o.kind == K_MAJB) {          // c_l^dag + c_l, c_l^dag - c_l
+    const double on = o.n == j ? 1.0 : 0.0;
+    U = mk(on, 0);
+    V = mk(o.kind == K_MAJA ? on : -on, 0);
+    return;
+  }
+  cd u, v; int su, sv;
+  plane(o, u, su, v, sv);
+  const double rl = 1.0 / sqrt((double)L);
+  U = scal(mul(u, expi(su * M_PI * (double)o.n * j / L)), rl);
+  V = scal(mul(v, expi(sv * M_PI * (double)o.n * j / L)), rl);
+}
+
+// <0| O_a O_b |0>_c = sum_j V_a(j) U_b(j), also for site-local Majoranas
+__device__ cd contract_z(const Op& a, const Op& b, int L) {
+  const bool ma = a.kind >= K_MAJA, mb = b.kind >= K_MAJA;
+  if (!ma && !mb) return contract(a, b, L);
+  cd Ua, Va, Ub, Vb;
+  const int j = ma ? a.n : b.n;                         // the only site that contributes
+  at_site(a, j, L, Ua, Va);
+  at_site(b, j, L, Ub, Vb);
+  return mul(Va, Ub);
+}
+
+// A over the listed operators (rows in list order, contractions in string order, pos)
+__global__ void zfill_kernel(int n4, const Op* __restrict__ ops, int L, cd* A) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)n4 * n4;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int g = (int)(idx / n4), h = (int)(idx % n4);
+    if (g > h) continue;
+    cd val = mk(0, 0);
+    if (g != h) {
+      const Op a = ops[g], b = ops[h];
+      val = (a.pos < b.pos) ? contract_z(a, b, L) : scal(contract_z(b, a, L), -1.0);
+    }
+    A[(size_t)g * n4 + h] = val;
+    A[(size_t)h * n4 + g] = scal(val, -1.0);
+  }
+}
+
+// S = the E block left after the elimination; c0 = norm2 Pf(A_FF)
+__global__ void zextract_kernel(int n4, int n2, const cd* A, const cd* pf, double norm2, cd* S, cd* c0,
+                                unsigned* status) {
+  const int nE = n4 - n2;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)nE * nE;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(idx / nE), b = (int)(idx % nE);
+    S[idx] = a == b ? mk(0, 0) : A[(size_t)(n2 + a) * n4 + (n2 + b)];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const cd p = *pf;
+    *c0 = scal(p, norm2);
+    if (!(abs2(p) > 1e-200) || !isfinite(p.x) || !isfinite(p.y)) atomicOr(status, kStTableSingular);
+  }
+}
+
 }  // namespace
+
+// Contraction table of <phi_a| B_1 A_2 B_2 ... B_j A_{j+1} |phi_b> for two states of parity
+// `parity` and j <= J.  String order: [bra vacuum: d_k^dag, k != pi, ascending] [bra
+// excitations of every mode, descending: d_p (c_pi at pi)] [B_1 A_2 B_2 A_3 ... B_J A_{J+1}]
+// [ket excitations, ascending: d_q^dag (c_pi^dag at pi)] [ket vacuum: d_k, k != pi,
+// descending].  With F = both vacua (their block's Pfaffian is the vacuum norm, so it is well
+// conditioned) and E = the rest in string order, one element is
+//   Z_ab = n_P^2 Pf(A_FF) Pf(S[sel, sel]),  S = A_EE + A_FE^T A_FF^{-1} A_FE,
+// with sel = (a's modes: E index L - 1 - i, i descending) ++ (the first 2j string operators:
+// L .. L + 2j - 1) ++ (b's modes: L + 2J + i, ascending), an even subset, so moving the ket
+// vacuum block next to the bra's costs no sign.  S: (2L + 2J)^2 complex, row-major; c0z: the
+// scalar n_P^2 Pf(A_FF).
+tgba_status z_table(Basis& b, int parity, int J, double* S_dev, double* c0z_dev, cudaStream_t st) {
+  const int L = b.L;
+  const Modes md = make_modes(L, parity, b.h);
+  std::vector<Op> F1, F2, E;
+  int pos = 0;
+  for (int i = 0; i < L; ++i)                               // bra vacuum
+    if (md.nlab[i] != L) F1.push_back({K_DDAG, md.nlab[i], pos++, md.theta[i]});
+  for (int i = L - 1; i >= 0; --i) {                        // bra excitations, descending
+    if (md.nlab[i] == L) E.push_back({K_C, L, pos++, 0.0});
+    else E.push_back({K_D, md.nlab[i], pos++, md.theta[i]});
+  }
+  for (int l = 1; l <= J; ++l) {                            // the string
+    E.push_back({K_MAJB, l, pos++, 0.0});
+    E.push_back({K_MAJA, l + 1, pos++, 0.0});
+  }
+  for (int i = 0; i < L; ++i) {                             // ket excitations, ascending
+    if (md.nlab[i] == L) E.push_back({K_CDAG, L, pos++, 0.0});
+    else E.push_back({K_DDAG, md.nlab[i], pos++, md.theta[i]});
+  }
+  for (int i = L - 1; i >= 0; --i)                          // ket vacuum, descending
+    if (md.nlab[i] != L) F2.push_back({K_D, md.nlab[i], pos++, md.theta[i]});
+  std::vector<Op> ops(F1);
+  ops.insert(ops.end(), F2.begin(), F2.end());
+  ops.insert(ops.end(), E.begin(), E.end());
+  const int n4 = (int)ops.size(), n2 = (int)(F1.size() + F2.size());
+  // work: A (n4^2), the Gauss vector (n4), Pf(A_FF), the operator list
+  const size_t work_bytes = sizeof(cd) * ((size_t)n4 * n4 + n4 + 1) + sizeof(Op) * n4 + 256;
+  char* work = nullptr;
+  TGBA_CUDA(cudaMallocAsync((void**)&work, work_bytes, st));
+  struct FreeW {
+    char* p; cudaStream_t s;
+    ~FreeW() { cudaFreeAsync(p, s); }
+  } free_w{work, st};
+  cd* A = (cd*)work;
+  cd* tau = A + (size_t)n4 * n4;
+  cd* pf = tau + n4;
+  Op* d_ops = (Op*)(((uintptr_t)(pf + 1) + 63) & ~(uintptr_t)63);
+  TGBA_CUDA(cudaMemcpyAsync(d_ops, ops.data(), sizeof(Op) * n4, cudaMemcpyHostToDevice, st));
+  int sms = 0;
+  TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
+  auto grid = [&](int64_t work_items) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((work_items + 255) / 256, (int64_t)sms * 4));
+  };
+  zfill_kernel<<<grid((int64_t)n4 * n4), 256, 0, st>>>(n4, d_ops, L, A);
+  pf_init<<<1, 1, 0, st>>>(pf);
+  for (int k = 0; k < n2; k += 2) {
+    pivot_kernel<<<1, 256, 0, st>>>(n4, n2, k, A, tau, pf);
+    const int64_t m = n4 - (k + 2);
+    update_kernel<<<grid(m * m), 256, 0, st>>>(n4, k, A, tau);
+  }
+  const double nrm = parity ? b.norm_r : b.norm_ns;
+  zextract_kernel<<<grid((int64_t)(n4 - n2) * (n4 - n2)), 256, 0, st>>>(n4, n2, A, pf, nrm * nrm, (cd*)S_dev,
+                                                                       (cd*)c0z_dev, b.d_status);
+  TGBA_CUDA(cudaGetLastError());
+  b.launches += 3 + n2;
+  return TGBA_OK;
+}
 
 tgba_status build_table(Basis& b, cudaStream_t st) {
   const int L = b.L, n4 = 4 * L;
@@ -314,9 +443,9 @@ tgba_status build_table(Basis& b, cudaStream_t st) {
   fill_kernel<<<grid((int64_t)n4 * n4), 256, 0, st>>>(L, b.d_nlab, b.d_theta, A);
   pf_init<<<1, 1, 0, st>>>(pf);
   for (int k = 0; k < 2 * L; k += 2) {
-    pivot_kernel<<<1, 256, 0, st>>>(L, k, A, tau, pf);
+    pivot_kernel<<<1, 256, 0, st>>>(n4, 2 * L, k, A, tau, pf);
     const int64_t m = n4 - (k + 2);
-    update_kernel<<<grid(m * m), 256, 0, st>>>(L, k, A, tau);
+    update_kernel<<<grid(m * m), 256, 0, st>>>(n4, k, A, tau);
   }
   finalize_kernel<<<grid((int64_t)4 * L * L), 256, 0, st>>>(L, b.d_nlab, b.vac_norm, A, pf, b.d_table, b.d_c0,
                                                            b.d_status);

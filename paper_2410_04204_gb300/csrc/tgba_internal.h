@@ -182,6 +182,12 @@ tgba_status x_direct(Basis& b, int s, const int32_t* pairs, int64_t n, double* o
 // <phi_a| sigma^x_1 sigma^x_{jmid+1} |phi_b> for pairs of parity `parity` (jmid >= 0), or X (jmid < 0)
 tgba_status direct_elements(Basis& b, int s, int parity, int jmid, const int32_t* pairs, int64_t n, double* out,
                             cudaStream_t st);
+// reduced form of the same-parity elements: the contraction table of the string up to J
+// (table.cu; S [2L + 2J]^2 complex, c0z one complex) and its Pfaffians (direct.cu)
+tgba_status z_table(Basis& b, int parity, int J, double* S_dev, double* c0z_dev, cudaStream_t st);
+size_t z_reduced_smem(int max_qp, int j);
+tgba_status z_reduced_elements(Basis& b, int s, int parity, int j, int J, const double* S, const double* c0z,
+                               const int32_t* pairs, int64_t n, double* out, cudaStream_t st);
 // real P of every (NS state of sector s_ns, R state of sector s_r) pair, out [n_ns][n_r] row-major
 tgba_status run_pfaffian_cross(Basis& b, int s_ns, int s_r, double* out, cudaStream_t st);
 

@@ -18,7 +18,7 @@ _NAMES = {0: "TGBA_OK", 1: "TGBA_EINVAL", 2: "TGBA_ENOMEM", 3: "TGBA_ECUDA", 4: 
 
 # every symbol include/tgba.h declares
 SYMBOLS = ("tgba_last_error", "tgba_device_count", "tgba_build_basis", "tgba_basis_info", "tgba_basis_totals",
-           "tgba_basis_free", "tgba_compute_x", "tgba_x_stats", "tgba_x_export", "tgba_x_pairs", "tgba_x_direct", "tgba_table",
+           "tgba_basis_free", "tgba_compute_x", "tgba_x_stats", "tgba_x_export", "tgba_x_pairs", "tgba_x_direct", "tgba_z_elements", "tgba_table",
            "tgba_assemble_heff", "tgba_eigvals", "tgba_eigvals_ex", "tgba_dsf", "tgba_dsf_k", "tgba_quench", "tgba_quench_ordered", "tgba_quench_correlators", "tgba_screen_create",
            "tgba_screen_nparams", "tgba_screen_params", "tgba_screen_grad", "tgba_screen_train",
            "tgba_screen_predict", "tgba_screen_free", "tgba_table_noalloc", "tgba_profile", "tgba_fp64_peak")
@@ -70,6 +70,7 @@ def lib():
             "tgba_x_export": (_I32, [_VP, _I32, _VP, _VP]),
             "tgba_x_pairs": (_I32, [_VP, _I32, _VP, _I64, _VP, _VP]),
             "tgba_x_direct": (_I32, [_VP, _I32, _VP, _I64, _VP, _VP]),
+            "tgba_z_elements": (_I32, [_VP, _I32, _I32, _I32, _VP, _I64, _VP, _VP]),
             "tgba_table": (_I32, [_VP, _VP, _VP, _VP]),
             "tgba_assemble_heff": (_I32, [_VP, _D, _VP, _D, _VP, _VP]),
             "tgba_eigvals": (_I32, [_VP, _VP, _I32, _VP, _VP]),
@@ -220,6 +221,16 @@ def tgba_x_direct(b, s, pairs, out, stream=None):
     _cuda_tensor(pairs, torch.int32, name="pairs")
     _cuda_tensor(out, torch.complex128, pairs.shape[0], name="out")
     _check(lib().tgba_x_direct(b, s, _ptr(pairs), pairs.shape[0], _ptr(out), _stream(stream)))
+
+
+def tgba_z_elements(b, s, parity, j, pairs, out, stream=None):
+    """<phi_a| sigma^x_1 sigma^x_{j+1} |phi_b> for states of one parity (0 NS, 1 R) of sector s.
+    pairs: int32 CUDA tensor [n, 2] (state indices of that parity); out: complex128 CUDA tensor [n]."""
+    import torch
+    _cuda_tensor(pairs, torch.int32, name="pairs")
+    _cuda_tensor(out, torch.complex128, pairs.shape[0], name="out")
+    _check(lib().tgba_z_elements(b, s, parity, j, _ptr(pairs), pairs.shape[0], _ptr(out), _stream(stream)))
+
 
 def tgba_table(b, table_out=None, stream=None):
     """Returns C0 (complex); fills table_out (float64 CUDA tensor, 2L x 2L) if given."""

@@ -1,6 +1,7 @@
 """Equal-time connected correlators after the quench (tgba_quench_correlators: Majorana-string
-elements by direct Pfaffians, then Re(B^H Z B)) against exact diagonalisation on a complete
-basis and against the oracle on truncated ones."""
+elements in the reduced form, then Re(B^H Z B)) against exact diagonalisation on a complete
+basis and against the oracle (direct Pfaffians of the whole string) on truncated ones, up to
+the paper's L = 60."""
 import numpy as np
 import pytest
 import torch
@@ -41,10 +42,11 @@ def test_complete_basis_equals_ed():
         tgba.tgba_basis_free(b)
 
 
-@pytest.mark.parametrize("L,mq,trunc,order", [(12, 6, 80, 1), (10, 10, 6.0, 0)])
-def test_truncated_against_oracle(L, mq, trunc, order):
-    h, h0, hx, j_max, t_max, n_t = 1.0, 0.5, 0.1, 3, 8.0, 33
-    b = tgba.tgba_build_basis(L, h, [0], mq)
+@pytest.mark.parametrize("L,mq,cut,trunc,order,j_max", [(12, 6, None, 80, 1, 3), (10, 10, None, 6.0, 0, 3),
+                                                       (60, 4, 3.0, 40, 1, 8)])
+def test_truncated_against_oracle(L, mq, cut, trunc, order, j_max):
+    h, h0, hx, t_max, n_t = 1.0, 0.5, 0.1, 8.0, 33
+    b = tgba.tgba_build_basis(L, h, [0], mq, -1.0 if cut is None else cut)
     try:
         tgba.tgba_compute_x(b)
         chi, mx, corr = _run(b, h0, hx, float(trunc), order, t_max, n_t, j_max)
@@ -53,11 +55,11 @@ def test_truncated_against_oracle(L, mq, trunc, order):
         else:
             from oracle import basis as obs
             from oracle import modes as md
-            ns, r = obs.sector_basis(L, h, 0, mq)
+            ns, r = obs.sector_basis(L, h, 0, mq, cut)
             E = np.array([x.E for x in ns] + [x.E for x in r])
             size = int(np.sum(E <= md.vacuum_energy(L, md.NS, h) + trunc + 1e-9))
         assert chi == size
-        t, mo, co = otgba.quench_correlators(L, h, h0, hx, mq, None, order, size, t_max, n_t, j_max)
+        t, mo, co = otgba.quench_correlators(L, h, h0, hx, mq, cut, order, size, t_max, n_t, j_max)
         assert np.abs(mx - mo).max() < 1e-9
         assert np.abs(corr - co).max() < 1e-9
     finally:
@@ -65,13 +67,13 @@ def test_truncated_against_oracle(L, mq, trunc, order):
 
 
 def test_rejects_strings_that_do_not_fit():
-    b = tgba.tgba_build_basis(40, 1.0, [0], 2, 2.0)
+    b = tgba.tgba_build_basis(120, 1.0, [0], 2, 1.0)     # Pfaffians of size 4 + 2 j_max = 204: too big
     try:
         tgba.tgba_compute_x(b)
         mx = torch.empty(4, dtype=torch.float64, device="cuda")
-        corr = torch.empty(4 * 30, dtype=torch.float64, device="cuda")
+        corr = torch.empty(4 * 100, dtype=torch.float64, device="cuda")
         with pytest.raises(tgba.TgbaError) as e:
-            tgba.tgba_quench_correlators(b, 0, 0.5, 0.1, 4.0, 1, 1.0, 4, 30, mx, corr)
+            tgba.tgba_quench_correlators(b, 0, 0.5, 0.1, 4.0, 1, 1.0, 4, 100, mx, corr)
         assert e.value.code == tgba.TGBA_EINVAL
     finally:
         tgba.tgba_basis_free(b)
