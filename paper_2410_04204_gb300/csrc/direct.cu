@@ -17,7 +17,9 @@
 // two states of one parity (the equal-time correlators after a quench): after the
 // Jordan-Wigner map, with A_l = c_l^dag + c_l and B_l = c_l^dag - c_l (1 - 2 n_l = A_l B_l),
 // sigma^x_1 sigma^x_{j+1} = B_1 A_2 B_2 ... B_j A_{j+1}, a string of 2j Majoranas that takes the
-// place of sigma^x_1, between vacua of the same parity.
+// place of sigma^x_1, between vacua of the same parity.  z_reduced_kernel evaluates those
+// elements from the contraction table of z_table instead (the vacua contracted once): a
+// Pfaffian of size M_a + 2j + M_b per element, which reaches chains the direct string does not.
 #include <cuComplex.h>
 
 #include <algorithm>
