@@ -3,6 +3,9 @@
 * L = 40 (k = 0, ~1e4 states): the FP32 Lorentzian sum against an FP64 sum of the same FP64
   weights (the stated FP32 tolerance), eigenvalue consistency, and the E8 mass ratio m2/m1
   from the weights, a loose physics check against the E8 value of Table 1.
+* L = 60, h_par = 0.05, k = 0, the paper's chi ~ 1600 (Table 1's run): every TGBA mass ratio
+  m_n/m_1 printed in Table 1 (n = 2..7) has a peak of S(k = 0, w) within 0.4 % of it, and the
+  E8 theory value of m6/m1, which the paper's own run misses by 1.3 %, has none.
 * L = 80 quench: at t = 0 the normalised magnetisation of the ferromagnetic initial state
   equals Pfeuty's closed form (1 - h0^2)^(1/8) once the retained weight ||c0||^2 -> 1;
   ||c0||^2 grows with nested cutoffs and never exceeds 1.
@@ -56,6 +59,39 @@ def test_dsf_L40():
         m1, m2 = dv[big[0]], dv[big[1]]
         theory = load_table1()["m2/m1"][1]
         assert abs(m2 / m1 - theory) / theory < 0.02, (m1, m2, m2 / m1)
+    finally:
+        tgba.tgba_basis_free(b)
+
+
+def test_table1_tgba_ratios_L60():
+    """The cutoff 5.34681 above the NS vacuum keeps the lowest 1601 k = 0 states (the 1600th and
+    1601st are degenerate): the paper's chi = 1600 at "E_cut ~ 5.4".  m_1 is the lowest excited
+    state with weight; a peak is a state whose weight w_a = L |<a|sigma^x_1|0>|^2 is at least
+    0.4 % of m_1's."""
+    L, h, hx, cut = 60, 1.0, 0.05, 5.34681
+    b = tgba.tgba_build_basis(L, h, [0], 10, cut)
+    try:
+        info = tgba.tgba_basis_info(b, 0, 10)
+        n = info["n_ns"] + info["n_r"]
+        assert n == 1601
+        tgba.tgba_compute_x(b)
+        S = torch.empty(64, dtype=torch.float32, device="cuda")
+        wts = torch.empty(n, dtype=torch.float64, device="cuda")
+        dE = torch.empty(n, dtype=torch.float64, device="cuda")
+        ev = torch.empty(1, dtype=torch.float64, device="cuda")
+        tgba.tgba_dsf(b, 0, hx, 0.0, 6.0, 64, 0.01, S, ev, 1, wts, dE)
+        w, d = wts.cpu().numpy(), dE.cpu().numpy()
+        exc = d > 1e-9
+        i1 = np.flatnonzero(exc)[np.argmin(d[exc])]
+        m1, w1 = d[i1], w[i1]
+        assert w1 > 0.1
+        peaks = d[exc & (w >= 4e-3 * w1)] / m1
+        table = load_table1()
+        for name, (paper_tgba, theory) in table.items():
+            near = np.abs(peaks - paper_tgba).min() / paper_tgba
+            assert near < 4e-3, (name, paper_tgba, np.sort(peaks))
+        theory6 = table["m6/m1"][1]
+        assert np.abs(peaks - theory6).min() / theory6 > 4e-3
     finally:
         tgba.tgba_basis_free(b)
 
