@@ -6,6 +6,9 @@
 * L = 60, h_par = 0.05, k = 0, the paper's chi ~ 1600 (Table 1's run): every TGBA mass ratio
   m_n/m_1 printed in Table 1 (n = 2..7) has a peak of S(k = 0, w) within 0.4 % of it, and the
   E8 theory value of m6/m1, which the paper's own run misses by 1.3 %, has none.
+* L = 60 quench (h_perp, h_par) = (0.5, 0) -> (1, 0.05), overlap-ordered chi = 2000, t to 480
+  (Appendix C): the power spectrum of <sigma^x>(t) peaks at m_1 of the spectral calculation
+  above, and also at m_2 and at the gap m_2 - m_1.
 * L = 80 quench: at t = 0 the normalised magnetisation of the ferromagnetic initial state
   equals Pfeuty's closed form (1 - h0^2)^(1/8) once the retained weight ||c0||^2 -> 1;
   ||c0||^2 grows with nested cutoffs and never exceeds 1.
@@ -63,11 +66,8 @@ def test_dsf_L40():
         tgba.tgba_basis_free(b)
 
 
-def test_table1_tgba_ratios_L60():
-    """The cutoff 5.34681 above the NS vacuum keeps the lowest 1601 k = 0 states (the 1600th and
-    1601st are degenerate): the paper's chi = 1600 at "E_cut ~ 5.4".  m_1 is the lowest excited
-    state with weight; a peak is a state whose weight w_a = L |<a|sigma^x_1|0>|^2 is at least
-    0.4 % of m_1's."""
+def _dsf_L60():
+    """(dE, weights) of S(k = 0, w) at L = 60, h_par = 0.05 on the lowest 1601 k = 0 states."""
     L, h, hx, cut = 60, 1.0, 0.05, 5.34681
     b = tgba.tgba_build_basis(L, h, [0], 10, cut)
     try:
@@ -80,20 +80,60 @@ def test_table1_tgba_ratios_L60():
         dE = torch.empty(n, dtype=torch.float64, device="cuda")
         ev = torch.empty(1, dtype=torch.float64, device="cuda")
         tgba.tgba_dsf(b, 0, hx, 0.0, 6.0, 64, 0.01, S, ev, 1, wts, dE)
-        w, d = wts.cpu().numpy(), dE.cpu().numpy()
-        exc = d > 1e-9
-        i1 = np.flatnonzero(exc)[np.argmin(d[exc])]
-        m1, w1 = d[i1], w[i1]
-        assert w1 > 0.1
-        peaks = d[exc & (w >= 4e-3 * w1)] / m1
-        table = load_table1()
-        for name, (paper_tgba, theory) in table.items():
-            near = np.abs(peaks - paper_tgba).min() / paper_tgba
-            assert near < 4e-3, (name, paper_tgba, np.sort(peaks))
-        theory6 = table["m6/m1"][1]
-        assert np.abs(peaks - theory6).min() / theory6 > 4e-3
+        return dE.cpu().numpy(), wts.cpu().numpy()
     finally:
         tgba.tgba_basis_free(b)
+
+
+def test_table1_tgba_ratios_L60():
+    """The cutoff 5.34681 above the NS vacuum keeps the lowest 1601 k = 0 states (the 1600th and
+    1601st are degenerate): the paper's chi = 1600 at "E_cut ~ 5.4".  m_1 is the lowest excited
+    state with weight; a peak is a state whose weight w_a = L |<a|sigma^x_1|0>|^2 is at least
+    0.4 % of m_1's."""
+    d, w = _dsf_L60()
+    exc = d > 1e-9
+    i1 = np.flatnonzero(exc)[np.argmin(d[exc])]
+    m1, w1 = d[i1], w[i1]
+    assert w1 > 0.1
+    peaks = d[exc & (w >= 4e-3 * w1)] / m1
+    table = load_table1()
+    for name, (paper_tgba, theory) in table.items():
+        near = np.abs(peaks - paper_tgba).min() / paper_tgba
+        assert near < 4e-3, (name, paper_tgba, np.sort(peaks))
+    theory6 = table["m6/m1"][1]
+    assert np.abs(peaks - theory6).min() / theory6 > 4e-3
+
+
+def test_quench_power_spectrum_L60():
+    """Overlap-ordered quench on the M <= 6, cutoff 8.984 basis (2000 of its ~3e4 states), 4801
+    times in [0, 480], Hann window, zero padded 16x: the strongest peak of |<sigma^x>(w)|^2 in
+    (0.1, 6) is m_1, and m_2 and m_2 - m_1 are peaks too (0.5 % of their value)."""
+    d, w = _dsf_L60()
+    exc = d > 1e-9
+    i1 = np.flatnonzero(exc)[np.argmin(d[exc])]
+    m1 = d[i1]
+    m2 = d[exc & (w >= 0.05 * w[i1]) & (d > 1.2 * m1)].min()
+    b = tgba.tgba_build_basis(60, 1.0, [0], 6, 8.984)
+    try:
+        tgba.tgba_compute_x(b)
+        t_max, n_t = 480.0, 4801
+        mx = torch.empty(n_t, dtype=torch.float64, device="cuda")
+        chi = tgba.tgba_quench_ordered(b, 0, 0.5, [0.05], [2000.0], 1, t_max, n_t, mx, method=1)
+        assert chi[0] == 2000
+        m = mx.cpu().numpy()
+    finally:
+        tgba.tgba_basis_free(b)
+    x = (m - m.mean()) * np.hanning(n_t)
+    pad = 16 * n_t
+    P = np.abs(np.fft.rfft(x, pad)) ** 2
+    om = 2 * np.pi * np.fft.rfftfreq(pad, d=t_max / (n_t - 1))
+    pk = [i for i in range(1, len(P) - 1) if P[i] > P[i - 1] and P[i] >= P[i + 1] and 0.1 < om[i] < 6.0]
+    pk.sort(key=lambda i: -P[i])
+    top = om[pk[0]]
+    assert abs(top - m1) < 5e-3 * m1, (top, m1)
+    strong = om[[i for i in pk if P[i] > 0.02 * P[pk[0]]]]
+    for f in (m2, m2 - m1):
+        assert np.abs(strong - f).min() < 5e-3 * f, (f, np.sort(strong))
 
 
 def test_quench_L80():
