@@ -19,7 +19,10 @@
 // largest n first, through an atomic counter; the autotuner of this file times both shapes and
 // keeps the faster.  Sizes n >= 16 keep the matrix in shared memory laid out [entry][thread].
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 
 #include "pfaffian_reg.cuh"
 #include "tgba_internal.h"
@@ -397,7 +400,45 @@ tgba_status run_pfaffians(Basis& b, const uint8_t* mask, cudaStream_t st) {
 
 // Autotuner: time every launch shape of the register sizes on this basis (CUDA events on the
 // stream, best of two runs each) and keep the fastest.
+// The choice made by autotune_pfaffians, kept for the process: a later handle with the same
+// Pfaffian workload (device, L, max_qp, largest size, element count and every sector's state
+// counts) takes it without timing the candidates again.  The choice only selects among
+// kernels that compute the same values.
+namespace {
+using TuneKey = std::tuple<int, int, int, int, int64_t, uint64_t>;
+std::mutex g_tune_mutex;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+
+TuneKey tune_key(const Basis& b) {
+  uint64_t h = 1469598103934665603ull;                     // FNV-1a over the sector shapes
+  auto mix = [&h](uint64_t v) {
+    for (int i = 0; i < 8; ++i) {
+      h ^= (v >> (8 * i)) & 0xffu;
+      h *= 1099511628211ull;
+    }
+  };
+  for (const Sector& sec : b.sectors) {
+    mix((uint64_t)sec.m);
+    mix((uint64_t)sec.n_ns);
+    mix((uint64_t)sec.n_r);
+  }
+  return TuneKey(b.device, b.L, b.max_qp, b.max_n, b.n_elements, h);
+}
+}  // namespace
+
 tgba_status autotune_pfaffians(Basis& b, cudaStream_t st) {
+  const TuneKey key = tune_key(b);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      b.tune_mode = it->second.first;
+      b.tune_threads = it->second.second;
+      b.tune_log.clear();
+      b.tuned = true;
+      return plan_pfaffians(b);
+    }
+  }
   struct Cand { int mode, threads; };
   const Cand cands[] = {{0, 64}, {0, 128}, {0, 256}, {1, 64}, {1, 128}, {1, 256}, {3, 128}};
   cudaEvent_t e0, e1;
@@ -431,6 +472,10 @@ tgba_status autotune_pfaffians(Basis& b, cudaStream_t st) {
   b.tune_mode = pick.mode;
   b.tune_threads = pick.threads;
   b.tuned = true;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = std::make_pair(pick.mode, pick.threads);
+  }
   return plan_pfaffians(b);
 }
 
