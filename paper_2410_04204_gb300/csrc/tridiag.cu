@@ -16,7 +16,8 @@
 //    and accumulates the symmetric product y = A v_j for step j; so every trailing element is
 //    read and written once per step with four FMAs.  The trailing lower triangle is cut into
 //    blocks of 32 rows x 16 columns, and each column group's blocks into chunks of up to
-//    kChunk consecutive blocks.  Warps draw chunks from a per-step ticket counter of the
+//    kChunk consecutive blocks, with the group's last kTail blocks as a separate tail chunk
+//    handed out after all the others.  Warps draw chunks from a per-step ticket counter of the
 //    group, so warps and CTAs that run faster (a less busy co-resident CTA, a less crowded
 //    SM sub-partition) take more of them.  In a block a lane owns one row: its row sum needs
 //    no communication, and its 16 column partial sums stay in registers over the chunk, then
@@ -55,6 +56,7 @@ constexpr int kMaxGroup = 16;                   // CTAs cooperating on one matri
 constexpr unsigned kSpinLimit = 1u << 24;       // bounded barrier wait (>= 100 ns per poll: over 1 s)
 constexpr int kRed = 64;                        // reduction scratch (doubles) after the vectors
 constexpr int kChunk = 8;                       // row blocks per chunk of the pass
+constexpr int kTail = 2;                        // last blocks of a column group: one chunk, handed out last
 constexpr int kMaxSmId = 1024;                  // SM ids registered by cta_role
 constexpr int kMaxGroups = kMaxNativeLd / kCols;
 constexpr int kSturmThreads = 64;                // bisection block: one item of 64 eigenvalues
@@ -159,9 +161,12 @@ __device__ __forceinline__ double block_sum(double x, double* red) {
 
 // Work of one step.  Column group g holds columns 16 g .. 16 g + 15; its blocks are the 32-row
 // blocks rb = g / 2 .. LB - 1 (rows 32 rb .. 32 rb + 31, LB = ld / 32), the first on the
-// diagonal.  A chunk is up to kChunk consecutive blocks of one group; the chunks of groups
-// g0 .. G - 1 are numbered group by group, cf[t] being the first chunk of group g0 + t.
-__device__ __forceinline__ int group_chunks(int g, int LB) { return (LB - (g >> 1) + kChunk - 1) / kChunk; }
+// diagonal.  The last min(nb, kTail) blocks of a group form its tail chunk; the blocks before
+// it are cut into chunks of up to kChunk.  Chunks 0 .. NCH1 - 1 are those of the heads, group
+// by group (cf[t] the first of group g0 + t, cf[NG] = NCH1), and chunk NCH1 + t is group
+// g0 + t's tail: so the last chunks of a step are the small ones.
+__device__ __forceinline__ int group_head(int g, int LB) { return max(0, LB - (g >> 1) - kTail); }
+__device__ __forceinline__ int group_chunks(int g, int LB) { return (group_head(g, LB) + kChunk - 1) / kChunk; }
 
 __device__ __forceinline__ void load_block(double (&a)[kCols], const double* __restrict__ p) {
 #pragma unroll
@@ -352,7 +357,7 @@ __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsi
     // chunks go out one at a time from the step's ticket counter (the next ticket is drawn
     // while a chunk is computed), so warps and CTAs that run faster take more of them.
     {
-      const int NCH = cf[NG];
+      const int NCH1 = cf[NG], NCH = NCH1 + NG;
       bool waited = !(C > 1 && (j + 1) % kCols != 0);   // column j lies in group g0
       unsigned c = 0;
       if (lane == 0) c = atomicAdd(tk + j, 1u);
@@ -360,18 +365,29 @@ __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsi
       while ((int)c < NCH) {
         unsigned cn = 0;
         if (lane == 0) cn = atomicAdd(tk + j, 1u);
-        int lo = 0, hi = NG;                          // cf[lo] <= c < cf[hi]
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (cf[mid] <= (int)c) lo = mid;
-          else hi = mid;
+        int lo = 0, rb, re;
+        if ((int)c < NCH1) {                          // a head chunk: cf[lo] <= c < cf[lo + 1]
+          int hi = NG;
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (cf[mid] <= (int)c) lo = mid;
+            else hi = mid;
+          }
+          const int gl = g0 + lo;
+          rb = (gl >> 1) + ((int)c - cf[lo]) * kChunk;
+          re = min(rb + kChunk, (gl >> 1) + group_head(gl, LB));
+        } else {                                      // a tail chunk
+          lo = (int)c - NCH1;
+          const int gl = g0 + lo;
+          rb = (gl >> 1) + group_head(gl, LB);
+          re = LB;
         }
-        const int g = g0 + lo, rb = (g >> 1) + ((int)c - cf[lo]) * kChunk;
+        const int g = g0 + lo;
         if (lo == 0 && !waited) {
           warp_wait(ccnt, col_arrivals, status);
           waited = true;
         }
-        sytrd_chunk(A, ld, LB, g, rb, min(rb + kChunk, LB), lane, (int)c, vwp, vwn, RP, CP);
+        sytrd_chunk(A, ld, LB, g, rb, re, lane, (int)c, vwp, vwn, RP, CP);
         c = __shfl_sync(0xffffffffu, cn, 0);
       }
     }
@@ -403,7 +419,11 @@ __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsi
             y3 += __ldcg(rr + g + 12);
           }
           for (; g <= gi; g += 4) y0 += __ldcg(rr + g);
-          for (int c = cf[t] + q4; c < cf[t + 1]; c += 4) y1 += __ldcg(CP + (int64_t)c * kCols + (i & (kCols - 1)));
+          const int nh = cf[t + 1] - cf[t];             // the group's head chunks, then its tail chunk
+          for (int x = q4; x <= nh; x += 4) {
+            const int c = x < nh ? cf[t] + x : cf[NG] + t;
+            y1 += __ldcg(CP + (int64_t)c * kCols + (i & (kCols - 1)));
+          }
           y = (y0 + y1) + (y2 + y3);
         }
         y += __shfl_xor_sync(0xffffffffu, y, 1);
@@ -725,7 +745,7 @@ int64_t round32(int64_t x) { return (x + 31) / 32 * 32; }
 int64_t max_chunks(int ld) {
   const int LB = ld >> 5;
   int64_t c = 0;
-  for (int g = 0; g < ld / kCols; ++g) c += (LB - (g >> 1) + kChunk - 1) / kChunk;
+  for (int g = 0; g < ld / kCols; ++g) c += (std::max(0, LB - (g >> 1) - kTail) + kChunk - 1) / kChunk + 1;
   return c;
 }
 
