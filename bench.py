@@ -260,7 +260,7 @@ def screening_leg(b24, tgba, inputs, torch):
 
 # DRAM bytes of one sytrd_groups launch on the L = 24 all-sector workload, measured with ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum); None until measured for the current kernel.
-SYTRD_TRAFFIC = None
+SYTRD_TRAFFIC = 487853093632 + 493968308224
 
 
 def eigen_solver_leg(b, w, evs, tgba, torch):
