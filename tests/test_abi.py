@@ -56,3 +56,19 @@ def test_null_handles_rejected():
     with pytest.raises(tgba.TgbaError) as e:
         tgba.tgba_basis_totals(None)
     assert e.value.code == tgba.TGBA_EINVAL
+
+
+def test_null_handles_rejected_by_every_handle_call():
+    """Each entry point that takes a basis handle checks it on the host before anything else
+    (no device needed): a null handle is TGBA_EINVAL."""
+    lib = tgba.lib()
+    calls = {
+        "tgba_x_direct": (None, 0, None, 0, None, None),
+        "tgba_z_elements": (None, 0, 0, 1, None, 0, None, None),
+        "tgba_x_pairs": (None, 0, None, 0, None, None),
+        "tgba_eigvals": (None, None, 0, None, None),
+        "tgba_quench_correlators": (None, 0, 0.5, 0.1, 1.0, 1, 1.0, 2, 1, None, None, None, None, None),
+    }
+    for name, args in calls.items():
+        assert getattr(lib, name)(*args) == tgba.TGBA_EINVAL, name
+
