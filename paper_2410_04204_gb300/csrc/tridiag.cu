@@ -608,7 +608,8 @@ __device__ __forceinline__ int sturm_count32(const float* __restrict__ d, const 
   return cnt;
 }
 
-// Eigenvalues of the tridiagonal matrices by bisection, one thread per eigenvalue.  The grid
+// Eigenvalues of the tridiagonal matrices by bisection, one thread per eigenvalue (d and e^2 in
+// shared memory, as floats for the single-precision steps and then as doubles).  The grid
 // is persistent: a block takes items (a matrix and item_len <= 64 consecutive eigenvalue indices) from
 // the queue until none is left, so the SMs stay evenly loaded.  Per item: Gershgorin bounds
 // [lo, hi] and ||T||; a 64-point grid of single-precision counts shared by the block, then
@@ -638,14 +639,12 @@ sturm_bisect(const TriSlot* __restrict__ slots, const int2* __restrict__ items, 
     const double* E = D + n;
     double* d = sm;
     double* e2 = sm + n;
-    float* d32 = (float*)(sm + 2 * n);
+    float* d32 = (float*)sm;                                  // the same memory, first phase
     float* e32 = d32 + n;
     double lo = 1e300, hi = -1e300;
     for (int i = threadIdx.x; i < n; i += kSturmThreads) {
       const double di = D[i];
       const double el = i > 0 ? fabs(E[i - 1]) : 0.0, er = i + 1 < n ? fabs(E[i]) : 0.0;
-      d[i] = di;
-      e2[i] = i + 1 < n ? E[i] * E[i] : 0.0;
       lo = fmin(lo, di - el - er);
       hi = fmax(hi, di + el + er);
     }
@@ -670,8 +669,8 @@ sturm_bisect(const TriSlot* __restrict__ slots, const int2* __restrict__ items, 
     frexp(tnorm, &ex);
     const double sig = ldexp(1.0, -ex);
     for (int i = threadIdx.x; i < n; i += kSturmThreads) {
-      d32[i] = (float)(d[i] * sig);
-      e32[i] = (float)(e2[i] * sig * sig);
+      d32[i] = (float)(D[i] * sig);
+      e32[i] = i + 1 < n ? (float)(E[i] * E[i] * sig * sig) : 0.0f;
     }
     __syncthreads();
     const double eps = 0x1p-53;
@@ -683,20 +682,27 @@ sturm_bisect(const TriSlot* __restrict__ slots, const int2* __restrict__ items, 
     const float step = (b0 - a0) * (1.0f / kSturmThreads);
     if (threadIdx.x > 0) grid_cnt[threadIdx.x] = sturm_count32(d32, e32, n, fmaf(step, (float)threadIdx.x, a0));
     __syncthreads();
-    if (k >= n || (int)threadIdx.x >= item_len) continue;
+    const bool active = k < n && (int)threadIdx.x < item_len;
     float a32 = a0, b32 = b0;                                 // count32(a32) <= k < count32(b32)
-    {
+    if (active) {
       int c = 1;
       while (c < kSturmThreads && grid_cnt[c] <= k) ++c;      // grid_cnt is non-decreasing in c
       if (c > 1) a32 = fmaf(step, (float)(c - 1), a0);
       if (c < kSturmThreads) b32 = fmaf(step, (float)c, a0);
+      for (int i2 = 0; i2 < 64 && b32 - a32 > dl32; ++i2) {
+        const float mid = 0.5f * (a32 + b32);
+        if (mid <= a32 || mid >= b32) break;
+        if (sturm_count32(d32, e32, n, mid) <= k) a32 = mid;
+        else b32 = mid;
+      }
     }
-    for (int i2 = 0; i2 < 64 && b32 - a32 > dl32; ++i2) {
-      const float mid = 0.5f * (a32 + b32);
-      if (mid <= a32 || mid >= b32) break;
-      if (sturm_count32(d32, e32, n, mid) <= k) a32 = mid;
-      else b32 = mid;
+    __syncthreads();                                          // the FP32 arrays are done with
+    for (int i = threadIdx.x; i < n; i += kSturmThreads) {    // d and e^2 in FP64, over them
+      d[i] = D[i];
+      e2[i] = i + 1 < n ? E[i] * E[i] : 0.0;
     }
+    __syncthreads();
+    if (!active) continue;
     // FP64: the FP32 bracket widened by the bound, checked; else the Gershgorin interval
     const double dl = (double)dl32 / sig;
     double a = (double)a32 / sig - dl, b = (double)b32 / sig + dl;
@@ -848,8 +854,8 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
   const int64_t slot_doubles = round32(((int64_t)B * sizeof(TriSlot) + 7) / 8);
   const int64_t map_doubles = round32(((int64_t)2 * grid * sizeof(CtaWork) + 7) / 8);   // by block, by SM
   // bisection items: item_len consecutive eigenvalue indices of one matrix, 64 (a block's
-  // threads) unless that gives the persistent blocks fewer than two items each, then 32
-  const size_t smem2 = (size_t)2 * n_max * (sizeof(double) + sizeof(float));   // d, e^2 in FP64 and FP32
+  // threads) unless that gives fewer items than resident blocks, then 32
+  const size_t smem2 = (size_t)2 * n_max * sizeof(double);   // d, e^2: FP32 first, then FP64, in turn
   TGBA_CUDA(cudaFuncSetAttribute(sturm_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
   int bis_per_sm = 0;
   TGBA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bis_per_sm, sturm_bisect, kSturmThreads, smem2));
@@ -860,7 +866,7 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
     for (const TriSlot& t : slots) c += (t.n + len - 1) / len;
     return c;
   };
-  if (count_items(item_len) < 2 * (int64_t)bis_per_sm * sms) item_len = kSturmThreads / 2;
+  if (count_items(item_len) < (int64_t)bis_per_sm * sms) item_len = kSturmThreads / 2;
   std::vector<int2> items;
   for (int q = 0; q < B; ++q)
     for (int k0 = 0; k0 < slots[q].n; k0 += item_len) items.push_back(make_int2(q, k0));
