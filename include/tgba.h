@@ -159,8 +159,10 @@ tgba_status tgba_assemble_heff(tgba_basis b, double h_x, tgba_screen screen, dou
  *   0  automatic: 1 when every sector has at most 6400 states (rounded up to a multiple of
  *      32), else 2;
  *   1  native: Householder tridiagonalisation, a group of CTAs per matrix (one cooperative
- *      launch, SMs shared out by work), then
- *      bisection on Sturm counts (TGBA_EINVAL if a sector is too large);
+ *      launch, SMs shared out by work), then bisection on Sturm counts, the first steps in
+ *      single precision within a proven bracket and the last in FP64 to 4 eps ||T||
+ *      (TGBA_EINVAL if a sector is too large; TGBA_ETIMEOUT if a bounded device wait of the
+ *      tridiagonalisation gave up);
  *   2  cuSOLVER XsyevBatched, each matrix padded to the largest sector size with decoupled
  *      diagonal entries above its Gershgorin bound.
  * A non-finite matrix entry gives TGBA_ENUMERIC.  tgba_eigvals is method 0.  Blocks on `stream`. */
