@@ -114,9 +114,6 @@ __device__ __forceinline__ unsigned long long ord_key(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
-__device__ __forceinline__ double ord_val(unsigned long long k) {
-  return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
-}
 
 // rows of the NS block: one warp per row a (coalesced across b)
 __global__ void gersh_rows(int64_t kn, int64_t kr, const double* __restrict__ Q, const double* __restrict__ E, double c,
