@@ -1,5 +1,5 @@
-"""Equal-time correlators <sigma^x_1 sigma^x_{j+1}>(t) after the quench (the
-correlation-function passage of the appendix): the Majorana-string elements pinned by the
+"""Equal-time correlators <sigma^x_1 sigma^x_{j+1}>(t) after the quench (the correlation-function
+passage of the appendix): the Majorana-string elements pinned by the
 basis's orthonormality (j = 0) and Hermiticity, and the connected correlators by exact
 diagonalisation on a complete basis."""
 import numpy as np
