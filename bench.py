@@ -44,6 +44,14 @@ def parse():
     p.add_argument("--no-screening", action="store_true")
     p.add_argument("--no-solver-comparison", action="store_true",
                    help="skip the one-off native vs cuSOLVER eigen-solver timing after the timed steps")
+    g = p.add_argument_group("single stage on a small seeded case (for kernel profilers: ncu -k ... -c ...)")
+    g.add_argument("--stage", choices=["eig", "pfaffian", "direct"],
+                   help="run one stage --reps times and print its CUDA-event timings instead of the benchmark")
+    g.add_argument("--sectors", type=int, nargs="+", default=[0, 1, 2, 3])
+    g.add_argument("--pairs", type=int, default=20000)
+    g.add_argument("--L", type=int, default=None)
+    g.add_argument("--hx", type=float, nargs="+", default=None)
+    g.add_argument("--reps", type=int, default=1)
     return p.parse_args()
 
 
@@ -417,8 +425,81 @@ def run_gb300(args):
     return 0
 
 
+# ------------------------------------------------------------------ one stage, for profilers
+def run_stage(args):
+    """One stage of the path on sectors of the L = 24, h_z = 1, M <= 6 basis with its cutoff:
+    eig = the native batched eigenvalue solver (one fill per matrix, one tridiagonalisation
+    launch, one bisection launch); pfaffian = the Pfaffian stage; direct = the paper-literal X
+    (tgba_x_direct) of --pairs seeded pairs of the first listed sector, with its algorithmic FP64
+    flops per element (the operator-string matrix, 4 m (m - 1) L, plus the complex Parlett-Reid
+    elimination, sum over j = m - 2, m - 4, ..., 2 of 8 j (j - 1) + 6 j, for the string length
+    m = 2L + M_a + M_b).  Prints one line of CUDA-event timings (not benchmark numbers when run
+    under a profiler)."""
+    import numpy as np
+    import torch
+
+    from paper_2410_04204_gb300 import inputs, tgba
+
+    w = inputs.SECTORS_L24
+    L = args.L or w.L
+    hx = args.hx or [w.h_x[0]]
+    torch.cuda.set_device(0)
+    b = tgba.tgba_build_basis(L, w.h_z, args.sectors, w.max_qp, w.e_cut)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    try:
+        tgba.tgba_compute_x(b)
+        n_states = sum(x + y for x, y in tgba.tgba_sector_sizes(b))
+        if args.stage == "direct":
+            info = tgba.tgba_basis_info(b, 0)
+            n_ns, n_r = info["n_ns"], info["n_r"]
+            pairs = inputs.sample_pairs(n_ns, n_r, args.pairs, tag=L)
+            M = info["nqp"]
+            m = 2 * L + M[pairs[:, 0]].astype(np.int64) + M[n_ns + pairs[:, 1]].astype(np.int64)
+            flops = float(sum(4 * mm * (mm - 1) * L + sum(8 * j * (j - 1) + 6 * j for j in range(int(mm) - 2, 0, -2))
+                              for mm in m))
+            p = torch.tensor(pairs, dtype=torch.int32, device="cuda")
+            out = torch.empty(len(pairs), dtype=torch.complex128, device="cuda")
+            times = []
+            for _ in range(max(1, args.reps)):
+                torch.cuda.synchronize()
+                e0.record()
+                tgba.tgba_x_direct(b, 0, p, out)
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            assert torch.isfinite(torch.view_as_real(out)).all()
+            best = min(times)
+            print("stage=direct L=%d sector=%d pairs=%d mean_string=%.1f ms=%s elements_per_s=%.3e gflops=%.1f"
+                  % (L, args.sectors[0], len(pairs), float(m.mean()), [round(t, 3) for t in times],
+                     len(pairs) / best * 1e3, flops / best / 1e6))
+            return 0
+        ev = torch.empty(len(hx) * n_states, dtype=torch.float64, device="cuda")
+        times = []
+        for _ in range(max(1, args.reps)):
+            torch.cuda.synchronize()
+            e0.record()
+            if args.stage == "eig":
+                tgba.tgba_eigvals(b, hx, ev, method=1)
+            else:
+                tgba.tgba_compute_x(b)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        prof = tgba.tgba_profile(b)
+        if args.stage == "eig":
+            assert torch.isfinite(ev).all()
+        print("stage=%s L=%d sectors=%s states=%d ms=%s tridiag_ms=%.3f bisect_ms=%.3f pfaffian_ms=%.3f"
+              % (args.stage, L, args.sectors, n_states, [round(t, 3) for t in times], prof["tridiag_ms"],
+                 prof["bisect_ms"], prof["pfaffian_ms"]))
+    finally:
+        tgba.tgba_basis_free(b)
+    return 0
+
+
 def main():
     args = parse()
+    if args.stage:
+        return run_stage(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gb300(args)

@@ -170,6 +170,20 @@ tgba_status tgba_eigvals(tgba_basis b, const double* h_x, int32_t n_hx, double* 
 tgba_status tgba_eigvals_ex(tgba_basis b, const double* h_x, int32_t n_hx, int32_t method, double* evals_dev,
                             void* stream);
 
+/* Failure-detection check of the bounded waits of the native solver (method 1); not in the
+   paper.  The CTAs of a group that works on one matrix meet at barriers in global memory whose
+   waits are bounded: after spin_limit polls (about 100 ns each; the normal limit is 2^24) a
+   wait gives up, sets a status bit and the group leaves the matrix, so a lost CTA can never
+   hang the GPU.  This call runs tgba_eigvals_ex(method 1) with the given poll limit and, if
+   withhold_matrix >= 0, with the CTA of rank withhold_rank in the group of the
+   withhold_matrix-th (field, sector) matrix (fields outer, sectors inner, empty sectors
+   skipped) leaving before its first barrier, so that its group waits for an arrival that never
+   comes.  The result is then TGBA_ETIMEOUT (the status word is cleared and the handle stays
+   usable; the eigenvalues of that matrix are meaningless).  TGBA_EINVAL if that CTA's group has
+   fewer than two CTAs (nothing would wait) or the rank is outside it.  Blocks on `stream`. */
+tgba_status tgba_eigvals_wait_check(tgba_basis b, const double* h_x, int32_t n_hx, uint32_t spin_limit,
+                                    int32_t withhold_matrix, int32_t withhold_rank, double* evals_dev, void* stream);
+
 /* ---------------------------------------------------------------- S(k=0, w) (Eq. 8-9)
  * Dynamic structure factor of sector index s (which must be the k = 0 sector, m = 0):
  * S(w_i) = 2 pi sum_a w_a L_eta(w_i - (E_a - E_0)), w_a = L |<psi_0|sigma^x_1|psi_a>|^2,
@@ -280,12 +294,14 @@ tgba_status tgba_screen_free(tgba_screen s);
  * that cannot afford the implicit synchronisation of cudaMalloc/cudaFree.  Nothing is allocated:
  * the work matrix (4L x 4L complex) and the per-call inputs live in statically sized device
  * arrays of the library (about 1 MiB, held on every GPU that loads the library until the
- * process exits), so L is limited to 64 (TGBA_ELIMIT beyond).  The first call on a device looks
- * up the addresses of those arrays (cudaGetSymbolAddress) and must come before any stream
- * capture.  All calls share the arrays: calls that overlap on the GPU, from any thread or
- * stream, race and must be serialised by the caller.  table_dev: caller-owned double
- * [2L][2L] (row-major, the real table R of tgba_table); c0_dev: caller-owned double [2]
- * receiving C0 = <0_NS|c_1 + c_1^dag|0_R>.  Blocks on `stream`. */
+ * process exits), so L is limited to 64 (TGBA_ELIMIT beyond).  The first call on a device, and
+ * the first after a cudaDeviceReset, looks up the device addresses of those arrays
+ * (cudaGetSymbolAddress, which may load the library's device code); make that call before any
+ * stream capture begins.  Every call waits for its work to finish: it reads a status word back
+ * to the host.  All calls share the arrays, which keep the last call's contents: calls that
+ * overlap on the GPU, from any thread or stream, race and must be serialised by the caller.
+ * table_dev: caller-owned double [2L][2L] (row-major, the real table R of tgba_table); c0_dev:
+ * caller-owned double [2] receiving C0 = <0_NS|c_1 + c_1^dag|0_R>.  Blocks on `stream`. */
 tgba_status tgba_table_noalloc(int32_t L, double J, double h_z, double* table_dev, double* c0_dev, void* stream);
 
 /* ---------------------------------------------------------------- measurement
@@ -316,37 +332,6 @@ typedef struct {
   int32_t eig_cluster, pad_;
 } tgba_prof;
 tgba_status tgba_profile(tgba_basis b, tgba_prof* out);
-
-/* ---------------------------------------------------------------- learned pair screener
- * Not in the paper (the paper has no counterpart): a 3-layer MLP (width 256, ReLU, FP32
- * parameters) that predicts log10|X_ab| from the two quasiparticle momentum sets, trained on
- * exact elements of the Pfaffian path, and used by tgba_compute_x to skip the Pfaffians of pairs
- * it predicts below the threshold.  Features (D = 20): k/pi of the NS state's modes (ascending,
- * zero padded to 8), k/pi of the R state's modes, M_a/8, M_b/8, 24/L, 1.  Target:
- * log10|X| + (M_a+M_b)/2 log10(L/24), clipped at -30.  Parameters, flat FP32: W1 [256][20],
- * b1 [256], W2 [256][256], b2 [256], w3 [256], b3 [1].  A pair is skipped when
- * predicted log10|V| = y - (M_a+M_b)/2 log10(L/24) + log10(L |h_x|) < log10(tau) - margin, with
- * margin = 3 x the validation RMSE of training (always kept: states with more than 8
- * quasiparticles).  Layer 2 of the inference runs on the tensor cores in BF16. */
-
-/* A screener with the given parameters (params_host: n floats, see above) or, if params_host is
-   NULL, He-normal weights drawn from `seed`.  width must be 256. */
-tgba_status tgba_screen_create(int32_t width, const float* params_host, uint64_t seed, tgba_screen* out);
-tgba_status tgba_screen_nparams(tgba_screen s, int64_t* n);
-tgba_status tgba_screen_params(tgba_screen s, float* params_host);
-/* Forward and back-propagation of one batch (no update): x_dev float [B][20], t_dev float [B];
-   grad_dev float [nparams] receives d(mean (y - t)^2)/d params, loss_host the loss. */
-tgba_status tgba_screen_grad(tgba_screen s, const float* x_dev, const float* t_dev, int64_t B, float* grad_dev,
-                             double* loss_host, void* stream);
-/* Train a new screener on n_samples pairs drawn uniformly (SplitMix64 from `seed`) from all
-   NS x R pairs of the given bases, labelled by their exact X: Adam, batches of 4096, `epochs`
-   passes, the last 5 % held out.  stats_host (optional, 4 doubles): train RMSE, validation RMSE,
-   margin, seconds.  Blocks on `stream`. */
-tgba_status tgba_screen_train(const tgba_basis* sets, int32_t n_sets, int64_t n_samples, uint64_t seed,
-                              int32_t width, int32_t epochs, tgba_screen* out, double* stats_host, void* stream);
-/* Predicted y (see above) of every pair of sector s: pred_dev float [n_ns][n_r]. */
-tgba_status tgba_screen_predict(tgba_screen s, tgba_basis b, int32_t sector, float* pred_dev, void* stream);
-tgba_status tgba_screen_free(tgba_screen s);
 
 /* ---------------------------------------------------------------- measurement helper
  * Achieved FP64 rate of a DFMA-chain kernel on the current device (GFLOP/s, best of `reps`),

@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
 leg of ``bench.py`` may import it.  The product package never imports it and shares no code,
-table or constant with it; the only thing both sides use is ``tests/inputs.py`` (seeded input
+table or constant with it; the only thing both sides use is ``paper_2410_04204_gb300/inputs.py`` (seeded input
 recipes that hold none of the method's arithmetic).
 
 Modules

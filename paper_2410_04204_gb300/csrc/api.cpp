@@ -458,6 +458,27 @@ tgba_status tgba_eigvals_ex(tgba_basis h, const double* h_x, int32_t n_hx, int32
   return check_status(*b, st);
 }
 
+tgba_status tgba_eigvals_wait_check(tgba_basis h, const double* h_x, int32_t n_hx, uint32_t spin_limit,
+                                    int32_t withhold_matrix, int32_t withhold_rank, double* evals_dev, void* stream) {
+  Basis* b = (Basis*)h;
+  BASIS_OK(b);
+  if (!h_x || n_hx < 1) return fail(TGBA_EINVAL, "need at least one h_x");
+  for (int i = 0; i < n_hx; ++i)
+    if (!std::isfinite(h_x[i])) return fail(TGBA_EINVAL, "h_x must be finite");
+  if (spin_limit < 1) return fail(TGBA_EINVAL, "spin_limit must be at least 1");
+  if (!b->x_valid) return fail(TGBA_EINVAL, "no X computed yet: call tgba_compute_x");
+  if (!evals_dev && b->n_states > 0) return fail(TGBA_EINVAL, "null output");
+  int64_t n_max = 0;
+  for (const Sector& s : b->sectors) n_max = std::max(n_max, s.n_ns + s.n_r);
+  if ((n_max + 31) / 32 * 32 > kMaxNativeLd)
+    return fail(TGBA_EINVAL, "the native eigen-solver takes sectors of at most " + std::to_string(kMaxNativeLd) + " states");
+  cudaStream_t st = (cudaStream_t)stream;
+  const WaitCheck check{spin_limit, withhold_matrix, withhold_rank};
+  tgba_status r = eig_all_sectors_native(*b, h_x, n_hx, evals_dev, st, &check);
+  if (r != TGBA_OK) return r;
+  return check_status(*b, st);
+}
+
 tgba_status tgba_dsf(tgba_basis h, int32_t s, double h_x, double w_min, double w_max, int32_t n_w, double eta,
                      float* S_dev, double* evals_dev, int32_t n_ev, double* weights_dev, double* dE_dev,
                      void* stream) {

@@ -18,6 +18,8 @@
 // and records max |Im| of the rotated entries so a violation is reported, never dropped.
 //
 // The sums over sites j = 1..L are closed-form geometric series of plane waves.
+#include <cuda.h>
+
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -484,24 +486,57 @@ struct NoAllocPtrs {
   int* nlab = nullptr;
   double* c0 = nullptr;
   unsigned* status = nullptr;
-  bool ready = false;
+  unsigned long long ctx = 0;   // the context the addresses belong to (0: not looked up)
 };
 
 constexpr int kMaxDevices = 64;
 NoAllocPtrs g_noalloc_ptrs[kMaxDevices];
 std::mutex g_noalloc_mutex;
 
-// Device addresses of the arrays above, looked up once per device (the device current).
+// Identity of the current CUDA context, from the driver (cuCtxGetCurrent, cuCtxGetId: IDs are
+// unique for the life of the process).  A cudaDeviceReset destroys the device's primary
+// context; the next one gets a new ID, and with it the module (and its static arrays) is
+// loaded again, possibly at other addresses.
+tgba_status current_context_id(unsigned long long* id) {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  if (!get_current || !get_id) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    void *f1 = nullptr, *f2 = nullptr;
+    TGBA_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1));
+    TGBA_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2));
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return fail(TGBA_ECUDA, "the CUDA driver does not provide cuCtxGetCurrent/cuCtxGetId");
+    get_current = (GetCurrent)f1;
+    get_id = (GetId)f2;
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr || get_id(ctx, id) != CUDA_SUCCESS)
+    return fail(TGBA_ECUDA, "no current CUDA context");
+  return TGBA_OK;
+}
+
+// Device addresses of the arrays above, looked up once per device and context (the device
+// current): the host-side names of __device__ arrays are not device addresses.
 tgba_status noalloc_setup(int dev, NoAllocPtrs& out) {
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  TGBA_CUDA(cudaSetDevice(dev));               // makes the device's primary context current
+  unsigned long long ctx = 0;
+  tgba_status r = current_context_id(&ctx);
+  if (r != TGBA_OK) return r;
   NoAllocPtrs& p = g_noalloc_ptrs[dev];
-  if (!p.ready) {
-    TGBA_CUDA(cudaGetSymbolAddress((void**)&p.work, g_noalloc_work));
-    TGBA_CUDA(cudaGetSymbolAddress((void**)&p.theta, g_noalloc_theta));
-    TGBA_CUDA(cudaGetSymbolAddress((void**)&p.nlab, g_noalloc_nlab));
-    TGBA_CUDA(cudaGetSymbolAddress((void**)&p.c0, g_noalloc_c0));
-    TGBA_CUDA(cudaGetSymbolAddress((void**)&p.status, g_noalloc_status));
-    p.ready = true;
+  if (p.ctx != ctx) {
+    p = NoAllocPtrs{};
+    NoAllocPtrs q;
+    TGBA_CUDA(cudaGetSymbolAddress((void**)&q.work, g_noalloc_work));
+    TGBA_CUDA(cudaGetSymbolAddress((void**)&q.theta, g_noalloc_theta));
+    TGBA_CUDA(cudaGetSymbolAddress((void**)&q.nlab, g_noalloc_nlab));
+    TGBA_CUDA(cudaGetSymbolAddress((void**)&q.c0, g_noalloc_c0));
+    TGBA_CUDA(cudaGetSymbolAddress((void**)&q.status, g_noalloc_status));
+    q.ctx = ctx;
+    p = q;
   }
   out = p;
   return TGBA_OK;

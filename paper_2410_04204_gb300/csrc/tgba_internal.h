@@ -207,8 +207,15 @@ tgba_status eig_sym(Basis& b, int64_t n, double* a, double* w, bool vectors, cud
 // field h, sector s written at evals + h * n_states + ev_off.  method: 0 = native when every
 // sector fits (n <= kMaxNativeLd), else the library; 1 = native; 2 = cuSOLVER XsyevBatched
 tgba_status eig_all_sectors(Basis& b, const double* hx, int n_hx, double* evals, int method, cudaStream_t st);
-// tridiag.cu: Householder tridiagonalisation by thread-block clusters + Sturm bisection
-tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double* evals, cudaStream_t st);
+// tridiag.cu: Householder tridiagonalisation by groups of CTAs + Sturm bisection.  check
+// (optional): the group waits' poll limit and a CTA that leaves before its first barrier, to
+// make the bounded waits run out (failure-detection checks)
+struct WaitCheck {
+  unsigned spin_limit;
+  int withhold_matrix, withhold_rank;
+};
+tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double* evals, cudaStream_t st,
+                                   const WaitCheck* check = nullptr);
 
 // dsf.cu
 tgba_status dsf(Basis& b, int s, double h_x, double w_min, double w_max, int n_w, double eta, float* S,

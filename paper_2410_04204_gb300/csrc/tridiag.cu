@@ -109,7 +109,8 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 // published by the CTA barrier plus a GPU-scope fence before the arrival, and read after it
 // through L2.  The wait is bounded: on timeout it records kStTimeout and returns false, and
 // the kernel leaves the matrix (the other CTAs of the group then time out as well).
-__device__ __forceinline__ bool group_barrier(unsigned* cnt, unsigned target, int C, int* flag, unsigned* status) {
+__device__ __forceinline__ bool group_barrier(unsigned* cnt, unsigned target, int C, int* flag, unsigned* status,
+                                              unsigned limit) {
   __syncthreads();
   if (C == 1) return true;
   if (threadIdx.x == 0) {
@@ -117,7 +118,7 @@ __device__ __forceinline__ bool group_barrier(unsigned* cnt, unsigned target, in
     atomicAdd(cnt, 1u);
     int ok = 1;
     for (unsigned it = 0; ld_acquire(cnt) < target; ++it) {
-      if (it > kSpinLimit) {
+      if (it > limit) {
         ok = 0;
         atomicOr(status, kStTimeout);
         break;
@@ -134,9 +135,9 @@ __device__ __forceinline__ bool group_barrier(unsigned* cnt, unsigned target, in
 // One warp waits (every lane acquiring for itself, bounded like group_barrier) until the
 // counter reaches target; on timeout it records kStTimeout and goes on (the result is then
 // reported as failed).
-__device__ __forceinline__ void warp_wait(const unsigned* cnt, unsigned target, unsigned* status) {
+__device__ __forceinline__ void warp_wait(const unsigned* cnt, unsigned target, unsigned* status, unsigned limit) {
   for (unsigned it = 0; ld_acquire(cnt) < target; ++it) {
-    if (it > kSpinLimit) {
+    if (it > limit) {
       if ((threadIdx.x & 31) == 0) atomicOr(status, kStTimeout);
       return;
     }
@@ -267,7 +268,7 @@ __device__ __forceinline__ void sytrd_chunk(double* __restrict__ A, int ld, int 
 template <int WARPS>
 __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsigned* cnt, unsigned* ccnt,
                                           unsigned* tk, double* __restrict__ ws, unsigned* __restrict__ status,
-                                          int* flag) {
+                                          int* flag, unsigned limit) {
   extern __shared__ double sm[];
   unsigned arrivals = 0, col_arrivals = 0;
   const int n = S.n, ld = S.ld, LB = ld >> 5, G = ld / kCols;
@@ -384,7 +385,7 @@ __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsi
         }
         const int g = g0 + lo;
         if (lo == 0 && !waited) {
-          warp_wait(ccnt, col_arrivals, status);
+          warp_wait(ccnt, col_arrivals, status, limit);
           waited = true;
         }
         sytrd_chunk(A, ld, LB, g, rb, re, lane, (int)c, vwp, vwn, RP, CP);
@@ -392,7 +393,7 @@ __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsi
       }
     }
     arrivals += C;
-    if (!group_barrier(cnt, arrivals, C, flag, status)) return false;
+    if (!group_barrier(cnt, arrivals, C, flag, status, limit)) return false;
     // rows j + 1 .. n - 1, interleaved over the group's CTAs and, within a CTA, over quads of
     // lanes (row i to CTA i mod C; the long rows at the bottom are shared out): y_i = row sums
     // of the blocks of groups g0 .. i/16 + the column sums of the chunks of column i's group.
@@ -438,7 +439,7 @@ __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsi
     dot = block_sum<WARPS>(dot, red);
     if (threadIdx.x == 0) __stcg(dots + rank, dot);
     arrivals += C;
-    if (!group_barrier(cnt, arrivals, C, flag, status)) return false;
+    if (!group_barrier(cnt, arrivals, C, flag, status, limit)) return false;
     double pv = 0.0;
     for (int r = 0; r < C; ++r) pv += __ldcg(dots + r);
     const double Kc = 0.5 * tau * pv;
@@ -512,20 +513,25 @@ __device__ bool cta_role(const CtaWork* __restrict__ work_blk, const CtaWork* __
 }
 
 // counters: [B] barrier arrivals, [B] column-j reads, then each matrix's step tickets
-// (at 2 B + tk_off, one per step); reg: the SM registration of cta_role.
+// (at 2 B + tk_off, one per step); reg: the SM registration of cta_role.  limit: polls before
+// a group wait gives up.  withhold_q >= 0 (failure-detection checks only): the CTA of rank
+// withhold_rank in the group of matrix withhold_q leaves after the registration, so the
+// group's other CTAs wait for arrivals that never come, until their limit.
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 12 / WARPS)
 sytrd_groups(const TriSlot* __restrict__ slots, int B, const CtaWork* __restrict__ work_blk,
              const CtaWork* __restrict__ work_sm, int per_sm, int sms, unsigned* __restrict__ reg,
-             unsigned* __restrict__ counters, double* __restrict__ ws, unsigned* __restrict__ status) {
+             unsigned* __restrict__ counters, double* __restrict__ ws, unsigned* __restrict__ status,
+             unsigned limit, int withhold_q, int withhold_rank) {
   __shared__ int flag;
   __shared__ CtaWork cw_s;
   if (!cta_role(work_blk, work_sm, per_sm, sms, reg, status, &cw_s)) return;
   const CtaWork cw = cw_s;
   const int C = cw.C, rank = cw.rank;
+  if (cw.first == withhold_q && rank == withhold_rank) return;
   for (int q = cw.first; q < B; q += cw.stride)
     if (!sytrd_matrix<WARPS>(slots[q], C, rank, counters + q, counters + B + q, counters + 2 * B + slots[q].tk_off,
-                             ws, status, &flag))
+                             ws, status, &flag, limit))
       return;
 }
 
@@ -757,7 +763,8 @@ int64_t max_chunks(int ld) {
 
 }  // namespace
 
-tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double* evals, cudaStream_t st) {
+tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double* evals, cudaStream_t st,
+                                   const WaitCheck* check) {
   std::vector<TriSlot> slots;
   std::vector<std::pair<int, int>> who;     // (field, sector)
   int64_t total = 0, tk_total = 0;
@@ -912,15 +919,28 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  const unsigned limit = check ? check->spin_limit : kSpinLimit;
+  int withhold_q = -1, withhold_rank = -1;
+  if (check && check->withhold_matrix >= 0) {
+    int C_q = 0;                                 // the group size of that matrix (0: no CTA starts on it)
+    for (const CtaWork& w : map)
+      if (w.first == check->withhold_matrix) C_q = w.C;
+    if (C_q < 2 || check->withhold_rank < 0 || check->withhold_rank >= C_q)
+      return fail(TGBA_EINVAL, "the withheld CTA must belong to a group of two or more CTAs");
+    withhold_q = check->withhold_matrix;
+    withhold_rank = check->withhold_rank;
+  }
   for (int e = 0; e < 3; ++e)
     if (b.eig_ev[e] == nullptr) TGBA_CUDA(cudaEventCreate(&b.eig_ev[e]));
   TGBA_CUDA(cudaEventRecord(b.eig_ev[0], st));
   if (per_sm == 2)
     TGBA_CUDA(cudaLaunchKernelEx(&cfg, sytrd_groups<6>, (const TriSlot*)d_slots, B, (const CtaWork*)d_map,
-                                 (const CtaWork*)d_sm_map, per_sm, sms, d_reg, d_cnt, ws, b.d_status));
+                                 (const CtaWork*)d_sm_map, per_sm, sms, d_reg, d_cnt, ws, b.d_status, limit,
+                                 withhold_q, withhold_rank));
   else
     TGBA_CUDA(cudaLaunchKernelEx(&cfg, sytrd_groups<12>, (const TriSlot*)d_slots, B, (const CtaWork*)d_map,
-                                 (const CtaWork*)d_sm_map, per_sm, sms, d_reg, d_cnt, ws, b.d_status));
+                                 (const CtaWork*)d_sm_map, per_sm, sms, d_reg, d_cnt, ws, b.d_status, limit,
+                                 withhold_q, withhold_rank));
   ++b.launches;
   TGBA_CUDA(cudaEventRecord(b.eig_ev[1], st));
   const int bis_grid = std::min(n_items, bis_per_sm * sms);

@@ -19,7 +19,7 @@ _NAMES = {0: "TGBA_OK", 1: "TGBA_EINVAL", 2: "TGBA_ENOMEM", 3: "TGBA_ECUDA", 4: 
 # every symbol include/tgba.h declares
 SYMBOLS = ("tgba_last_error", "tgba_device_count", "tgba_build_basis", "tgba_basis_info", "tgba_basis_totals",
            "tgba_basis_free", "tgba_compute_x", "tgba_x_stats", "tgba_x_export", "tgba_x_pairs", "tgba_x_direct", "tgba_z_elements", "tgba_table",
-           "tgba_assemble_heff", "tgba_eigvals", "tgba_eigvals_ex", "tgba_dsf", "tgba_dsf_k", "tgba_quench", "tgba_quench_ordered", "tgba_quench_correlators", "tgba_screen_create",
+           "tgba_assemble_heff", "tgba_eigvals", "tgba_eigvals_ex", "tgba_eigvals_wait_check", "tgba_dsf", "tgba_dsf_k", "tgba_quench", "tgba_quench_ordered", "tgba_quench_correlators", "tgba_screen_create",
            "tgba_screen_nparams", "tgba_screen_params", "tgba_screen_grad", "tgba_screen_train",
            "tgba_screen_predict", "tgba_screen_free", "tgba_table_noalloc", "tgba_profile", "tgba_fp64_peak")
 
@@ -75,6 +75,7 @@ def lib():
             "tgba_assemble_heff": (_I32, [_VP, _D, _VP, _D, _VP, _VP]),
             "tgba_eigvals": (_I32, [_VP, _VP, _I32, _VP, _VP]),
             "tgba_eigvals_ex": (_I32, [_VP, _VP, _I32, _I32, _VP, _VP]),
+            "tgba_eigvals_wait_check": (_I32, [_VP, _VP, _I32, ctypes.c_uint32, _I32, _I32, _VP, _VP]),
             "tgba_dsf": (_I32, [_VP, _I32, _D, _D, _D, _I32, _D, _VP, _VP, _I32, _VP, _VP, _VP]),
             "tgba_dsf_k": (_I32, [_VP, _I32, _I32, _D, _D, _D, _I32, _D, _VP, _VP, _I32, _VP, _VP, _VP]),
             "tgba_quench": (_I32, [_VP, _I32, _D, _VP, _VP, _I32, _D, _I32, _I32, _VP, _VP, _VP, _VP]),
@@ -255,6 +256,16 @@ def tgba_eigvals(b, h_x, evals_out, stream=None, method=0):
     hx = np.ascontiguousarray(np.atleast_1d(np.asarray(h_x, np.float64)))
     _cuda_tensor(evals_out, torch.float64, len(hx) * _n_states(b), name="evals_out")
     _check(lib().tgba_eigvals_ex(b, hx.ctypes.data, len(hx), int(method), _ptr(evals_out), _stream(stream)))
+
+
+def tgba_eigvals_wait_check(b, h_x, evals_out, spin_limit, withhold_matrix=-1, withhold_rank=0, stream=None):
+    """The native solver with a short wait limit and, optionally, one CTA withheld from its
+    group (failure-detection check of the bounded waits)."""
+    import torch
+    hx = np.ascontiguousarray(np.atleast_1d(np.asarray(h_x, np.float64)))
+    _cuda_tensor(evals_out, torch.float64, len(hx) * _n_states(b), name="evals_out")
+    _check(lib().tgba_eigvals_wait_check(b, hx.ctypes.data, len(hx), int(spin_limit), int(withhold_matrix),
+                                         int(withhold_rank), _ptr(evals_out), _stream(stream)))
 
 
 def tgba_dsf(b, s, h_x, w_min, w_max, n_w, eta, S_out, evals_out=None, n_ev=0, weights_out=None, dE_out=None,

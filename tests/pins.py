@@ -14,7 +14,7 @@ from oracle import tgba
 
 
 def spectrum_error(N, h, h_x, sectors=None):
-    """max |TGBA eigenvalues - ED eigenvalues| over sectors with the untruncated basis (P:49:
+    """max |TGBA eigenvalues - ED eigenvalues| over sectors with the untruncated basis (Method section:
     without truncation the method is exact)."""
     worst = 0.0
     for m in (range(N) if sectors is None else sectors):

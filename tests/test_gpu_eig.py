@@ -138,3 +138,29 @@ def test_native_rejects_oversized_and_reports_overflow():
         assert np.isfinite(ev.cpu().numpy()).all()
     finally:
         tgba.tgba_basis_free(b)
+
+
+def test_bounded_group_wait_times_out_and_handle_survives():
+    """Failure detection without a GPU fault: one CTA of the group that shares a matrix leaves
+    before its first barrier (an arrival that never comes), the group's waits give up after a
+    short poll limit, and the call returns TGBA_ETIMEOUT; the same handle then solves normally
+    and matches the library solver.  One L = 24 sector gives one matrix and a group of 16 CTAs."""
+    w = inputs.SECTORS_L24
+    b = tgba.tgba_build_basis(w.L, w.h_z, [0], w.max_qp, w.e_cut)
+    try:
+        tgba.tgba_compute_x(b)
+        n = sum(_sizes(b))
+        ev = torch.empty(n, dtype=torch.float64, device="cuda")
+        with pytest.raises(tgba.TgbaError) as e:
+            tgba.tgba_eigvals_wait_check(b, [0.1], ev, spin_limit=1 << 12, withhold_matrix=0, withhold_rank=3)
+        assert e.value.code == tgba.TGBA_ETIMEOUT
+        with pytest.raises(tgba.TgbaError) as e:       # a withheld CTA outside the group
+            tgba.tgba_eigvals_wait_check(b, [0.1], ev, spin_limit=1 << 12, withhold_matrix=0, withhold_rank=99)
+        assert e.value.code == tgba.TGBA_EINVAL
+        tgba.tgba_eigvals_wait_check(b, [0.1], ev, spin_limit=1 << 24)   # nothing withheld: normal solve
+        got = ev.cpu().numpy()
+        ref = _evals(b, [0.1], 2)[0]
+        assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+        assert np.array_equal(_evals(b, [0.1], 1)[0], got)
+    finally:
+        tgba.tgba_basis_free(b)

@@ -42,13 +42,32 @@ def reference(L, h):
         tgba.tgba_basis_free(b)
 
 
-@pytest.mark.parametrize("L,h", [(24, 1.0), (40, 0.7)])
+@pytest.mark.parametrize("L,h", [(24, 1.0), (40, 0.7), (64, 1.0)])
 def test_noalloc_table_matches_regular_entry_point(L, h):
+    """L = 64 is the size limit: there the work matrix fills the static array exactly."""
     want_t, want_c0 = reference(L, h)
     for _ in range(2):
         got_t, got_c0 = noalloc(L, h)
         assert np.abs(got_t - want_t).max() <= 1e-10 * np.abs(want_t).max()
         assert abs(got_c0 - want_c0) <= 1e-10 * abs(want_c0)
+
+
+def test_noalloc_calls_take_no_device_memory():
+    """After a first call (which may load the library's device code, static arrays included),
+    repeated calls leave the device's free memory and torch's allocator unchanged."""
+    L = 64
+    table = torch.empty(4 * L * L, dtype=torch.float64, device="cuda")
+    c0 = torch.empty(2, dtype=torch.float64, device="cuda")
+    tgba.tgba_table_noalloc(L, 1.0, table, c0)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for h in (0.5, 1.0, 1.5):
+        tgba.tgba_table_noalloc(L, h, table, c0)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0
 
 
 def test_noalloc_rejects_chains_beyond_its_work_area():
