@@ -38,6 +38,9 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--workload", default="L24_all_sectors", choices=["L24_all_sectors", "L80_k0_quench"],
+                   help="L24_all_sectors: every sector of L = 24, H_eff and all eigenvalues for two h_x; "
+                        "L80_k0_quench: the L = 80 quench, 64 (h_x, cutoff) variants, 2000 times")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-budget-s", type=float, default=12.0)
@@ -117,10 +120,12 @@ class Clocks:
 def oracle_sample(w, budget_s, tag=0):
     """Time the oracle on a bounded, seeded sample of the workload and extrapolate to one step.
 
-    Sample: pairs drawn uniformly from the oracle's own basis of a few sectors, each evaluated
-    by a direct Pfaffian of size 2N+M+M' (Appendix A as written), and one complex128 numpy
-    eigvalsh of a sector-sized Hermitian matrix.  Step estimate = elements x (time per pair) +
-    2 h_x x sum over sectors of the eigensolve time scaled by (n / n_ref)^3."""
+    Sample: pairs drawn uniformly from the oracle's own basis of a few sectors, evaluated by
+    both of the oracle's routes: the direct Pfaffian of size 2N+M+M' per element (Appendix A as
+    written) and the reduced form (one Schur complement of the vacuum operators, then a Pfaffian
+    of size M+M' per element), each on all host cores and on one thread; and one complex128
+    numpy eigvalsh of a sector-sized Hermitian matrix.  Step estimate = elements x (time per
+    pair) + 2 h_x x sum over sectors of the eigensolve time scaled by (n / n_ref)^3."""
     import numpy as np
 
     from oracle import basis as obs
@@ -131,31 +136,42 @@ def oracle_sample(w, budget_s, tag=0):
     sectors = sorted(g.choice(w.sectors, size=min(3, len(w.sectors)), replace=False).tolist())
     bases = {m: obs.sector_basis(w.L, w.h_z, m, w.max_qp, w.e_cut, w.max_per_parity) for m in sectors}
     sizes = {m: (len(ns), len(r)) for m, (ns, r) in bases.items()}
-    t_pairs, n_pairs, threads = 0.0, 0, 1
-    while t_pairs < 0.6 * budget_s and n_pairs < 65536:
-        batch = []
-        for m in sectors:
-            ns, r = bases[m]
-            if ns and r:
-                for a, bb in inputs.sample_pairs(len(ns), len(r), 256, tag=1000 * tag + m + n_pairs):
-                    batch.append((ns[a].modes, r[bb].modes))
-        t0 = time.perf_counter()
-        _, threads = oel.x_elements(w.L, w.h_z, batch, return_threads=True)
-        t_pairs += time.perf_counter() - t0
-        n_pairs += len(batch)
+
+    def time_pairs(fn, budget, threads, per_sector, cap):
+        t, n, used, rnd = 0.0, 0, 1, 0
+        while t < budget and n < cap:
+            batch = []
+            for m in sectors:
+                ns, r = bases[m]
+                if ns and r:
+                    for a, bb in inputs.sample_pairs(len(ns), len(r), per_sector, tag=1000 * tag + 97 * rnd + m):
+                        batch.append((ns[a].modes, r[bb].modes))
+            t0 = time.perf_counter()
+            _, used = fn(w.L, w.h_z, batch, n_threads=threads, return_threads=True)
+            t += time.perf_counter() - t0
+            n += len(batch)
+            rnd += 1
+        return t / max(n, 1), n, used
+
+    rows = {}
+    for name, fn, share, per_sector, cap in (("direct", oel.x_elements, 0.35, 256, 65536),
+                                             ("reduced", oel.x_elements_reduced, 0.25, 20000, 4_000_000)):
+        t_all, n_all, threads = time_pairs(fn, share * budget_s, 0, per_sector, cap)
+        t_one, n_one, _ = time_pairs(fn, 0.1 * budget_s, 1, max(64, per_sector // 8), cap)
+        rows[name] = dict(t_pair=t_all, n_pairs=n_all, threads=threads, t_pair_1thread=t_one, n_pairs_1thread=n_one)
     n_ref = max(a + b for a, b in sizes.values())
     h = g.standard_normal((n_ref, n_ref)) + 1j * g.standard_normal((n_ref, n_ref))
     h = h + h.conj().T
     t0 = time.perf_counter()
     np.linalg.eigvalsh(h)
     t_eig = time.perf_counter() - t0
-    return dict(t_pair=t_pairs / n_pairs, n_pairs=n_pairs, t_eig=t_eig, n_ref=n_ref, threads=threads,
-                sectors=sectors)
+    return dict(rows=rows, t_eig=t_eig, n_ref=n_ref, threads=rows["reduced"]["threads"], sectors=sectors)
 
 
-def oracle_step_seconds(w, s, sector_sizes):
+def oracle_step_seconds(w, s, sector_sizes, form="reduced", one_thread=False):
     n_el = sum(a * b for a, b in sector_sizes)
-    t = n_el * s["t_pair"]
+    row = s["rows"][form]
+    t = n_el * (row["t_pair_1thread"] if one_thread else row["t_pair"])
     for a, b in sector_sizes:
         t += len(w.h_x) * s["t_eig"] * ((a + b) / s["n_ref"]) ** 3
     return t, n_el
@@ -171,8 +187,23 @@ def oracle_sector_sizes(w):
 
 
 def sample_text(s):
-    return ("%d seeded pairs from sectors %s by direct Pfaffian, %d threads; one complex128 eigvalsh "
-            "of n=%d; extrapolated to the full step" % (s["n_pairs"], s["sectors"], s["threads"], s["n_ref"]))
+    r = s["rows"]
+    return ("seeded pairs from sectors %s: %d by the reduced form (Schur complement, Pfaffian of size M+M' per "
+            "element; value), %d by direct Pfaffians of size 2N+M+M'; %d threads; one complex128 eigvalsh of "
+            "n=%d (numpy threads); extrapolated to the full step"
+            % (s["sectors"], r["reduced"]["n_pairs"], r["direct"]["n_pairs"], s["threads"], s["n_ref"]))
+
+
+def cpu_rows(w, s, sizes):
+    """Elements/s of the step for each oracle route, all host cores and one thread (the
+    eigensolves always with numpy's threads)."""
+    out = {}
+    for form in ("reduced", "direct"):
+        for one, tag in ((False, "all_cores"), (True, "1_thread")):
+            t, n_el = oracle_step_seconds(w, s, sizes, form, one)
+            out["%s_%s" % (form, tag)] = n_el / t
+    out["pfaffian_pairs_per_s"] = {f: 1.0 / s["rows"][f]["t_pair"] for f in ("reduced", "direct")}
+    return out
 
 
 def run_reference(args):
@@ -196,7 +227,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(w, sum(a * b for a, b in sizes), sum(a + b for a, b in sizes)),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": s["threads"], "kind": "oracle", "sample": sample_text(s)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": s["threads"], "kind": "oracle", "sample": sample_text(s),
+                             "rows": cpu_rows(w, s, sizes)},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -415,9 +447,131 @@ def run_gb300(args):
     tgba.tgba_basis_free(b)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s = oracle_sample(w, args.cpu_budget_s)
-        t_cpu, _ = oracle_step_seconds(w, s, oracle_sector_sizes(w))
+        sizes_o = oracle_sector_sizes(w)
+        t_cpu, _ = oracle_step_seconds(w, s, sizes_o)
         line["cpu_baseline"] = {"value": n_el / t_cpu, "unit": UNIT, "cores": s["threads"], "kind": "oracle",
-                                "sample": sample_text(s)}
+                                "sample": sample_text(s), "rows": cpu_rows(w, s, sizes_o)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+# ------------------------------------------------------------------ the L = 80 quench workload
+def quench_variants(tgba, inputs, b, w):
+    """The 64 (h_x, cutoff) variants: the nested cutoffs keep 5000 i of the basis' lowest
+    states (i = 1..8), each with the 8 fields."""
+    info = tgba.tgba_basis_info(b, 0, w.max_qp)
+    E = info["E0"]
+    e_vac = E[:info["n_ns"]].min()
+    cuts = inputs.nested_cutoffs(E - e_vac, inputs.QUENCH_L80_KEEP)
+    hxs = [hx for _ in cuts for hx in inputs.QUENCH_L80_HX]
+    ecs = [c for c in cuts for _ in inputs.QUENCH_L80_HX]
+    return hxs, ecs, cuts
+
+
+def run_gb300_quench(args):
+    """One step = the Pfaffian stage of the L = 80, M <= 10 basis (3.8e8 elements, one X for
+    every variant) and the quench of all 64 variants (batched Chebyshev propagation, one graph),
+    2000 times in [0, 100]."""
+    import torch
+
+    from paper_2410_04204_gb300 import build as libbuild
+    from paper_2410_04204_gb300 import inputs, tgba
+
+    rank, local_rank, world = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    if not os.path.exists(libbuild.LIB):
+        libbuild.build()
+    w = inputs.QUENCH_L80
+    q = w.quench
+    stream = torch.cuda.current_stream()
+    peak_gflops = tgba.tgba_fp64_peak(5)
+    b = tgba.tgba_build_basis(w.L, w.h_z, w.sectors, w.max_qp, w.e_cut, w.max_per_parity)
+    _, n_el, _ = tgba.tgba_basis_totals(b)
+    hxs, ecs, cuts = quench_variants(tgba, inputs, b, w)
+    nv, n_t = len(hxs), q["n_t"]
+    mx = torch.empty(nv * n_t, dtype=torch.float64, device="cuda")
+    nrm = torch.empty(nv, dtype=torch.float64, device="cuda")
+    chi = None
+
+    def step():
+        nonlocal chi
+        tgba.tgba_compute_x(b)
+        chi = tgba.tgba_quench(b, 0, q["h_z0"], hxs, ecs, q["t_max"], n_t, mx, nrm, method=2)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches0 = tgba.tgba_profile(b)["kernel_launches"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    profs = []
+    clocks = Clocks(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        profs.append(tgba.tgba_profile(b))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = tgba.tgba_profile(b)["kernel_launches"] - launches0
+    step_ms = [a.elapsed_time(c) for a, c in ev]
+    ms, value = aggregate(statistics.mean(step_ms), n_el, world, dist, "cuda")
+    pf_ms = statistics.mean(p["pfaffian_ms"] for p in profs)
+    tab_ms = statistics.mean(p["table_ms"] for p in profs)
+    q_ms = statistics.mean(p["quench_ms"] for p in profs)
+    prof = profs[-1]
+    q_gflops = prof["quench_flops"] / (q_ms * 1e-3) / 1e9
+    peak_src = "live FP64 DFMA-chain kernel (tgba_fp64_peak); MEASURED_PEAKS.json has no FP64 entry"
+    roofline = {"bound": "alu", "kernel": "Chebyshev steps: FP64 GEMMs on the X block (cuBLAS DGEMM) + cheb_step",
+                "achieved": q_gflops, "peak": peak_gflops, "unit": "GFLOP/s", "frac": q_gflops / peak_gflops,
+                "traffic": None, "peak_source": peak_src, "flops_per_launch": prof["quench_flops"], "ms": q_ms,
+                "terms_K": prof["quench_terms"]}
+    host_mx = torch.empty(nv * n_t, dtype=torch.float64, pin_memory=True)
+    e2e_s, h2d = [], 0
+    for _ in range(max(1, args.e2e_steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b2 = tgba.tgba_build_basis(w.L, w.h_z, w.sectors, w.max_qp, w.e_cut, w.max_per_parity)
+        tgba.tgba_compute_x(b2)
+        tgba.tgba_quench(b2, 0, q["h_z0"], hxs, ecs, q["t_max"], n_t, mx, nrm, method=2)
+        host_mx.copy_(mx, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_s.append(time.perf_counter() - t0)
+        h2d = tgba.tgba_profile(b2)["upload_bytes"]
+        tgba.tgba_basis_free(b2)
+    tgba.tgba_basis_free(b)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "L": w.L, "h_z": w.h_z, "h_z0": q["h_z0"], "max_qp": w.max_qp,
+                       "e_cut": w.e_cut, "max_per_parity": w.max_per_parity, "elements": n_el,
+                       "variants": nv, "h_x": list(inputs.QUENCH_L80_HX), "cutoffs": cuts,
+                       "chi": [int(c) for c in chi[::len(inputs.QUENCH_L80_HX)]], "t_max": q["t_max"], "n_t": n_t,
+                       "l2": "inputs larger than L2 (3.2 GB X block per step)"},
+            "roofline": roofline,
+            "stages_ms": {"table": tab_ms, "pfaffian": pf_ms, "quench_propagation": q_ms,
+                          "quench_rest": ms - tab_ms - pf_ms - q_ms},
+            "pfaffian_stage": {"ms": pf_ms, "elements_per_s": n_el / (pf_ms * 1e-3),
+                               "gflops": prof["pfaffian_flops"] / (pf_ms * 1e-3) / 1e9,
+                               "frac": prof["pfaffian_flops"] / (pf_ms * 1e-3) / 1e9 / peak_gflops},
+            "clocks": clk,
+            "e2e": {"value": world * n_el / statistics.mean(e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": nv * n_t * 8},
+            "gpu_launches": launches}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -502,6 +656,8 @@ def main():
         return run_stage(args)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "L80_k0_quench":
+        return run_gb300_quench(args)
     return run_gb300(args)
 
 

@@ -321,7 +321,11 @@ tgba_status tgba_table_noalloc(int32_t L, double J, double h_z, double* table_de
  * the last native tgba_eigvals (0 if none ran); tridiag_flops: its algorithmic FP64 flops,
  * sum over matrices of sum_{m=1}^{n-1} 4 m (m + 1) (two FMAs of the rank-2 update and two of
  * the symmetric product per element of the trailing lower triangle, ~4n^3/3); eig_matrices:
- * matrices in that batch; eig_cluster: CTAs per matrix. */
+ * matrices in that batch; eig_cluster: CTAs per matrix.
+ * quench_ms: device time of the last batched Chebyshev propagation of tgba_quench (the graph of
+ * its K steps over all variants); quench_terms: K; quench_flops: its algorithmic FP64 flops,
+ * K sum over variants of 8 n_NS n_R (two real vectors, both off-diagonal blocks, one FMA per
+ * entry). */
 typedef struct {
   double table_ms, pfaffian_ms, pfaffian_flops;
   int64_t pfaffian_launches, kernel_launches, upload_bytes, evaluated;
@@ -330,6 +334,8 @@ typedef struct {
   double tridiag_ms, bisect_ms, tridiag_flops;
   int64_t eig_matrices;
   int32_t eig_cluster, pad_;
+  double quench_ms, quench_flops;
+  int64_t quench_terms;
 } tgba_prof;
 tgba_status tgba_profile(tgba_basis b, tgba_prof* out);
 

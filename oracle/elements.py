@@ -76,6 +76,29 @@ def x_elements(N, h, pairs, n_threads=0, return_threads=False):
     return (vals, used) if return_threads else vals
 
 
+def x_elements_reduced(N, h, pairs, n_threads=0, return_threads=False):
+    """X for a list of (NS modes, R modes) pairs by the reduced form (a second CPU route, used
+    as the faster CPU baseline): the string of every element keeps the same vacuum and sigma
+    operators F and adds its excitation operators, so with the Schur complement S of the
+    contraction matrix of the string that holds ALL excitation operators (NS d_p for every NS
+    mode, descending; R ones for every R mode, ascending), X = n_NS n_R Pf(A_FF) Pf(S[sel, sel]).
+    Pinned to x_elements in the tests."""
+    th_ns = md.theta(N, md.NS, h)
+    th_r = md.theta(N, md.R, h)
+    all_ns = list(range(N))
+    string = (_bra_vacuum(N, md.NS, th_ns) + _bra_excitations(N, md.NS, th_ns, all_ns)
+              + [(nat.OP_SIGMA1, 0.0, 0.0)]
+              + _ket_excitations(N, md.R, th_r, list(range(N))) + _ket_vacuum(N, md.R, th_r))
+    n_vac_ns = len(_bra_vacuum(N, md.NS, th_ns))
+    is_f = [1] * n_vac_ns + [0] * N + [1] + [0] * N + [1] * (len(string) - n_vac_ns - 2 * N - 1)
+    S, pf = nat.reduced_table(N, string, is_f)
+    # E positions: NS mode i sits at N - 1 - i (descending block), R mode j at N + j
+    sels = [[N - 1 - i for i in sorted(a, reverse=True)] + [N + j for j in sorted(b)] for a, b in pairs]
+    scale = md.vacuum_norm(N, md.NS, h) * md.vacuum_norm(N, md.R, h)
+    vals, used = nat.reduced_batch(S, pf, scale, sels, n_threads)
+    return (vals, used) if return_threads else vals
+
+
 def x_block(N, h, ns_states, r_states, n_threads=0):
     """Dense X[a, b] over two lists of basis states."""
     pairs = [(a.modes, b.modes) for a in ns_states for b in r_states]

@@ -33,6 +33,13 @@ def lib():
             L.oracle_wick_batch.restype = ctypes.c_int
             L.oracle_wick_batch.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+            L.oracle_reduced_table.restype = ctypes.c_int
+            L.oracle_reduced_table.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            L.oracle_reduced_batch.restype = ctypes.c_int
+            L.oracle_reduced_batch.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                               ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_int]
             L.oracle_pfaffian_batch.restype = None
             L.oracle_pfaffian_batch.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
             _lib = L
@@ -65,6 +72,38 @@ def wick_batch(N, strings, n_threads=0):
     out = np.zeros(len(strings), dtype=np.complex128)
     used = lib().oracle_wick_batch(int(N), len(strings), offsets.ctypes.data, kinds.ctypes.data,
                                    ks.ctypes.data, th.ctypes.data, out.ctypes.data, int(n_threads))
+    return out, used
+
+
+def reduced_table(N, string, is_f):
+    """(S, Pf(A_FF)) of the reduced form over one operator string: S is the Schur complement
+    onto the operators with is_f = 0, in string order."""
+    m = len(string)
+    kinds = np.array([o[0] for o in string], dtype=np.int32)
+    ks = np.array([o[1] for o in string], dtype=np.float64)
+    th = np.array([o[2] for o in string], dtype=np.float64)
+    f = np.ascontiguousarray(np.asarray(is_f, dtype=np.int32))
+    nE = int(m - f.sum())
+    S = np.zeros((nE, nE), dtype=np.complex128)
+    pf = np.zeros(1, dtype=np.complex128)
+    if lib().oracle_reduced_table(int(N), m, kinds.ctypes.data, ks.ctypes.data, th.ctypes.data, f.ctypes.data,
+                                  S.ctypes.data, pf.ctypes.data):
+        raise ZeroDivisionError("the F block of the contraction matrix is singular")
+    return S, pf[0]
+
+
+def reduced_batch(S, pf, scale, sels, n_threads=0):
+    """scale Pf(A_FF) Pf(S[sel, sel]) for each index list in sels.  Returns (values, threads)."""
+    S = np.ascontiguousarray(S, dtype=np.complex128)
+    lens = np.array([len(x) for x in sels], dtype=np.int64)
+    off = np.zeros(len(sels) + 1, dtype=np.int64)
+    np.cumsum(lens, out=off[1:])
+    idx = np.ascontiguousarray(np.concatenate([np.asarray(x, np.int32) for x in sels]) if len(sels) and off[-1]
+                               else np.zeros(1, np.int32), dtype=np.int32)
+    pfa = np.array([pf.real, pf.imag], dtype=np.float64)
+    out = np.zeros(len(sels), dtype=np.complex128)
+    used = lib().oracle_reduced_batch(S.shape[0], S.ctypes.data, pfa.ctypes.data, float(scale), len(sels),
+                                      off.ctypes.data, idx.ctypes.data, out.ctypes.data, int(n_threads))
     return out, used
 
 

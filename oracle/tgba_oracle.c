@@ -119,7 +119,7 @@ int oracle_wick_batch(int N, int n_strings, const long long* offsets, const int*
                       const double* ks, const double* thetas, double* out_ri, int n_threads) {
   int used = 1;
 #ifdef _OPENMP
-  if (n_threads > 0) omp_set_num_threads(n_threads);
+  omp_set_num_threads(n_threads > 0 ? n_threads : omp_get_num_procs());
 #pragma omp parallel
   {
 #pragma omp single
@@ -156,4 +156,135 @@ void oracle_pfaffian_batch(int n, int count, double* mats_ri, double* out_ri) {
     out_ri[2 * (size_t)c] = creal(r);
     out_ri[2 * (size_t)c + 1] = cimag(r);
   }
+}
+
+/* ------------------------------------------------------------------ reduced form
+ * The same elements through the Schur complement identity for Pfaffians: for a skew matrix
+ * [[A_FF, A_FE], [-A_FE^T, A_EE]] with A_FF invertible,
+ *   Pf = Pf(A_FF) Pf(A_EE + A_FE^T A_FF^{-1} A_FE).
+ * Every element's operator string keeps the same operators F (both vacua and sigma) and adds
+ * the excitation operators of its two states, so with S = A_EE + A_FE^T A_FF^{-1} A_FE over ALL
+ * excitation operators E, an element is Pf(A_FF) Pf(S[sel, sel]) (moving F to the front of the
+ * string costs a sign (-1)^{M + (N-1)(M+M')} = +1 for even M, M').  A second, independent CPU
+ * route to the same numbers (it shares only op_coeffs and oracle_pfaffian with the direct one),
+ * used as the faster CPU baseline. */
+
+/* A over one string of m operators (strict upper triangle of V^T U, made skew), row-major. */
+static void contraction_matrix(int N, int m, const int* kinds, const double* ks, const double* th, cplx* A) {
+  cplx* U = (cplx*)malloc(sizeof(cplx) * (size_t)m * N);
+  cplx* V = (cplx*)malloc(sizeof(cplx) * (size_t)m * N);
+  for (int a = 0; a < m; ++a) op_coeffs(N, kinds[a], ks[a], th[a], U + (size_t)a * N, V + (size_t)a * N);
+  for (int a = 0; a < m; ++a) {
+    A[(size_t)a * m + a] = 0.0;
+    for (int b = a + 1; b < m; ++b) {
+      cplx acc = 0.0;
+      for (int j = 0; j < N; ++j) acc += V[(size_t)a * N + j] * U[(size_t)b * N + j];
+      A[(size_t)a * m + b] = acc;
+      A[(size_t)b * m + a] = -acc;
+    }
+  }
+  free(U);
+  free(V);
+}
+
+/* Table of the reduced form.  The string has m operators; is_f[a] = 1 marks the F operators.
+   Writes S (nE x nE, row-major, E operators in string order) and Pf(A_FF) (re, im).  Returns 0,
+   or 1 if A_FF is singular. */
+int oracle_reduced_table(int N, int m, const int* kinds, const double* ks, const double* th, const int* is_f,
+                         double* S_ri, double* pf_ri) {
+  cplx* A = (cplx*)malloc(sizeof(cplx) * (size_t)m * m);
+  contraction_matrix(N, m, kinds, ks, th, A);
+  int nF = 0;
+  for (int a = 0; a < m; ++a) nF += is_f[a] != 0;
+  const int nE = m - nF;
+  int* fi = (int*)malloc(sizeof(int) * (nF > 0 ? nF : 1));
+  int* ei = (int*)malloc(sizeof(int) * (nE > 0 ? nE : 1));
+  for (int a = 0, f = 0, e = 0; a < m; ++a) {
+    if (is_f[a]) fi[f++] = a;
+    else ei[e++] = a;
+  }
+  /* Z = A_FF^{-1} A_FE by Gaussian elimination with partial pivoting on [A_FF | A_FE] */
+  cplx* M = (cplx*)malloc(sizeof(cplx) * (size_t)nF * (nF + nE));
+  const int w = nF + nE;
+  for (int r = 0; r < nF; ++r) {
+    for (int c = 0; c < nF; ++c) M[(size_t)r * w + c] = A[(size_t)fi[r] * m + fi[c]];
+    for (int c = 0; c < nE; ++c) M[(size_t)r * w + nF + c] = A[(size_t)fi[r] * m + ei[c]];
+  }
+  int singular = 0;
+  for (int k = 0; k < nF && !singular; ++k) {
+    int piv = k;
+    for (int r = k + 1; r < nF; ++r)
+      if (cabs(M[(size_t)r * w + k]) > cabs(M[(size_t)piv * w + k])) piv = r;
+    if (M[(size_t)piv * w + k] == 0.0) { singular = 1; break; }
+    if (piv != k)
+      for (int c = 0; c < w; ++c) {
+        cplx t = M[(size_t)k * w + c];
+        M[(size_t)k * w + c] = M[(size_t)piv * w + c];
+        M[(size_t)piv * w + c] = t;
+      }
+    for (int r = 0; r < nF; ++r) {
+      if (r == k) continue;
+      const cplx f = M[(size_t)r * w + k] / M[(size_t)k * w + k];
+      if (f == 0.0) continue;
+      for (int c = k; c < w; ++c) M[(size_t)r * w + c] -= f * M[(size_t)k * w + c];
+    }
+  }
+  if (!singular) {
+    /* S = A_EE + A_FE^T Z, Z[r][c] = M[r][nF + c] / M[r][r] */
+    for (int i = 0; i < nE; ++i)
+      for (int j = 0; j < nE; ++j) {
+        cplx acc = A[(size_t)ei[i] * m + ei[j]];
+        for (int r = 0; r < nF; ++r)
+          acc += A[(size_t)fi[r] * m + ei[i]] * (M[(size_t)r * w + nF + j] / M[(size_t)r * w + r]);
+        S_ri[2 * ((size_t)i * nE + j)] = creal(acc);
+        S_ri[2 * ((size_t)i * nE + j) + 1] = cimag(acc);
+      }
+    cplx* F = (cplx*)malloc(sizeof(cplx) * (size_t)(nF > 0 ? nF : 1) * (nF > 0 ? nF : 1));
+    for (int r = 0; r < nF; ++r)
+      for (int c = 0; c < nF; ++c) F[(size_t)r * nF + c] = A[(size_t)fi[r] * m + fi[c]];
+    cplx p = oracle_pfaffian(F, nF);
+    pf_ri[0] = creal(p);
+    pf_ri[1] = cimag(p);
+    free(F);
+  }
+  free(M); free(fi); free(ei); free(A);
+  return singular;
+}
+
+/* out[p] = scale Pf(A_FF) Pf(S[sel_p, sel_p]) for each pair p; sel_p = idx[off[p] .. off[p+1]-1]
+   (positions in E, ascending).  Returns the number of threads used. */
+int oracle_reduced_batch(int nE, const double* S_ri, const double* pf_ri, double scale, int n_pairs,
+                         const long long* off, const int* idx, double* out_ri, int n_threads) {
+  int used = 1;
+#ifdef _OPENMP
+  omp_set_num_threads(n_threads > 0 ? n_threads : omp_get_num_procs());
+#pragma omp parallel
+  {
+#pragma omp single
+    used = omp_get_num_threads();
+  }
+#endif
+  const cplx* S = (const cplx*)S_ri;
+  const cplx pf = (pf_ri[0] + I * pf_ri[1]) * scale;
+  int nmax = 0;
+  for (int p = 0; p < n_pairs; ++p) {
+    int n = (int)(off[p + 1] - off[p]);
+    if (n > nmax) nmax = n;
+  }
+#pragma omp parallel
+  {
+    cplx* B = (cplx*)malloc(sizeof(cplx) * (size_t)(nmax > 0 ? nmax * nmax : 1));
+#pragma omp for schedule(dynamic, 256)
+    for (int p = 0; p < n_pairs; ++p) {
+      const int* sel = idx + off[p];
+      const int n = (int)(off[p + 1] - off[p]);
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) B[(size_t)i * n + j] = S[(size_t)sel[i] * nE + sel[j]];
+      const cplx r = pf * oracle_pfaffian(B, n);
+      out_ri[2 * (size_t)p] = creal(r);
+      out_ri[2 * (size_t)p + 1] = cimag(r);
+    }
+    free(B);
+  }
+  return used;
 }

@@ -57,13 +57,15 @@ static void release(Basis* b) {
   void* ptrs[] = {b->d_E_ns, b->d_E_r, b->d_M_ns, b->d_M_r, b->d_sel_ns, b->d_sel_r, b->d_modes_ns, b->d_modes_r,
                   b->d_theta, b->d_nlab, b->d_table, b->d_c0, b->d_work, b->d_P, b->d_status,
                   b->d_eig_a, b->d_eig_w, b->d_eig_work, b->d_eig_info, b->d_scratch, b->d_mask,
-                  b->d_reg_rects, b->d_counter};
+                  b->d_reg_rects, b->d_counter, b->d_blas_ws};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int e = 0; e < 3; ++e) {
     if (b->ev[e]) cudaEventDestroy(b->ev[e]);
     if (b->eig_ev[e]) cudaEventDestroy(b->eig_ev[e]);
   }
+  for (int e = 0; e < 2; ++e)
+    if (b->q_ev[e]) cudaEventDestroy(b->q_ev[e]);
   for (RectList& L : b->rect_lists)
     if (L.d_rects) cudaFree(L.d_rects);
   if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
@@ -672,6 +674,14 @@ tgba_status tgba_profile(tgba_basis h, tgba_prof* out) {
   }
   out->tridiag_flops = b->tridiag_flops;
   out->eig_matrices = b->eig_matrices;
+  if (b->q_ev_recorded) {
+    float t = 0;
+    TGBA_CUDA(cudaEventSynchronize(b->q_ev[1]));
+    TGBA_CUDA(cudaEventElapsedTime(&t, b->q_ev[0], b->q_ev[1]));
+    out->quench_ms = t;
+  }
+  out->quench_flops = b->quench_flops;
+  out->quench_terms = b->quench_terms;
   out->eig_cluster = b->eig_cluster;
   return TGBA_OK;
 }

@@ -105,44 +105,6 @@ __global__ void gather_kernel(int64_t kn, int64_t kr, const int32_t* __restrict_
   }
 }
 
-// ---- Chebyshev propagation (large variants): e^{-iHt} = e^{-iE_c t} sum_k (2 - d_k0)(-i)^k J_k(Rt) T_k(H'),
-// H' = (H~ - E_c)/R with the spectrum of H~ inside [E_c - R, E_c + R].
-
-// Gershgorin bounds of H~ (diagonal E, off-diagonal blocks c Q with Q the row-major [kn][kr]
-// block of P): lo/hi reduced through an order-preserving integer encoding of the doubles.
-__device__ __forceinline__ unsigned long long ord_key(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-}
-
-// rows of the NS block: one warp per row a (coalesced across b)
-__global__ void gersh_rows(int64_t kn, int64_t kr, const double* __restrict__ Q, const double* __restrict__ E, double c,
-                           unsigned long long* __restrict__ hi, unsigned long long* __restrict__ lo_neg) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < kn; a += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    double sum = 0.0;
-    for (int64_t b = lane; b < kr; b += 32) sum += fabs(Q[a * kr + b]);
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) {
-      const double r = fabs(c) * sum;
-      atomicMax(hi, ord_key(E[a] + r));
-      atomicMax(lo_neg, ord_key(-(E[a] - r)));
-    }
-  }
-}
-
-// columns (R states): one thread per column b (coalesced across b)
-__global__ void gersh_cols(int64_t kn, int64_t kr, const double* __restrict__ Q, const double* __restrict__ E, double c,
-                           unsigned long long* __restrict__ hi, unsigned long long* __restrict__ lo_neg) {
-  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < kr; b += (int64_t)gridDim.x * blockDim.x) {
-    double sum = 0.0;
-    for (int64_t a = 0; a < kn; ++a) sum += fabs(Q[a * kr + b]);
-    const double r = fabs(c) * sum;
-    atomicMax(hi, ord_key(E[kn + b] + r));
-    atomicMax(lo_neg, ord_key(-(E[kn + b] - r)));
-  }
-}
-
 // Eq. 11 at each time t: || Psi^chi(t) - Psi^chi'(t) ||^2 = sum over the larger subspace of
 // |B'_a - B_a|^2 (B_a = 0 for states the smaller one lacks).  The smaller subspace's NS and R
 // lists are prefixes of the larger one's (nested truncations in one ranking).  B, B': [Re | Im]
@@ -224,90 +186,6 @@ __global__ void gather_energy(int64_t kn, int64_t kr, const int32_t* __restrict_
     E[i] = i < kn ? E_ns[idx_ns[i]] : E_r[idx_r[i - kn]];
 }
 
-// V[:, 0:2] = [Re c~0 | Im c~0]
-__global__ void cheb_start(int64_t n, const double* __restrict__ c, double* __restrict__ V) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    V[i] = c[2 * i];
-    V[n + i] = c[2 * i + 1];
-  }
-}
-
-// next = alpha (HX + E x - E_c x) / R - beta prev, on the n x 2 block (HX holds the off-diagonal part)
-__global__ void cheb_step(int64_t n, const double* __restrict__ E, double ec, double inv_r, double alpha, double beta,
-                          const double* __restrict__ HX, const double* __restrict__ x, const double* __restrict__ prev,
-                          double* __restrict__ next) {
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < 2 * n; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = q < n ? q : q - n;
-    const double h = HX[q] + (E[i] - ec) * x[q];
-    next[q] = alpha * inv_r * h - (prev ? beta * prev[q] : 0.0);
-  }
-}
-
-// alpha_k(t) = (2 - d_k0) J_k(R t), k = 0..K, by Miller's backward recurrence for J_k
-// (J_{k-1} = (2k/x) J_k - J_{k+1} from a start far above k and x, normalised by
-// J_0 + 2 sum J_2j = 1), one thread per time.
-__global__ void bessel_kernel(int n_t, int t0, double dt, double R, int K, int m_start, double* __restrict__ out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n_t) return;
-  const double x = R * dt * (double)(t0 + c);
-  double* a = out + (int64_t)c * (K + 1);
-  if (x == 0.0) {
-    a[0] = 1.0;
-    for (int k = 1; k <= K; ++k) a[k] = 0.0;
-    return;
-  }
-  double jp1 = 0.0, j = 1e-300, norm = 0.0;
-  for (int k = m_start; k >= 1; --k) {
-    const double jm1 = (2.0 * k / x) * j - jp1;
-    jp1 = j;
-    j = jm1;                                   // j = J_{k-1} (unnormalised)
-    if (k - 1 <= K) a[k - 1] = j;
-    if ((k - 1) % 2 == 0 && k - 1 > 0) norm += 2.0 * j;
-    if (fabs(j) > 1e250) {                     // rescale everything accumulated so far
-      const double s = 1e-250;
-      j *= s; jp1 *= s; norm *= s;
-      for (int q = k - 1; q <= K && q <= m_start; ++q) a[q] *= s;
-    }
-  }
-  norm += j;                                   // + J_0
-  const double inv = 1.0 / norm;
-  a[0] *= inv;
-  for (int k = 1; k <= K; ++k) a[k] *= 2.0 * inv;
-}
-
-// Gamma_kl = Re(i^{k-l} mu_kl), mu_kl = v_k^H X~ v_l from G = V^T (X~ V) over the n x 2 blocks:
-// mu = (G_rr + G_ii) + i (G_ri - G_ir)
-__global__ void gamma_kernel(int K1, const double* __restrict__ G, double* __restrict__ Gam) {
-  const int64_t ld = 2 * (int64_t)K1;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)K1 * K1; q += (int64_t)gridDim.x * blockDim.x) {
-    const int k = (int)(q / K1), l = (int)(q % K1);
-    // G is column-major (ld = 2 K1): entry (row, col) at col * ld + row
-    const double rr = G[(2 * l) * ld + 2 * k], ii = G[(2 * l + 1) * ld + 2 * k + 1];
-    const double ri = G[(2 * l + 1) * ld + 2 * k], ir = G[(2 * l) * ld + 2 * k + 1];
-    const double re = rr + ii, im = ri - ir;
-    double g;
-    switch (((k - l) % 4 + 4) % 4) {           // Re(i^{k-l} (re + i im))
-      case 0: g = re; break;
-      case 1: g = -im; break;
-      case 2: g = -re; break;
-      default: g = im; break;
-    }
-    Gam[(int64_t)l * K1 + k] = g;
-  }
-}
-
-// mx[t] = alpha(t)^T (Gamma alpha(t)) / norm2 (GA precomputed, one warp per time)
-__global__ void cheb_quad(int K1, int cnt, const double* __restrict__ A, const double* __restrict__ GA,
-                          const double* __restrict__ norm2, double* __restrict__ mx) {
-  const int lane = threadIdx.x & 31;
-  const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (col >= cnt) return;
-  double acc = 0.0;
-  for (int k = lane; k < K1; k += 32) acc += A[(int64_t)col * K1 + k] * GA[(int64_t)col * K1 + k];
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) mx[col] = acc / norm2[0];
-}
-
 int blocks_for(int64_t work) {
   int64_t g = (work + 255) / 256;
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
@@ -322,13 +200,6 @@ tgba_status blas_fail(cublasStatus_t s, const char* what) {
 void destroy_blas(void* h) { cublasDestroy((cublasHandle_t)h); }
 
 constexpr int64_t kEigenMaxStates = 4096;   // automatic method: eigendecomposition up to here
-
-static double ord_val_host(unsigned long long k) {
-  const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
-  double d;
-  std::memcpy(&d, &b, sizeof(d));
-  return d;
-}
 
 tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* trunc, int nv, int order, double t_max,
                    int n_t, int method, double* mx, double* norm_out, double* eps_out, int64_t* chi_out, cudaStream_t st,
@@ -384,6 +255,11 @@ tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* t
     cublasStatus_t cs = cublasCreate(&bh);
     if (cs != CUBLAS_STATUS_SUCCESS) return blas_fail(cs, "create");
     b.blas = bh;
+    // an explicit workspace, so that calls captured into a graph allocate nothing
+    constexpr size_t kWs = 32u << 20;
+    TGBA_CUDA(cudaMalloc(&b.d_blas_ws, kWs));
+    cs = cublasSetWorkspace(bh, b.d_blas_ws, kWs);
+    if (cs != CUBLAS_STATUS_SUCCESS) return blas_fail(cs, "workspace");
   }
   cublasSetStream(bh, st);
   const double e_ns = b.e_ns_vac * b.J;
@@ -478,18 +354,23 @@ tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* t
     ~FreeB() { if (p) cudaFreeAsync(p, s); }
   } free_b{Bbuf[0], st};
   int64_t knp = 0, krp = 0;
+  std::vector<int> cheb_vars;
   for (int v = 0; v < nv; ++v) {
     const std::vector<int32_t>& ins = sel_ns[v];
     const std::vector<int32_t>& ir = sel_r[v];
     const int64_t kn = (int64_t)ins.size(), kr = (int64_t)ir.size(), n = kn + kr;
     if (chi_out) chi_out[v] = n;
     const bool cheb = method == 2 || (method == 0 && n > kEigenMaxStates);
+    if (cheb) {                                     // propagated together after this loop
+      cheb_vars.push_back(v);
+      continue;
+    }
     double* Bcur = Bbuf[v & 1];
     double* Bprev = Bbuf[(v + 1) & 1];
     const int nb = std::min(n_t, 256);
     // scratch layout (doubles): shared part, then the eigen-path buffers
     const int64_t shared = n + 2 * n + 2 * n + 8 + kn * kr + 2 * L + (kn + kr + 2) / 2 + 8;
-    const int64_t need = shared + (cheb ? 0 : n * n + 3 * (2 * n * nb));
+    const int64_t need = shared + n * n + 3 * (2 * n * nb);
     double* sc;
     tgba_status r = scratch(b, need, &sc);
     if (r != TGBA_OK) return r;
@@ -645,80 +526,69 @@ tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* t
       }
       knp = kn;
       krp = kr;
-    } else {
-      // energies of the kept states and the Gershgorin interval of H~
-      gather_energy<<<blocks_for(n), 256, 0, st>>>(kn, kr, idx, idx + kn, b.d_E_ns + sec.ns_off, b.d_E_r + sec.r_off, E);
-      unsigned long long* bnd = (unsigned long long*)(norm2 + 2);
-      TGBA_CUDA(cudaMemsetAsync(bnd, 0, 2 * sizeof(unsigned long long), st));
-      const double coff = -b.L * hx[v] * cabs;
-      gersh_rows<<<blocks_for(32 * kn), 256, 0, st>>>(kn, kr, Q, E, coff, bnd, bnd + 1);
-      gersh_cols<<<blocks_for(kr), 256, 0, st>>>(kn, kr, Q, E, coff, bnd, bnd + 1);
-      TGBA_CUDA(cudaGetLastError());
-      b.launches += 3;
-      unsigned long long hb[2];
-      TGBA_CUDA(cudaMemcpyAsync(hb, bnd, sizeof(hb), cudaMemcpyDeviceToHost, st));
-      TGBA_CUDA(cudaStreamSynchronize(st));
-      const double emax = ord_val_host(hb[0]), emin = -ord_val_host(hb[1]);
-      const double ec = 0.5 * (emax + emin), R = 0.5 * (emax - emin) * 1.01 + 1e-9;
-      const double xmax = R * t_max;
-      // terms: J_k(x) < 1e-16 beyond k ~ x + 10 x^(1/3) + 30 (Bessel tail above the turning point)
-      const int K = (int)std::ceil(xmax + 10.0 * std::cbrt(xmax) + 30.0);
-      const int K1 = K + 1;
-      int m_start = K + 30 + (int)std::ceil(std::sqrt(40.0 * std::max<double>(K, xmax)));
-      m_start += m_start & 1;
-      double *V = nullptr, *W = nullptr, *HX = nullptr, *G = nullptr, *Gam = nullptr, *Abuf = nullptr, *GA = nullptr;
-      const size_t bytes = sizeof(double) * ((size_t)2 * n * 2 * K1 + 2 * n + 4 * (size_t)K1 * K1 + (size_t)K1 * K1 +
-                                             2 * (size_t)K1 * nb);
-      TGBA_CUDA(cudaMallocAsync(&V, bytes, st));
-      W = V + (size_t)n * 2 * K1;
-      HX = W + (size_t)n * 2 * K1;
-      G = HX + 2 * n;
-      Gam = G + 4 * (size_t)K1 * K1;
-      Abuf = Gam + (size_t)K1 * K1;
-      GA = Abuf + (size_t)K1 * nb;
-      auto offdiag = [&](const double* x, double* out, int cols, double scale) -> cublasStatus_t {
-        // out_NS = scale Q^T x_R, out_R = scale Q x_NS  (column blocks of height n)
-        cublasStatus_t q = CUBLAS_STATUS_SUCCESS;
-        if (kn > 0 && kr > 0) {
-          q = cublasDgemm(bh, CUBLAS_OP_T, CUBLAS_OP_N, (int)kn, cols, (int)kr, &scale, Q, (int)kr, x + kn, (int)n, &zero,
-                          out, (int)n);
-          if (q == CUBLAS_STATUS_SUCCESS)
-            q = cublasDgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, (int)kr, cols, (int)kn, &scale, Q, (int)kr, x, (int)n, &zero,
-                            out + kn, (int)n);
-        }
-        return q;
-      };
-      if (!(kn > 0 && kr > 0)) TGBA_CUDA(cudaMemsetAsync(HX, 0, 2 * n * sizeof(double), st));
-      cheb_start<<<blocks_for(n), 256, 0, st>>>(n, c, V);
-      ++b.launches;
-      for (int k = 0; k < K; ++k) {                  // V_{k+1} = 2 H' V_k - V_{k-1}  (V_1 = H' V_0)
-        const double* xk = V + (size_t)k * 2 * n;
-        if ((cs = offdiag(xk, HX, 2, coff)) != CUBLAS_STATUS_SUCCESS) { cudaFreeAsync(V, st); return blas_fail(cs, "chebyshev step"); }
-        cheb_step<<<blocks_for(2 * n), 256, 0, st>>>(n, E, ec, 1.0 / R, k == 0 ? 1.0 : 2.0, 1.0, HX, xk,
-                                                     k == 0 ? nullptr : xk - 2 * n, V + (size_t)(k + 1) * 2 * n);
-        ++b.launches;
-      }
-      TGBA_CUDA(cudaGetLastError());
-      // moments: G = V^T (X~ V), X~ = |C0| [[0, Q^T], [Q, 0]]
-      if ((cs = offdiag(V, W, 2 * K1, cq)) != CUBLAS_STATUS_SUCCESS) { cudaFreeAsync(V, st); return blas_fail(cs, "moments"); }
-      if (!(kn > 0 && kr > 0)) TGBA_CUDA(cudaMemsetAsync(W, 0, (size_t)n * 2 * K1 * sizeof(double), st));
-      cs = cublasDgemm(bh, CUBLAS_OP_T, CUBLAS_OP_N, 2 * K1, 2 * K1, (int)n, &one, V, (int)n, W, (int)n, &zero, G, 2 * K1);
-      if (cs != CUBLAS_STATUS_SUCCESS) { cudaFreeAsync(V, st); return blas_fail(cs, "gram"); }
-      gamma_kernel<<<blocks_for((int64_t)K1 * K1), 256, 0, st>>>(K1, G, Gam);
-      ++b.launches;
-      for (int t0 = 0; t0 < n_t; t0 += nb) {
-        const int cnt = std::min(nb, n_t - t0);
-        bessel_kernel<<<(cnt + 127) / 128, 128, 0, st>>>(cnt, t0, dt, R, K, m_start, Abuf);
-        cs = cublasDgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, K1, cnt, K1, &one, Gam, K1, Abuf, K1, &zero, GA, K1);
-        if (cs != CUBLAS_STATUS_SUCCESS) { cudaFreeAsync(V, st); return blas_fail(cs, "gamma alpha"); }
-        cheb_quad<<<(cnt * 32 + 255) / 256, 256, 0, st>>>(K1, cnt, Abuf, GA, norm2, mx + (int64_t)v * n_t + t0);
-        TGBA_CUDA(cudaGetLastError());
-        b.launches += 2;
-      }
-      TGBA_CUDA(cudaFreeAsync(V, st));
     }
     if (norm_out) TGBA_CUDA(cudaMemcpyAsync(norm_out + v, norm2, sizeof(double), cudaMemcpyDeviceToDevice, st));
     TGBA_CUDA(cudaStreamSynchronize(st));       // the next variant may grow the shared scratch
+  }
+  if (!cheb_vars.empty()) {
+    // every variant keeps a prefix of the NS ranking and a prefix of the R ranking: the union
+    // is the longest of each
+    const std::vector<int32_t>* un_ns = &sel_ns[cheb_vars[0]];
+    const std::vector<int32_t>* un_r = &sel_r[cheb_vars[0]];
+    for (int v : cheb_vars) {
+      if (sel_ns[v].size() > un_ns->size()) un_ns = &sel_ns[v];
+      if (sel_r[v].size() > un_r->size()) un_r = &sel_r[v];
+    }
+    const int64_t kn = (int64_t)un_ns->size(), kr = (int64_t)un_r->size(), n = kn + kr;
+    double* ub = nullptr;
+    const size_t udoubles = (size_t)n + 2 * n + 8 + (size_t)kn * kr + 2 * L + (n + 2) / 2 + 8;
+    TGBA_CUDA(cudaMallocAsync(&ub, udoubles * sizeof(double), st));
+    struct FreeU {
+      double* p; cudaStream_t s;
+      ~FreeU() { cudaFreeAsync(p, s); }
+    } free_u{ub, st};
+    double* E = ub;
+    double* c = E + n;
+    double* norm2 = c + 2 * n;
+    double* Q = norm2 + 8;
+    double* dth_dev = Q + (size_t)kn * kr;
+    int32_t* idx = (int32_t*)(dth_dev + 2 * L);
+    TGBA_CUDA(cudaMemcpyAsync(dth_dev, dth.data(), 2 * L * sizeof(double), cudaMemcpyHostToDevice, st));
+    TGBA_CUDA(cudaMemcpyAsync(idx, un_ns->data(), kn * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    TGBA_CUDA(cudaMemcpyAsync(idx + kn, un_r->data(), kr * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    TGBA_CUDA(cudaMemsetAsync(norm2, 0, sizeof(double), st));
+    overlap_kernel<<<blocks_for(n), 256, 0, st>>>(kn, kr, idx, idx + kn, sec.ns_off, sec.r_off, b.d_M_ns, b.d_M_r,
+                                                 b.d_modes_ns, b.d_modes_r, b.max_qp, b.d_nlab, dth_dev, base[0],
+                                                 base[1], s_re, s_im, g_re, g_im, L, c, norm2);
+    gather_energy<<<blocks_for(n), 256, 0, st>>>(kn, kr, idx, idx + kn, b.d_E_ns + sec.ns_off, b.d_E_r + sec.r_off, E);
+    b.launches += 2;
+    if (kn > 0 && kr > 0) {
+      gather_kernel<<<blocks_for(kn * kr), 256, 0, st>>>(kn, kr, idx, idx + kn, sec.n_r, b.d_P + sec.x_off, Q);
+      ++b.launches;
+    }
+    TGBA_CUDA(cudaGetLastError());
+    // ||c0||^2 of each variant: sums of |c~0|^2 over its two prefixes
+    std::vector<double> ch(2 * n), pre(n + 1, 0.0);
+    TGBA_CUDA(cudaMemcpyAsync(ch.data(), c, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TGBA_CUDA(cudaStreamSynchronize(st));
+    for (int64_t q = 0; q < n; ++q) pre[q + 1] = pre[q] + (ch[2 * q] * ch[2 * q] + ch[2 * q + 1] * ch[2 * q + 1]);
+    std::vector<ChebVariant> cv;
+    std::vector<double> norms(nv, 0.0);
+    for (int v : cheb_vars) {
+      ChebVariant x;
+      x.out = v;
+      x.kn = (int64_t)sel_ns[v].size();
+      x.kr = (int64_t)sel_r[v].size();
+      x.hx = hx[v];
+      x.norm2 = pre[x.kn] + (pre[kn + x.kr] - pre[kn]);
+      norms[v] = x.norm2;
+      cv.push_back(x);
+    }
+    tgba_status r = quench_cheb_batch(b, Q, kn, kr, E, c, cv, t_max, n_t, mx, st);
+    if (r != TGBA_OK) return r;
+    if (norm_out)
+      for (int v : cheb_vars) TGBA_CUDA(cudaMemcpyAsync(norm_out + v, &norms[v], sizeof(double), cudaMemcpyHostToDevice, st));
+    TGBA_CUDA(cudaStreamSynchronize(st));
   }
   TGBA_CUDA(cudaStreamSynchronize(st));
   return check_status(b, st);

@@ -158,6 +158,11 @@ struct Basis {
   // eigen solver scratch
   void* solver = nullptr;          // cusolverDnHandle_t
   void* blas = nullptr;            // cublasHandle_t
+  double* d_blas_ws = nullptr;     // its workspace (set explicitly, so captured calls allocate nothing)
+  int quench_terms = 0;            // Chebyshev terms K of the last batched quench propagation
+  double quench_flops = 0;         // its algorithmic FP64 flops (K sum 8 n_NS n_R)
+  cudaEvent_t q_ev[2] = {nullptr, nullptr};   // around its graph launch
+  bool q_ev_recorded = false;
   double* d_eig_a = nullptr; double* d_eig_w = nullptr; double* d_eig_work = nullptr;
   double* d_scratch = nullptr; int64_t scratch_cap = 0;
   int* d_eig_info = nullptr;
@@ -233,6 +238,19 @@ tgba_status dsf_k(Basis& b, int s, int s0, double h_x, double w_min, double w_ma
 tgba_status quench(Basis& b, int s, double h0, const double* hx, const double* trunc, int nv, int order, double t_max,
                    int n_t, int method, double* mx, double* norm, double* eps, int64_t* chi, cudaStream_t st,
                    int j_max = 0, double* corr = nullptr);
+
+// cheb.cu: batched Chebyshev propagation of quench variants whose kept sets are prefixes of one
+// NS ranking and one R ranking.  Q: the X block of the union (col-major kr_max x kn_max), E:
+// the union's energies (NS rows, then R rows), c: c~0 on the union (complex interleaved).
+// Variant i writes mx[out][n_t].
+struct ChebVariant {
+  int out;
+  int64_t kn, kr;
+  double hx, norm2;
+};
+tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t kr_max, const double* E,
+                              const double* c, const std::vector<ChebVariant>& vars, double t_max, int n_t,
+                              double* mx, cudaStream_t st);
 
 // screen.cu
 struct Screen;

@@ -43,6 +43,11 @@ SCREEN_L60 = Workload("L60_k0_screen", 60, 1.0, (0.05,), 6, 8.984, None, (0,))
 QUENCH_L80 = Workload("L80_k0_quench", 80, 1.0, (0.1,), 10, 6.551, 20000, (0,),
                       quench=dict(h_z0=0.5, t_max=100.0, n_t=2000))
 
+# Config 5 variants: 8 longitudinal fields x 8 nested energy cutoffs; cutoff i keeps the
+# 5000 i lowest states of the basis (about 2500 i per parity), the last one the whole capped basis.
+QUENCH_L80_HX = (0.025, 0.05, 0.075, 0.1, 0.125, 0.15, 0.175, 0.2)
+QUENCH_L80_KEEP = tuple(5000 * i for i in range(1, 9))
+
 SCREEN_TAUS = (1e-12, 1e-11, 1e-10, 1e-9, 1e-8)
 
 
@@ -57,6 +62,23 @@ def random_skew(n, count, tag=0, complex_=False):
     if complex_:
         a = a + 1j * g.standard_normal((count, n, n))
     return a - np.swapaxes(a, 1, 2)
+
+
+def nested_cutoffs(energies, keep):
+    """Energy cutoffs (above the NS vacuum) that keep the keep[i] lowest of the given state
+    energies: midpoints between consecutive distinct levels; -1 (keep all) where keep[i] is at
+    least the number of states."""
+    e = np.sort(np.asarray(energies, dtype=np.float64))
+    out = []
+    for k in keep:
+        if k >= len(e):
+            out.append(-1.0)
+            continue
+        lo = k
+        while lo > 0 and e[lo] - e[lo - 1] < 1e-6:      # not inside a degenerate level
+            lo -= 1
+        out.append(float(0.5 * (e[lo - 1] + e[lo])))
+    return out
 
 
 def sample_pairs(n_a, n_b, count, tag=0):

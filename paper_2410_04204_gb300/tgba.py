@@ -44,7 +44,8 @@ class _Prof(ctypes.Structure):
                 ("upload_bytes", ctypes.c_int64), ("evaluated", ctypes.c_int64),
                 ("tune_mode", ctypes.c_int32), ("tune_threads", ctypes.c_int32), ("tune_ms", ctypes.c_double * 8),
                 ("tridiag_ms", ctypes.c_double), ("bisect_ms", ctypes.c_double), ("tridiag_flops", ctypes.c_double),
-                ("eig_matrices", ctypes.c_int64), ("eig_cluster", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("eig_matrices", ctypes.c_int64), ("eig_cluster", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("quench_ms", ctypes.c_double), ("quench_flops", ctypes.c_double), ("quench_terms", ctypes.c_int64)]
 
 
 _lib = None

@@ -84,3 +84,15 @@ def test_overlaps_match_fock_space(focks):
         vac0 = fock.states(N, h0, parity, [bs.State(parity, (), 0.0)], F)[:, 0]
         brute = fock.states(N, h, parity, st, F).conj().T @ vac0
         assert np.abs(brute - el.overlaps(N, h, h0, parity, st)).max() < 1e-13
+
+
+@pytest.mark.parametrize("L,h", [(8, 1.0), (12, 0.7), (12, 1.3)])
+def test_reduced_form_equals_direct_pfaffians(L, h):
+    """The oracle's second route (Schur complement of the vacuum and sigma operators, one small
+    Pfaffian per element) gives the direct Pfaffians of the whole string, which the Fock-space
+    tests above pin."""
+    ns, r = bs.sector_basis(L, h, 0, min(L, 6))
+    pairs = [(a.modes, b.modes) for a in ns[::3] for b in r[::5]][:300]
+    d = el.x_elements(L, h, pairs)
+    red = el.x_elements_reduced(L, h, pairs)
+    assert np.abs(d - red).max() <= 1e-12 * np.abs(d).max()
