@@ -68,6 +68,7 @@ template <int NMAX, int T>
 __device__ double pfaffian_smem(double* W, int n) {
   using P = Packed<NMAX>;
   double pf = 1.0;
+  unsigned odd = 0;                    // parity of the exchanges, applied to pf at the end
   for (int k = 0; k + 1 < n; k += 2) {
     const int r = k + 1;
     int p = r;
@@ -90,7 +91,7 @@ __device__ double pfaffian_smem(double* W, int n) {
         W[P::idx(r, x) * T] = W[P::idx(p, x) * T];
         W[P::idx(p, x) * T] = a;
       }
-      pf = neg(pf);
+      odd ^= 1u;
     }
     const double a = W[P::idx(k, r) * T];
     if (is_zero(a)) return 0.0;        // the whole column is zero: Pf = 0 exactly

@@ -21,8 +21,14 @@ __device__ __forceinline__ double sel(bool s, double y, double x) {        // s 
   const int hi = s ? __double2hiint(y) : __double2hiint(x);
   return __hiloint2double(hi, lo);
 }
+// The sign-bit XOR is written in inline PTX: as plain C++ the compiler recognises it as a
+// (conditional) floating-point negation and issues it on the FP64 pipe.
 __device__ __forceinline__ double flip_if(bool s, double x) {               // s ? -x : x
-  return __hiloint2double(__double2hiint(x) ^ (s ? (int)0x80000000 : 0), __double2loint(x));
+  const unsigned m = s ? 0x80000000u : 0u;
+  double r;
+  asm("{\n\t.reg .b32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\txor.b32 hi, hi, %2;\n\tmov.b64 %0, {lo, hi};\n\t}"
+      : "=d"(r) : "d"(x), "r"(m));
+  return r;
 }
 __device__ __forceinline__ double neg(double x) { return flip_if(true, x); }
 __device__ __forceinline__ bool is_zero(double x) { return abs_bits(x) == 0ull; }
@@ -90,7 +96,8 @@ struct ExchangeAll<N, K, N> {
 
 template <int N, int K>
 struct Eliminate {
-  static __device__ __forceinline__ void run(double (&W)[N][N], double& pf) {
+  // pf: product of the pivots; odd: parity of the exchanges (the sign is applied once at the end)
+  static __device__ __forceinline__ void run(double (&W)[N][N], double& pf, unsigned& odd) {
     constexpr int R = K + 1;
     // pivot: largest |W[K][x]|, x > K (integer comparison of the magnitudes' bit patterns)
     int p = R;
@@ -102,7 +109,7 @@ struct Eliminate {
     }
     ExchangeAll<N, K, R + 1>::run(p, W);
     const double a = W[K][R];
-    pf = flip_if(p != R, pf);
+    odd ^= (p != R) ? 1u : 0u;
     pf *= a;
     if (K + 2 < N) {
       const double ia = sel(is_zero(a), 0.0, recip_nr(a));   // a == 0: whole column zero, pf is already 0
@@ -116,20 +123,21 @@ struct Eliminate {
           W[i][j] = fma(W[R][i], W[K][j], fma(-W[K][i], W[R][j], W[i][j]));
         }
       }
-      Eliminate<N, K + 2>::run(W, pf);
+      Eliminate<N, K + 2>::run(W, pf, odd);
     }
   }
 };
 template <int N>
 struct Eliminate<N, N> {
-  static __device__ __forceinline__ void run(double (&)[N][N], double&) {}
+  static __device__ __forceinline__ void run(double (&)[N][N], double&, unsigned&) {}
 };
 
 template <int N>
 __device__ __forceinline__ double pfaffian_regs(double (&W)[N][N]) {
   double pf = 1.0;
-  Eliminate<N, 0>::run(W, pf);
-  return pf;
+  unsigned odd = 0;
+  Eliminate<N, 0>::run(W, pf, odd);
+  return flip_if(odd != 0, pf);
 }
 
 }  // namespace tgba

@@ -1,6 +1,6 @@
 """Writes dsf_L18.txt: the oracle's S(k=0, w) on the frequency grid of the L = 40 benchmark
 workload (4096 points in [0, 10], Lorentzian eta = 0.01) for the largest k = 0 basis its direct
-Pfaffians finish in minutes: L = 18, h_z = 1, h_x = 0.1, every state with M <= 6 (2420 states).
+Pfaffians finish in minutes: L = 18, h_z = 1, h_x = 0.1, every state with M <= 6 (2429 states).
 
 Calls only the oracle: X by direct Pfaffians of the whole operator string (Appendix A,
 Eq. S1-S2), H_eff (Eq. 2, S4), dense eigenpairs, the weights w_a = L |<psi_0|sigma^x_1|psi_a>|^2

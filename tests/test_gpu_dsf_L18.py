@@ -1,6 +1,6 @@
 """S(k=0, w) on the frequency grid of the L = 40 benchmark workload (4096 points in [0, 10],
 eta = 0.01; Eq. 8-9) against the oracle, on the largest k = 0 basis whose direct Pfaffians the
-oracle finishes in minutes: L = 18, h_z = 1, h_x = 0.1, all 2420 states with M <= 6.  The oracle's
+oracle finishes in minutes: L = 18, h_z = 1, h_x = 0.1, all 2429 states with M <= 6.  The oracle's
 values are stored by tests/golden/make_dsf_L18.py (X by direct Pfaffians of the whole operator
 string, dense eigenpairs, an FP64 Lorentzian sum).
 
