@@ -56,7 +56,7 @@ tgba_status scratch(Basis& b, int64_t doubles, double** out) {
 static void release(Basis* b) {
   void* ptrs[] = {b->d_E_ns, b->d_E_r, b->d_M_ns, b->d_M_r, b->d_sel_ns, b->d_sel_r, b->d_modes_ns, b->d_modes_r,
                   b->d_theta, b->d_nlab, b->d_table, b->d_c0, b->d_work, b->d_P, b->d_status,
-                  b->d_eig_a, b->d_eig_w, b->d_eig_work, b->d_eig_info, b->d_scratch, b->d_mask,
+                  b->d_eig_a, b->d_eig_w, b->d_eig_work, b->d_eig_info, b->d_scratch,
                   b->d_reg_rects, b->d_counter, b->d_blas_ws};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -193,7 +193,7 @@ static tgba_status compute_x_graph(Basis& b, cudaStream_t st) {
     r = build_table(b, cs);
     if (r == TGBA_OK) {
       cudaEventRecordWithFlags(b.ev[1], cs, cudaEventRecordExternal);
-      r = run_pfaffians(b, nullptr, cs);
+      r = run_pfaffians(b, cs);
       cudaEventRecordWithFlags(b.ev[2], cs, cudaEventRecordExternal);
     }
     cudaGraph_t g = nullptr;
@@ -228,24 +228,19 @@ static tgba_status compute_x(Basis& b, Screen* screen, double tau, double hx, cu
     if ((r = build_table(b, st)) != TGBA_OK) return r;
     b.c0_host_valid = false;
     TGBA_CUDA(cudaEventRecord(b.ev[1], st));
-    if (!b.d_mask) TGBA_CUDA(cudaMalloc(&b.d_mask, std::max<int64_t>(1, b.n_elements)));
-    for (size_t s = 0; s < b.sectors.size(); ++s)
-      if ((r = screen_score(*screen, b, (int)s, tau, hx, nullptr, b.d_mask + b.sectors[s].x_off, st)) != TGBA_OK)
-        return r;
-    if ((r = run_pfaffians(b, b.d_mask, st)) != TGBA_OK) return r;
+    int64_t kept = 0;
+    if ((r = screen_pfaffians(*screen, b, tau, hx, &kept, st)) != TGBA_OK) return r;
     TGBA_CUDA(cudaEventRecord(b.ev[2], st));
     b.ev_recorded = true;
+    b.x_evaluated = kept;
+    b.x_screened = b.n_elements - kept;
   }
   b.x_valid = true;
   b.x_screen = screen;
   b.x_tau = tau;
-  b.x_evaluated = b.n_elements;
-  b.x_screened = 0;
-  if (screen) {
-    int64_t kept = 0;
-    if ((r = count_mask(b, &kept, st)) != TGBA_OK) return r;
-    b.x_evaluated = kept;
-    b.x_screened = b.n_elements - kept;
+  if (!screen) {
+    b.x_evaluated = b.n_elements;
+    b.x_screened = 0;
   }
   return TGBA_OK;
 }
@@ -635,7 +630,7 @@ tgba_status tgba_screen_predict(tgba_screen s, tgba_basis h, int32_t sector, flo
   BASIS_OK(b);
   if (!s || !pred_dev) return fail(TGBA_EINVAL, "null argument");
   if (sector < 0 || sector >= (int)b->sectors.size()) return fail(TGBA_EINVAL, "sector index out of range");
-  return screen_score(*(Screen*)s, *b, sector, 1.0, 1.0, pred_dev, nullptr, (cudaStream_t)stream);
+  return screen_score(*(Screen*)s, *b, sector, pred_dev, (cudaStream_t)stream);
 }
 
 tgba_status tgba_screen_free(tgba_screen s) {

@@ -46,7 +46,6 @@ struct Args {
   const uint8_t* sel_ns;
   const uint8_t* sel_r;
   int max_qp;
-  const uint8_t* mask;
   double* P;
   unsigned* status;
   unsigned long long* counter;
@@ -139,7 +138,6 @@ __device__ __forceinline__ Elem locate(const Args& g, const Rect& rc, int64_t ti
 // one element of exact size N in registers
 template <int N>
 __device__ __forceinline__ void element_reg(const Args& g, const Elem& e, int ma) {
-  if (g.mask != nullptr && g.mask[e.out] == 0) { g.P[e.out] = 0.0; return; }
   if constexpr (N == 0) {
     g.P[e.out] = 1.0;
   } else {
@@ -196,6 +194,49 @@ __global__ void __launch_bounds__(T, MINB) pf_reg_queue(Args g) {
   }
 }
 
+// Pfaffians of the pairs the screener kept (sizes n <= NMAXR): list n / 2 holds counts[n / 2]
+// entries from list_off[n / 2]; a warp takes the next 32 entries of one size (largest n first)
+// from an atomic counter.  Screened pairs are not visited (their P stays 0).
+template <int NMAXR, int T, int MINB>
+__global__ void __launch_bounds__(T, MINB) pf_list_queue(Args g, const uint8_t* __restrict__ M_ns,
+                                                         const unsigned* __restrict__ counts,
+                                                         const int64_t* __restrict__ list_off,
+                                                         const PairEntry* __restrict__ lists) {
+  constexpr int NS = NMAXR / 2 + 1;
+  __shared__ int64_t first[NS + 1];               // first tile of size n = 2 (NS - 1 - i), i = 0..NS-1
+  __shared__ unsigned cnt[NS];
+  if (threadIdx.x == 0) {
+    int64_t acc = 0;
+    for (int i = 0; i < NS; ++i) {
+      const int h = NS - 1 - i;
+      cnt[h] = counts[h];
+      first[i] = acc;
+      acc += (cnt[h] + 31) / 32;
+    }
+    first[NS] = acc;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(g.counter, 1ull);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if ((int64_t)t >= first[NS]) return;
+    int i = 0;
+    while (i + 1 < NS && first[i + 1] <= (int64_t)t) ++i;
+    const int h = NS - 1 - i;
+    const int64_t idx = ((int64_t)t - first[i]) * 32 + lane;
+    if (idx >= (int64_t)cnt[h]) continue;
+    const PairEntry pe = lists[list_off[h] + idx];
+    Elem e;
+    e.out = pe.out;
+    e.sa = g.sel_ns + (size_t)pe.a * g.max_qp;
+    e.sb = g.sel_r + (size_t)pe.b * g.max_qp;
+    e.live = true;
+    dispatch_n<0, NMAXR>(2 * h, g, e, M_ns[pe.a]);
+  }
+}
+
 // Shared-memory variant for 16 <= n <= NMAX.
 template <int NMAX, int T>
 __global__ void __launch_bounds__(T) pf_smem(Args g) {
@@ -207,7 +248,6 @@ __global__ void __launch_bounds__(T) pf_smem(Args g) {
     const Rect rc = g.rects[find_rect(g.rects, g.n_rects, t)];
     const Elem e = locate(g, rc, t, lane);
     if (!e.live) continue;
-    if (g.mask != nullptr && g.mask[e.out] == 0) { g.P[e.out] = 0.0; continue; }
     const int n = rc.n, ma = rc.Ma;
     for (int i = 0; i < n - 1; ++i) {
       const int si = i < ma ? e.sa[i] : e.sb[i - ma];
@@ -381,7 +421,42 @@ tgba_status plan_pfaffians(Basis& b) {
   return TGBA_OK;
 }
 
-tgba_status run_pfaffians(Basis& b, const uint8_t* mask, cudaStream_t st) {
+tgba_status run_pfaffian_lists(Basis& b, const unsigned* counts, const int64_t* list_off, const PairEntry* lists,
+                               cudaStream_t st) {
+  if (b.max_reg_n < 0 || b.reg_rects_total == 0) return TGBA_OK;
+  int sms = 0;
+  TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
+  auto kern = b.max_reg_n <= 12 ? pf_list_queue<12, 128, 3> : pf_list_queue<14, 128, 2>;
+  TGBA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+  int per_sm = 0;
+  TGBA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0));
+  Args g;
+  g.rects = nullptr; g.n_rects = 0; g.n_tiles = 0;
+  g.R = b.d_table; g.two_l = 2 * b.L; g.sel_ns = b.d_sel_ns; g.sel_r = b.d_sel_r; g.max_qp = b.max_qp;
+  g.P = b.d_P; g.status = b.d_status; g.counter = b.d_counter;
+  TGBA_CUDA(cudaMemsetAsync(b.d_counter, 0, sizeof(unsigned long long), st));
+  kern<<<std::max(1, per_sm) * sms, 128, 0, st>>>(g, b.d_M_ns, counts, list_off, lists);
+  TGBA_CUDA(cudaGetLastError());
+  ++b.launches;
+  return TGBA_OK;
+}
+
+tgba_status run_pfaffians_smem_classes(Basis& b, cudaStream_t st) {
+  for (const PfLaunch& pl : b.pf_plan) {
+    if (pl.kind != 2) continue;
+    const RectList& L = b.rect_lists[pl.list];
+    Args g;
+    g.rects = L.d_rects; g.n_rects = L.n_rects; g.n_tiles = L.n_tiles;
+    g.R = b.d_table; g.two_l = 2 * b.L; g.sel_ns = b.d_sel_ns; g.sel_r = b.d_sel_r; g.max_qp = b.max_qp;
+    g.P = b.d_P; g.status = b.d_status; g.counter = b.d_counter;
+    kernel_of(pl.kind, pl.size, pl.threads)<<<pl.grid, pl.threads, pl.smem, st>>>(g);
+    TGBA_CUDA(cudaGetLastError());
+    ++b.launches;
+  }
+  return TGBA_OK;
+}
+
+tgba_status run_pfaffians(Basis& b, cudaStream_t st) {
   for (const PfLaunch& pl : b.pf_plan) {
     const RectList& L = b.rect_lists[pl.list];
     Args g;
@@ -390,7 +465,7 @@ tgba_status run_pfaffians(Basis& b, const uint8_t* mask, cudaStream_t st) {
     g.n_rects = queue ? b.reg_rects_total : L.n_rects;
     g.n_tiles = queue ? b.reg_tiles_total : L.n_tiles;
     g.R = b.d_table; g.two_l = 2 * b.L; g.sel_ns = b.d_sel_ns; g.sel_r = b.d_sel_r; g.max_qp = b.max_qp;
-    g.mask = mask; g.P = b.d_P; g.status = b.d_status; g.counter = b.d_counter;
+    g.P = b.d_P; g.status = b.d_status; g.counter = b.d_counter;
     if (queue) TGBA_CUDA(cudaMemsetAsync(b.d_counter, 0, sizeof(unsigned long long), st));
     kernel_of(pl.kind, pl.size, pl.threads)<<<pl.grid, pl.threads, pl.smem, st>>>(g);
     TGBA_CUDA(cudaGetLastError());
@@ -456,7 +531,7 @@ tgba_status autotune_pfaffians(Basis& b, cudaStream_t st) {
     float t = 1e30f;
     for (int rep = 0; rep < 2 && r == TGBA_OK; ++rep) {
       cudaEventRecord(e0, st);
-      if ((r = run_pfaffians(b, nullptr, st)) != TGBA_OK) break;
+      if ((r = run_pfaffians(b, st)) != TGBA_OK) break;
       cudaEventRecord(e1, st);
       cudaEventSynchronize(e1);
       float ms = 0;

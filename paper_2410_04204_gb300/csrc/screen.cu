@@ -11,8 +11,9 @@
 //
 // Training runs in FP32 on the CUDA cores (tiled SGEMM below).  Inference factors layer 1 into
 // per-state partials, h1(a, b) = relu(A_a + B_b) with A_a = W1[:, NS part] x_a and
-// B_b = W1[:, R part] x_b + b1, and runs layer 2 on the tensor cores (BF16 inputs, FP32
-// accumulation, mma.sync m16n8k16), fused with the ReLU, the dot with w3 and the threshold.
+// B_b = W1[:, R part] x_b + b1, and runs layer 2 on the tensor cores (tcgen05 MMAs, BF16
+// inputs, FP32 accumulation in tensor memory; screen_tc.cu), fused with the ReLU, the dot with
+// w3, the threshold and the compaction of the kept pairs into per-size work lists.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -250,104 +251,6 @@ __global__ void state_partials(int64_t n_states, bool ns, const int16_t* __restr
   }
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<uint32_t*>(&v);
-}
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// One warp scores 16 pairs (one NS state a, R states b0 .. b0+15 of a row of the sector).
-// Layer 2 on the tensor cores: A fragments of h1 = relu(A_a + B_b) (BF16), B fragments of W2
-// from shared memory; per 64-output group the accumulators go through relu(. + b2) . w3.
-// out: predicted log10|V| - log10(tau) + margin, i.e. >= 0 keeps the pair; with mask != NULL
-// the byte decision is written instead (1 = keep).
-template <int H>
-__global__ void __launch_bounds__(256) score_pairs(int64_t n_ns, int64_t n_r, const float* __restrict__ Apart,
-                                                   const float* __restrict__ Bpart,
-                                                   const __nv_bfloat16* __restrict__ W2b,
-                                                   const float* __restrict__ b2, const float* __restrict__ w3,
-                                                   const float* __restrict__ b3, const uint8_t* __restrict__ M_ns,
-                                                   const uint8_t* __restrict__ M_r, float shift, float half_log_l,
-                                                   float* __restrict__ pred, uint8_t* __restrict__ mask) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __nv_bfloat16* W2s = reinterpret_cast<__nv_bfloat16*>(smem_raw);          // [H][H + 8]
-  constexpr int LD = H + 8;
-  for (int e = threadIdx.x; e < H * H / 8; e += blockDim.x) {
-    const int o = (e * 8) / H, i = (e * 8) % H;
-    *reinterpret_cast<uint4*>(W2s + o * LD + i) = *reinterpret_cast<const uint4*>(W2b + o * H + i);
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
-  const int g = lane >> 2, tq = lane & 3;
-  const int64_t col_tiles = (n_r + 15) / 16;
-  const int64_t tiles = n_ns * col_tiles;
-  for (int64_t tile = (int64_t)blockIdx.x * warps + warp; tile < tiles; tile += (int64_t)gridDim.x * warps) {
-    const int64_t a = tile / col_tiles, bb0 = (tile - a * col_tiles) * 16;
-    const int64_t r0 = bb0 + g, r1 = bb0 + g + 8;
-    const float* Aa = Apart + a * H;
-    const float* B0 = Bpart + (r0 < n_r ? r0 : n_r - 1) * H;
-    const float* B1 = Bpart + (r1 < n_r ? r1 : n_r - 1) * H;
-    float part0 = 0.f, part1 = 0.f;     // partial w3 . relu(z2) of rows r0, r1
-    for (int n0 = 0; n0 < H; n0 += 64) {
-      float acc[8][4] = {};
-#pragma unroll 2
-      for (int k0 = 0; k0 < H; k0 += 16) {
-        const int c0 = k0 + 2 * tq, c1 = c0 + 8;
-        uint32_t af[4];
-        af[0] = pack_bf16(fmaxf(Aa[c0] + B0[c0], 0.f), fmaxf(Aa[c0 + 1] + B0[c0 + 1], 0.f));
-        af[1] = pack_bf16(fmaxf(Aa[c0] + B1[c0], 0.f), fmaxf(Aa[c0 + 1] + B1[c0 + 1], 0.f));
-        af[2] = pack_bf16(fmaxf(Aa[c1] + B0[c1], 0.f), fmaxf(Aa[c1 + 1] + B0[c1 + 1], 0.f));
-        af[3] = pack_bf16(fmaxf(Aa[c1] + B1[c1], 0.f), fmaxf(Aa[c1 + 1] + B1[c1 + 1], 0.f));
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const __nv_bfloat16* wrow = W2s + (n0 + 8 * j + g) * LD + k0 + 2 * tq;
-          const uint32_t bw0 = *reinterpret_cast<const uint32_t*>(wrow);
-          const uint32_t bw1 = *reinterpret_cast<const uint32_t*>(wrow + 8);
-          mma_bf16(acc[j], af, bw0, bw1);
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int c = n0 + 8 * j + 2 * tq;
-        part0 += fmaxf(acc[j][0] + b2[c], 0.f) * w3[c] + fmaxf(acc[j][1] + b2[c + 1], 0.f) * w3[c + 1];
-        part1 += fmaxf(acc[j][2] + b2[c], 0.f) * w3[c] + fmaxf(acc[j][3] + b2[c + 1], 0.f) * w3[c + 1];
-      }
-    }
-    part0 += __shfl_xor_sync(0xffffffffu, part0, 1);
-    part0 += __shfl_xor_sync(0xffffffffu, part0, 2);
-    part1 += __shfl_xor_sync(0xffffffffu, part1, 1);
-    part1 += __shfl_xor_sync(0xffffffffu, part1, 2);
-    if (tq == 0) {
-      const float y0 = part0 + b3[0], y1 = part1 + b3[0];
-      // states with more than Q quasiparticles are outside the model: always kept
-      if (r0 < n_r) {
-        const float v = y0 - half_log_l * (M_ns[a] + M_r[r0]) + shift;
-        if (pred) pred[a * n_r + r0] = y0;
-        if (mask) mask[a * n_r + r0] = (v >= 0.f || M_ns[a] > kQ || M_r[r0] > kQ) ? 1 : 0;
-      }
-      if (r1 < n_r) {
-        const float v = y1 - half_log_l * (M_ns[a] + M_r[r1]) + shift;
-        if (pred) pred[a * n_r + r1] = y1;
-        if (mask) mask[a * n_r + r1] = (v >= 0.f || M_ns[a] > kQ || M_r[r1] > kQ) ? 1 : 0;
-      }
-    }
-  }
-}
-
-__global__ void count_kept(int64_t n, const uint8_t* __restrict__ m, unsigned long long* out) {
-  unsigned long long c = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) c += m[i];
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(out, c);
-}
-
 int blocks(int64_t work, int t = 256) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((work + t - 1) / t, 152 * 16));
 }
@@ -363,21 +266,6 @@ uint64_t splitmix64(uint64_t x) {
 }  // namespace
 
 // ----------------------------------------------------------------------------- host side
-tgba_status count_mask(Basis& b, int64_t* kept, cudaStream_t st) {
-  unsigned long long* d = nullptr;
-  unsigned long long h = 0;
-  TGBA_CUDA(cudaMallocAsync(&d, sizeof(*d), st));
-  TGBA_CUDA(cudaMemsetAsync(d, 0, sizeof(*d), st));
-  count_kept<<<1024, 256, 0, st>>>(b.n_elements, b.d_mask, d);
-  TGBA_CUDA(cudaGetLastError());
-  TGBA_CUDA(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
-  TGBA_CUDA(cudaFreeAsync(d, st));
-  TGBA_CUDA(cudaStreamSynchronize(st));
-  ++b.launches;
-  *kept = (int64_t)h;
-  return TGBA_OK;
-}
-
 tgba_status screen_create(int H, const float* params, uint64_t seed, Screen** out) {
   Screen* s = new Screen();
   s->H = H;
@@ -503,10 +391,28 @@ static tgba_status refresh_bf16(Screen& s, cudaStream_t st) {
   return TGBA_OK;
 }
 
-// Scores of all pairs of sector `sec`: pred (float [n_ns][n_r], optional) receives y, mask
-// (optional) the keep decisions for |V| threshold tau at field hx.
-tgba_status screen_score(Screen& s, Basis& b, int sidx, double tau, double hx, float* pred, uint8_t* mask,
-                         cudaStream_t st) {
+// Layer-1 partials of every state of the basis (all sectors): part [n_ns_total + n_r_total][H],
+// NS states first.  The caller frees *part (stream-ordered).
+static tgba_status state_partials_all(Screen& s, Basis& b, float** part, cudaStream_t st) {
+  const int H = s.H;
+  const int64_t n_ns = (int64_t)b.ns.E.size(), n_r = (int64_t)b.r.E.size();
+  TGBA_CUDA(cudaMallocAsync(part, (size_t)std::max<int64_t>(1, n_ns + n_r) * H * 4, st));
+  const float* W1 = s.theta;
+  const float* b1 = W1 + (int64_t)H * kD;
+  if (n_ns > 0)
+    state_partials<<<blocks(n_ns * H), 256, 0, st>>>(n_ns, true, b.d_modes_ns, b.d_M_ns, b.max_qp, b.d_nlab, b.L, H, W1,
+                                                    b1, *part);
+  if (n_r > 0)
+    state_partials<<<blocks(n_r * H), 256, 0, st>>>(n_r, false, b.d_modes_r, b.d_M_r, b.max_qp, b.d_nlab, b.L, H, W1,
+                                                   b1, *part + n_ns * H);
+  TGBA_CUDA(cudaGetLastError());
+  b.launches += 2;
+  return TGBA_OK;
+}
+
+// Predicted y of every pair of sector `sidx`: pred float [n_ns][n_r].  Pairs outside the
+// model (a state with more than Q quasiparticles) get 0.
+tgba_status screen_score(Screen& s, Basis& b, int sidx, float* pred, cudaStream_t st) {
   if (s.H != 256) return fail(TGBA_EINVAL, "inference supports width 256");
   const Sector& sec = b.sectors[sidx];
   if (sec.n_ns == 0 || sec.n_r == 0) return TGBA_OK;
@@ -514,35 +420,67 @@ tgba_status screen_score(Screen& s, Basis& b, int sidx, double tau, double hx, f
     tgba_status r = refresh_bf16(s, st);
     if (r != TGBA_OK) return r;
   }
-  const int H = s.H;
+  std::vector<Rect> rects;
+  for (const RectList& L : b.rect_lists)
+    for (const Rect& rc : L.rects)
+      if (rc.ns0 >= sec.ns_off && rc.ns0 < sec.ns_off + sec.n_ns) rects.push_back(rc);
   float* part = nullptr;
-  TGBA_CUDA(cudaMallocAsync(&part, (size_t)(sec.n_ns + sec.n_r) * H * 4, st));
-  const float* W1 = s.theta;
-  const float* b1 = W1 + (int64_t)H * kD;
-  const float* b2 = b1 + H + (int64_t)H * H;
-  const float* w3 = b2 + H;
-  const float* b3 = w3 + H;
-  state_partials<<<blocks(sec.n_ns * H), 256, 0, st>>>(sec.n_ns, true, b.d_modes_ns + sec.ns_off * b.max_qp,
-                                                      b.d_M_ns + sec.ns_off, b.max_qp, b.d_nlab, b.L, H, W1, b1, part);
-  state_partials<<<blocks(sec.n_r * H), 256, 0, st>>>(sec.n_r, false, b.d_modes_r + sec.r_off * b.max_qp,
-                                                     b.d_M_r + sec.r_off, b.max_qp, b.d_nlab, b.L, H, W1, b1,
-                                                     part + sec.n_ns * H);
+  tgba_status r = state_partials_all(s, b, &part, st);
+  if (r != TGBA_OK) return r;
+  const int H = s.H;
+  const float* b2 = s.theta + (int64_t)H * kD + H + (int64_t)H * H;
+  TGBA_CUDA(cudaMemsetAsync(pred, 0, (size_t)sec.n_ns * sec.n_r * 4, st));
+  r = score_rects_tc(b, rects, part, part + (int64_t)b.ns.E.size() * H, s.W2b, b2, b2 + H, b2 + 2 * H, 0.f, 0.f,
+                     pred, sec.x_off, nullptr, nullptr, nullptr, st);
+  cudaFreeAsync(part, st);
+  return r;
+}
+
+// The screened Pfaffian stage (after the contraction table): P = 0, the register-size pairs
+// scored and the kept ones compacted into per-size lists, their Pfaffians from the lists, and
+// the shared-memory sizes (n >= 16) without screening.  *kept: pairs evaluated by Pfaffian.
+tgba_status screen_pfaffians(Screen& s, Basis& b, double tau, double hx, int64_t* kept, cudaStream_t st) {
+  if (s.H != 256) return fail(TGBA_EINVAL, "inference supports width 256");
+  if (!s.w2b_valid) {
+    tgba_status r = refresh_bf16(s, st);
+    if (r != TGBA_OK) return r;
+  }
+  const int H = s.H;
+  constexpr int kSizes = 8;                                     // n = 0, 2, ..., 14
+  std::vector<int64_t> off(kSizes + 1, 0);
+  for (const Rect& rc : b.reg_rects) off[rc.n / 2 + 1] += (int64_t)rc.rows * rc.w;
+  for (int i = 0; i < kSizes; ++i) off[i + 1] += off[i];
+  TGBA_CUDA(cudaMemsetAsync(b.d_P, 0, (size_t)std::max<int64_t>(1, b.n_elements) * sizeof(double), st));
+  void* lb = nullptr;
+  const size_t list_bytes = (size_t)std::max<int64_t>(1, off[kSizes]) * sizeof(PairEntry);
+  TGBA_CUDA(cudaMallocAsync(&lb, list_bytes + 64 * sizeof(int64_t), st));
+  PairEntry* lists = (PairEntry*)lb;
+  int64_t* d_off = (int64_t*)((char*)lb + list_bytes);
+  unsigned* d_cnt = (unsigned*)(d_off + 16);
+  TGBA_CUDA(cudaMemcpyAsync(d_off, off.data(), kSizes * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  TGBA_CUDA(cudaMemsetAsync(d_cnt, 0, kSizes * sizeof(unsigned), st));
+  float* part = nullptr;
+  tgba_status r = state_partials_all(s, b, &part, st);
+  if (r != TGBA_OK) { cudaFreeAsync(lb, st); return r; }
+  const float* b2 = s.theta + (int64_t)H * kD + H + (int64_t)H * H;
   // keep iff y - (n/2) log10(L/24) + log10(L hx) >= log10(tau) - margin
   const float half_log_l = (float)(0.5 * std::log10(b.L / 24.0));
   const float shift = (float)(std::log10(b.L * std::fabs(hx)) - std::log10(tau) + s.margin);
-  const size_t smem = (size_t)H * (H + 8) * 2;
-  auto kern = score_pairs<256>;
-  TGBA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0, sms = 0;
-  TGBA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));
-  TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
-  const int64_t tiles = sec.n_ns * ((sec.n_r + 15) / 16);
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((tiles + 7) / 8, (int64_t)std::max(1, per_sm) * sms));
-  kern<<<grid, 256, smem, st>>>(sec.n_ns, sec.n_r, part, part + sec.n_ns * H, s.W2b, b2, w3, b3, b.d_M_ns + sec.ns_off,
-                                b.d_M_r + sec.r_off, shift, half_log_l, pred, mask);
-  TGBA_CUDA(cudaGetLastError());
-  b.launches += 3;
+  r = score_rects_tc(b, b.reg_rects, part, part + (int64_t)b.ns.E.size() * H, s.W2b, b2, b2 + H, b2 + 2 * H, shift,
+                     half_log_l, nullptr, 0, d_cnt, d_off, lists, st);
+  if (r == TGBA_OK) r = run_pfaffian_lists(b, d_cnt, d_off, lists, st);
+  if (r == TGBA_OK) r = run_pfaffians_smem_classes(b, st);
+  unsigned hc[kSizes] = {};
+  if (r == TGBA_OK) {
+    TGBA_CUDA(cudaMemcpyAsync(hc, d_cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  }
   cudaFreeAsync(part, st);
+  cudaFreeAsync(lb, st);
+  if (r != TGBA_OK) return r;
+  TGBA_CUDA(cudaStreamSynchronize(st));
+  int64_t k = b.n_elements - off[kSizes];                       // sizes n >= 16: all evaluated
+  for (int i = 0; i < kSizes; ++i) k += hc[i];
+  *kept = k;
   return TGBA_OK;
 }
 

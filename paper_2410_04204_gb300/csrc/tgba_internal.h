@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libtgba.so.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -122,7 +123,6 @@ struct Basis {
   bool table_valid = false;
   // Pfaffian stage
   double* d_P = nullptr;           // X_ab = C0 (-i)^{(M_a+M_b)/2} P_ab, P real, [n_elements]
-  uint8_t* d_mask = nullptr;       // screening decisions (1 = Pfaffian evaluated), [n_elements]
   bool x_valid = false;
   const void* x_screen = nullptr;
   double x_tau = 0;
@@ -179,7 +179,7 @@ tgba_status build_table(Basis& b, cudaStream_t st);
 // pfaffian.cu
 tgba_status plan_pfaffians(Basis& b);
 tgba_status autotune_pfaffians(Basis& b, cudaStream_t st);
-tgba_status run_pfaffians(Basis& b, const uint8_t* d_mask, cudaStream_t st);
+tgba_status run_pfaffians(Basis& b, cudaStream_t st);
 tgba_status run_pfaffian_pairs(Basis& b, int s, const int32_t* pairs, int64_t n, double* out, cudaStream_t st);
 // direct.cu: X of explicit pairs by the paper-literal Pfaffian of size 2L + M_a + M_b
 size_t x_direct_smem(int L, int max_qp, int jmid);
@@ -252,6 +252,24 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
                               const double* c, const std::vector<ChebVariant>& vars, double t_max, int n_t,
                               double* mx, cudaStream_t st);
 
+// A pair kept by the screener: X element index and the global NS and R state indices.
+struct PairEntry {
+  int64_t out;
+  int32_t a, b;
+};
+// screen_tc.cu: tensor-core scoring of the pairs of `rects` (see the file); pred (optional) gets
+// y at (element index - pred_base); counts/list_off/lists (optional) receive the kept pairs per
+// size n / 2.  Apart/Bpart: layer-1 partials of every NS / R state of the basis (global index).
+tgba_status score_rects_tc(Basis& b, const std::vector<Rect>& rects, const float* Apart, const float* Bpart,
+                           const __nv_bfloat16* W2b, const float* b2, const float* w3, const float* b3, float shift,
+                           float half_log_l, float* pred, int64_t pred_base, unsigned* counts,
+                           const int64_t* list_off, PairEntry* lists, cudaStream_t st);
+// pfaffian.cu: Pfaffians of the kept pairs (sizes n <= 14, lists per n / 2), and the launches of
+// the shared-memory size classes (n >= 16) without screening
+tgba_status run_pfaffian_lists(Basis& b, const unsigned* counts, const int64_t* list_off, const PairEntry* lists,
+                               cudaStream_t st);
+tgba_status run_pfaffians_smem_classes(Basis& b, cudaStream_t st);
+
 // screen.cu
 struct Screen;
 tgba_status screen_create(int H, const float* params, uint64_t seed, Screen** out);
@@ -261,9 +279,8 @@ tgba_status screen_params(Screen& s, float* host);
 tgba_status screen_grad(Screen& s, const float* x, const float* t, int64_t B, float* grad, double* loss, cudaStream_t st);
 tgba_status screen_train(Basis** sets, int n_sets, int64_t n_samples, uint64_t seed, int H, int epochs, Screen** out,
                          double* stats, cudaStream_t st);
-tgba_status screen_score(Screen& s, Basis& b, int sidx, double tau, double hx, float* pred, uint8_t* mask,
-                         cudaStream_t st);
-tgba_status count_mask(Basis& b, int64_t* kept, cudaStream_t st);   // number of 1 bytes in d_mask
+tgba_status screen_score(Screen& s, Basis& b, int sidx, float* pred, cudaStream_t st);
+tgba_status screen_pfaffians(Screen& s, Basis& b, double tau, double hx, int64_t* kept, cudaStream_t st);
 
 // status word
 tgba_status check_status(Basis& b, cudaStream_t st);

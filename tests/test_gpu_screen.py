@@ -104,3 +104,42 @@ def test_train_and_screen_small():
                 tgba.tgba_basis_free(b)
     finally:
         tgba.tgba_screen_free(s)
+
+
+def test_screened_stage_keeps_exactly_the_predicted_pairs():
+    """The tensor-core scoring compacts the kept pairs into per-size lists: every pair whose
+    prediction passes the threshold gets the exact Pfaffian (bit for bit the unscreened value),
+    every other pair 0, and the counts of tgba_x_stats agree.  Random weights with a bias that
+    drops about half of the pairs; pairs within 1e-4 of the threshold are not judged (the two
+    sides may round the comparison differently)."""
+    L, mq, hx, tau = 16, 6, 0.1, 1e-8
+    theta = mlp.init(H, 7).astype(np.float32)
+    s = tgba.tgba_screen_create(H, theta)
+    b = tgba.tgba_build_basis(L, 1.0, [0], mq)
+    try:
+        g = GpuSector(b, 0, mq)
+        pred = torch.empty(g.n_ns * g.n_r, dtype=torch.float32, device="cuda")
+        tgba.tgba_screen_predict(s, b, 0, pred)
+        y = pred.cpu().numpy().reshape(g.n_ns, g.n_r).astype(np.float64)
+        n = g.nqp[:g.n_ns, None].astype(np.float64) + g.nqp[None, g.n_ns:]
+        margin = 1.0                                       # a created (untrained) screener's margin
+        v = y - 0.5 * math.log10(L / 24.0) * n + (math.log10(L * hx) - math.log10(tau) + margin)
+        med = float(np.median(v))
+        theta[-1] -= med                                   # shift b3 so that about half is dropped
+        tgba.tgba_screen_free(s)
+        s = tgba.tgba_screen_create(H, theta)
+        v = v - med
+        tgba.tgba_compute_x(b)
+        exact = g.x()
+        tgba.tgba_compute_x(b, s, tau, hx)
+        scr = g.x()
+        n_eval, n_scr = tgba.tgba_x_stats(b)
+        keep, drop = v >= 1e-4, v <= -1e-4
+        assert drop.sum() > 0.2 * v.size and keep.sum() > 0.2 * v.size
+        assert np.array_equal(scr[keep], exact[keep])
+        assert np.all(scr[drop] == 0)
+        assert n_eval + n_scr == v.size
+        assert keep.sum() <= n_eval <= v.size - drop.sum()
+    finally:
+        tgba.tgba_basis_free(b)
+        tgba.tgba_screen_free(s)
