@@ -339,6 +339,20 @@ typedef struct {
 } tgba_prof;
 tgba_status tgba_profile(tgba_basis b, tgba_prof* out);
 
+/* ---------------------------------------------------------------- FP64 products on the tensor cores
+ * Not in the paper: the FP64 matrix products of the batched quench propagation run through
+ * this routine, exposed for direct use and testing.  C = A B^T with A [M][K] (row i at A + i lda,
+ * K contiguous), B [N][K] (row j at B + j ldb), C column-major M x N (entry (i, j) at
+ * C + i + j ldc); all device pointers, FP64.  Each operand row is scaled by a power of two and cut
+ * into seven signed 7-bit digits held exactly in BF16; the tensor cores (tcgen05 MMAs, FP32
+ * accumulation in tensor memory) sum the digit products, exactly for the three leading digit
+ * diagonals over chunks of 256 K values, and the chunks are added into a 48-bit running sum
+ * (a pair of FP32 numbers).  The error is about 1e-14 of sum_k |A_ik B_jk|.  M, N, K >= 1
+ * (TGBA_EINVAL otherwise); the slice buffers (14 bytes per input element) are allocated for the
+ * call (TGBA_ENOMEM).  Blocks on `stream`. */
+tgba_status tgba_dgemm_tc(int32_t M, int32_t N, int32_t K, const double* A, int64_t lda, const double* B, int64_t ldb,
+                          double* C, int64_t ldc, void* stream);
+
 /* ---------------------------------------------------------------- measurement helper
  * Achieved FP64 rate of a DFMA-chain kernel on the current device (GFLOP/s, best of `reps`),
  * the denominator for FP64 roofline fractions. */

@@ -1,0 +1,460 @@
+// FP64 matrix products on the fifth-generation tensor cores, by splitting the FP64 operands
+// into BF16 slices (fixed-point digits) whose products the tensor cores sum exactly in FP32.
+//
+// GB300 runs FP64 at about 1.25 TFLOP/s on its CUDA cores but BF16 MMAs at about 2 PFLOP/s.
+// C = A B^T (A: M x K, B: N x K, both with K contiguous in their slices) is computed as follows.
+//  * Slicing.  Row i of A gets an exponent e_i with max_k |A_ik| <= 2^e_i; r = A_ik 2^-e_i is
+//    cut into S = 7 signed base-128 digits, d_0 = rint(128 r), r <- 128 r - d_0, d_1 = rint(128 r),
+//    ... (|d_0| <= 128, |d_p| <= 64 after it; every step exact in FP64), and slice p stores
+//    d_p 2^{-7p} in BF16 (exact: at most 8 significant bits).  So A_ik = 2^{e_i - 7} sum_p
+//    slice_p + O(2^{e_i - 50}).  B's rows (the columns of C) are cut the same way.
+//  * Products.  C_ij = 2^{e_i + f_j - 14} sum_{p + q <= 6} (A_p B_q^T)_ij.  The products of
+//    digit diagonal d = p + q carry the scale 2^{-7d}; over a chunk of 256 K values each of
+//    the sums of diagonals 0, 1 and 2 stays below 2^24 units of its scale, so FP32
+//    accumulation of those diagonals is exact, and they get one TMEM accumulator each.
+//    Diagonals 3..6 share a fourth accumulator; their FP32 rounding is below 2^-45 of the
+//    leading term.
+//  * Chunks.  After every 256 K values the four accumulators are folded into a running sum per
+//    element kept as an unevaluated pair of FP32 numbers (hi + lo, error-free two-sum: about
+//    48 bits), by CUDA-core FP32 arithmetic, while the tensor cores fill the second set of
+//    accumulators (two sets of 4 x 64 columns = all 512 TMEM columns).  At the end of the tile
+//    C_ij = 2^{e_i + f_j - 14} (hi + lo) in FP64.
+//  The relative error of C is that of FP64 accumulation with a 48-bit running sum: a few 1e-14.
+//
+// Tiles: 128 rows of A x up to 64 rows of B (n_eff, a multiple of 16, per tile) x K in blocks of
+// 32 (64-byte rows, 64-byte swizzle).  The slices of one (row block, K block) are stored
+// contiguously, already in the shared-memory image the MMA descriptors read, so each stage is
+// two bulk copies (cp.async.bulk: 56 KB of A slices, 28 KB of B slices) completing on an
+// mbarrier.  Warp 0 issues the copies, warp 1 the MMAs (one thread each), warps 2-5 fold the
+// accumulators and write C.  Two smem stages, two accumulator sets.  Every wait is bounded: on
+// timeout the kernel records TGBA_ETIMEOUT's status bit, every role leaves, in-flight copies and
+// MMAs are waited for (bounded) and the tensor memory is freed.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "tgba_internal.h"
+
+namespace tgba {
+namespace {
+
+constexpr int kS = 7;                     // slices per operand
+constexpr int kKB = 32;                   // K per block (64-byte rows)
+constexpr int kTMr = 128;                 // rows of A per tile
+constexpr int kTNr = 64;                  // rows of B per tile
+constexpr int kChunkBlocks = 8;           // K blocks per exact FP32 chunk (256 K values)
+constexpr uint32_t kASlice = kTMr * kKB * 2;          // 8 KB
+constexpr uint32_t kBSlice = kTNr * kKB * 2;          // 4 KB
+constexpr uint32_t kAStage = kS * kASlice;            // 56 KB
+constexpr uint32_t kBStage = kS * kBSlice;            // 28 KB
+constexpr int kStages = 2;
+constexpr uint32_t kSmem = 1024 + kStages * (kAStage + kBStage) + 256;
+constexpr unsigned kWait = 1u << 24;                   // polls of a bounded wait
+constexpr int kThreads = 192;
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of element (r, k) in a tile slice: 64-byte rows, 16-byte chunks XOR (r / 2) mod 4
+__host__ __device__ __forceinline__ uint32_t sw64(int r, int k) {
+  return (uint32_t)(r * 64 + ((((k >> 3) ^ (r >> 1)) & 3) << 4) + (k & 7) * 2);
+}
+
+// Descriptor: start >> 4, LBO 1 (unused for swizzled K-major), SBO 512 B (8-row groups),
+// version 1, swizzle mode 4 = 64 B.
+__device__ __forceinline__ uint64_t desc64(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) |
+         ((uint64_t)4 << 61);
+}
+
+__device__ __forceinline__ uint32_t idesc_f16(int n) {        // D f32, A/B bf16, K-major, M = 128
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTMr >> 4) << 24);
+}
+
+__device__ __forceinline__ void bar_init(uint64_t* b, unsigned n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ bool bar_try(uint64_t* b, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; also gives up when another role has aborted
+__device__ __forceinline__ bool bar_wait(uint64_t* b, unsigned parity, volatile int* abort_flag) {
+  for (unsigned it = 0; it < kWait; ++it) {
+    if (bar_try(b, parity)) return true;
+    if ((it & 255u) == 255u && *abort_flag) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void bar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   su32(dst)),
+               "l"(src), "r"(bytes), "r"(su32(b))
+               : "memory");
+}
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void commit(uint64_t* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// hi + lo += x, error-free (Knuth's two-sum on hi, the error collected in lo)
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (x - bb);
+  hi = s;
+  lo += err;
+}
+
+struct GemmArgs {
+  const EmuTile* tiles;
+  int n_tiles;
+  const __nv_bfloat16* A;     // [row block][K block][slice] tile images
+  const __nv_bfloat16* B;
+  int a_kb, b_kb;             // K blocks per row block of A / of B (the stride between row blocks)
+  const int* ea;              // row exponents of A [M]
+  const int* eb;              // row exponents of B [N]
+  int M, N;
+  double* C;                  // C[i + j ldc]
+  int64_t ldc;
+  unsigned* status;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) dgemm_tc_kernel(GemmArgs g) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = su32(smem_raw);
+  unsigned char* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  unsigned char* sA = base;                                  // [stage] A slices
+  unsigned char* sB = base + kStages * kAStage;              // [stage] B slices
+  uint64_t* bars = (uint64_t*)(sB + kStages * kBStage);
+  uint64_t* full = bars;               // [2] stage loaded
+  uint64_t* empty = bars + 2;          // [2] stage consumed by the MMAs
+  uint64_t* accf = bars + 4;           // [2] accumulator set written
+  uint64_t* acce = bars + 6;           // [2] accumulator set read
+  uint32_t* tslot = (uint32_t*)(bars + 8);
+  __shared__ volatile int s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2; ++s) {
+      bar_init(full + s, 1);
+      bar_init(empty + s, 1);
+      bar_init(accf + s, 1);
+      bar_init(acce + s, 4);
+    }
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(su32(tslot)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int t = blockIdx.x; t < g.n_tiles && !s_abort; t += gridDim.x) {
+        const EmuTile tl = g.tiles[t];
+        for (int kb = 0; kb < tl.nkb; ++kb, ++it) {
+          const int st = it & 1;
+          if (!bar_wait(empty + st, ((it >> 1) & 1u) ^ 1u, &s_abort)) { atomicOr(g.status, kStTimeout); s_abort = 1; break; }
+          bar_expect(full + st, kAStage + kBStage);
+          bulk_load(sA + st * kAStage, g.A + ((size_t)tl.rb * g.a_kb + kb) * (kAStage / 2), kAStage, full + st);
+          bulk_load(sB + st * kBStage, g.B + ((size_t)tl.cb * g.b_kb + kb) * (kBStage / 2), kBStage, full + st);
+        }
+      }
+      if (s_abort) {                                  // copies still in flight land before the CTA leaves
+        const volatile int never = 0;
+        for (uint32_t j = (it >= 2 ? it - 2 : 0); j < it; ++j) bar_wait(full + (j & 1), (j >> 1) & 1u, (volatile int*)&never);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t it = 0, chunk = 0;
+      uint64_t* last = nullptr;
+      for (int t = blockIdx.x; t < g.n_tiles && !s_abort; t += gridDim.x) {
+        const EmuTile tl = g.tiles[t];
+        const uint32_t id = idesc_f16(tl.n_eff);
+        for (int kb0 = 0; kb0 < tl.nkb && !s_abort; kb0 += kChunkBlocks, ++chunk) {
+          const int set = chunk & 1;
+          if (!bar_wait(acce + set, ((chunk >> 1) & 1u) ^ 1u, &s_abort)) { atomicOr(g.status, kStTimeout); s_abort = 1; break; }
+          fence_after();
+          const uint32_t dbase = tmem + (uint32_t)set * 256u;
+          const int kb1 = min(tl.nkb, kb0 + kChunkBlocks);
+          for (int kb = kb0; kb < kb1; ++kb, ++it) {
+            const int st = it & 1;
+            if (!bar_wait(full + st, (it >> 1) & 1u, &s_abort)) { atomicOr(g.status, kStTimeout); s_abort = 1; break; }
+            fence_after();
+            const uint32_t a0 = su32(sA + st * kAStage), b0 = su32(sB + st * kBStage);
+#pragma unroll 1
+            for (int p = 0; p < kS; ++p)
+#pragma unroll 1
+              for (int q = 0; p + q < kS; ++q) {
+                const int d = min(p + q, 3);
+                // first write of accumulator d in this chunk overwrites it: pair (0, d) for d <= 2,
+                // (0, 3) for the shared one, at the chunk's first K block
+                const bool first = kb == kb0 && p == 0 && q == (d < 3 ? d : 3);
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks)
+                  mma(dbase + (uint32_t)d * 64u, desc64(a0 + p * kASlice + ks * 32), desc64(b0 + q * kBSlice + ks * 32), id,
+                      (first && ks == 0) ? 0u : 1u);
+              }
+            commit(empty + st);                       // the stage's smem is free once these complete
+            last = empty + st;
+          }
+          commit(accf + set);                         // the chunk's accumulators are complete
+          last = accf + set;
+        }
+      }
+      if (s_abort && last) {                          // MMAs still in flight finish before the dealloc
+        const volatile int never = 0;
+        bar_wait(last, 0u, (volatile int*)&never);
+        bar_wait(last, 1u, (volatile int*)&never);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------------ epilogue (warps 2-5)
+    const int quad = warp & 3;                        // TMEM lanes 32 quad .. 32 quad + 31
+    const int r = quad * 32 + lane;                   // row of the tile
+    uint32_t chunk = 0;
+    for (int t = blockIdx.x; t < g.n_tiles && !s_abort; t += gridDim.x) {
+      const EmuTile tl = g.tiles[t];
+      float hi[kTNr], lo[kTNr];
+#pragma unroll
+      for (int c = 0; c < kTNr; ++c) { hi[c] = 0.f; lo[c] = 0.f; }
+      for (int kb0 = 0; kb0 < tl.nkb; kb0 += kChunkBlocks, ++chunk) {
+        const int set = chunk & 1;
+        if (!bar_wait(accf + set, (chunk >> 1) & 1u, &s_abort)) {
+          if (lane == 0) atomicOr(g.status, kStTimeout);
+          s_abort = 1;
+          break;
+        }
+        fence_after();
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)set * 256u;
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float v[32];
+            ld32(lane_base + (uint32_t)d * 64u + (uint32_t)h * 32u, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) two_sum_add(hi[h * 32 + j], lo[h * 32 + j], v[j]);
+          }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) bar_arrive(acce + set);
+      }
+      if (s_abort) break;
+      const int i = tl.rb * kTMr + r;
+      if (i < g.M) {
+        const int e_i = g.ea[i];
+#pragma unroll 4
+        for (int c = 0; c < kTNr; ++c) {
+          const int j = tl.cb * kTNr + c;
+          if (c < tl.n_eff && j < g.N) {
+            const double v = ((double)hi[c] + (double)lo[c]);
+            g.C[(int64_t)i + (int64_t)j * g.ldc] = ldexp(v, e_i + g.eb[j] - 14);
+          }
+        }
+      }
+    }
+  }
+  // teardown: everything issued has completed or been abandoned after a bounded wait
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+// Row exponents: e[i] = smallest e with max_k |X(i, k)| <= 2^e (0 for a zero row).  One warp per row.
+__global__ void row_exponents(int rows, int K, const double* __restrict__ src, int64_t row_stride, int64_t k_stride,
+                              int k_split, int64_t k_jump, const double* __restrict__ w, double w_shift,
+                              int* __restrict__ e) {
+  const int lane = threadIdx.x & 31;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < rows; i += (gridDim.x * blockDim.x) >> 5) {
+    double m = 0.0;
+    for (int k = lane; k < K; k += 32) {
+      const int64_t off = (int64_t)i * row_stride + (int64_t)k * k_stride + (k >= k_split ? k_jump : 0);
+      double x = src[off];
+      if (w) x *= w[k] - w_shift;
+      m = fmax(m, fabs(x));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) {
+      int ex = 0;
+      if (m > 0.0) {
+        frexp(m, &ex);                 // m = f 2^ex, f in [0.5, 1): m < 2^ex
+      }
+      e[i] = ex;
+    }
+  }
+}
+
+// Slices of X (rows x K, element (i, k) at src[i row_stride + k k_stride (+ k_jump for k >= k_split)],
+// optionally times w[k]) as tile images [row block][K block][slice][tile rows][32] (bf16, 64-byte
+// swizzle); rows and K beyond the matrix are zero.
+__global__ void slice_tiles(int rows, int K, const double* __restrict__ src, int64_t row_stride, int64_t k_stride,
+                            int k_split, int64_t k_jump, const double* __restrict__ w, double w_shift,
+                            const int* __restrict__ e, int tile_rows, int n_kb, __nv_bfloat16* __restrict__ out) {
+  const int n_rb = (rows + tile_rows - 1) / tile_rows;
+  const int64_t total = (int64_t)n_rb * tile_rows * n_kb * kKB;
+  const uint32_t slice_bytes = (uint32_t)tile_rows * kKB * 2;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(q % ((int64_t)n_kb * kKB));
+    const int i = (int)(q / ((int64_t)n_kb * kKB));
+    const int rb = i / tile_rows, r = i % tile_rows, kb = k / kKB, kk = k % kKB;
+    double x = 0.0;
+    if (i < rows && k < K) {
+      const int64_t off = (int64_t)i * row_stride + (int64_t)k * k_stride + (k >= k_split ? k_jump : 0);
+      x = src[off];
+      if (w) x *= w[k] - w_shift;
+    }
+    unsigned char* tile = (unsigned char*)out + ((size_t)rb * n_kb + kb) * kS * slice_bytes;
+    const uint32_t o = sw64(r, kk);
+    double rr = (i < rows) ? ldexp(x, -e[i]) : 0.0;   // in [-1, 1]
+    double scale = 1.0;
+#pragma unroll
+    for (int p = 0; p < kS; ++p) {
+      const double y = rr * 128.0;
+      const double d = rint(y);
+      rr = y - d;
+      *(__nv_bfloat16*)(tile + (size_t)p * slice_bytes + o) = __double2bfloat16(d * scale);
+      scale *= 0.0078125;                           // 2^-7
+    }
+  }
+}
+
+}  // namespace
+
+size_t emu_operand_elems(int rows, int K, int tile_rows) {
+  const int n_rb = (rows + tile_rows - 1) / tile_rows, n_kb = (K + kKB - 1) / kKB;
+  return (size_t)n_rb * n_kb * kS * tile_rows * kKB;
+}
+
+// Slices of a matrix X (rows x K) for dgemm_tc: element (i, k) at src[i row_stride + k k_stride],
+// k >= k_split shifted by k_jump more (two K ranges of one buffer); if w != nullptr, times
+// (w[k] - w_shift).  out: bf16 [emu_operand_elems], e: int [rows].  tile_rows: 128 for A, 64 for B.
+tgba_status emu_slice(Basis& b, const double* src, int64_t row_stride, int64_t k_stride, int k_split, int64_t k_jump,
+                      const double* w, double w_shift, int rows, int K, int tile_rows, __nv_bfloat16* out, int* e,
+                      cudaStream_t st) {
+  if (rows <= 0 || K <= 0) return TGBA_OK;
+  const int n_kb = (K + kKB - 1) / kKB;
+  row_exponents<<<(int)std::min<int64_t>(((int64_t)rows * 32 + 255) / 256, 152 * 16), 256, 0, st>>>(
+      rows, K, src, row_stride, k_stride, k_split, k_jump, w, w_shift, e);
+  ++b.launches;
+  const int n_rb = (rows + tile_rows - 1) / tile_rows;
+  const int64_t total = (int64_t)n_rb * tile_rows * n_kb * kKB;
+  slice_tiles<<<(int)std::min<int64_t>((total + 255) / 256, 152 * 64), 256, 0, st>>>(
+      rows, K, src, row_stride, k_stride, k_split, k_jump, w, w_shift, e, tile_rows, n_kb, out);
+  TGBA_CUDA(cudaGetLastError());
+  ++b.launches;
+  return TGBA_OK;
+}
+
+// C = A B^T for sliced operands (see emu_slice), over the given output tiles.
+tgba_status emu_gemm(Basis& b, const __nv_bfloat16* A, const int* ea, int M, int Ka, const __nv_bfloat16* B,
+                     const int* eb, int N, int Kb, const EmuTile* d_tiles, int n_tiles, double* C, int64_t ldc,
+                     cudaStream_t st) {
+  if (n_tiles == 0) return TGBA_OK;
+  GemmArgs g;
+  g.tiles = d_tiles; g.n_tiles = n_tiles;
+  g.A = A; g.B = B;
+  g.a_kb = (Ka + kKB - 1) / kKB;
+  g.b_kb = (Kb + kKB - 1) / kKB;
+  g.ea = ea; g.eb = eb; g.M = M; g.N = N; g.C = C; g.ldc = ldc; g.status = b.d_status;
+  TGBA_CUDA(cudaFuncSetAttribute(dgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
+  int sms = 0;
+  TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
+  dgemm_tc_kernel<<<std::min(n_tiles, sms), kThreads, kSmem, st>>>(g);
+  TGBA_CUDA(cudaGetLastError());
+  ++b.launches;
+  return TGBA_OK;
+}
+
+int emu_tile_rows_a() { return kTMr; }
+int emu_tile_rows_b() { return kTNr; }
+int emu_k_block() { return kKB; }
+
+}  // namespace tgba
+
+extern "C" tgba_status tgba_dgemm_tc(int32_t M, int32_t N, int32_t K, const double* A, int64_t lda, const double* B,
+                                     int64_t ldb, double* C, int64_t ldc, void* stream) {
+  using namespace tgba;
+  if (M < 1 || N < 1 || K < 1) return fail(TGBA_EINVAL, "need M, N, K >= 1");
+  if (!A || !B || !C) return fail(TGBA_EINVAL, "null pointer");
+  if (lda < K || ldb < K || ldc < M) return fail(TGBA_EINVAL, "leading dimensions too small");
+  cudaStream_t st = (cudaStream_t)stream;
+  Basis ctx;
+  TGBA_CUDA(cudaGetDevice(&ctx.device));
+  const size_t ea = emu_operand_elems(M, K, emu_tile_rows_a()), eb = emu_operand_elems(N, K, emu_tile_rows_b());
+  const int TR = emu_tile_rows_a(), TC = emu_tile_rows_b(), KB = emu_k_block();
+  std::vector<EmuTile> tiles;
+  for (int rb = 0; rb < (M + TR - 1) / TR; ++rb)
+    for (int cb = 0; cb < (N + TC - 1) / TC; ++cb)
+      tiles.push_back(EmuTile{rb, cb, std::min(TC, (N - cb * TC + 15) / 16 * 16), (K + KB - 1) / KB});
+  void* buf = nullptr;
+  const size_t bytes = (ea + eb) * 2 + (size_t)(M + N) * 4 + tiles.size() * sizeof(EmuTile) + 64;
+  cudaError_t e = cudaMallocAsync(&buf, bytes, st);
+  if (e != cudaSuccess) { cudaGetLastError(); return fail(TGBA_ENOMEM, "slice buffers of tgba_dgemm_tc"); }
+  struct Free { void* p; cudaStream_t s; ~Free() { cudaFreeAsync(p, s); } } fr{buf, st};
+  __nv_bfloat16* As = (__nv_bfloat16*)buf;
+  __nv_bfloat16* Bs = As + ea;
+  int* xa = (int*)(Bs + eb);
+  int* xb = xa + M;
+  EmuTile* dt = (EmuTile*)(((uintptr_t)(xb + N) + 15) & ~(uintptr_t)15);
+  ctx.d_status = (unsigned*)(dt + tiles.size());
+  TGBA_CUDA(cudaMemsetAsync(ctx.d_status, 0, sizeof(unsigned), st));
+  TGBA_CUDA(cudaMemcpyAsync(dt, tiles.data(), tiles.size() * sizeof(EmuTile), cudaMemcpyHostToDevice, st));
+  tgba_status r = emu_slice(ctx, A, lda, 1, K, 0, nullptr, 0.0, M, K, TR, As, xa, st);
+  if (r == TGBA_OK) r = emu_slice(ctx, B, ldb, 1, K, 0, nullptr, 0.0, N, K, TC, Bs, xb, st);
+  if (r == TGBA_OK) r = emu_gemm(ctx, As, xa, M, K, Bs, xb, N, K, dt, (int)tiles.size(), C, ldc, st);
+  if (r != TGBA_OK) return r;
+  unsigned w = 0;
+  TGBA_CUDA(cudaMemcpyAsync(&w, ctx.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  TGBA_CUDA(cudaStreamSynchronize(st));
+  ctx.d_status = nullptr;
+  if (w & kStTimeout) return fail(TGBA_ETIMEOUT, "a bounded wait of the tensor-core GEMM gave up");
+  return TGBA_OK;
+}

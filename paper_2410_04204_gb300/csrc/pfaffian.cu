@@ -114,7 +114,7 @@ __device__ double pfaffian_smem(double* W, int n) {
       }
     }
   }
-  return pf;
+  return flip_if(odd != 0, pf);
 }
 
 struct Elem {

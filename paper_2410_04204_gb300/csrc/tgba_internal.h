@@ -270,6 +270,24 @@ tgba_status run_pfaffian_lists(Basis& b, const unsigned* counts, const int64_t* 
                                cudaStream_t st);
 tgba_status run_pfaffians_smem_classes(Basis& b, cudaStream_t st);
 
+// dgemm_tc.cu: FP64 products on the tensor cores (BF16 slices, exact FP32 chunk sums, 48-bit
+// running sums).  An operand (rows x K) is sliced by emu_slice into tile images of 128 (A) or 64
+// (B) rows; emu_gemm computes C = A B^T over a list of output tiles (row block, column block,
+// columns used n_eff (a multiple of 16, <= 64), K blocks nkb).
+struct EmuTile {
+  int32_t rb, cb, n_eff, nkb;
+};
+size_t emu_operand_elems(int rows, int K, int tile_rows);
+int emu_tile_rows_a();
+int emu_tile_rows_b();
+int emu_k_block();
+tgba_status emu_slice(Basis& b, const double* src, int64_t row_stride, int64_t k_stride, int k_split, int64_t k_jump,
+                      const double* w, double w_shift, int rows, int K, int tile_rows, __nv_bfloat16* out, int* e,
+                      cudaStream_t st);
+tgba_status emu_gemm(Basis& b, const __nv_bfloat16* A, const int* ea, int M, int Ka, const __nv_bfloat16* B,
+                     const int* eb, int N, int Kb, const EmuTile* d_tiles, int n_tiles, double* C, int64_t ldc,
+                     cudaStream_t st);
+
 // screen.cu
 struct Screen;
 tgba_status screen_create(int H, const float* params, uint64_t seed, Screen** out);

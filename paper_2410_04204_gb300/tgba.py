@@ -21,7 +21,7 @@ SYMBOLS = ("tgba_last_error", "tgba_device_count", "tgba_build_basis", "tgba_bas
            "tgba_basis_free", "tgba_compute_x", "tgba_x_stats", "tgba_x_export", "tgba_x_pairs", "tgba_x_direct", "tgba_z_elements", "tgba_table",
            "tgba_assemble_heff", "tgba_eigvals", "tgba_eigvals_ex", "tgba_eigvals_wait_check", "tgba_dsf", "tgba_dsf_k", "tgba_quench", "tgba_quench_ordered", "tgba_quench_correlators", "tgba_screen_create",
            "tgba_screen_nparams", "tgba_screen_params", "tgba_screen_grad", "tgba_screen_train",
-           "tgba_screen_predict", "tgba_screen_free", "tgba_table_noalloc", "tgba_profile", "tgba_fp64_peak")
+           "tgba_screen_predict", "tgba_screen_free", "tgba_table_noalloc", "tgba_dgemm_tc", "tgba_profile", "tgba_fp64_peak")
 
 
 class TgbaError(RuntimeError):
@@ -92,6 +92,7 @@ def lib():
             "tgba_screen_predict": (_I32, [_VP, _VP, _I32, _VP, _VP]),
             "tgba_screen_free": (_I32, [_VP]),
             "tgba_table_noalloc": (_I32, [_I32, _D, _D, _VP, _VP, _VP]),
+            "tgba_dgemm_tc": (_I32, [_I32, _I32, _I32, _VP, _I64, _VP, _I64, _VP, _I64, _VP]),
             "tgba_profile": (_I32, [_VP, _P(_Prof)]),
             "tgba_fp64_peak": (_I32, [_I32, _P(_D)]),
         }
@@ -412,6 +413,16 @@ def tgba_profile(b):
     out["tune_ms"] = list(p.tune_ms)[:7]
     out.pop("pad_")
     return out
+
+
+def tgba_dgemm_tc(M, N, K, A, lda, B, ldb, C, ldc, stream=None):
+    """C = A B^T in FP64 on the tensor cores: A [M][K] (ld lda), B [N][K] (ld ldb), C column-major
+    (ld ldc); float64 CUDA tensors."""
+    import torch
+    for t, name in ((A, "A"), (B, "B"), (C, "C")):
+        _cuda_tensor(t, torch.float64, name=name)
+    _check(lib().tgba_dgemm_tc(int(M), int(N), int(K), _ptr(A), int(lda), _ptr(B), int(ldb), _ptr(C), int(ldc),
+                               _stream(stream)))
 
 
 def tgba_fp64_peak(reps=5):
