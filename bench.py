@@ -58,6 +58,15 @@ def parse():
     return p.parse_args()
 
 
+def measured_peaks():
+    """The measured peaks the driver writes (MEASURED_PEAKS.json), or {} when absent."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
@@ -246,18 +255,21 @@ def aggregate(ms_local, n_elements, world, dist=None, device=None):
     return ms, world * n_elements / (ms * 1e-3)
 
 
-def screening_leg(b24, tgba, inputs, torch):
-    """Learned screening: train on 2e6 exact pairs of the L = 24 sectors (this workload), then
-    time the Pfaffian stage with and without screening at L = 60 (k = 0, 2.25e8 pairs) for each
-    tau, and measure the relative error of the lowest 20 eigenvalues at L = 40 (k = 0, n ~ 1e4,
-    where a dense check is affordable)."""
+def screening_leg(b24, tgba, inputs, torch, bf16_peak_tflops):
+    """Learned screening: train on 2e6 exact pairs of the L = 24 sectors (this workload), then,
+    at L = 60 (k = 0, M <= 6, 2.25e8 pairs) and L = 80 (k = 0, M <= 10, 3.8e8 pairs), time the
+    Pfaffian stage with and without screening for each tau, time the inference alone
+    (tgba_screen_predict), and bound what any screener could gain: the share of Pfaffian work
+    (F(n)-weighted) on pairs with |V| = L h_x |X| < tau (a perfect screener's saving, from the
+    exact X) against the inference's own floor (2 * 256 * 256 FLOP per pair at the BF16 tensor
+    peak).  Also the relative error of the lowest 20 eigenvalues at L = 40 (k = 0, n ~ 1e4)."""
     s, st = tgba.tgba_screen_train([b24], 2_000_000, inputs.SEED, 10)
     out = {"trained_on": "2e6 pairs of L24_all_sectors", "train": {k: round(v, 4) for k, v in st.items()}}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def timed(f):
+    def timed(f, reps=2):
         best = 1e30
-        for _ in range(2):
+        for _ in range(reps):
             torch.cuda.synchronize()
             e0.record()
             f()
@@ -266,19 +278,45 @@ def screening_leg(b24, tgba, inputs, torch):
             best = min(best, e0.elapsed_time(e1))
         return best
 
-    w4 = inputs.SCREEN_L60
-    b = tgba.tgba_build_basis(w4.L, w4.h_z, [0], w4.max_qp, w4.e_cut)
-    hx = w4.h_x[0]
-    t_exact = timed(lambda: tgba.tgba_compute_x(b))
-    rows = []
-    for tau in inputs.SCREEN_TAUS:
-        t_scr = timed(lambda: tgba.tgba_compute_x(b, s, tau, hx))
-        ev, sc = tgba.tgba_x_stats(b)
-        rows.append({"tau": tau, "screened_fraction": sc / (ev + sc), "ms": round(t_scr, 2),
-                     "speedup": t_exact / t_scr})
-    tgba.tgba_basis_free(b)
-    out["L60_k0"] = {"exact_ms": round(t_exact, 2), "taus": rows}
+    def F(n):
+        return sum(2 * m * (m - 1) + m for m in range(n - 2, 0, -2))
+
+    for name, w in (("L60_k0", inputs.SCREEN_L60), ("L80_k0", inputs.QUENCH_L80)):
+        b = tgba.tgba_build_basis(w.L, w.h_z, [0], w.max_qp, w.e_cut, w.max_per_parity)
+        hx = w.h_x[0]
+        t_exact = timed(lambda: tgba.tgba_compute_x(b))
+        pf_exact = tgba.tgba_profile(b)["pfaffian_ms"]
+        info = tgba.tgba_basis_info(b, 0, w.max_qp)
+        nns, nr = info["n_ns"], info["n_r"]
+        x = torch.empty(nns * nr, dtype=torch.complex128, device="cuda")
+        tgba.tgba_x_export(b, 0, x)
+        absv = (x.abs() * (w.L * hx)).view(nns, nr)
+        del x
+        M = torch.tensor(info["nqp"].astype("int64"), device="cuda")
+        fl = torch.tensor([float(F(k)) for k in range(0, 41)], dtype=torch.float64, device="cuda")
+        flw = fl[M[:nns, None] + M[None, nns:]]
+        tot = flw.sum().item()
+        perfect = {str(tau): (flw * (absv < tau)).sum().item() / tot for tau in inputs.SCREEN_TAUS}
+        del absv, flw
+        pred = torch.empty(nns * nr, dtype=torch.float32, device="cuda")
+        t_inf = timed(lambda: tgba.tgba_screen_predict(s, b, 0, pred))
+        del pred
+        rows = []
+        for tau in inputs.SCREEN_TAUS:
+            t_scr = timed(lambda: tgba.tgba_compute_x(b, s, tau, hx))
+            ev, sc = tgba.tgba_x_stats(b)
+            rows.append({"tau": tau, "screened_fraction": sc / (ev + sc), "ms": round(t_scr, 2),
+                         "speedup": t_exact / t_scr})
+        floor_ms = nns * nr * 2.0 * 256 * 256 / (bf16_peak_tflops * 1e12) * 1e3
+        best_saving = max(perfect.values()) * pf_exact
+        out[name] = {"pairs": nns * nr, "exact_ms": round(t_exact, 2), "pfaffian_ms": round(pf_exact, 2),
+                     "inference_ms": round(t_inf, 2), "inference_floor_ms": round(floor_ms, 2),
+                     "perfect_screener_work_fraction": perfect,
+                     "perfect_screener_max_saving_ms": round(best_saving, 2),
+                     "screening_can_pay": floor_ms < best_saving, "taus": rows}
+        tgba.tgba_basis_free(b)
     w3 = inputs.DSF_L40
+    hx = w3.h_x[0]
     b = tgba.tgba_build_basis(w3.L, w3.h_z, [0], w3.max_qp, w3.e_cut)
     info = tgba.tgba_basis_info(b, 0, w3.max_qp)
     n = info["n_ns"] + info["n_r"]
@@ -443,7 +481,7 @@ def run_gb300(args):
     if not args.no_solver_comparison:
         line["eigen_solver"] = eigen_solver_leg(b, w, evs, tgba, torch)
     if not args.no_screening:
-        line["screening"] = screening_leg(b, tgba, inputs, torch)
+        line["screening"] = screening_leg(b, tgba, inputs, torch, measured_peaks().get("bf16_tflops", 1945.0))
     tgba.tgba_basis_free(b)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s = oracle_sample(w, args.cpu_budget_s)

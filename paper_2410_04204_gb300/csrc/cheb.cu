@@ -22,9 +22,14 @@
 // the propagation: with the spectrum inside, ||v_K|| <= ||v_0||, while any part outside grows
 // like cosh(K acosh|x|); if the check fails the propagation is redone with Gershgorin bounds.
 //
-// Variants with the same kept set (differing only in h_x) form a group.  Iteration k runs,
-// per group, two FP64 GEMMs on the top-left block of Q (cuBLAS) and one elementwise kernel for
-// the three-term recurrence; the K iterations of all groups are captured into one CUDA graph.
+// Layout: all variants' vectors side by side on the union of the kept states (NS rows, then R
+// rows), two real columns (Re, Im of c~0's propagation) per variant, variants ordered by
+// decreasing kept set; entries outside a variant's set stay 0.  Every FP64 product (the
+// off-diagonal blocks in each step, the Lanczos steps and the moments) runs on the tensor cores
+// through the sliced products of dgemm_tc.cu: Q is sliced once in both orientations, each
+// step slices the current vectors, and the output tiles of each step skip the (row block,
+// column block) pairs that no variant's kept set reaches.  The K steps are captured into one
+// CUDA graph.
 #include <cublas_v2.h>
 
 #include <algorithm>
@@ -51,10 +56,19 @@ __device__ __forceinline__ double block_reduce(double x, double* sh) {
   return s;
 }
 
-// energy of row `row` of a kept set with kn NS rows (NS rows first), from the union energies
-// (kn_max NS rows, then the R rows)
-__device__ __forceinline__ double row_energy(const double* __restrict__ E, int64_t row, int64_t kn, int64_t kn_max) {
-  return row < kn ? E[row] : E[kn_max + (row - kn)];
+// dst (cols x rows, row-major) = transpose of src (rows x cols, row-major), 32 x 32 tiles
+__global__ void transpose_kernel(int64_t rows, int64_t cols, const double* __restrict__ src, double* __restrict__ dst) {
+  __shared__ double t[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) t[i][threadIdx.x] = src[r * cols + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) dst[c * rows + r] = t[threadIdx.x][i];
+  }
 }
 
 // Lanczos start vectors: a fixed pseudo-random vector per column (SplitMix64 of the row), unit norm
@@ -129,41 +143,51 @@ __global__ void abs_sums_r(int64_t kn, int64_t kr, const double* __restrict__ Q,
   }
 }
 
-// v_0 of a group: column 2j = Re c~0, 2j + 1 = Im c~0 on the group's kept rows
-__global__ void cheb_init(int64_t chi, int64_t kn, int64_t kn_max, int cols, const double* __restrict__ c,
-                          double* __restrict__ V) {
-  const int64_t total = chi * cols;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = q % chi;
-    const int col = (int)(q / chi);
-    const int64_t u = row < kn ? row : kn_max + (row - kn);
-    V[q] = c[2 * u + (col & 1)];
+// Per column of the union layout: coupling g, centre E_c, 1/R, and the kept set (kn NS rows
+// from 0, kr R rows from kn_max).  Padding columns have kn = kr = 0 and stay 0.
+struct ColPrm {
+  double g, ec, invr;
+  int64_t kn, kr;
+};
+
+__device__ __forceinline__ bool kept(int64_t row, int64_t kn_max, const ColPrm& p) {
+  return row < kn_max ? row < p.kn : row - kn_max < p.kr;
+}
+
+// v_0: column 2j = Re c~0, 2j + 1 = Im c~0 on the kept rows of its variant
+__global__ void cheb_init(int64_t n, int64_t kn_max, int cols, const ColPrm* __restrict__ prm,
+                          const double* __restrict__ c, double* __restrict__ V) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * cols; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = q % n;
+    const int col = (int)(q / n);
+    V[q] = kept(row, kn_max, prm[col]) ? c[2 * row + (col & 1)] : 0.0;
   }
 }
 
-// v_{k+1} = alpha (g Y + (E - E_c) v_k) / R - beta v_{k-1} on one group; per variant j of the
-// group (columns 2j, 2j + 1): prm[3 j] = g, prm[3 j + 1] = E_c, prm[3 j + 2] = 1/R
-__global__ void cheb_step(int64_t chi, int64_t kn, int64_t kn_max, int cols, const double* __restrict__ E,
-                          const double* __restrict__ prm, double alpha, double beta, const double* __restrict__ Y,
+// v_{k+1} = alpha (g Y + (E - E_c) v_k) / R - beta v_{k-1}, 0 outside each column's kept rows
+__global__ void cheb_step(int64_t n, int64_t kn_max, int cols, const double* __restrict__ E,
+                          const ColPrm* __restrict__ prm, double alpha, double beta, const double* __restrict__ Y,
                           const double* __restrict__ x, const double* __restrict__ prev, double* __restrict__ next) {
-  const int64_t total = chi * cols;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = q % chi;
-    const int j = (int)(q / chi) >> 1;
-    const double g = prm[3 * j], ec = prm[3 * j + 1], ir = prm[3 * j + 2];
-    const double h = fma(g, Y[q], (row_energy(E, row, kn, kn_max) - ec) * x[q]);
-    next[q] = alpha * ir * h - (prev ? beta * prev[q] : 0.0);
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * cols; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = q % n;
+    const ColPrm p = prm[q / n];
+    double v = 0.0;
+    if (kept(row, kn_max, p)) {
+      const double h = fma(p.g, Y[q], (E[row] - p.ec) * x[q]);
+      v = alpha * p.invr * h - (prev ? beta * prev[q] : 0.0);
+    }
+    next[q] = v;
   }
 }
 
 // per column: ||v_0||^2 and ||v_K||^2 (one block per column)
-__global__ void cheb_norms(int64_t chi, int cols, const double* __restrict__ V0, const double* __restrict__ VK,
+__global__ void cheb_norms(int64_t n, const double* __restrict__ V0, const double* __restrict__ VK,
                            double* __restrict__ out) {
   __shared__ double sh[32];
   const int c = blockIdx.x;
   double s0 = 0.0, sk = 0.0;
-  for (int64_t i = threadIdx.x; i < chi; i += blockDim.x) {
-    const double a = V0[(int64_t)c * chi + i], b = VK[(int64_t)c * chi + i];
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double a = V0[(int64_t)c * n + i], b = VK[(int64_t)c * n + i];
     s0 = fma(a, a, s0);
     sk = fma(b, b, sk);
   }
@@ -172,25 +196,17 @@ __global__ void cheb_norms(int64_t chi, int cols, const double* __restrict__ V0,
   if (threadIdx.x == 0) { out[2 * c] = s0; out[2 * c + 1] = sk; }
 }
 
-// W = (E - E_c) V for the Re and Im columns of one variant over all k: V columns at stride S
-// (the k blocks of its group), W packed [re: chi x K1][im: chi x K1]
-__global__ void cheb_weight(int64_t chi, int64_t kn, int64_t kn_max, int K1, int64_t S, const double* __restrict__ E,
-                            double ec, const double* __restrict__ Vre, double* __restrict__ W) {
-  const int64_t total = 2 * chi * K1;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = q % chi;
-    const int64_t k = (q / chi) % K1;
-    const int part = (int)(q / (chi * K1));
-    W[q] = (row_energy(E, row, kn, kn_max) - ec) * Vre[k * S + part * chi + row];
-  }
+// energies of a kept set in its own order: kn NS rows, then kr R rows
+__global__ void kept_energy(int64_t kn, int64_t kr, int64_t kn_max, const double* __restrict__ E, double* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < kn + kr; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = i < kn ? E[i] : E[kn_max + (i - kn)];
 }
 
-// Re(v_0^H v_1) of one variant
-__global__ void cheb_dot01(int64_t chi, int64_t S, const double* __restrict__ Vre, double* __restrict__ out) {
+// Re(v_0^H v_1) of one variant (columns c, c + 1 of v_0 and of v_1)
+__global__ void cheb_dot01(int64_t n, const double* __restrict__ v0, const double* __restrict__ v1, double* __restrict__ out) {
   __shared__ double sh[32];
   double s = 0.0;
-  for (int64_t i = threadIdx.x; i < chi; i += blockDim.x)
-    s = fma(Vre[i], Vre[S + i], fma(Vre[chi + i], Vre[S + chi + i], s));
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s = fma(v0[i], v1[i], fma(v0[n + i], v1[n + i], s));
   s = block_reduce(s, sh);
   if (threadIdx.x == 0) *out = s;
 }
@@ -305,71 +321,135 @@ struct DevBuf {
   ~DevBuf() { if (p) cudaFreeAsync(p, s); }
 };
 
+int64_t r16(int64_t x) { return (x + 15) / 16 * 16; }
+
+// Output tiles of one off-diagonal product: rows (row blocks of 128) x the vector columns (blocks
+// of 64).  Column c needs output rows below out_c[c] and K values below k_c[c]; a tile keeps the
+// columns up to the last one that needs any of its rows, and the K range they need.
+std::vector<EmuTile> product_tiles(int64_t rows, int64_t cols, const std::vector<int64_t>& out_c,
+                                   const std::vector<int64_t>& k_c) {
+  const int TR = emu_tile_rows_a(), TC = emu_tile_rows_b(), KB = emu_k_block();
+  std::vector<EmuTile> t;
+  for (int64_t rb = 0; rb * TR < rows; ++rb)
+    for (int64_t cb = 0; cb * TC < cols; ++cb) {
+      int64_t last = -1, kmax = 0;
+      for (int64_t c = cb * TC; c < std::min(cols, (cb + 1) * TC); ++c)
+        if (out_c[c] > rb * TR && k_c[c] > 0) {
+          last = c - cb * TC;
+          kmax = std::max(kmax, k_c[c]);
+        }
+      if (last < 0) continue;
+      t.push_back(EmuTile{(int32_t)rb, (int32_t)cb, (int32_t)std::min<int64_t>(TC, r16(last + 1)),
+                          (int32_t)((kmax + KB - 1) / KB)});
+    }
+  return t;
+}
+
 }  // namespace
 
 tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t kr_max, const double* E,
                               const double* c, const std::vector<ChebVariant>& vars, double t_max, int n_t,
                               double* mx, cudaStream_t st) {
   if (vars.empty()) return TGBA_OK;
-  const int64_t n_un = kn_max + kr_max;
-  const double cabs = std::hypot(b.c0_host[0], b.c0_host[1]);
-  cublasHandle_t bh = (cublasHandle_t)b.blas;
-  const double one = 1.0, zero = 0.0;
-  cublasStatus_t cs;
-  auto offdiag = [&](const double* x, int64_t ldx, double* y, int64_t ldy, int64_t kn, int64_t kr, int cols) {
-    // y_NS = Q^T x_R, y_R = Q x_NS on the top-left kr x kn block of Q (ld kr_max)
-    cublasStatus_t q = cublasDgemm(bh, CUBLAS_OP_T, CUBLAS_OP_N, (int)kn, cols, (int)kr, &one, Q, (int)kr_max, x + kn,
-                                   (int)ldx, &zero, y, (int)ldy);
-    if (q == CUBLAS_STATUS_SUCCESS)
-      q = cublasDgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, (int)kr, cols, (int)kn, &one, Q, (int)kr_max, x, (int)ldx, &zero,
-                      y + kn, (int)ldy);
-    return q;
-  };
   for (const ChebVariant& v : vars)
     if (!(std::fabs(v.hx) * b.L >= 1e-3))
       return fail(TGBA_EINVAL, "the Chebyshev quench path needs |h_x| L >= 1e-3 (it reads <sigma^x> off the energy); "
                                "use method 1 for h_x = 0");
-  // distinct fields: Lanczos bounds on the union of the kept states
+  const int64_t n_un = kn_max + kr_max;
+  const double cabs = std::hypot(b.c0_host[0], b.c0_host[1]);
+  const int TR = emu_tile_rows_a(), TC = emu_tile_rows_b();
+  tgba_status r = emu_prepare(b);
+  if (r != TGBA_OK) return r;
+  // ---- Q sliced in both orientations: A_ns (NS rows, K = R) and A_r (R rows, K = NS)
+  DevBuf qbuf(st);
+  const size_t ens = emu_operand_elems((int)kn_max, (int)std::max<int64_t>(1, kr_max), TR);
+  const size_t er = emu_operand_elems((int)kr_max, (int)std::max<int64_t>(1, kn_max), TR);
+  const bool coupled = kn_max > 0 && kr_max > 0;
+  TGBA_CUDA(cudaMallocAsync(&qbuf.p, (ens + er) * 2 + (size_t)(n_un + 16) * 4 + 256, st));
+  __nv_bfloat16* A_ns = (__nv_bfloat16*)qbuf.p;
+  __nv_bfloat16* A_r = A_ns + ens;
+  int* e_ns = (int*)(A_r + er);
+  int* e_r = e_ns + kn_max;
+  if (coupled) {
+    if ((r = emu_slice(b, Q, kr_max, 1, (int)kr_max, 0, nullptr, 0.0, (int)kn_max, (int)kr_max, TR, A_ns, e_ns, st)) !=
+        TGBA_OK)
+      return r;
+    double* Qt = nullptr;                               // R rows, NS contiguous
+    TGBA_CUDA(cudaMallocAsync(&Qt, (size_t)kn_max * kr_max * sizeof(double), st));
+    transpose_kernel<<<dim3((unsigned)((kr_max + 31) / 32), (unsigned)((kn_max + 31) / 32)), dim3(32, 8), 0, st>>>(
+        kn_max, kr_max, Q, Qt);
+    ++b.launches;
+    r = emu_slice(b, Qt, kn_max, 1, (int)kn_max, 0, nullptr, 0.0, (int)kr_max, (int)kn_max, TR, A_r, e_r, st);
+    cudaFreeAsync(Qt, st);
+    if (r != TGBA_OK) return r;
+  }
+  // B-operand slices of the current vectors (at most 128 + 63 columns per product)
+  auto vec_slices = [&](int cols) {
+    return std::max(emu_operand_elems(cols, (int)std::max<int64_t>(1, kr_max), TC),
+                    emu_operand_elems(cols, (int)std::max<int64_t>(1, kn_max), TC));
+  };
+  // off-diagonal product Y = A x on the union layout (x, Y: n_un x cols, ld n_un)
+  auto offdiag = [&](const double* x, double* Y, int cols, __nv_bfloat16* Bs, int* eb, const EmuTile* t_ns, int n_ns,
+                     const EmuTile* t_r, int n_r) -> tgba_status {
+    tgba_status q = emu_slice(b, x + kn_max, n_un, 1, (int)kr_max, 0, nullptr, 0.0, cols, (int)kr_max, TC, Bs, eb, st);
+    if (q == TGBA_OK) q = emu_gemm(b, A_ns, e_ns, (int)kn_max, (int)kr_max, Bs, eb, cols, (int)kr_max, t_ns, n_ns, Y, n_un, st);
+    if (q == TGBA_OK) q = emu_slice(b, x, n_un, 1, (int)kn_max, 0, nullptr, 0.0, cols, (int)kn_max, TC, Bs, eb, st);
+    if (q == TGBA_OK)
+      q = emu_gemm(b, A_r, e_r, (int)kr_max, (int)kn_max, Bs, eb, cols, (int)kn_max, t_r, n_r, Y + kn_max, n_un, st);
+    return q;
+  };
+  // ---- Lanczos bounds on the union for each distinct field
   std::vector<double> fields;
   for (const ChebVariant& v : vars)
     if (std::find(fields.begin(), fields.end(), v.hx) == fields.end()) fields.push_back(v.hx);
   const int nh = (int)fields.size();
+  const int nhp = (int)std::max<int64_t>(TC, (nh + TC - 1) / TC * TC);
   std::vector<double> lo(nh), hi(nh);
   {
     const int m = (int)std::min<int64_t>(kLanczosSteps, n_un);
+    std::vector<int64_t> out_ns(nhp, 0), out_r(nhp, 0), k_ns(nhp, 0), k_r(nhp, 0);
+    for (int i = 0; i < nh; ++i) { out_ns[i] = kn_max; k_ns[i] = kr_max; out_r[i] = kr_max; k_r[i] = kn_max; }
+    const std::vector<EmuTile> tn = product_tiles(kn_max, nhp, out_ns, k_ns), tr = product_tiles(kr_max, nhp, out_r, k_r);
     DevBuf buf(st);
-    const size_t doubles = (size_t)4 * n_un * nh + 2 * (size_t)m * nh + nh;
-    TGBA_CUDA(cudaMallocAsync(&buf.p, doubles * sizeof(double), st));
+    const size_t vs = vec_slices(nhp);
+    const size_t doubles = (size_t)4 * n_un * nhp + 2 * (size_t)m * nhp + nhp;
+    const size_t tb = (tn.size() + tr.size()) * sizeof(EmuTile);
+    TGBA_CUDA(cudaMallocAsync(&buf.p, doubles * 8 + vs * 2 + (size_t)nhp * 4 + tb + 512, st));
     double* q0 = (double*)buf.p;
-    double* q1 = q0 + n_un * nh;
-    double* q2 = q1 + n_un * nh;
-    double* Y = q2 + n_un * nh;
-    double* al = Y + n_un * nh;
-    double* be = al + (size_t)m * nh;
-    double* g = be + (size_t)m * nh;
-    std::vector<double> gh(nh);
+    double* q1 = q0 + n_un * nhp;
+    double* q2 = q1 + n_un * nhp;
+    double* Y = q2 + n_un * nhp;
+    double* al = Y + n_un * nhp;
+    double* be = al + (size_t)m * nhp;
+    double* g = be + (size_t)m * nhp;
+    EmuTile* dt = (EmuTile*)(((uintptr_t)(g + nhp) + 15) & ~(uintptr_t)15);
+    __nv_bfloat16* Bs = (__nv_bfloat16*)(((uintptr_t)(dt + tn.size() + tr.size()) + 255) & ~(uintptr_t)255);
+    int* eb = (int*)(Bs + vs);
+    std::vector<double> gh(nhp, 0.0);
     for (int i = 0; i < nh; ++i) gh[i] = -b.L * fields[i] * cabs;
-    TGBA_CUDA(cudaMemcpyAsync(g, gh.data(), nh * sizeof(double), cudaMemcpyHostToDevice, st));
-    TGBA_CUDA(cudaMemsetAsync(q0, 0, n_un * nh * sizeof(double), st));
-    TGBA_CUDA(cudaMemsetAsync(be, 0, (size_t)m * nh * sizeof(double), st));
+    TGBA_CUDA(cudaMemcpyAsync(g, gh.data(), nhp * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (!tn.empty()) TGBA_CUDA(cudaMemcpyAsync(dt, tn.data(), tn.size() * sizeof(EmuTile), cudaMemcpyHostToDevice, st));
+    if (!tr.empty())
+      TGBA_CUDA(cudaMemcpyAsync(dt + tn.size(), tr.data(), tr.size() * sizeof(EmuTile), cudaMemcpyHostToDevice, st));
+    TGBA_CUDA(cudaMemsetAsync(q0, 0, 4 * (size_t)n_un * nhp * sizeof(double), st));
+    TGBA_CUDA(cudaMemsetAsync(be, 0, (size_t)m * nhp * sizeof(double), st));
     lz_start<<<nh, kRedThreads, 0, st>>>(n_un, q1);
     ++b.launches;
     double *qp = q0, *qc = q1, *qn = q2;
     for (int j = 0; j < m; ++j) {
-      if (kn_max > 0 && kr_max > 0) {
-        if ((cs = offdiag(qc, n_un, Y, n_un, kn_max, kr_max, nh)) != CUBLAS_STATUS_SUCCESS) return blas_fail(cs, "lanczos");
-      } else {
-        TGBA_CUDA(cudaMemsetAsync(Y, 0, n_un * nh * sizeof(double), st));
+      if (coupled) {
+        if ((r = offdiag(qc, Y, nhp, Bs, eb, dt, (int)tn.size(), dt + tn.size(), (int)tr.size())) != TGBA_OK) return r;
       }
       lz_step<<<nh, kRedThreads, 0, st>>>(n_un, E, g, Y, qp, qc, qn, al, be, j, m);
       ++b.launches;
       double* t = qp; qp = qc; qc = qn; qn = t;
     }
     TGBA_CUDA(cudaGetLastError());
-    std::vector<double> ha((size_t)m * nh), hb((size_t)m * nh);
+    std::vector<double> ha((size_t)m * nhp), hb((size_t)m * nhp);
     TGBA_CUDA(cudaMemcpyAsync(ha.data(), al, ha.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     TGBA_CUDA(cudaMemcpyAsync(hb.data(), be, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     TGBA_CUDA(cudaStreamSynchronize(st));
+    if ((r = check_status(b, st)) != TGBA_OK) return r;
     for (int i = 0; i < nh; ++i) {
       int mm = m;                                   // stop at a breakdown (an invariant subspace)
       for (int j = 1; j < m; ++j)
@@ -383,7 +463,7 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
   auto gershgorin = [&](int i, double* l, double* h) -> tgba_status {
     if (rs.empty()) {
       rs.assign(n_un, 0.0);
-      if (kn_max > 0 && kr_max > 0) {
+      if (coupled) {
         DevBuf buf(st);
         TGBA_CUDA(cudaMallocAsync(&buf.p, n_un * sizeof(double), st));
         abs_sums_ns<<<blocks_for(32 * kn_max), 256, 0, st>>>(kn_max, kr_max, Q, (double*)buf.p);
@@ -405,19 +485,22 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
     }
     return TGBA_OK;
   };
-  // groups: variants with the same kept set, ordered by size
+  // ---- columns: variants by decreasing kept set, Re and Im of each, padded to a tile multiple
   std::vector<int> ord(vars.size());
   for (size_t i = 0; i < vars.size(); ++i) ord[i] = (int)i;
   std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
-    return vars[x].kn != vars[y].kn ? vars[x].kn < vars[y].kn : vars[x].kr < vars[y].kr;
+    return vars[x].kn != vars[y].kn ? vars[x].kn > vars[y].kn : vars[x].kr > vars[y].kr;
   });
-  struct Grp { int64_t kn, kr, chi; std::vector<int> members; int64_t v_off, s; };
-  std::vector<Grp> groups;
-  for (int i : ord) {
-    if (groups.empty() || groups.back().kn != vars[i].kn || groups.back().kr != vars[i].kr)
-      groups.push_back({vars[i].kn, vars[i].kr, vars[i].kn + vars[i].kr, {}, 0, 0});
-    groups.back().members.push_back(i);
-  }
+  const int ncol = 2 * (int)vars.size();
+  const int ncolp = (ncol + TC - 1) / TC * TC;
+  std::vector<int64_t> out_ns(ncolp, 0), out_r(ncolp, 0), k_ns(ncolp, 0), k_r(ncolp, 0);
+  for (int j = 0; j < (int)ord.size(); ++j)
+    for (int h = 0; h < 2; ++h) {
+      const ChebVariant& v = vars[ord[j]];
+      out_ns[2 * j + h] = v.kn; k_ns[2 * j + h] = v.kr;
+      out_r[2 * j + h] = v.kr; k_r[2 * j + h] = v.kn;
+    }
+  const std::vector<EmuTile> tn = product_tiles(kn_max, ncolp, out_ns, k_ns), tr = product_tiles(kr_max, ncolp, out_r, k_r);
   const int dt_n = n_t;
   const double dt = n_t > 1 ? t_max / (n_t - 1) : 0.0;
   cudaStream_t cap = nullptr;
@@ -431,8 +514,7 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
       const int i = (int)(std::find(fields.begin(), fields.end(), vars[v].hx) - fields.begin());
       double l = lo[i], h = hi[i];
       if (attempt == 1) {
-        tgba_status r = gershgorin(i, &l, &h);
-        if (r != TGBA_OK) return r;
+        if ((r = gershgorin(i, &l, &h)) != TGBA_OK) return r;
       }
       const double half = 0.5 * (h - l);
       ec[v] = 0.5 * (h + l);
@@ -441,69 +523,62 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
       K = std::max(K, (int)std::ceil(xmax + 10.0 * std::cbrt(xmax) + 30.0));
     }
     const int K1 = K + 1;
-    // storage: per group [k][column][row], columns 2j (Re), 2j + 1 (Im) of member j
-    int64_t total = 0, y_max = 0, chi_max = 0, n_par = 0;
-    for (Grp& g : groups) {
-      g.s = g.chi * 2 * (int64_t)g.members.size();
-      g.v_off = total;
-      total += g.s * K1;
-      y_max = std::max(y_max, g.s);
-      chi_max = std::max(chi_max, g.chi);
-      n_par += 3 * (int64_t)g.members.size();
-    }
-    const size_t need = sizeof(double) * ((size_t)total + y_max + n_par + 2 * 2 * (size_t)vars.size() + 8);
+    const int64_t S = n_un * ncolp;                      // one step's vectors
+    const size_t vs = vec_slices(ncolp);
+    const size_t tb = (tn.size() + tr.size()) * sizeof(EmuTile);
+    const size_t need = sizeof(double) * ((size_t)S * K1 + S + 2 * (size_t)ncolp + 8) + ncolp * sizeof(ColPrm) + vs * 2 +
+                        (size_t)ncolp * 4 + tb + 1024;
     size_t free_b = 0, tot_b = 0;
     TGBA_CUDA(cudaMemGetInfo(&free_b, &tot_b));
-    if (need + ((size_t)1 << 30) > free_b)
+    if (need + ((size_t)2 << 30) > free_b)
       return fail(TGBA_ENOMEM, "the Chebyshev vectors of the batched quench need " + std::to_string(need >> 20) +
                                    " MiB of device memory");
     DevBuf vbuf(st);
     TGBA_CUDA(cudaMallocAsync(&vbuf.p, need, st));
     double* V = (double*)vbuf.p;
-    double* Y = V + total;
-    double* prm = Y + y_max;
-    double* nrm = prm + n_par;
-    std::vector<double> hp;
-    for (Grp& g : groups)
-      for (int i : g.members) {
-        hp.push_back(-b.L * vars[i].hx * cabs);
-        hp.push_back(ec[i]);
-        hp.push_back(1.0 / R[i]);
-      }
-    TGBA_CUDA(cudaMemcpyAsync(prm, hp.data(), hp.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-    // v_0, then the K steps of every group, captured once and launched as one graph
-    for (Grp& g : groups)
-      cheb_init<<<blocks_for(g.s), 256, 0, st>>>(g.chi, g.kn, kn_max, 2 * (int)g.members.size(), c, V + g.v_off);
-    TGBA_CUDA(cudaGetLastError());
-    b.launches += (int64_t)groups.size();
-    TGBA_CUDA(cudaStreamSynchronize(st));
-    if ((cs = cublasSetStream(bh, cap)) != CUBLAS_STATUS_SUCCESS) return blas_fail(cs, "set stream");
-    TGBA_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    cs = CUBLAS_STATUS_SUCCESS;
-    int64_t graph_launches = 0;
-    for (int k = 0; k < K && cs == CUBLAS_STATUS_SUCCESS; ++k) {
-      int64_t po = 0;
-      for (Grp& g : groups) {
-        const int cols = 2 * (int)g.members.size();
-        double* vk = V + g.v_off + (int64_t)k * g.s;
-        if (g.kn > 0 && g.kr > 0) {
-          cs = offdiag(vk, g.chi, Y, g.chi, g.kn, g.kr, cols);
-          if (cs != CUBLAS_STATUS_SUCCESS) break;
-        } else {
-          cudaMemsetAsync(Y, 0, g.s * sizeof(double), cap);
-        }
-        cheb_step<<<blocks_for(g.s), 256, 0, cap>>>(g.chi, g.kn, kn_max, cols, E, prm + po, k == 0 ? 1.0 : 2.0, 1.0, Y,
-                                                     vk, k == 0 ? nullptr : vk - g.s, vk + g.s);
-        ++graph_launches;
-        po += 3 * (int64_t)g.members.size();
-      }
+    double* Y = V + (size_t)S * K1;
+    double* nrm = Y + S;
+    ColPrm* prm = (ColPrm*)(nrm + 2 * (size_t)ncolp + 8);
+    EmuTile* dtl = (EmuTile*)(((uintptr_t)(prm + ncolp) + 15) & ~(uintptr_t)15);
+    __nv_bfloat16* Bs = (__nv_bfloat16*)(((uintptr_t)(dtl + tn.size() + tr.size()) + 255) & ~(uintptr_t)255);
+    int* eb = (int*)(Bs + vs);
+    std::vector<ColPrm> hp(ncolp, ColPrm{0.0, 0.0, 0.0, 0, 0});
+    for (int j = 0; j < (int)ord.size(); ++j) {
+      const int v = ord[j];
+      for (int h = 0; h < 2; ++h) hp[2 * j + h] = ColPrm{-b.L * vars[v].hx * cabs, ec[v], 1.0 / R[v], vars[v].kn, vars[v].kr};
     }
+    TGBA_CUDA(cudaMemcpyAsync(prm, hp.data(), ncolp * sizeof(ColPrm), cudaMemcpyHostToDevice, st));
+    if (!tn.empty()) TGBA_CUDA(cudaMemcpyAsync(dtl, tn.data(), tn.size() * sizeof(EmuTile), cudaMemcpyHostToDevice, st));
+    if (!tr.empty())
+      TGBA_CUDA(cudaMemcpyAsync(dtl + tn.size(), tr.data(), tr.size() * sizeof(EmuTile), cudaMemcpyHostToDevice, st));
+    TGBA_CUDA(cudaMemsetAsync(Y, 0, S * sizeof(double), st));
+    cheb_init<<<blocks_for(S), 256, 0, st>>>(n_un, kn_max, ncolp, prm, c, V);
+    TGBA_CUDA(cudaGetLastError());
+    ++b.launches;
+    TGBA_CUDA(cudaStreamSynchronize(st));
+    // the K steps of all variants, captured once and launched as one graph
+    TGBA_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    cudaStream_t keep = st;
+    st = cap;                                            // offdiag launches on `st`
+    tgba_status cr = TGBA_OK;
+    const int64_t launches0 = b.launches.load();
+    for (int k = 0; k < K && cr == TGBA_OK; ++k) {
+      double* vk = V + (size_t)k * S;
+      if (coupled)
+        cr = offdiag(vk, Y, ncolp, Bs, eb, dtl, (int)tn.size(), dtl + tn.size(), (int)tr.size());
+      if (cr != TGBA_OK) break;
+      cheb_step<<<blocks_for(S), 256, 0, cap>>>(n_un, kn_max, ncolp, E, prm, k == 0 ? 1.0 : 2.0, 1.0, Y, vk,
+                                                 k == 0 ? nullptr : vk - S, vk + S);
+      ++b.launches;
+    }
+    st = keep;
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(cap, &graph);
-    cublasSetStream(bh, st);
-    if (cs != CUBLAS_STATUS_SUCCESS) {
+    const int64_t graph_launches = b.launches.load() - launches0;
+    b.launches -= graph_launches;                        // counted when the graph runs
+    if (cr != TGBA_OK) {
       if (graph) cudaGraphDestroy(graph);
-      return blas_fail(cs, "chebyshev step");
+      return cr;
     }
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture (Chebyshev steps)");
     cudaGraphExec_t exec = nullptr;
@@ -521,78 +596,103 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
     b.quench_flops = 0;
     for (const ChebVariant& v : vars) b.quench_flops += 8.0 * (double)K * (double)v.kn * (double)v.kr;
     // the interval check: ||v_K|| <= ||v_0|| for every column
+    cheb_norms<<<ncolp, kRedThreads, 0, st>>>(n_un, V, V + (size_t)K * S, nrm);
+    TGBA_CUDA(cudaGetLastError());
+    ++b.launches;
     {
-      int64_t co = 0;
-      for (Grp& g : groups) {
-        const int cols = 2 * (int)g.members.size();
-        cheb_norms<<<cols, kRedThreads, 0, st>>>(g.chi, cols, V + g.v_off, V + g.v_off + (int64_t)K * g.s, nrm + 2 * co);
-        co += cols;
-      }
-      TGBA_CUDA(cudaGetLastError());
-      b.launches += (int64_t)groups.size();
-      std::vector<double> hn(2 * co);
+      std::vector<double> hn(2 * (size_t)ncolp);
       TGBA_CUDA(cudaMemcpyAsync(hn.data(), nrm, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
       TGBA_CUDA(cudaStreamSynchronize(st));
+      if ((r = check_status(b, st)) != TGBA_OK) return r;
       bool ok = true;
-      for (int64_t q = 0; q < co; ++q)
+      for (int q = 0; q < ncolp; ++q)
         if (!(hn[2 * q + 1] <= hn[2 * q] * (1.0 + 1e-6) + 1e-300)) ok = false;
       if (!ok) {
         if (attempt == 1) return fail(TGBA_ENUMERIC, "the Chebyshev expansion left its Gershgorin interval");
         continue;                               // redo with Gershgorin bounds
       }
     }
-    // moments and <sigma^x>(t), one variant at a time
+    // ---- moments (tensor-core FP64 products) and <sigma^x>(t), one variant at a time
+    int64_t chi_max = 0;
+    for (const ChebVariant& v : vars) chi_max = std::max<int64_t>(chi_max, v.kn + v.kr);
     const int nb = std::min(dt_n, 256);
     const int m_start = [&] {
       int ms = K + 30 + (int)std::ceil(std::sqrt(40.0 * K));
       return ms + (ms & 1);
     }();
+    std::vector<EmuTile> tg;
+    for (int rb = 0; rb * TR < K1; ++rb)
+      for (int cb = 0; cb * TC < K1; ++cb) tg.push_back(EmuTile{rb, cb, (int32_t)std::min<int64_t>(TC, r16(K1 - cb * TC)), 0});
+    const size_t sa = emu_operand_elems(K1, (int)chi_max, TR), sb = emu_operand_elems(K1, (int)chi_max, TC);
     DevBuf mbuf(st);
-    const size_t mdoubles = (size_t)2 * chi_max * K1 + 4 * (size_t)K1 * K1 + 2 * (size_t)K1 * nb + 8;
-    TGBA_CUDA(cudaMallocAsync(&mbuf.p, mdoubles * sizeof(double), st));
-    double* W = (double*)mbuf.p;
-    double* Grr = W + 2 * chi_max * K1;
+    const size_t mdoubles = 4 * (size_t)K1 * K1 + 2 * (size_t)K1 * nb + chi_max + 8;
+    TGBA_CUDA(cudaMallocAsync(&mbuf.p, mdoubles * 8 + (2 * sa + 2 * sb) * 2 + 4 * (size_t)K1 * 4 +
+                                           tg.size() * sizeof(EmuTile) + 1024, st));
+    double* Grr = (double*)mbuf.p;
     double* Gii = Grr + (size_t)K1 * K1;
     double* Gri = Gii + (size_t)K1 * K1;
     double* Gam = Gri + (size_t)K1 * K1;
     double* Ab = Gam + (size_t)K1 * K1;
     double* GA = Ab + (size_t)K1 * nb;
-    double* d01 = GA + (size_t)K1 * nb;
-    for (Grp& g : groups)
-      for (size_t j = 0; j < g.members.size(); ++j) {
-        const int v = g.members[j];
-        const double* vre = V + g.v_off + (int64_t)(2 * j) * g.chi;
-        cheb_weight<<<blocks_for(2 * g.chi * K1), 256, 0, st>>>(g.chi, g.kn, kn_max, K1, g.s, E, ec[v], vre, W);
-        cheb_dot01<<<1, kRedThreads, 0, st>>>(g.chi, g.s, vre, d01);
-        const int ldv = (int)g.s;
-        cs = cublasDgemm(bh, CUBLAS_OP_T, CUBLAS_OP_N, K1, K1, (int)g.chi, &one, vre, ldv, W, (int)g.chi, &zero, Grr, K1);
-        if (cs == CUBLAS_STATUS_SUCCESS)
-          cs = cublasDgemm(bh, CUBLAS_OP_T, CUBLAS_OP_N, K1, K1, (int)g.chi, &one, vre + g.chi, ldv, W + g.chi * K1,
-                           (int)g.chi, &zero, Gii, K1);
-        if (cs == CUBLAS_STATUS_SUCCESS)
-          cs = cublasDgemm(bh, CUBLAS_OP_T, CUBLAS_OP_N, K1, K1, (int)g.chi, &one, vre, ldv, W + g.chi * K1, (int)g.chi,
-                           &zero, Gri, K1);
-        if (cs != CUBLAS_STATUS_SUCCESS) return blas_fail(cs, "chebyshev moments");
-        cheb_gamma<<<blocks_for((int64_t)K1 * K1), 256, 0, st>>>(K1, Grr, Gii, Gri, Gam);
-        double h01 = 0.0;
-        TGBA_CUDA(cudaMemcpyAsync(&h01, d01, sizeof(double), cudaMemcpyDeviceToHost, st));
-        TGBA_CUDA(cudaStreamSynchronize(st));
-        const double scale = 1.0 / (b.L * vars[v].hx * vars[v].norm2);
-        for (int t0 = 0; t0 < dt_n; t0 += nb) {
-          const int cnt = std::min(nb, dt_n - t0);
-          cheb_bessel<<<(cnt + 127) / 128, 128, 0, st>>>(cnt, t0, dt, R[v], K, m_start, Ab);
-          cs = cublasDgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, K1, cnt, K1, &one, Gam, K1, Ab, K1, &zero, GA, K1);
-          if (cs != CUBLAS_STATUS_SUCCESS) return blas_fail(cs, "gamma a");
-          cheb_mx<<<(cnt * 32 + 255) / 256, 256, 0, st>>>(K1, cnt, Ab, GA, R[v] * h01, scale,
-                                                          mx + (int64_t)vars[v].out * n_t + t0);
-          b.launches += 2;
-        }
-        TGBA_CUDA(cudaGetLastError());
-        b.launches += 3;
+    double* Ek = GA + (size_t)K1 * nb;
+    double* d01 = Ek + chi_max;
+    EmuTile* dtg = (EmuTile*)(((uintptr_t)(d01 + 8) + 15) & ~(uintptr_t)15);
+    __nv_bfloat16* Vr = (__nv_bfloat16*)(((uintptr_t)(dtg + tg.size()) + 255) & ~(uintptr_t)255);
+    __nv_bfloat16* Vi = Vr + sa;
+    __nv_bfloat16* Wr = Vi + sa;
+    __nv_bfloat16* Wi = Wr + sb;
+    int* evr = (int*)(Wi + sb);
+    int* evi = evr + K1;
+    int* ewr = evi + K1;
+    int* ewi = ewr + K1;
+    cublasHandle_t bh = (cublasHandle_t)b.blas;
+    const double one = 1.0, zero = 0.0;
+    cublasStatus_t cs;
+    for (int j = 0; j < (int)ord.size(); ++j) {
+      const ChebVariant& vv = vars[ord[j]];
+      const int v = ord[j];
+      const int64_t kn = vv.kn, kr = vv.kr, chi = kn + kr;
+      const double* vre = V + (size_t)(2 * j) * n_un;       // column 2j of step 0; step k at + k S
+      kept_energy<<<blocks_for(chi), 256, 0, st>>>(kn, kr, kn_max, E, Ek);
+      cheb_dot01<<<1, kRedThreads, 0, st>>>(n_un, vre, vre + S, d01);
+      b.launches += 2;
+      std::vector<EmuTile> tgv(tg);
+      for (EmuTile& t : tgv) t.nkb = (int32_t)((chi + emu_k_block() - 1) / emu_k_block());
+      TGBA_CUDA(cudaMemcpyAsync(dtg, tgv.data(), tgv.size() * sizeof(EmuTile), cudaMemcpyHostToDevice, st));
+      // rows k of V (K = the kept rows in their own order: kn NS rows, then kr R rows)
+      const int64_t jump = kn_max - kn;
+      if ((r = emu_slice(b, vre, S, 1, (int)kn, jump, nullptr, 0.0, K1, (int)chi, TR, Vr, evr, st)) != TGBA_OK) return r;
+      if ((r = emu_slice(b, vre + n_un, S, 1, (int)kn, jump, nullptr, 0.0, K1, (int)chi, TR, Vi, evi, st)) != TGBA_OK)
+        return r;
+      if ((r = emu_slice(b, vre, S, 1, (int)kn, jump, Ek, ec[v], K1, (int)chi, TC, Wr, ewr, st)) != TGBA_OK) return r;
+      if ((r = emu_slice(b, vre + n_un, S, 1, (int)kn, jump, Ek, ec[v], K1, (int)chi, TC, Wi, ewi, st)) != TGBA_OK)
+        return r;
+      if ((r = emu_gemm(b, Vr, evr, K1, (int)chi, Wr, ewr, K1, (int)chi, dtg, (int)tgv.size(), Grr, K1, st)) != TGBA_OK)
+        return r;
+      if ((r = emu_gemm(b, Vi, evi, K1, (int)chi, Wi, ewi, K1, (int)chi, dtg, (int)tgv.size(), Gii, K1, st)) != TGBA_OK)
+        return r;
+      if ((r = emu_gemm(b, Vr, evr, K1, (int)chi, Wi, ewi, K1, (int)chi, dtg, (int)tgv.size(), Gri, K1, st)) != TGBA_OK)
+        return r;
+      cheb_gamma<<<blocks_for((int64_t)K1 * K1), 256, 0, st>>>(K1, Grr, Gii, Gri, Gam);
+      ++b.launches;
+      double h01 = 0.0;
+      TGBA_CUDA(cudaMemcpyAsync(&h01, d01, sizeof(double), cudaMemcpyDeviceToHost, st));
+      TGBA_CUDA(cudaStreamSynchronize(st));            // also: tgv may be reused by the next variant
+      const double scale = 1.0 / (b.L * vv.hx * vv.norm2);
+      for (int t0 = 0; t0 < dt_n; t0 += nb) {
+        const int cnt = std::min(nb, dt_n - t0);
+        cheb_bessel<<<(cnt + 127) / 128, 128, 0, st>>>(cnt, t0, dt, R[v], K, m_start, Ab);
+        cs = cublasDgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, K1, cnt, K1, &one, Gam, K1, Ab, K1, &zero, GA, K1);
+        if (cs != CUBLAS_STATUS_SUCCESS) return blas_fail(cs, "gamma a");
+        cheb_mx<<<(cnt * 32 + 255) / 256, 256, 0, st>>>(K1, cnt, Ab, GA, R[v] * h01, scale,
+                                                        mx + (int64_t)vv.out * n_t + t0);
+        b.launches += 2;
       }
+      TGBA_CUDA(cudaGetLastError());
+    }
     b.quench_terms = K;
     TGBA_CUDA(cudaStreamSynchronize(st));
-    return TGBA_OK;
+    return check_status(b, st);
   }
   return TGBA_OK;
 }

@@ -4,17 +4,18 @@
 // GB300 runs FP64 at about 1.25 TFLOP/s on its CUDA cores but BF16 MMAs at about 2 PFLOP/s.
 // C = A B^T (A: M x K, B: N x K, both with K contiguous in their slices) is computed as follows.
 //  * Slicing.  Row i of A gets an exponent e_i with max_k |A_ik| <= 2^e_i; r = A_ik 2^-e_i is
-//    cut into S = 7 signed base-128 digits, d_0 = rint(128 r), r <- 128 r - d_0, d_1 = rint(128 r),
-//    ... (|d_0| <= 128, |d_p| <= 64 after it; every step exact in FP64), and slice p stores
-//    d_p 2^{-7p} in BF16 (exact: at most 8 significant bits).  So A_ik = 2^{e_i - 7} sum_p
-//    slice_p + O(2^{e_i - 50}).  B's rows (the columns of C) are cut the same way.
-//  * Products.  C_ij = 2^{e_i + f_j - 14} sum_{p + q <= 6} (A_p B_q^T)_ij.  The products of
-//    digit diagonal d = p + q carry the scale 2^{-7d}; over a chunk of 256 K values each of
+//    cut into S = 6 signed base-256 digits, d_0 = rint(256 r), r <- 256 r - d_0, d_1 = rint(256 r),
+//    ... (|d_0| <= 256, |d_p| <= 128 after it; every step exact in FP64), and slice p stores
+//    d_p 2^{-8p} in BF16 (exact: at most 8 significant bits).  So A_ik = 2^{e_i - 8} sum_p
+//    slice_p + O(2^{e_i - 49}).  B's rows (the columns of C) are cut the same way.
+//  * Products.  C_ij = 2^{e_i + f_j - 16} sum_{p + q <= 5} (A_p B_q^T)_ij.  The products of
+//    digit diagonal d = p + q carry the scale 2^{-8d}; over a chunk of 128 K values each of
 //    the sums of diagonals 0, 1 and 2 stays below 2^24 units of its scale, so FP32
 //    accumulation of those diagonals is exact, and they get one TMEM accumulator each.
-//    Diagonals 3..6 share a fourth accumulator; their FP32 rounding is below 2^-45 of the
-//    leading term.
-//  * Chunks.  After every 256 K values the four accumulators are folded into a running sum per
+//    Diagonals 3..5 share a fourth accumulator, whose FP32 rounding stays near 2^-48 of the
+//    leading term (measured: an earlier base-128 split with the shared accumulator from
+//    diagonal 3 erred by up to 1.5e-12).
+//  * Chunks.  After every 128 K values the four accumulators are folded into a running sum per
 //    element kept as an unevaluated pair of FP32 numbers (hi + lo, error-free two-sum: about
 //    48 bits), by CUDA-core FP32 arithmetic, while the tensor cores fill the second set of
 //    accumulators (two sets of 4 x 64 columns = all 512 TMEM columns).  At the end of the tile
@@ -24,9 +25,9 @@
 // Tiles: 128 rows of A x up to 64 rows of B (n_eff, a multiple of 16, per tile) x K in blocks of
 // 32 (64-byte rows, 64-byte swizzle).  The slices of one (row block, K block) are stored
 // contiguously, already in the shared-memory image the MMA descriptors read, so each stage is
-// two bulk copies (cp.async.bulk: 56 KB of A slices, 28 KB of B slices) completing on an
+// two bulk copies (cp.async.bulk: 48 KB of A slices, 24 KB of B slices) completing on an
 // mbarrier.  Warp 0 issues the copies, warp 1 the MMAs (one thread each), warps 2-5 fold the
-// accumulators and write C.  Two smem stages, two accumulator sets.  Every wait is bounded: on
+// accumulators and write C.  Three smem stages, two accumulator sets.  Every wait is bounded: on
 // timeout the kernel records TGBA_ETIMEOUT's status bit, every role leaves, in-flight copies and
 // MMAs are waited for (bounded) and the tensor memory is freed.
 #include <cuda_bf16.h>
@@ -40,16 +41,16 @@
 namespace tgba {
 namespace {
 
-constexpr int kS = 7;                     // slices per operand
+constexpr int kS = 6;                     // slices per operand (base-256 digits)
 constexpr int kKB = 32;                   // K per block (64-byte rows)
 constexpr int kTMr = 128;                 // rows of A per tile
 constexpr int kTNr = 64;                  // rows of B per tile
-constexpr int kChunkBlocks = 8;           // K blocks per exact FP32 chunk (256 K values)
+constexpr int kChunkBlocks = 4;           // K blocks per exact FP32 chunk (128 K values)
 constexpr uint32_t kASlice = kTMr * kKB * 2;          // 8 KB
 constexpr uint32_t kBSlice = kTNr * kKB * 2;          // 4 KB
-constexpr uint32_t kAStage = kS * kASlice;            // 56 KB
-constexpr uint32_t kBStage = kS * kBSlice;            // 28 KB
-constexpr int kStages = 2;
+constexpr uint32_t kAStage = kS * kASlice;            // 48 KB
+constexpr uint32_t kBStage = kS * kBSlice;            // 24 KB
+constexpr int kStages = 3;
 constexpr uint32_t kSmem = 1024 + kStages * (kAStage + kBStage) + 256;
 constexpr unsigned kWait = 1u << 24;                   // polls of a bounded wait
 constexpr int kThreads = 192;
@@ -162,17 +163,19 @@ __global__ void __launch_bounds__(kThreads, 1) dgemm_tc_kernel(GemmArgs g) {
   unsigned char* sA = base;                                  // [stage] A slices
   unsigned char* sB = base + kStages * kAStage;              // [stage] B slices
   uint64_t* bars = (uint64_t*)(sB + kStages * kBStage);
-  uint64_t* full = bars;               // [2] stage loaded
-  uint64_t* empty = bars + 2;          // [2] stage consumed by the MMAs
-  uint64_t* accf = bars + 4;           // [2] accumulator set written
-  uint64_t* acce = bars + 6;           // [2] accumulator set read
-  uint32_t* tslot = (uint32_t*)(bars + 8);
+  uint64_t* full = bars;               // [kStages] stage loaded
+  uint64_t* empty = bars + kStages;    // [kStages] stage consumed by the MMAs
+  uint64_t* accf = bars + 2 * kStages; // [2] accumulator set written
+  uint64_t* acce = accf + 2;           // [2] accumulator set read
+  uint32_t* tslot = (uint32_t*)(acce + 2);
   __shared__ volatile int s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < kStages; ++s) {
       bar_init(full + s, 1);
       bar_init(empty + s, 1);
+    }
+    for (int s = 0; s < 2; ++s) {
       bar_init(accf + s, 1);
       bar_init(acce + s, 4);
     }
@@ -195,8 +198,8 @@ __global__ void __launch_bounds__(kThreads, 1) dgemm_tc_kernel(GemmArgs g) {
       for (int t = blockIdx.x; t < g.n_tiles && !s_abort; t += gridDim.x) {
         const EmuTile tl = g.tiles[t];
         for (int kb = 0; kb < tl.nkb; ++kb, ++it) {
-          const int st = it & 1;
-          if (!bar_wait(empty + st, ((it >> 1) & 1u) ^ 1u, &s_abort)) { atomicOr(g.status, kStTimeout); s_abort = 1; break; }
+          const int st = it % kStages;
+          if (!bar_wait(empty + st, ((it / kStages) & 1u) ^ 1u, &s_abort)) { atomicOr(g.status, kStTimeout); s_abort = 1; break; }
           bar_expect(full + st, kAStage + kBStage);
           bulk_load(sA + st * kAStage, g.A + ((size_t)tl.rb * g.a_kb + kb) * (kAStage / 2), kAStage, full + st);
           bulk_load(sB + st * kBStage, g.B + ((size_t)tl.cb * g.b_kb + kb) * (kBStage / 2), kBStage, full + st);
@@ -204,7 +207,8 @@ __global__ void __launch_bounds__(kThreads, 1) dgemm_tc_kernel(GemmArgs g) {
       }
       if (s_abort) {                                  // copies still in flight land before the CTA leaves
         const volatile int never = 0;
-        for (uint32_t j = (it >= 2 ? it - 2 : 0); j < it; ++j) bar_wait(full + (j & 1), (j >> 1) & 1u, (volatile int*)&never);
+        for (uint32_t j = (it >= kStages ? it - kStages : 0); j < it; ++j)
+          bar_wait(full + (j % kStages), (j / kStages) & 1u, (volatile int*)&never);
       }
     }
   } else if (warp == 1) {
@@ -222,8 +226,8 @@ __global__ void __launch_bounds__(kThreads, 1) dgemm_tc_kernel(GemmArgs g) {
           const uint32_t dbase = tmem + (uint32_t)set * 256u;
           const int kb1 = min(tl.nkb, kb0 + kChunkBlocks);
           for (int kb = kb0; kb < kb1; ++kb, ++it) {
-            const int st = it & 1;
-            if (!bar_wait(full + st, (it >> 1) & 1u, &s_abort)) { atomicOr(g.status, kStTimeout); s_abort = 1; break; }
+            const int st = it % kStages;
+            if (!bar_wait(full + st, (it / kStages) & 1u, &s_abort)) { atomicOr(g.status, kStTimeout); s_abort = 1; break; }
             fence_after();
             const uint32_t a0 = su32(sA + st * kAStage), b0 = su32(sB + st * kBStage);
 #pragma unroll 1
@@ -293,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1) dgemm_tc_kernel(GemmArgs g) {
           const int j = tl.cb * kTNr + c;
           if (c < tl.n_eff && j < g.N) {
             const double v = ((double)hi[c] + (double)lo[c]);
-            g.C[(int64_t)i + (int64_t)j * g.ldc] = ldexp(v, e_i + g.eb[j] - 14);
+            g.C[(int64_t)i + (int64_t)j * g.ldc] = ldexp(v, e_i + g.eb[j] - 16);
           }
         }
       }
@@ -357,11 +361,11 @@ __global__ void slice_tiles(int rows, int K, const double* __restrict__ src, int
     double scale = 1.0;
 #pragma unroll
     for (int p = 0; p < kS; ++p) {
-      const double y = rr * 128.0;
+      const double y = rr * 256.0;
       const double d = rint(y);
       rr = y - d;
       *(__nv_bfloat16*)(tile + (size_t)p * slice_bytes + o) = __double2bfloat16(d * scale);
-      scale *= 0.0078125;                           // 2^-7
+      scale *= 0.00390625;                          // 2^-8
     }
   }
 }
@@ -393,21 +397,33 @@ tgba_status emu_slice(Basis& b, const double* src, int64_t row_stride, int64_t k
   return TGBA_OK;
 }
 
-// C = A B^T for sliced operands (see emu_slice), over the given output tiles.
+// Kernel attributes and the SM count, once per device (outside any stream capture).
+tgba_status emu_prepare(Basis& b) {
+  static int sms_of[64] = {0};
+  if (b.device < 0 || b.device >= 64) return fail(TGBA_ELIMIT, "device index");
+  if (sms_of[b.device] == 0) {
+    TGBA_CUDA(cudaFuncSetAttribute(dgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
+    int sms = 0;
+    TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
+    sms_of[b.device] = sms;
+  }
+  b.emu_sms = sms_of[b.device];
+  return TGBA_OK;
+}
+
+// C = A B^T for sliced operands (see emu_slice), over the given output tiles (emu_prepare first).
 tgba_status emu_gemm(Basis& b, const __nv_bfloat16* A, const int* ea, int M, int Ka, const __nv_bfloat16* B,
                      const int* eb, int N, int Kb, const EmuTile* d_tiles, int n_tiles, double* C, int64_t ldc,
                      cudaStream_t st) {
   if (n_tiles == 0) return TGBA_OK;
+  if (b.emu_sms <= 0) return fail(TGBA_EINVAL, "emu_prepare was not called");
   GemmArgs g;
   g.tiles = d_tiles; g.n_tiles = n_tiles;
   g.A = A; g.B = B;
   g.a_kb = (Ka + kKB - 1) / kKB;
   g.b_kb = (Kb + kKB - 1) / kKB;
   g.ea = ea; g.eb = eb; g.M = M; g.N = N; g.C = C; g.ldc = ldc; g.status = b.d_status;
-  TGBA_CUDA(cudaFuncSetAttribute(dgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
-  int sms = 0;
-  TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
-  dgemm_tc_kernel<<<std::min(n_tiles, sms), kThreads, kSmem, st>>>(g);
+  dgemm_tc_kernel<<<std::min(n_tiles, b.emu_sms), kThreads, kSmem, st>>>(g);
   TGBA_CUDA(cudaGetLastError());
   ++b.launches;
   return TGBA_OK;
@@ -447,7 +463,8 @@ extern "C" tgba_status tgba_dgemm_tc(int32_t M, int32_t N, int32_t K, const doub
   ctx.d_status = (unsigned*)(dt + tiles.size());
   TGBA_CUDA(cudaMemsetAsync(ctx.d_status, 0, sizeof(unsigned), st));
   TGBA_CUDA(cudaMemcpyAsync(dt, tiles.data(), tiles.size() * sizeof(EmuTile), cudaMemcpyHostToDevice, st));
-  tgba_status r = emu_slice(ctx, A, lda, 1, K, 0, nullptr, 0.0, M, K, TR, As, xa, st);
+  tgba_status r = emu_prepare(ctx);
+  if (r == TGBA_OK) r = emu_slice(ctx, A, lda, 1, K, 0, nullptr, 0.0, M, K, TR, As, xa, st);
   if (r == TGBA_OK) r = emu_slice(ctx, B, ldb, 1, K, 0, nullptr, 0.0, N, K, TC, Bs, xb, st);
   if (r == TGBA_OK) r = emu_gemm(ctx, As, xa, M, K, Bs, xb, N, K, dt, (int)tiles.size(), C, ldc, st);
   if (r != TGBA_OK) return r;

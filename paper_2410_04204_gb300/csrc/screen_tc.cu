@@ -14,7 +14,7 @@
 //      y = w3 . relu(z2 + b2) + b3 per row;
 //   4. a pair is kept when y - (n/2) log10(L/24) + log10(L |h_x|) >= log10(tau) - margin, or when
 //      a state has more quasiparticles than the model's features hold; kept pairs go to the
-//      work list of their size (one atomic per warp), and (prediction mode) y is stored.
+//      work list of their size (one atomic per tile), and (prediction mode) y is stored.
 // Every mbarrier wait is bounded: on timeout the kernel records TGBA_ETIMEOUT's status bit,
 // waits (bounded again) for its MMAs, frees its tensor memory and returns.
 #include <cuda_bf16.h>
@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(kTM, 1) score_tc(ScoreArgs g) {
   uint64_t* bar = (uint64_t*)(w3s + kH);
   uint32_t* tmem_slot = (uint32_t*)(bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ unsigned s_cnt[5];                   // kept pairs per warp of the tile, then the tile's base
 
   for (int e = tid; e < kH * (kH / 8); e += kTM) {          // W2 rows, 16 bytes at a time
     const int row = e >> 5, c16 = e & 31;
@@ -248,14 +249,20 @@ __global__ void __launch_bounds__(kTM, 1) score_tc(ScoreArgs g) {
     }
     // 4. decision, prediction, compaction
     if (valid && g.pred) g.pred[out - g.pred_base] = y;
-    if (g.counts) {
+    if (g.counts) {                                   // one atomic per tile (the tile has one size)
       const bool keep = valid && (!model || y - g.half_log_l * (float)rc.n + g.shift >= 0.f);
       const unsigned m = __ballot_sync(0xffffffffu, keep);
-      unsigned base_idx = 0;
-      if (lane == 0 && m) base_idx = atomicAdd(g.counts + (rc.n >> 1), (unsigned)__popc(m));
-      base_idx = __shfl_sync(0xffffffffu, base_idx, 0);
+      if (lane == 0) s_cnt[warp] = (unsigned)__popc(m);
+      __syncthreads();
+      if (tid == 0) {
+        const unsigned tot = s_cnt[0] + s_cnt[1] + s_cnt[2] + s_cnt[3];
+        s_cnt[4] = tot ? atomicAdd(g.counts + (rc.n >> 1), tot) : 0u;
+      }
+      __syncthreads();
       if (keep) {
-        const int64_t slot = g.list_off[rc.n >> 1] + base_idx + __popc(m & ((1u << lane) - 1u));
+        unsigned before = s_cnt[4];
+        for (int w = 0; w < warp; ++w) before += s_cnt[w];
+        const int64_t slot = g.list_off[rc.n >> 1] + before + __popc(m & ((1u << lane) - 1u));
         g.lists[slot] = PairEntry{out, (int32_t)a, (int32_t)b};
       }
     }

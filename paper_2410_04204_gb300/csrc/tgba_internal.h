@@ -159,6 +159,7 @@ struct Basis {
   void* solver = nullptr;          // cusolverDnHandle_t
   void* blas = nullptr;            // cublasHandle_t
   double* d_blas_ws = nullptr;     // its workspace (set explicitly, so captured calls allocate nothing)
+  int emu_sms = 0;                 // SMs for the tensor-core FP64 products (emu_prepare)
   int quench_terms = 0;            // Chebyshev terms K of the last batched quench propagation
   double quench_flops = 0;         // its algorithmic FP64 flops (K sum 8 n_NS n_R)
   cudaEvent_t q_ev[2] = {nullptr, nullptr};   // around its graph launch
@@ -284,6 +285,7 @@ int emu_k_block();
 tgba_status emu_slice(Basis& b, const double* src, int64_t row_stride, int64_t k_stride, int k_split, int64_t k_jump,
                       const double* w, double w_shift, int rows, int K, int tile_rows, __nv_bfloat16* out, int* e,
                       cudaStream_t st);
+tgba_status emu_prepare(Basis& b);
 tgba_status emu_gemm(Basis& b, const __nv_bfloat16* A, const int* ea, int M, int Ka, const __nv_bfloat16* B,
                      const int* eb, int N, int Kb, const EmuTile* d_tiles, int n_tiles, double* C, int64_t ldc,
                      cudaStream_t st);

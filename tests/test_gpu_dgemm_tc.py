@@ -1,10 +1,10 @@
 """FP64 products on the tensor cores (tgba_dgemm_tc: BF16 slices of the FP64 operands, tcgen05
-MMAs, exact FP32 sums of the leading digit diagonals per chunk of 256 K values, 48-bit running
+MMAs, exact FP32 sums of the leading digit diagonals per chunk of 128 K values, 48-bit running
 sums) through the C ABI.
 
 * Exactness of the tensor cores' FP32 accumulation: integer operands of at most 14 bits have
-  only the digit diagonals 0..2, which the design sums exactly, so C must equal the integer
-  product bit for bit (K = 4096: 16 chunks, sums up to 2^38).
+  two base-256 digits, hence only the digit diagonals 0..2, which the design sums exactly, so C
+  must equal the integer product bit for bit (K = 4096: 32 chunks, sums up to 2^38).
 * Accuracy: random operands whose rows span six decades, ragged sizes (M, N, K not multiples
   of the 128 x 64 x 32 tiles), against an extended-precision reference: error <= 1e-13 of
   sum_k |A_ik B_jk|, and against cuBLAS FP64.
