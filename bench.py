@@ -41,7 +41,7 @@ def parse():
     p.add_argument("--workload", default="L24_all_sectors", choices=["L24_all_sectors", "L80_k0_quench"],
                    help="L24_all_sectors: every sector of L = 24, H_eff and all eigenvalues for two h_x; "
                         "L80_k0_quench: the L = 80 quench, 64 (h_x, cutoff) variants, 2000 times")
-    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--e2e-steps", type=int, default=2, help="end-to-end steps (0: skip, for profiler runs)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-budget-s", type=float, default=12.0)
     p.add_argument("--no-screening", action="store_true")
@@ -449,7 +449,7 @@ def run_gb300(args):
     # state tables, the step, and the eigenvalues read back to pinned host memory
     host_ev = torch.empty(len(w.h_x) * n_states, dtype=torch.float64, pin_memory=True)
     e2e_s, h2d = [], 0
-    for k in range(max(1, args.e2e_steps)):
+    for k in range(args.e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         b2 = tgba.tgba_build_basis(w.L, w.h_z, w.sectors, w.max_qp, w.e_cut)
@@ -462,7 +462,7 @@ def run_gb300(args):
         e2e_s.append(time.perf_counter() - t0)
         h2d = tgba.tgba_profile(b2)["upload_bytes"]
         tgba.tgba_basis_free(b2)
-    e2e_value = world * n_el / statistics.mean(e2e_s)
+    e2e_value = world * n_el / statistics.mean(e2e_s) if e2e_s else None
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -580,7 +580,7 @@ def run_gb300_quench(args):
                 "terms_K": prof["quench_terms"]}
     host_mx = torch.empty(nv * n_t, dtype=torch.float64, pin_memory=True)
     e2e_s, h2d = [], 0
-    for _ in range(max(1, args.e2e_steps)):
+    for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         b2 = tgba.tgba_build_basis(w.L, w.h_z, w.sectors, w.max_qp, w.e_cut, w.max_per_parity)
@@ -607,8 +607,8 @@ def run_gb300_quench(args):
                                "gflops": prof["pfaffian_flops"] / (pf_ms * 1e-3) / 1e9,
                                "frac": prof["pfaffian_flops"] / (pf_ms * 1e-3) / 1e9 / peak_gflops},
             "clocks": clk,
-            "e2e": {"value": world * n_el / statistics.mean(e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": nv * n_t * 8},
+            "e2e": {"value": world * n_el / statistics.mean(e2e_s) if e2e_s else None, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": nv * n_t * 8},
             "gpu_launches": launches}
     if rank == 0:
         print(json.dumps(line), flush=True)
