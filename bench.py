@@ -48,13 +48,15 @@ def parse():
     p.add_argument("--no-solver-comparison", action="store_true",
                    help="skip the one-off native vs cuSOLVER eigen-solver timing after the timed steps")
     g = p.add_argument_group("single stage on a small seeded case (for kernel profilers: ncu -k ... -c ...)")
-    g.add_argument("--stage", choices=["eig", "pfaffian", "direct"],
+    g.add_argument("--stage", choices=["eig", "pfaffian", "direct", "dgemm"],
                    help="run one stage --reps times and print its CUDA-event timings instead of the benchmark")
     g.add_argument("--sectors", type=int, nargs="+", default=[0, 1, 2, 3])
     g.add_argument("--pairs", type=int, default=20000)
     g.add_argument("--L", type=int, default=None)
     g.add_argument("--hx", type=float, nargs="+", default=None)
     g.add_argument("--reps", type=int, default=1)
+    g.add_argument("--mnk", type=int, nargs=3, default=[8192, 128, 20000],
+                   help="dgemm stage: C (M x N) = A (M x K) B^T (N x K) on the tensor cores")
     return p.parse_args()
 
 
@@ -601,7 +603,11 @@ def run_gb300_quench(args):
                        "chi": [int(c) for c in chi[::len(inputs.QUENCH_L80_HX)]], "t_max": q["t_max"], "n_t": n_t,
                        "l2": "inputs larger than L2 (3.2 GB X block per step)"},
             "roofline": roofline,
-            "stages_ms": {"table": tab_ms, "pfaffian": pf_ms, "quench_propagation": q_ms,
+            "stages_ms": {"table": tab_ms, "pfaffian": pf_ms,
+                          "quench_slicing_and_bounds": statistics.mean(p["quench_prep_ms"] for p in profs),
+                          "quench_propagation": q_ms,
+                          "quench_moments": statistics.mean(p["quench_gram_ms"] for p in profs),
+                          "quench_time_sums": statistics.mean(p["quench_eval_ms"] for p in profs),
                           "quench_rest": ms - tab_ms - pf_ms - q_ms},
             "pfaffian_stage": {"ms": pf_ms, "elements_per_s": n_el / (pf_ms * 1e-3),
                                "gflops": prof["pfaffian_flops"] / (pf_ms * 1e-3) / 1e9,
@@ -636,6 +642,27 @@ def run_stage(args):
     L = args.L or w.L
     hx = args.hx or [w.h_x[0]]
     torch.cuda.set_device(0)
+    if args.stage == "dgemm":
+        # FP64 product on the tensor cores: 2 M N K FP64 flops, 21 BF16 slice products of each
+        M, N, K = args.mnk
+        g = torch.Generator(device="cuda").manual_seed(inputs.SEED)
+        A = torch.randn(M, K, dtype=torch.float64, device="cuda", generator=g)
+        B = torch.randn(N, K, dtype=torch.float64, device="cuda", generator=g)
+        C = torch.empty(N, M, dtype=torch.float64, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        times = []
+        for _ in range(max(1, args.reps)):
+            torch.cuda.synchronize()
+            e0.record()
+            tgba.tgba_dgemm_tc(M, N, K, A, K, B, K, C, M)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        err = ((C.T - A @ B.T).abs().max() / (A.abs() @ B.abs().T).max()).item()
+        best = min(times)
+        print("stage=dgemm M=%d N=%d K=%d ms=%s fp64_equiv_tflops=%.2f max_rel_err=%.2e"
+              % (M, N, K, [round(t, 3) for t in times], 2.0 * M * N * K / best / 1e9, err))
+        return 0
     b = tgba.tgba_build_basis(L, w.h_z, args.sectors, w.max_qp, w.e_cut)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     try:

@@ -325,7 +325,9 @@ tgba_status tgba_table_noalloc(int32_t L, double J, double h_z, double* table_de
  * quench_ms: device time of the last batched Chebyshev propagation of tgba_quench (the graph of
  * its K steps over all variants); quench_terms: K; quench_flops: its algorithmic FP64 flops,
  * K sum over variants of 8 n_NS n_R (two real vectors, both off-diagonal blocks, one FMA per
- * entry). */
+ * entry); quench_prep_ms, quench_gram_ms, quench_eval_ms: host-clock times of its other
+ * stages (the slicing of X and the Lanczos bounds; the moments; the Bessel sums over the time
+ * grid). */
 typedef struct {
   double table_ms, pfaffian_ms, pfaffian_flops;
   int64_t pfaffian_launches, kernel_launches, upload_bytes, evaluated;
@@ -336,6 +338,7 @@ typedef struct {
   int32_t eig_cluster, pad_;
   double quench_ms, quench_flops;
   int64_t quench_terms;
+  double quench_prep_ms, quench_gram_ms, quench_eval_ms;
 } tgba_prof;
 tgba_status tgba_profile(tgba_basis b, tgba_prof* out);
 

@@ -677,6 +677,9 @@ tgba_status tgba_profile(tgba_basis h, tgba_prof* out) {
   }
   out->quench_flops = b->quench_flops;
   out->quench_terms = b->quench_terms;
+  out->quench_prep_ms = b->quench_prep_ms;
+  out->quench_gram_ms = b->quench_gram_ms;
+  out->quench_eval_ms = b->quench_eval_ms;
   out->eig_cluster = b->eig_cluster;
   return TGBA_OK;
 }

@@ -30,9 +30,8 @@
 // step slices the current vectors, and the output tiles of each step skip the (row block,
 // column block) pairs that no variant's kept set reaches.  The K steps are captured into one
 // CUDA graph.
-#include <cublas_v2.h>
-
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -278,10 +277,6 @@ int blocks_for(int64_t work) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
 }
 
-tgba_status blas_fail(cublasStatus_t s, const char* what) {
-  return fail(TGBA_ECUDA, std::string("cuBLAS ") + what + " failed with status " + std::to_string((int)s));
-}
-
 // extreme eigenvalues of the symmetric tridiagonal matrix (a [m], b [m] with b[0] unused) by
 // bisection on Sturm counts
 void tridiag_extremes(const double* a, const double* b, int m, double* lo, double* hi) {
@@ -358,6 +353,12 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
   const int64_t n_un = kn_max + kr_max;
   const double cabs = std::hypot(b.c0_host[0], b.c0_host[1]);
   const int TR = emu_tile_rows_a(), TC = emu_tile_rows_b();
+  // stage times (host clock around synchronised sections)
+  using clk = std::chrono::steady_clock;
+  TGBA_CUDA(cudaStreamSynchronize(st));
+  const auto t_start = clk::now();
+  auto ms_since = [](clk::time_point t0) { return std::chrono::duration<double, std::milli>(clk::now() - t0).count(); };
+  b.quench_prep_ms = b.quench_gram_ms = b.quench_eval_ms = 0.0;
   tgba_status r = emu_prepare(b);
   if (r != TGBA_OK) return r;
   // ---- Q sliced in both orientations: A_ns (NS rows, K = R) and A_r (R rows, K = NS)
@@ -556,6 +557,7 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
     TGBA_CUDA(cudaGetLastError());
     ++b.launches;
     TGBA_CUDA(cudaStreamSynchronize(st));
+    b.quench_prep_ms = ms_since(t_start);     // slicing of Q, Lanczos, set-up (last attempt)
     // the K steps of all variants, captured once and launched as one graph
     TGBA_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
     cudaStream_t keep = st;
@@ -612,83 +614,103 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
         continue;                               // redo with Gershgorin bounds
       }
     }
-    // ---- moments (tensor-core FP64 products) and <sigma^x>(t), one variant at a time
+    // ---- moments and <sigma^x>(t), one variant at a time, with the variant's own number of
+    // terms K_v <= K (the other columns' longer expansions cost it nothing): the Gram matrices
+    // of its first K_v + 1 vectors and the Bessel sums over the whole time grid are tensor-core
+    // FP64 products as well
     int64_t chi_max = 0;
     for (const ChebVariant& v : vars) chi_max = std::max<int64_t>(chi_max, v.kn + v.kr);
-    const int nb = std::min(dt_n, 256);
-    const int m_start = [&] {
-      int ms = K + 30 + (int)std::ceil(std::sqrt(40.0 * K));
-      return ms + (ms & 1);
-    }();
-    std::vector<EmuTile> tg;
-    for (int rb = 0; rb * TR < K1; ++rb)
-      for (int cb = 0; cb * TC < K1; ++cb) tg.push_back(EmuTile{rb, cb, (int32_t)std::min<int64_t>(TC, r16(K1 - cb * TC)), 0});
-    const size_t sa = emu_operand_elems(K1, (int)chi_max, TR), sb = emu_operand_elems(K1, (int)chi_max, TC);
+    std::vector<int> Kv(vars.size());
+    for (size_t v = 0; v < vars.size(); ++v) {
+      const double xmax = R[v] * t_max;
+      Kv[v] = std::min(K, (int)std::ceil(xmax + 10.0 * std::cbrt(xmax) + 30.0));
+    }
+    const int64_t nt = std::max(1, dt_n);
+    const size_t sa = std::max(emu_operand_elems(K1, (int)chi_max, TR), emu_operand_elems(K1, K1, TR));
+    const size_t sb = std::max(emu_operand_elems(K1, (int)chi_max, TC), emu_operand_elems((int)nt, K1, TC));
+    const size_t n_tiles_max = (size_t)((K1 + TR - 1) / TR) * (size_t)std::max<int64_t>((K1 + TC - 1) / TC, (nt + TC - 1) / TC);
     DevBuf mbuf(st);
-    const size_t mdoubles = 4 * (size_t)K1 * K1 + 2 * (size_t)K1 * nb + chi_max + 8;
-    TGBA_CUDA(cudaMallocAsync(&mbuf.p, mdoubles * 8 + (2 * sa + 2 * sb) * 2 + 4 * (size_t)K1 * 4 +
-                                           tg.size() * sizeof(EmuTile) + 1024, st));
+    const size_t mdoubles = 4 * (size_t)K1 * K1 + 2 * (size_t)K1 * nt + chi_max + 8;
+    TGBA_CUDA(cudaMallocAsync(&mbuf.p, mdoubles * 8 + (2 * sa + 2 * sb) * 2 + 4 * ((size_t)K1 + nt) * 4 +
+                                           n_tiles_max * sizeof(EmuTile) + 1024, st));
     double* Grr = (double*)mbuf.p;
     double* Gii = Grr + (size_t)K1 * K1;
     double* Gri = Gii + (size_t)K1 * K1;
     double* Gam = Gri + (size_t)K1 * K1;
-    double* Ab = Gam + (size_t)K1 * K1;
-    double* GA = Ab + (size_t)K1 * nb;
-    double* Ek = GA + (size_t)K1 * nb;
+    double* Ab = Gam + (size_t)K1 * K1;                   // a_k(t): [t][K_v + 1]
+    double* GA = Ab + (size_t)K1 * nt;                    // Gamma a(t): column-major (K_v + 1) x n_t
+    double* Ek = GA + (size_t)K1 * nt;
     double* d01 = Ek + chi_max;
     EmuTile* dtg = (EmuTile*)(((uintptr_t)(d01 + 8) + 15) & ~(uintptr_t)15);
-    __nv_bfloat16* Vr = (__nv_bfloat16*)(((uintptr_t)(dtg + tg.size()) + 255) & ~(uintptr_t)255);
+    __nv_bfloat16* Vr = (__nv_bfloat16*)(((uintptr_t)(dtg + n_tiles_max) + 255) & ~(uintptr_t)255);
     __nv_bfloat16* Vi = Vr + sa;
     __nv_bfloat16* Wr = Vi + sa;
     __nv_bfloat16* Wi = Wr + sb;
     int* evr = (int*)(Wi + sb);
     int* evi = evr + K1;
     int* ewr = evi + K1;
-    int* ewi = ewr + K1;
-    cublasHandle_t bh = (cublasHandle_t)b.blas;
-    const double one = 1.0, zero = 0.0;
-    cublasStatus_t cs;
+    int* ewi = ewr + (K1 > nt ? K1 : nt);
+    auto grid_tiles = [&](int64_t rows, int64_t cols, int64_t kdim) {
+      std::vector<EmuTile> t;
+      for (int64_t rb = 0; rb * TR < rows; ++rb)
+        for (int64_t cb = 0; cb * TC < cols; ++cb)
+          t.push_back(EmuTile{(int32_t)rb, (int32_t)cb, (int32_t)std::min<int64_t>(TC, r16(cols - cb * TC)),
+                              (int32_t)((kdim + emu_k_block() - 1) / emu_k_block())});
+      return t;
+    };
     for (int j = 0; j < (int)ord.size(); ++j) {
       const ChebVariant& vv = vars[ord[j]];
       const int v = ord[j];
+      const int k1 = Kv[v] + 1;
       const int64_t kn = vv.kn, kr = vv.kr, chi = kn + kr;
       const double* vre = V + (size_t)(2 * j) * n_un;       // column 2j of step 0; step k at + k S
+      TGBA_CUDA(cudaStreamSynchronize(st));
+      const auto t_gram = clk::now();
       kept_energy<<<blocks_for(chi), 256, 0, st>>>(kn, kr, kn_max, E, Ek);
       cheb_dot01<<<1, kRedThreads, 0, st>>>(n_un, vre, vre + S, d01);
       b.launches += 2;
-      std::vector<EmuTile> tgv(tg);
-      for (EmuTile& t : tgv) t.nkb = (int32_t)((chi + emu_k_block() - 1) / emu_k_block());
+      const std::vector<EmuTile> tgv = grid_tiles(k1, k1, chi);
       TGBA_CUDA(cudaMemcpyAsync(dtg, tgv.data(), tgv.size() * sizeof(EmuTile), cudaMemcpyHostToDevice, st));
       // rows k of V (K = the kept rows in their own order: kn NS rows, then kr R rows)
       const int64_t jump = kn_max - kn;
-      if ((r = emu_slice(b, vre, S, 1, (int)kn, jump, nullptr, 0.0, K1, (int)chi, TR, Vr, evr, st)) != TGBA_OK) return r;
-      if ((r = emu_slice(b, vre + n_un, S, 1, (int)kn, jump, nullptr, 0.0, K1, (int)chi, TR, Vi, evi, st)) != TGBA_OK)
+      if ((r = emu_slice(b, vre, S, 1, (int)kn, jump, nullptr, 0.0, k1, (int)chi, TR, Vr, evr, st)) != TGBA_OK) return r;
+      if ((r = emu_slice(b, vre + n_un, S, 1, (int)kn, jump, nullptr, 0.0, k1, (int)chi, TR, Vi, evi, st)) != TGBA_OK)
         return r;
-      if ((r = emu_slice(b, vre, S, 1, (int)kn, jump, Ek, ec[v], K1, (int)chi, TC, Wr, ewr, st)) != TGBA_OK) return r;
-      if ((r = emu_slice(b, vre + n_un, S, 1, (int)kn, jump, Ek, ec[v], K1, (int)chi, TC, Wi, ewi, st)) != TGBA_OK)
+      if ((r = emu_slice(b, vre, S, 1, (int)kn, jump, Ek, ec[v], k1, (int)chi, TC, Wr, ewr, st)) != TGBA_OK) return r;
+      if ((r = emu_slice(b, vre + n_un, S, 1, (int)kn, jump, Ek, ec[v], k1, (int)chi, TC, Wi, ewi, st)) != TGBA_OK)
         return r;
-      if ((r = emu_gemm(b, Vr, evr, K1, (int)chi, Wr, ewr, K1, (int)chi, dtg, (int)tgv.size(), Grr, K1, st)) != TGBA_OK)
+      if ((r = emu_gemm(b, Vr, evr, k1, (int)chi, Wr, ewr, k1, (int)chi, dtg, (int)tgv.size(), Grr, k1, st)) != TGBA_OK)
         return r;
-      if ((r = emu_gemm(b, Vi, evi, K1, (int)chi, Wi, ewi, K1, (int)chi, dtg, (int)tgv.size(), Gii, K1, st)) != TGBA_OK)
+      if ((r = emu_gemm(b, Vi, evi, k1, (int)chi, Wi, ewi, k1, (int)chi, dtg, (int)tgv.size(), Gii, k1, st)) != TGBA_OK)
         return r;
-      if ((r = emu_gemm(b, Vr, evr, K1, (int)chi, Wi, ewi, K1, (int)chi, dtg, (int)tgv.size(), Gri, K1, st)) != TGBA_OK)
+      if ((r = emu_gemm(b, Vr, evr, k1, (int)chi, Wi, ewi, k1, (int)chi, dtg, (int)tgv.size(), Gri, k1, st)) != TGBA_OK)
         return r;
-      cheb_gamma<<<blocks_for((int64_t)K1 * K1), 256, 0, st>>>(K1, Grr, Gii, Gri, Gam);
+      cheb_gamma<<<blocks_for((int64_t)k1 * k1), 256, 0, st>>>(k1, Grr, Gii, Gri, Gam);
       ++b.launches;
       double h01 = 0.0;
       TGBA_CUDA(cudaMemcpyAsync(&h01, d01, sizeof(double), cudaMemcpyDeviceToHost, st));
-      TGBA_CUDA(cudaStreamSynchronize(st));            // also: tgv may be reused by the next variant
+      TGBA_CUDA(cudaStreamSynchronize(st));            // also: the tile list is reused below
+      b.quench_gram_ms += ms_since(t_gram);
+      const auto t_eval = clk::now();
+      // a_k(t) for the whole grid, Gamma a(t) (Gamma symmetric: its rows are its columns), the sums
       const double scale = 1.0 / (b.L * vv.hx * vv.norm2);
-      for (int t0 = 0; t0 < dt_n; t0 += nb) {
-        const int cnt = std::min(nb, dt_n - t0);
-        cheb_bessel<<<(cnt + 127) / 128, 128, 0, st>>>(cnt, t0, dt, R[v], K, m_start, Ab);
-        cs = cublasDgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, K1, cnt, K1, &one, Gam, K1, Ab, K1, &zero, GA, K1);
-        if (cs != CUBLAS_STATUS_SUCCESS) return blas_fail(cs, "gamma a");
-        cheb_mx<<<(cnt * 32 + 255) / 256, 256, 0, st>>>(K1, cnt, Ab, GA, R[v] * h01, scale,
-                                                        mx + (int64_t)vv.out * n_t + t0);
-        b.launches += 2;
-      }
+      const int ms = [&] {
+        int m0 = Kv[v] + 30 + (int)std::ceil(std::sqrt(40.0 * Kv[v]));
+        return m0 + (m0 & 1);
+      }();
+      cheb_bessel<<<(int)((nt + 127) / 128), 128, 0, st>>>((int)nt, 0, dt, R[v], Kv[v], ms, Ab);
+      ++b.launches;
+      const std::vector<EmuTile> tt = grid_tiles(k1, nt, k1);
+      TGBA_CUDA(cudaMemcpyAsync(dtg, tt.data(), tt.size() * sizeof(EmuTile), cudaMemcpyHostToDevice, st));
+      if ((r = emu_slice(b, Gam, k1, 1, k1, 0, nullptr, 0.0, k1, k1, TR, Vr, evr, st)) != TGBA_OK) return r;
+      if ((r = emu_slice(b, Ab, k1, 1, k1, 0, nullptr, 0.0, (int)nt, k1, TC, Wr, ewi, st)) != TGBA_OK) return r;
+      if ((r = emu_gemm(b, Vr, evr, k1, k1, Wr, ewi, (int)nt, k1, dtg, (int)tt.size(), GA, k1, st)) != TGBA_OK) return r;
+      cheb_mx<<<(int)((nt * 32 + 255) / 256), 256, 0, st>>>(k1, (int)nt, Ab, GA, R[v] * h01, scale,
+                                                              mx + (int64_t)vv.out * n_t);
+      ++b.launches;
       TGBA_CUDA(cudaGetLastError());
+      TGBA_CUDA(cudaStreamSynchronize(st));
+      b.quench_eval_ms += ms_since(t_eval);
     }
     b.quench_terms = K;
     TGBA_CUDA(cudaStreamSynchronize(st));

@@ -162,6 +162,7 @@ struct Basis {
   int emu_sms = 0;                 // SMs for the tensor-core FP64 products (emu_prepare)
   int quench_terms = 0;            // Chebyshev terms K of the last batched quench propagation
   double quench_flops = 0;         // its algorithmic FP64 flops (K sum 8 n_NS n_R)
+  double quench_prep_ms = 0, quench_gram_ms = 0, quench_eval_ms = 0;   // its other stages
   cudaEvent_t q_ev[2] = {nullptr, nullptr};   // around its graph launch
   bool q_ev_recorded = false;
   double* d_eig_a = nullptr; double* d_eig_w = nullptr; double* d_eig_work = nullptr;

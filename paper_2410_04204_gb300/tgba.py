@@ -45,7 +45,9 @@ class _Prof(ctypes.Structure):
                 ("tune_mode", ctypes.c_int32), ("tune_threads", ctypes.c_int32), ("tune_ms", ctypes.c_double * 8),
                 ("tridiag_ms", ctypes.c_double), ("bisect_ms", ctypes.c_double), ("tridiag_flops", ctypes.c_double),
                 ("eig_matrices", ctypes.c_int64), ("eig_cluster", ctypes.c_int32), ("pad_", ctypes.c_int32),
-                ("quench_ms", ctypes.c_double), ("quench_flops", ctypes.c_double), ("quench_terms", ctypes.c_int64)]
+                ("quench_ms", ctypes.c_double), ("quench_flops", ctypes.c_double), ("quench_terms", ctypes.c_int64),
+                ("quench_prep_ms", ctypes.c_double), ("quench_gram_ms", ctypes.c_double),
+                ("quench_eval_ms", ctypes.c_double)]
 
 
 _lib = None
