@@ -313,33 +313,41 @@ __global__ void __launch_bounds__(kThreads, 1) dgemm_tc_kernel(GemmArgs g) {
   }
 }
 
-// Row exponents: e[i] = smallest e with max_k |X(i, k)| <= 2^e (0 for a zero row).  One warp per row.
+// GB300's FP64 pipe is slow, so the slicing works on the bit patterns with integer operations
+// (only the optional weight takes two FP64 operations per element).
+__device__ __forceinline__ double weighted(const double* __restrict__ src, int64_t off, const double* __restrict__ w,
+                                          double w_shift, int k) {
+  const double x = src[off];
+  return w ? x * (w[k] - w_shift) : x;
+}
+
+// Row exponents: e[i] = smallest e with max_k |X(i, k)| < 2^e (0 for a zero row), from the
+// largest magnitude's exponent field (integer maximum of the magnitudes' bit patterns).  One
+// warp per row.
 __global__ void row_exponents(int rows, int K, const double* __restrict__ src, int64_t row_stride, int64_t k_stride,
                               int k_split, int64_t k_jump, const double* __restrict__ w, double w_shift,
                               int* __restrict__ e) {
   const int lane = threadIdx.x & 31;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < rows; i += (gridDim.x * blockDim.x) >> 5) {
-    double m = 0.0;
+    unsigned long long m = 0ull;
     for (int k = lane; k < K; k += 32) {
       const int64_t off = (int64_t)i * row_stride + (int64_t)k * k_stride + (k >= k_split ? k_jump : 0);
-      double x = src[off];
-      if (w) x *= w[k] - w_shift;
-      m = fmax(m, fabs(x));
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(weighted(src, off, w, w_shift, k));
+      m = max(m, bits & 0x7fffffffffffffffull);
     }
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) {
-      int ex = 0;
-      if (m > 0.0) {
-        frexp(m, &ex);                 // m = f 2^ex, f in [0.5, 1): m < 2^ex
-      }
-      e[i] = ex;
+      const int ef = (int)(m >> 52);                     // biased exponent of the largest magnitude
+      e[i] = m == 0ull ? 0 : (ef == 0 ? -1021 : ef - 1022);   // max < 2^(ef - 1022)
     }
   }
 }
 
 // Slices of X (rows x K, element (i, k) at src[i row_stride + k k_stride (+ k_jump for k >= k_split)],
-// optionally times w[k]) as tile images [row block][K block][slice][tile rows][32] (bf16, 64-byte
-// swizzle); rows and K beyond the matrix are zero.
+// optionally times w[k] - w_shift) as tile images [row block][K block][slice][tile rows][32] (bf16,
+// 64-byte swizzle); rows and K beyond the matrix are zero.  The value 2^-e x (|.| < 1) is rounded
+// to a 48-bit fixed-point integer F (from the mantissa and exponent fields), which is cut into
+// six balanced base-256 digits, d_p = round(F / 2^(40 - 8p)), F -= d_p 2^(40 - 8p).
 __global__ void slice_tiles(int rows, int K, const double* __restrict__ src, int64_t row_stride, int64_t k_stride,
                             int k_split, int64_t k_jump, const double* __restrict__ w, double w_shift,
                             const int* __restrict__ e, int tile_rows, int n_kb, __nv_bfloat16* __restrict__ out) {
@@ -350,23 +358,29 @@ __global__ void slice_tiles(int rows, int K, const double* __restrict__ src, int
     const int k = (int)(q % ((int64_t)n_kb * kKB));
     const int i = (int)(q / ((int64_t)n_kb * kKB));
     const int rb = i / tile_rows, r = i % tile_rows, kb = k / kKB, kk = k % kKB;
-    double x = 0.0;
+    long long F = 0;
     if (i < rows && k < K) {
       const int64_t off = (int64_t)i * row_stride + (int64_t)k * k_stride + (k >= k_split ? k_jump : 0);
-      x = src[off];
-      if (w) x *= w[k] - w_shift;
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(weighted(src, off, w, w_shift, k));
+      const int ef = (int)((bits >> 52) & 0x7ff);
+      if (ef != 0) {                                     // subnormals are below 2^-1022: they round to 0
+        const long long mant = (long long)((bits & 0x000fffffffffffffull) | 0x0010000000000000ull);
+        // |x| = mant 2^(ef - 1075); F = |x| 2^(48 - e) = mant 2^(ef - 1027 - e), a right shift
+        const int sh = 1027 + e[i] - ef;
+        if (sh <= 0) F = mant << (-sh);                  // only for |x| at the top of the range
+        else if (sh < 63) F = (mant + (1ll << (sh - 1))) >> sh;
+        if (bits >> 63) F = -F;
+      }
     }
     unsigned char* tile = (unsigned char*)out + ((size_t)rb * n_kb + kb) * kS * slice_bytes;
     const uint32_t o = sw64(r, kk);
-    double rr = (i < rows) ? ldexp(x, -e[i]) : 0.0;   // in [-1, 1]
-    double scale = 1.0;
 #pragma unroll
     for (int p = 0; p < kS; ++p) {
-      const double y = rr * 256.0;
-      const double d = rint(y);
-      rr = y - d;
-      *(__nv_bfloat16*)(tile + (size_t)p * slice_bytes + o) = __double2bfloat16(d * scale);
-      scale *= 0.00390625;                          // 2^-8
+      const int shp = 40 - 8 * p;
+      const long long d = shp > 0 ? ((F + (1ll << (shp - 1))) >> shp) : F;
+      F -= d << shp;
+      // d 2^(-8p): |d| <= 256, exact in FP32 and in BF16
+      *(__nv_bfloat16*)(tile + (size_t)p * slice_bytes + o) = __float2bfloat16_rn(ldexpf((float)d, -8 * p));
     }
   }
 }

@@ -13,13 +13,17 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
   return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 
-// Every data movement of the pivot exchange works on the two 32-bit halves of a double with
-// integer selects: a conditional 64-bit move written as a double select may otherwise become
-// a predicated FP64 add on the (1/64-rate) FP64 pipe.
+// Every data movement of the pivot exchange is an integer select of the 64-bit pattern, written
+// in inline PTX (selp.b64) so that the result is born as one 64-bit register pair: a select
+// written as a double select, or as two 32-bit selects reassembled into a double, was measured
+// to cost one FP64-pipe instruction (a DADD) per selected operand of a later FP64 operation.
 __device__ __forceinline__ double sel(bool s, double y, double x) {        // s ? y : x
-  const int lo = s ? __double2loint(y) : __double2loint(x);
-  const int hi = s ? __double2hiint(y) : __double2hiint(x);
-  return __hiloint2double(hi, lo);
+  unsigned long long r;
+  asm("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %3, 0;\n\tselp.b64 %0, %1, %2, p;\n\t}"
+      : "=l"(r)
+      : "l"((unsigned long long)__double_as_longlong(y)), "l"((unsigned long long)__double_as_longlong(x)),
+        "r"((int)s));
+  return __longlong_as_double((long long)r);
 }
 // The sign-bit XOR is written in inline PTX: as plain C++ the compiler recognises it as a
 // (conditional) floating-point negation and issues it on the FP64 pipe.
