@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--no-solver-comparison", action="store_true",
                    help="skip the one-off native vs cuSOLVER eigen-solver timing after the timed steps")
     g = p.add_argument_group("single stage on a small seeded case (for kernel profilers: ncu -k ... -c ...)")
-    g.add_argument("--stage", choices=["eig", "pfaffian", "direct", "dgemm"],
+    g.add_argument("--stage", choices=["eig", "pfaffian", "direct", "dgemm", "screen"],
                    help="run one stage --reps times and print its CUDA-event timings instead of the benchmark")
     g.add_argument("--sectors", type=int, nargs="+", default=[0, 1, 2, 3])
     g.add_argument("--pairs", type=int, default=20000)
@@ -299,16 +299,21 @@ def screening_leg(b24, tgba, inputs, torch, bf16_peak_tflops):
         flw = fl[M[:nns, None] + M[None, nns:]]
         tot = flw.sum().item()
         perfect = {str(tau): (flw * (absv < tau)).sum().item() / tot for tau in inputs.SCREEN_TAUS}
-        del absv, flw
+        del flw
         pred = torch.empty(nns * nr, dtype=torch.float32, device="cuda")
         t_inf = timed(lambda: tgba.tgba_screen_predict(s, b, 0, pred))
         del pred
         rows = []
+        xs = torch.empty(nns * nr, dtype=torch.complex128, device="cuda")
         for tau in inputs.SCREEN_TAUS:
             t_scr = timed(lambda: tgba.tgba_compute_x(b, s, tau, hx))
             ev, sc = tgba.tgba_x_stats(b)
-            rows.append({"tau": tau, "screened_fraction": sc / (ev + sc), "ms": round(t_scr, 2),
-                         "speedup": t_exact / t_scr})
+            tgba.tgba_x_export(b, 0, xs)
+            # pairs the network dropped although |V| >= tau (wrong drops: the error it makes)
+            wrong = ((xs.view(nns, nr) == 0) & (absv >= tau)).sum().item()
+            rows.append({"tau": tau, "screened_fraction": sc / (ev + sc), "wrongly_dropped_fraction": wrong / (ev + sc),
+                         "ms": round(t_scr, 2), "speedup": t_exact / t_scr})
+        del xs, absv
         floor_ms = nns * nr * 2.0 * 256 * 256 / (bf16_peak_tflops * 1e12) * 1e3
         best_saving = max(perfect.values()) * pf_exact
         out[name] = {"pairs": nns * nr, "exact_ms": round(t_exact, 2), "pfaffian_ms": round(pf_exact, 2),
@@ -642,6 +647,33 @@ def run_stage(args):
     L = args.L or w.L
     hx = args.hx or [w.h_x[0]]
     torch.cuda.set_device(0)
+    if args.stage == "screen":
+        # screener inference (tensor cores) on every pair of the L = 40, k = 0 basis, with a
+        # seeded untrained network: prediction, then the screened Pfaffian stage
+        w3 = inputs.DSF_L40
+        b = tgba.tgba_build_basis(w3.L, w3.h_z, [0], w3.max_qp, w3.e_cut)
+        s = tgba.tgba_screen_create(256, None, inputs.SEED)
+        try:
+            tgba.tgba_compute_x(b)
+            info = tgba.tgba_basis_info(b, 0, w3.max_qp)
+            pred = torch.empty(info["n_ns"] * info["n_r"], dtype=torch.float32, device="cuda")
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            times = []
+            for _ in range(max(1, args.reps)):
+                torch.cuda.synchronize()
+                e0.record()
+                tgba.tgba_screen_predict(s, b, 0, pred)
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            tgba.tgba_compute_x(b, s, 1e-8, w3.h_x[0])
+            torch.cuda.synchronize()
+            assert torch.isfinite(pred).all()
+            print("stage=screen L=%d pairs=%d predict_ms=%s" % (w3.L, pred.numel(), [round(t, 3) for t in times]))
+        finally:
+            tgba.tgba_screen_free(s)
+            tgba.tgba_basis_free(b)
+        return 0
     if args.stage == "dgemm":
         # FP64 product on the tensor cores: 2 M N K FP64 flops, 21 BF16 slice products of each
         M, N, K = args.mnk

@@ -15,20 +15,23 @@
 //    Diagonals 3..5 share a fourth accumulator, whose FP32 rounding stays near 2^-48 of the
 //    leading term (measured: an earlier base-128 split with the shared accumulator from
 //    diagonal 3 erred by up to 1.5e-12).
-//  * Chunks.  After every 128 K values the four accumulators are folded into a running sum per
-//    element kept as an unevaluated pair of FP32 numbers (hi + lo, error-free two-sum: about
-//    48 bits), by CUDA-core FP32 arithmetic, while the tensor cores fill the second set of
-//    accumulators (two sets of 4 x 64 columns = all 512 TMEM columns).  At the end of the tile
-//    C_ij = 2^{e_i + f_j - 14} (hi + lo) in FP64.
+//  * Chunks.  After every 128 K values the four accumulators (4 x 128 columns = all 512 TMEM
+//    columns) are folded into a running sum per element kept as an unevaluated pair of FP32
+//    numbers (hi + lo, error-free two-sum: about 48 bits), by CUDA-core FP32 arithmetic, while
+//    the producer keeps loading the next stages.  At the end of the tile
+//    C_ij = 2^{e_i + f_j - 16} (hi + lo) in FP64.
 //  The error of C is about 1e-13 of sum_k |A_ik B_jk| (measured up to 1.1e-13), dominated by
 //  the FP32 rounding of the accumulator that the digit diagonals 3..5 share.
 //
-// Tiles: 128 rows of A x up to 64 rows of B (n_eff, a multiple of 16, per tile) x K in blocks of
-// 32 (64-byte rows, 64-byte swizzle).  The slices of one (row block, K block) are stored
+// Tiles: 128 rows of A x up to 128 rows of B (n_eff, a multiple of 16, per tile) x K in blocks
+// of 32 (64-byte rows, 64-byte swizzle).  The slices of one (row block, K block) are stored
 // contiguously, already in the shared-memory image the MMA descriptors read, so each stage is
-// two bulk copies (cp.async.bulk: 48 KB of A slices, 24 KB of B slices) completing on an
-// mbarrier.  Warp 0 issues the copies, warp 1 the MMAs (one thread each), warps 2-5 fold the
-// accumulators and write C.  Three smem stages, two accumulator sets.  Every wait is bounded: on
+// two bulk copies (cp.async.bulk: 48 KB of A slices, 48 KB of B slices) completing on an
+// mbarrier.  Warp 0 issues the copies, warp 1 the MMAs (one thread each), warps 2-9 fold the
+// accumulators and write C (each TMEM lane quarter by two warps, 64 columns each).  Two smem
+// stages.  N = 128 per MMA instead of 64 halves the shared-memory operand traffic per flop:
+// measured at N = 64, the tensor pipe was busy 72% of the active cycles for 31% of its peak
+// FLOP rate.  Every wait is bounded: on
 // timeout the kernel records TGBA_ETIMEOUT's status bit, every role leaves, in-flight copies and
 // MMAs are waited for (bounded) and the tensor memory is freed.
 #include <cuda_bf16.h>
@@ -45,16 +48,17 @@ namespace {
 constexpr int kS = 6;                     // slices per operand (base-256 digits)
 constexpr int kKB = 32;                   // K per block (64-byte rows)
 constexpr int kTMr = 128;                 // rows of A per tile
-constexpr int kTNr = 64;                  // rows of B per tile
+constexpr int kTNr = 128;                 // rows of B per tile
 constexpr int kChunkBlocks = 4;           // K blocks per exact FP32 chunk (128 K values)
 constexpr uint32_t kASlice = kTMr * kKB * 2;          // 8 KB
 constexpr uint32_t kBSlice = kTNr * kKB * 2;          // 4 KB
 constexpr uint32_t kAStage = kS * kASlice;            // 48 KB
-constexpr uint32_t kBStage = kS * kBSlice;            // 24 KB
-constexpr int kStages = 3;
+constexpr uint32_t kBStage = kS * kBSlice;            // 48 KB
+constexpr int kStages = 2;
 constexpr uint32_t kSmem = 1024 + kStages * (kAStage + kBStage) + 256;
 constexpr unsigned kWait = 1u << 24;                   // polls of a bounded wait
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -118,20 +122,19 @@ __device__ __forceinline__ void commit(uint64_t* b) {
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr)
       : "memory");
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 // hi + lo += x, error-free (Knuth's two-sum on hi, the error collected in lo)
@@ -157,7 +160,7 @@ struct GemmArgs {
   unsigned* status;
 };
 
-__global__ void __launch_bounds__(kThreads, 1) dgemm_tc_kernel(GemmArgs g) {
+__global__ void __maxnreg__(200) dgemm_tc_kernel(GemmArgs g) {   // 320 threads, one CTA per SM
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = su32(smem_raw);
   unsigned char* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -166,9 +169,9 @@ __global__ void __launch_bounds__(kThreads, 1) dgemm_tc_kernel(GemmArgs g) {
   uint64_t* bars = (uint64_t*)(sB + kStages * kBStage);
   uint64_t* full = bars;               // [kStages] stage loaded
   uint64_t* empty = bars + kStages;    // [kStages] stage consumed by the MMAs
-  uint64_t* accf = bars + 2 * kStages; // [2] accumulator set written
-  uint64_t* acce = accf + 2;           // [2] accumulator set read
-  uint32_t* tslot = (uint32_t*)(acce + 2);
+  uint64_t* accf = bars + 2 * kStages; // accumulators written (one set)
+  uint64_t* acce = accf + 1;           // accumulators read
+  uint32_t* tslot = (uint32_t*)(acce + 1);
   __shared__ volatile int s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -176,10 +179,8 @@ __global__ void __launch_bounds__(kThreads, 1) dgemm_tc_kernel(GemmArgs g) {
       bar_init(full + s, 1);
       bar_init(empty + s, 1);
     }
-    for (int s = 0; s < 2; ++s) {
-      bar_init(accf + s, 1);
-      bar_init(acce + s, 4);
-    }
+    bar_init(accf, 1);
+    bar_init(acce, kEpiWarps);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -221,10 +222,10 @@ __global__ void __launch_bounds__(kThreads, 1) dgemm_tc_kernel(GemmArgs g) {
         const EmuTile tl = g.tiles[t];
         const uint32_t id = idesc_f16(tl.n_eff);
         for (int kb0 = 0; kb0 < tl.nkb && !s_abort; kb0 += kChunkBlocks, ++chunk) {
-          const int set = chunk & 1;
-          if (!bar_wait(acce + set, ((chunk >> 1) & 1u) ^ 1u, &s_abort)) { atomicOr(g.status, kStTimeout); s_abort = 1; break; }
+          // the epilogue has read the previous chunk's accumulators
+          if (!bar_wait(acce, (chunk & 1u) ^ 1u, &s_abort)) { atomicOr(g.status, kStTimeout); s_abort = 1; break; }
           fence_after();
-          const uint32_t dbase = tmem + (uint32_t)set * 256u;
+          const uint32_t dbase = tmem;
           const int kb1 = min(tl.nkb, kb0 + kChunkBlocks);
           for (int kb = kb0; kb < kb1; ++kb, ++it) {
             const int st = it % kStages;
@@ -241,14 +242,14 @@ __global__ void __launch_bounds__(kThreads, 1) dgemm_tc_kernel(GemmArgs g) {
                 const bool first = kb == kb0 && p == 0 && q == (d < 3 ? d : 3);
 #pragma unroll
                 for (int ks = 0; ks < 2; ++ks)
-                  mma(dbase + (uint32_t)d * 64u, desc64(a0 + p * kASlice + ks * 32), desc64(b0 + q * kBSlice + ks * 32), id,
+                  mma(dbase + (uint32_t)d * 128u, desc64(a0 + p * kASlice + ks * 32), desc64(b0 + q * kBSlice + ks * 32), id,
                       (first && ks == 0) ? 0u : 1u);
               }
             commit(empty + st);                       // the stage's smem is free once these complete
             last = empty + st;
           }
-          commit(accf + set);                         // the chunk's accumulators are complete
-          last = accf + set;
+          commit(accf);                               // the chunk's accumulators are complete
+          last = accf;
         }
       }
       if (s_abort && last) {                          // MMAs still in flight finish before the dealloc
@@ -258,46 +259,50 @@ __global__ void __launch_bounds__(kThreads, 1) dgemm_tc_kernel(GemmArgs g) {
       }
     }
   } else {
-    // ------------------------------------------------------------------ epilogue (warps 2-5)
+    // ------------------------------------------------------------------ epilogue (warps 2-9)
+    constexpr int kCols = kTNr / 2;                   // columns per epilogue warp
     const int quad = warp & 3;                        // TMEM lanes 32 quad .. 32 quad + 31
+    const int half = (warp - 2) >> 2;                 // columns kCols half .. kCols half + kCols - 1
     const int r = quad * 32 + lane;                   // row of the tile
     uint32_t chunk = 0;
     for (int t = blockIdx.x; t < g.n_tiles && !s_abort; t += gridDim.x) {
       const EmuTile tl = g.tiles[t];
-      float hi[kTNr], lo[kTNr];
+      float hi[kCols], lo[kCols];                     // registers: every index below is a constant
 #pragma unroll
-      for (int c = 0; c < kTNr; ++c) { hi[c] = 0.f; lo[c] = 0.f; }
+      for (int c = 0; c < kCols; ++c) { hi[c] = 0.f; lo[c] = 0.f; }
       for (int kb0 = 0; kb0 < tl.nkb; kb0 += kChunkBlocks, ++chunk) {
-        const int set = chunk & 1;
-        if (!bar_wait(accf + set, (chunk >> 1) & 1u, &s_abort)) {
+        if (!bar_wait(accf, chunk & 1u, &s_abort)) {
           if (lane == 0) atomicOr(g.status, kStTimeout);
           s_abort = 1;
           break;
         }
         fence_after();
-        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)set * 256u;
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * kCols);
+        if (half * kCols < tl.n_eff) {
 #pragma unroll
-        for (int d = 0; d < 4; ++d)
+          for (int d = 0; d < 4; ++d)
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float v[32];
-            ld32(lane_base + (uint32_t)d * 64u + (uint32_t)h * 32u, v);
+            for (int h = 0; h < kCols / 16; ++h) {
+              float v[16];
+              ld16(lane_base + (uint32_t)d * (uint32_t)kTNr + (uint32_t)h * 16u, v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) two_sum_add(hi[h * 32 + j], lo[h * 32 + j], v[j]);
-          }
+              for (int j = 0; j < 16; ++j) two_sum_add(hi[h * 16 + j], lo[h * 16 + j], v[j]);
+            }
+        }
         fence_before();
         __syncwarp();
-        if (lane == 0) bar_arrive(acce + set);
+        if (lane == 0) bar_arrive(acce);
       }
       if (s_abort) break;
       const int i = tl.rb * kTMr + r;
       if (i < g.M) {
         const int e_i = g.ea[i];
-#pragma unroll 4
-        for (int c = 0; c < kTNr; ++c) {
+#pragma unroll
+        for (int cc = 0; cc < kCols; ++cc) {
+          const int c = half * kCols + cc;
           const int j = tl.cb * kTNr + c;
           if (c < tl.n_eff && j < g.N) {
-            const double v = ((double)hi[c] + (double)lo[c]);
+            const double v = ((double)hi[cc] + (double)lo[cc]);
             g.C[(int64_t)i + (int64_t)j * g.ldc] = ldexp(v, e_i + g.eb[j] - 16);
           }
         }
@@ -332,8 +337,11 @@ __global__ void row_exponents(int rows, int K, const double* __restrict__ src, i
     unsigned long long m = 0ull;
     for (int k = lane; k < K; k += 32) {
       const int64_t off = (int64_t)i * row_stride + (int64_t)k * k_stride + (k >= k_split ? k_jump : 0);
-      const unsigned long long bits = (unsigned long long)__double_as_longlong(weighted(src, off, w, w_shift, k));
-      m = max(m, bits & 0x7fffffffffffffffull);
+      unsigned long long bits;                           // magnitude bits (an integer AND, not fabs)
+      asm("and.b64 %0, %1, 0x7fffffffffffffff;"
+          : "=l"(bits)
+          : "l"((unsigned long long)__double_as_longlong(weighted(src, off, w, w_shift, k))));
+      m = max(m, bits);
     }
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) {

@@ -9,8 +9,13 @@
 
 namespace tgba {
 
+// The magnitude's bit pattern, as an integer AND in inline PTX: written in C++ the compiler
+// recognises the sign-bit mask as fabs and issues it on the FP64 pipe (measured: one DADD per
+// pivot candidate).
 __device__ __forceinline__ unsigned long long abs_bits(double x) {
-  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  unsigned long long r;
+  asm("and.b64 %0, %1, 0x7fffffffffffffff;" : "=l"(r) : "l"((unsigned long long)__double_as_longlong(x)));
+  return r;
 }
 
 // Every data movement of the pivot exchange is an integer select of the 64-bit pattern, written
