@@ -160,7 +160,7 @@ struct GemmArgs {
   unsigned* status;
 };
 
-__global__ void __maxnreg__(200) dgemm_tc_kernel(GemmArgs g) {   // 320 threads, one CTA per SM
+__global__ void __maxnreg__(184) dgemm_tc_kernel(GemmArgs g) {   // 320 threads x 184 registers, one CTA per SM
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = su32(smem_raw);
   unsigned char* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
