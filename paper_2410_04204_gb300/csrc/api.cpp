@@ -57,7 +57,7 @@ static void release(Basis* b) {
   void* ptrs[] = {b->d_E_ns, b->d_E_r, b->d_M_ns, b->d_M_r, b->d_sel_ns, b->d_sel_r, b->d_modes_ns, b->d_modes_r,
                   b->d_theta, b->d_nlab, b->d_table, b->d_c0, b->d_work, b->d_P, b->d_status,
                   b->d_eig_a, b->d_eig_w, b->d_eig_work, b->d_eig_info, b->d_scratch,
-                  b->d_reg_rects, b->d_counter, b->d_blas_ws};
+                  b->d_reg_rects, b->d_counter, b->d_blas_ws, b->d_emu_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int e = 0; e < 3; ++e) {

@@ -319,23 +319,28 @@ struct DevBuf {
 int64_t r16(int64_t x) { return (x + 15) / 16 * 16; }
 
 // Output tiles of one off-diagonal product: rows (row blocks of 128) x the vector columns (blocks
-// of 64).  Column c needs output rows below out_c[c] and K values below k_c[c]; a tile keeps the
-// columns up to the last one that needs any of its rows, and the K range they need.
+// of 128).  Column c needs output rows below out_c[c] and K values below k_c[c]; a tile keeps the
+// columns up to the last one that needs any of its rows, the K range they need, and per group of
+// 16 columns the K range of its columns that need the tile's rows (one K block for a group with
+// none).
 std::vector<EmuTile> product_tiles(int64_t rows, int64_t cols, const std::vector<int64_t>& out_c,
                                    const std::vector<int64_t>& k_c) {
   const int TR = emu_tile_rows_a(), TC = emu_tile_rows_b(), KB = emu_k_block();
   std::vector<EmuTile> t;
   for (int64_t rb = 0; rb * TR < rows; ++rb)
     for (int64_t cb = 0; cb * TC < cols; ++cb) {
-      int64_t last = -1, kmax = 0;
+      int64_t last = -1, kmax = 0, kg[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       for (int64_t c = cb * TC; c < std::min(cols, (cb + 1) * TC); ++c)
         if (out_c[c] > rb * TR && k_c[c] > 0) {
           last = c - cb * TC;
           kmax = std::max(kmax, k_c[c]);
+          kg[last / 16] = std::max(kg[last / 16], k_c[c]);
         }
       if (last < 0) continue;
-      t.push_back(EmuTile{(int32_t)rb, (int32_t)cb, (int32_t)std::min<int64_t>(TC, r16(last + 1)),
-                          (int32_t)((kmax + KB - 1) / KB)});
+      EmuTile e{(int32_t)rb, (int32_t)cb, (int32_t)std::min<int64_t>(TC, r16(last + 1)),
+                (int32_t)((kmax + KB - 1) / KB)};
+      for (int q = 0; q < 8; ++q) e.gkb[q] = (int16_t)std::max<int64_t>(1, (kg[q] + KB - 1) / KB);
+      t.push_back(e);
     }
   return t;
 }
@@ -384,19 +389,19 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
     cudaFreeAsync(Qt, st);
     if (r != TGBA_OK) return r;
   }
-  // B-operand slices of the current vectors (at most 128 + 63 columns per product)
+  // B-operand slices of the current vectors (the columns padded to whole tiles)
   auto vec_slices = [&](int cols) {
     return std::max(emu_operand_elems(cols, (int)std::max<int64_t>(1, kr_max), TC),
                     emu_operand_elems(cols, (int)std::max<int64_t>(1, kn_max), TC));
   };
   // off-diagonal product Y = A x on the union layout (x, Y: n_un x cols, ld n_un)
-  auto offdiag = [&](const double* x, double* Y, int cols, __nv_bfloat16* Bs, int* eb, const EmuTile* t_ns, int n_ns,
-                     const EmuTile* t_r, int n_r) -> tgba_status {
+  auto offdiag = [&](const double* x, double* Y, int cols, __nv_bfloat16* Bs, int* eb, EmuTile* t_ns, int n_ns,
+                     int64_t c_ns, EmuTile* t_r, int n_r, int64_t c_r) -> tgba_status {
     tgba_status q = emu_slice(b, x + kn_max, n_un, 1, (int)kr_max, 0, nullptr, 0.0, cols, (int)kr_max, TC, Bs, eb, st);
-    if (q == TGBA_OK) q = emu_gemm(b, A_ns, e_ns, (int)kn_max, (int)kr_max, Bs, eb, cols, (int)kr_max, t_ns, n_ns, Y, n_un, st);
+    if (q == TGBA_OK) q = emu_gemm(b, A_ns, e_ns, (int)kn_max, (int)kr_max, Bs, eb, cols, (int)kr_max, t_ns, n_ns, c_ns, Y, n_un, st);
     if (q == TGBA_OK) q = emu_slice(b, x, n_un, 1, (int)kn_max, 0, nullptr, 0.0, cols, (int)kn_max, TC, Bs, eb, st);
     if (q == TGBA_OK)
-      q = emu_gemm(b, A_r, e_r, (int)kr_max, (int)kn_max, Bs, eb, cols, (int)kn_max, t_r, n_r, Y + kn_max, n_un, st);
+      q = emu_gemm(b, A_r, e_r, (int)kr_max, (int)kn_max, Bs, eb, cols, (int)kn_max, t_r, n_r, c_r, Y + kn_max, n_un, st);
     return q;
   };
   // ---- Lanczos bounds on the union for each distinct field
@@ -410,7 +415,9 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
     const int m = (int)std::min<int64_t>(kLanczosSteps, n_un);
     std::vector<int64_t> out_ns(nhp, 0), out_r(nhp, 0), k_ns(nhp, 0), k_r(nhp, 0);
     for (int i = 0; i < nh; ++i) { out_ns[i] = kn_max; k_ns[i] = kr_max; out_r[i] = kr_max; k_r[i] = kn_max; }
-    const std::vector<EmuTile> tn = product_tiles(kn_max, nhp, out_ns, k_ns), tr = product_tiles(kr_max, nhp, out_r, k_r);
+    std::vector<EmuTile> tn = product_tiles(kn_max, nhp, out_ns, k_ns), tr = product_tiles(kr_max, nhp, out_r, k_r);
+    const int64_t cn = emu_number_tiles(tn), cr_ = emu_number_tiles(tr);
+    if (cn < 0 || cr_ < 0) return fail(TGBA_EINVAL, "quench product tiles");
     DevBuf buf(st);
     const size_t vs = vec_slices(nhp);
     const size_t doubles = (size_t)4 * n_un * nhp + 2 * (size_t)m * nhp + nhp;
@@ -439,7 +446,7 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
     double *qp = q0, *qc = q1, *qn = q2;
     for (int j = 0; j < m; ++j) {
       if (coupled) {
-        if ((r = offdiag(qc, Y, nhp, Bs, eb, dt, (int)tn.size(), dt + tn.size(), (int)tr.size())) != TGBA_OK) return r;
+        if ((r = offdiag(qc, Y, nhp, Bs, eb, dt, (int)tn.size(), cn, dt + tn.size(), (int)tr.size(), cr_)) != TGBA_OK) return r;
       }
       lz_step<<<nh, kRedThreads, 0, st>>>(n_un, E, g, Y, qp, qc, qn, al, be, j, m);
       ++b.launches;
@@ -501,7 +508,9 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
       out_ns[2 * j + h] = v.kn; k_ns[2 * j + h] = v.kr;
       out_r[2 * j + h] = v.kr; k_r[2 * j + h] = v.kn;
     }
-  const std::vector<EmuTile> tn = product_tiles(kn_max, ncolp, out_ns, k_ns), tr = product_tiles(kr_max, ncolp, out_r, k_r);
+  std::vector<EmuTile> tn = product_tiles(kn_max, ncolp, out_ns, k_ns), tr = product_tiles(kr_max, ncolp, out_r, k_r);
+  const int64_t cn = emu_number_tiles(tn), cr_ = emu_number_tiles(tr);
+  if (cn < 0 || cr_ < 0) return fail(TGBA_EINVAL, "quench product tiles");
   const int dt_n = n_t;
   const double dt = n_t > 1 ? t_max / (n_t - 1) : 0.0;
   cudaStream_t cap = nullptr;
@@ -567,7 +576,7 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
     for (int k = 0; k < K && cr == TGBA_OK; ++k) {
       double* vk = V + (size_t)k * S;
       if (coupled)
-        cr = offdiag(vk, Y, ncolp, Bs, eb, dtl, (int)tn.size(), dtl + tn.size(), (int)tr.size());
+        cr = offdiag(vk, Y, ncolp, Bs, eb, dtl, (int)tn.size(), cn, dtl + tn.size(), (int)tr.size(), cr_);
       if (cr != TGBA_OK) break;
       cheb_step<<<blocks_for(S), 256, 0, cap>>>(n_un, kn_max, ncolp, E, prm, k == 0 ? 1.0 : 2.0, 1.0, Y, vk,
                                                  k == 0 ? nullptr : vk - S, vk + S);
@@ -650,12 +659,13 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
     int* evi = evr + K1;
     int* ewr = evi + K1;
     int* ewi = ewr + (K1 > nt ? K1 : nt);
-    auto grid_tiles = [&](int64_t rows, int64_t cols, int64_t kdim) {
+    auto grid_tiles = [&](int64_t rows, int64_t cols, int64_t kdim, int64_t& n_chunks) {
       std::vector<EmuTile> t;
       for (int64_t rb = 0; rb * TR < rows; ++rb)
         for (int64_t cb = 0; cb * TC < cols; ++cb)
           t.push_back(EmuTile{(int32_t)rb, (int32_t)cb, (int32_t)std::min<int64_t>(TC, r16(cols - cb * TC)),
                               (int32_t)((kdim + emu_k_block() - 1) / emu_k_block())});
+      n_chunks = emu_number_tiles(t);
       return t;
     };
     for (int j = 0; j < (int)ord.size(); ++j) {
@@ -669,7 +679,9 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
       kept_energy<<<blocks_for(chi), 256, 0, st>>>(kn, kr, kn_max, E, Ek);
       cheb_dot01<<<1, kRedThreads, 0, st>>>(n_un, vre, vre + S, d01);
       b.launches += 2;
-      const std::vector<EmuTile> tgv = grid_tiles(k1, k1, chi);
+      int64_t cg = 0;
+      const std::vector<EmuTile> tgv = grid_tiles(k1, k1, chi, cg);
+      if (cg < 0) return fail(TGBA_EINVAL, "quench moment tiles");
       TGBA_CUDA(cudaMemcpyAsync(dtg, tgv.data(), tgv.size() * sizeof(EmuTile), cudaMemcpyHostToDevice, st));
       // rows k of V (K = the kept rows in their own order: kn NS rows, then kr R rows)
       const int64_t jump = kn_max - kn;
@@ -679,11 +691,11 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
       if ((r = emu_slice(b, vre, S, 1, (int)kn, jump, Ek, ec[v], k1, (int)chi, TC, Wr, ewr, st)) != TGBA_OK) return r;
       if ((r = emu_slice(b, vre + n_un, S, 1, (int)kn, jump, Ek, ec[v], k1, (int)chi, TC, Wi, ewi, st)) != TGBA_OK)
         return r;
-      if ((r = emu_gemm(b, Vr, evr, k1, (int)chi, Wr, ewr, k1, (int)chi, dtg, (int)tgv.size(), Grr, k1, st)) != TGBA_OK)
+      if ((r = emu_gemm(b, Vr, evr, k1, (int)chi, Wr, ewr, k1, (int)chi, dtg, (int)tgv.size(), cg, Grr, k1, st)) != TGBA_OK)
         return r;
-      if ((r = emu_gemm(b, Vi, evi, k1, (int)chi, Wi, ewi, k1, (int)chi, dtg, (int)tgv.size(), Gii, k1, st)) != TGBA_OK)
+      if ((r = emu_gemm(b, Vi, evi, k1, (int)chi, Wi, ewi, k1, (int)chi, dtg, (int)tgv.size(), cg, Gii, k1, st)) != TGBA_OK)
         return r;
-      if ((r = emu_gemm(b, Vr, evr, k1, (int)chi, Wi, ewi, k1, (int)chi, dtg, (int)tgv.size(), Gri, k1, st)) != TGBA_OK)
+      if ((r = emu_gemm(b, Vr, evr, k1, (int)chi, Wi, ewi, k1, (int)chi, dtg, (int)tgv.size(), cg, Gri, k1, st)) != TGBA_OK)
         return r;
       cheb_gamma<<<blocks_for((int64_t)k1 * k1), 256, 0, st>>>(k1, Grr, Gii, Gri, Gam);
       ++b.launches;
@@ -700,11 +712,13 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
       }();
       cheb_bessel<<<(int)((nt + 127) / 128), 128, 0, st>>>((int)nt, 0, dt, R[v], Kv[v], ms, Ab);
       ++b.launches;
-      const std::vector<EmuTile> tt = grid_tiles(k1, nt, k1);
+      int64_t ct = 0;
+      const std::vector<EmuTile> tt = grid_tiles(k1, nt, k1, ct);
+      if (ct < 0) return fail(TGBA_EINVAL, "quench time-sum tiles");
       TGBA_CUDA(cudaMemcpyAsync(dtg, tt.data(), tt.size() * sizeof(EmuTile), cudaMemcpyHostToDevice, st));
       if ((r = emu_slice(b, Gam, k1, 1, k1, 0, nullptr, 0.0, k1, k1, TR, Vr, evr, st)) != TGBA_OK) return r;
       if ((r = emu_slice(b, Ab, k1, 1, k1, 0, nullptr, 0.0, (int)nt, k1, TC, Wr, ewi, st)) != TGBA_OK) return r;
-      if ((r = emu_gemm(b, Vr, evr, k1, k1, Wr, ewi, (int)nt, k1, dtg, (int)tt.size(), GA, k1, st)) != TGBA_OK) return r;
+      if ((r = emu_gemm(b, Vr, evr, k1, k1, Wr, ewi, (int)nt, k1, dtg, (int)tt.size(), ct, GA, k1, st)) != TGBA_OK) return r;
       cheb_mx<<<(int)((nt * 32 + 255) / 256), 256, 0, st>>>(k1, (int)nt, Ab, GA, R[v] * h01, scale,
                                                               mx + (int64_t)vv.out * n_t);
       ++b.launches;

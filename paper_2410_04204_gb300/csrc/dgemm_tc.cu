@@ -37,6 +37,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <vector>
 
@@ -51,7 +52,7 @@ constexpr int kTMr = 128;                 // rows of A per tile
 constexpr int kTNr = 128;                 // rows of B per tile
 constexpr int kChunkBlocks = 4;           // K blocks per exact FP32 chunk (128 K values)
 constexpr uint32_t kASlice = kTMr * kKB * 2;          // 8 KB
-constexpr uint32_t kBSlice = kTNr * kKB * 2;          // 4 KB
+constexpr uint32_t kBSlice = kTNr * kKB * 2;          // 8 KB
 constexpr uint32_t kAStage = kS * kASlice;            // 48 KB
 constexpr uint32_t kBStage = kS * kBSlice;            // 48 KB
 constexpr int kStages = 2;
@@ -147,8 +148,9 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
 }
 
 struct GemmArgs {
-  const EmuTile* tiles;
+  EmuTile* tiles;             // the output tiles, numbered by emu_number_tiles (arrival counters at 0)
   int n_tiles;
+  int64_t n_chunks;           // chunks of all tiles (a chunk: kChunkBlocks K blocks of one tile)
   const __nv_bfloat16* A;     // [row block][K block][slice] tile images
   const __nv_bfloat16* B;
   int a_kb, b_kb;             // K blocks per row block of A / of B (the stride between row blocks)
@@ -157,10 +159,56 @@ struct GemmArgs {
   int M, N;
   double* C;                  // C[i + j ldc]
   int64_t ldc;
+  double* part;               // [2 gridDim.x][kTNr][kTMr] partial tiles of the split tiles
   unsigned* status;
 };
 
-__global__ void __maxnreg__(184) dgemm_tc_kernel(GemmArgs g) {   // 320 threads x 184 registers, one CTA per SM
+// Work split (stream-K): the chunks of all tiles, tile after tile, are cut into gridDim.x
+// contiguous ranges of equal length, one per CTA.  A tile whose chunks fall to several CTAs is
+// a split tile: each of them writes its partial sum to a slot of g.part, and the last to arrive
+// (an atomic counter in the tile; no CTA waits for another) adds the partials in CTA order and
+// writes C, so the result does not depend on the arrival order.
+__device__ __forceinline__ int64_t range_start(int c, int64_t T, int G) { return (int64_t)c * T / G; }
+__device__ __forceinline__ int cta_of(int64_t x, int64_t T, int G) {    // the CTA whose range holds chunk x
+  return (int)(((x + 1) * G + T - 1) / T) - 1;
+}
+__device__ __forceinline__ int64_t tile_chunks(const EmuTile& t) { return (t.nkb + kChunkBlocks - 1) / kChunkBlocks; }
+
+struct Seg {
+  int t;                      // tile
+  int kb0, kb1;               // K blocks [kb0, kb1) of the tile
+  bool whole;                 // the segment is the whole tile
+};
+// the segment of tile t from chunk c on (c inside tile t), clipped at the CTA's range end; false past it
+__device__ __forceinline__ bool seg_at(const GemmArgs& g, int t, int64_t c, int64_t c_end, Seg& s) {
+  if (t >= g.n_tiles || c >= c_end) return false;
+  const EmuTile tl = g.tiles[t];
+  const int64_t n = tile_chunks(tl), s0 = c - tl.c0, s1 = min(n, c_end - tl.c0);
+  s.t = t;
+  s.kb0 = (int)(s0 * kChunkBlocks);
+  s.kb1 = (int)min((int64_t)tl.nkb, s1 * kChunkBlocks);
+  s.whole = s0 == 0 && s1 == n;
+  return true;
+}
+__device__ __forceinline__ int first_tile(const GemmArgs& g, int64_t c) {   // the tile holding chunk c
+  int lo = 0, hi = g.n_tiles - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (g.tiles[mid].c0 <= c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// columns of the tile that K block kb touches: the 16-column groups whose K extent reaches past it
+__device__ __forceinline__ int active_cols(const EmuTile& tl, int kb) {
+  int n = 0;
+#pragma unroll
+  for (int q = 0; q < kTNr / 16; ++q)
+    if (q * 16 < tl.n_eff && tl.gkb[q] > kb) n = (q + 1) * 16;
+  return n;
+}
+
+__global__ void __maxnreg__(168) dgemm_tc_kernel(GemmArgs g) {   // 320 threads x 168 registers, one CTA per SM
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = su32(smem_raw);
   unsigned char* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -192,14 +240,19 @@ __global__ void __maxnreg__(184) dgemm_tc_kernel(GemmArgs g) {   // 320 threads 
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tslot;
+  const int G = gridDim.x;
+  const int64_t T = g.n_chunks, c_begin = range_start(blockIdx.x, T, G), c_end = range_start(blockIdx.x + 1, T, G);
+  const int t_first = first_tile(g, c_begin);
 
   if (warp == 0) {
     // ------------------------------------------------------------------ producer
     if (lane == 0) {
       uint32_t it = 0;
-      for (int t = blockIdx.x; t < g.n_tiles && !s_abort; t += gridDim.x) {
-        const EmuTile tl = g.tiles[t];
-        for (int kb = 0; kb < tl.nkb; ++kb, ++it) {
+      Seg sg{t_first - 1, 0, 0, false};
+      for (int64_t c = c_begin; !s_abort && seg_at(g, sg.t + 1, c, c_end, sg);
+           c = g.tiles[sg.t].c0 + tile_chunks(g.tiles[sg.t])) {
+        const EmuTile tl = g.tiles[sg.t];
+        for (int kb = sg.kb0; kb < sg.kb1; ++kb, ++it) {
           const int st = it % kStages;
           if (!bar_wait(empty + st, ((it / kStages) & 1u) ^ 1u, &s_abort)) { atomicOr(g.status, kStTimeout); s_abort = 1; break; }
           bar_expect(full + st, kAStage + kBStage);
@@ -218,19 +271,23 @@ __global__ void __maxnreg__(184) dgemm_tc_kernel(GemmArgs g) {   // 320 threads 
     if (lane == 0) {
       uint32_t it = 0, chunk = 0;
       uint64_t* last = nullptr;
-      for (int t = blockIdx.x; t < g.n_tiles && !s_abort; t += gridDim.x) {
-        const EmuTile tl = g.tiles[t];
-        const uint32_t id = idesc_f16(tl.n_eff);
-        for (int kb0 = 0; kb0 < tl.nkb && !s_abort; kb0 += kChunkBlocks, ++chunk) {
+      Seg sg{t_first - 1, 0, 0, false};
+      for (int64_t c = c_begin; !s_abort && seg_at(g, sg.t + 1, c, c_end, sg);
+           c = g.tiles[sg.t].c0 + tile_chunks(g.tiles[sg.t])) {
+        const EmuTile tl = g.tiles[sg.t];
+        for (int kb0 = sg.kb0; kb0 < sg.kb1 && !s_abort; kb0 += kChunkBlocks, ++chunk) {
           // the epilogue has read the previous chunk's accumulators
           if (!bar_wait(acce, (chunk & 1u) ^ 1u, &s_abort)) { atomicOr(g.status, kStTimeout); s_abort = 1; break; }
           fence_after();
-          const uint32_t dbase = tmem;
-          const int kb1 = min(tl.nkb, kb0 + kChunkBlocks);
+          const int kb1 = min(sg.kb1, kb0 + kChunkBlocks);
           for (int kb = kb0; kb < kb1; ++kb, ++it) {
             const int st = it % kStages;
             if (!bar_wait(full + st, (it / kStages) & 1u, &s_abort)) { atomicOr(g.status, kStTimeout); s_abort = 1; break; }
             fence_after();
+            // columns whose K extent ends before this block are skipped (their rows of B are zero
+            // there); the chunk's first block touches the most columns, so its MMAs initialise
+            // every column that the epilogue reads
+            const uint32_t id = idesc_f16(active_cols(tl, kb));
             const uint32_t a0 = su32(sA + st * kAStage), b0 = su32(sB + st * kBStage);
 #pragma unroll 1
             for (int p = 0; p < kS; ++p)
@@ -242,7 +299,7 @@ __global__ void __maxnreg__(184) dgemm_tc_kernel(GemmArgs g) {   // 320 threads 
                 const bool first = kb == kb0 && p == 0 && q == (d < 3 ? d : 3);
 #pragma unroll
                 for (int ks = 0; ks < 2; ++ks)
-                  mma(dbase + (uint32_t)d * 128u, desc64(a0 + p * kASlice + ks * 32), desc64(b0 + q * kBSlice + ks * 32), id,
+                  mma(tmem + (uint32_t)d * 128u, desc64(a0 + p * kASlice + ks * 32), desc64(b0 + q * kBSlice + ks * 32), id,
                       (first && ks == 0) ? 0u : 1u);
               }
             commit(empty + st);                       // the stage's smem is free once these complete
@@ -265,29 +322,33 @@ __global__ void __maxnreg__(184) dgemm_tc_kernel(GemmArgs g) {   // 320 threads 
     const int half = (warp - 2) >> 2;                 // columns kCols half .. kCols half + kCols - 1
     const int r = quad * 32 + lane;                   // row of the tile
     uint32_t chunk = 0;
-    for (int t = blockIdx.x; t < g.n_tiles && !s_abort; t += gridDim.x) {
-      const EmuTile tl = g.tiles[t];
+    Seg sg{t_first - 1, 0, 0, false};
+    for (int64_t c = c_begin; !s_abort && seg_at(g, sg.t + 1, c, c_end, sg);
+         c = g.tiles[sg.t].c0 + tile_chunks(g.tiles[sg.t])) {
+      const EmuTile tl = g.tiles[sg.t];
       float hi[kCols], lo[kCols];                     // registers: every index below is a constant
 #pragma unroll
-      for (int c = 0; c < kCols; ++c) { hi[c] = 0.f; lo[c] = 0.f; }
-      for (int kb0 = 0; kb0 < tl.nkb; kb0 += kChunkBlocks, ++chunk) {
+      for (int cc = 0; cc < kCols; ++cc) { hi[cc] = 0.f; lo[cc] = 0.f; }
+      for (int kb0 = sg.kb0; kb0 < sg.kb1; kb0 += kChunkBlocks, ++chunk) {
         if (!bar_wait(accf, chunk & 1u, &s_abort)) {
           if (lane == 0) atomicOr(g.status, kStTimeout);
           s_abort = 1;
           break;
         }
         fence_after();
+        const int na = active_cols(tl, kb0);          // columns the chunk's MMAs wrote
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * kCols);
-        if (half * kCols < tl.n_eff) {
 #pragma unroll
-          for (int d = 0; d < 4; ++d)
+        for (int h = 0; h < kCols / 16; ++h) {
+          if (half * kCols + h * 16 < na) {
 #pragma unroll
-            for (int h = 0; h < kCols / 16; ++h) {
+            for (int d = 0; d < 4; ++d) {
               float v[16];
               ld16(lane_base + (uint32_t)d * (uint32_t)kTNr + (uint32_t)h * 16u, v);
 #pragma unroll
               for (int j = 0; j < 16; ++j) two_sum_add(hi[h * 16 + j], lo[h * 16 + j], v[j]);
             }
+          }
         }
         fence_before();
         __syncwarp();
@@ -295,17 +356,49 @@ __global__ void __maxnreg__(184) dgemm_tc_kernel(GemmArgs g) {   // 320 threads 
       }
       if (s_abort) break;
       const int i = tl.rb * kTMr + r;
-      if (i < g.M) {
-        const int e_i = g.ea[i];
+      const int c_lo = half * kCols;
+      if (sg.whole) {
+        if (i < g.M) {
+          const int e_i = g.ea[i];
 #pragma unroll
-        for (int cc = 0; cc < kCols; ++cc) {
-          const int c = half * kCols + cc;
-          const int j = tl.cb * kTNr + c;
-          if (c < tl.n_eff && j < g.N) {
-            const double v = ((double)hi[cc] + (double)lo[cc]);
-            g.C[(int64_t)i + (int64_t)j * g.ldc] = ldexp(v, e_i + g.eb[j] - 16);
+          for (int cc = 0; cc < kCols; ++cc) {
+            const int j = tl.cb * kTNr + c_lo + cc;
+            if (c_lo + cc < tl.n_eff && j < g.N)
+              g.C[(int64_t)i + (int64_t)j * g.ldc] = ldexp((double)hi[cc] + (double)lo[cc], e_i + g.eb[j] - 16);
           }
         }
+        continue;
+      }
+      // split tile: this CTA's partial to its slot (0: the tile its range starts in, 1: the tile it ends in)
+      const int slot = 2 * (int)blockIdx.x + (sg.t == t_first ? 0 : 1);
+      double* mine = g.part + (size_t)slot * kTNr * kTMr;
+#pragma unroll
+      for (int cc = 0; cc < kCols; ++cc)
+        if (c_lo + cc < tl.n_eff) mine[(size_t)(c_lo + cc) * kTMr + r] = (double)hi[cc] + (double)lo[cc];
+      // the last of the tile's CTAs to finish this warp's 32 x 64 block adds the parts (no waiting)
+      __threadfence();
+      __syncwarp();
+      const int c_a = cta_of(tl.c0, T, G), c_b = cta_of(tl.c0 + tile_chunks(tl) - 1, T, G);
+      int last = 0;
+      if (lane == 0) last = atomicAdd(&g.tiles[sg.t].arrivals[warp - 2], 1) == c_b - c_a;
+      if (__shfl_sync(0xffffffffu, last, 0)) {
+        __threadfence();
+        if (i < g.M) {
+          const int e_i = g.ea[i];
+#pragma unroll 4
+          for (int cc = 0; cc < kCols; ++cc) {
+            const int j = tl.cb * kTNr + c_lo + cc;
+            if (c_lo + cc < tl.n_eff && j < g.N) {
+              double v = 0.0;
+              for (int cta = c_a; cta <= c_b; ++cta) {
+                const int sl = 2 * cta + (range_start(cta, T, G) >= tl.c0 ? 0 : 1);
+                v += __ldcg(g.part + (size_t)sl * kTNr * kTMr + (size_t)(c_lo + cc) * kTMr + r);
+              }
+              g.C[(int64_t)i + (int64_t)j * g.ldc] = ldexp(v, e_i + g.eb[j] - 16);
+            }
+          }
+        }
+        if (lane == 0) g.tiles[sg.t].arrivals[warp - 2] = 0;   // every part has arrived: ready for the next launch
       }
     }
   }
@@ -420,33 +513,61 @@ tgba_status emu_slice(Basis& b, const double* src, int64_t row_stride, int64_t k
   return TGBA_OK;
 }
 
-// Kernel attributes and the SM count, once per device (outside any stream capture).
+// Kernel attributes and the SM count, once per device (outside any stream capture); the
+// partial-tile workspace of the work split, once per handle.
 tgba_status emu_prepare(Basis& b) {
   static int sms_of[64] = {0};
   if (b.device < 0 || b.device >= 64) return fail(TGBA_ELIMIT, "device index");
   if (sms_of[b.device] == 0) {
     TGBA_CUDA(cudaFuncSetAttribute(dgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
+    cudaFuncAttributes fa;
+    TGBA_CUDA(cudaFuncGetAttributes(&fa, dgemm_tc_kernel));
+    if (fa.maxThreadsPerBlock < kThreads) {
+      char msg[200];
+      snprintf(msg, sizeof msg, "dgemm_tc_kernel: %d registers, %zu B local, %zu B static shared: at most %d threads",
+               fa.numRegs, fa.localSizeBytes, fa.sharedSizeBytes, fa.maxThreadsPerBlock);
+      return fail(TGBA_ELIMIT, msg);
+    }
     int sms = 0;
     TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
     sms_of[b.device] = sms;
   }
   b.emu_sms = sms_of[b.device];
+  if (!b.d_emu_part) TGBA_CUDA(cudaMalloc(&b.d_emu_part, emu_part_bytes(b.emu_sms)));
   return TGBA_OK;
 }
 
-// C = A B^T for sliced operands (see emu_slice), over the given output tiles (emu_prepare first).
+size_t emu_part_bytes(int sms) { return (size_t)2 * sms * kTNr * kTMr * sizeof(double); }
+
+int64_t emu_number_tiles(std::vector<EmuTile>& tiles) {
+  int64_t c = 0;
+  for (EmuTile& t : tiles) {
+    if (t.nkb < 1 || t.n_eff < 16 || t.n_eff > kTNr || t.n_eff % 16) return -1;
+    t.c0 = c;
+    for (int q = 0; q < kTNr / 16; ++q) {
+      t.arrivals[q] = 0;
+      if (t.gkb[q] <= 0 || t.gkb[q] > t.nkb) t.gkb[q] = (int16_t)t.nkb;   // unset: the tile's whole K
+    }
+    c += (t.nkb + kChunkBlocks - 1) / kChunkBlocks;
+  }
+  return c;
+}
+
+// C = A B^T for sliced operands (see emu_slice), over the given output tiles (numbered by
+// emu_number_tiles, n_chunks its result; emu_prepare first).
 tgba_status emu_gemm(Basis& b, const __nv_bfloat16* A, const int* ea, int M, int Ka, const __nv_bfloat16* B,
-                     const int* eb, int N, int Kb, const EmuTile* d_tiles, int n_tiles, double* C, int64_t ldc,
-                     cudaStream_t st) {
+                     const int* eb, int N, int Kb, EmuTile* d_tiles, int n_tiles, int64_t n_chunks, double* C,
+                     int64_t ldc, cudaStream_t st) {
   if (n_tiles == 0) return TGBA_OK;
-  if (b.emu_sms <= 0) return fail(TGBA_EINVAL, "emu_prepare was not called");
+  if (b.emu_sms <= 0 || !b.d_emu_part) return fail(TGBA_EINVAL, "emu_prepare was not called");
+  if (n_chunks < n_tiles) return fail(TGBA_EINVAL, "tiles not numbered (emu_number_tiles)");
   GemmArgs g;
-  g.tiles = d_tiles; g.n_tiles = n_tiles;
+  g.tiles = d_tiles; g.n_tiles = n_tiles; g.n_chunks = n_chunks;
   g.A = A; g.B = B;
   g.a_kb = (Ka + kKB - 1) / kKB;
   g.b_kb = (Kb + kKB - 1) / kKB;
-  g.ea = ea; g.eb = eb; g.M = M; g.N = N; g.C = C; g.ldc = ldc; g.status = b.d_status;
-  dgemm_tc_kernel<<<std::min(n_tiles, b.emu_sms), kThreads, kSmem, st>>>(g);
+  g.ea = ea; g.eb = eb; g.M = M; g.N = N; g.C = C; g.ldc = ldc; g.part = b.d_emu_part; g.status = b.d_status;
+  dgemm_tc_kernel<<<(int)std::min<int64_t>(n_chunks, b.emu_sms), kThreads, kSmem, st>>>(g);
   TGBA_CUDA(cudaGetLastError());
   ++b.launches;
   return TGBA_OK;
@@ -473,12 +594,17 @@ extern "C" tgba_status tgba_dgemm_tc(int32_t M, int32_t N, int32_t K, const doub
   for (int rb = 0; rb < (M + TR - 1) / TR; ++rb)
     for (int cb = 0; cb < (N + TC - 1) / TC; ++cb)
       tiles.push_back(EmuTile{rb, cb, std::min(TC, (N - cb * TC + 15) / 16 * 16), (K + KB - 1) / KB});
+  const int64_t n_chunks = emu_number_tiles(tiles);
+  if (n_chunks < 0) return fail(TGBA_EINVAL, "tile list");
+  int sms = 0;
+  TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx.device));
   void* buf = nullptr;
-  const size_t bytes = (ea + eb) * 2 + (size_t)(M + N) * 4 + tiles.size() * sizeof(EmuTile) + 64;
+  const size_t bytes = emu_part_bytes(sms) + (ea + eb) * 2 + (size_t)(M + N) * 4 + tiles.size() * sizeof(EmuTile) + 64;
   cudaError_t e = cudaMallocAsync(&buf, bytes, st);
   if (e != cudaSuccess) { cudaGetLastError(); return fail(TGBA_ENOMEM, "slice buffers of tgba_dgemm_tc"); }
   struct Free { void* p; cudaStream_t s; ~Free() { cudaFreeAsync(p, s); } } fr{buf, st};
-  __nv_bfloat16* As = (__nv_bfloat16*)buf;
+  ctx.d_emu_part = (double*)buf;                      // the handle-less call brings its own workspace
+  __nv_bfloat16* As = (__nv_bfloat16*)((char*)buf + emu_part_bytes(sms));
   __nv_bfloat16* Bs = As + ea;
   int* xa = (int*)(Bs + eb);
   int* xb = xa + M;
@@ -489,12 +615,13 @@ extern "C" tgba_status tgba_dgemm_tc(int32_t M, int32_t N, int32_t K, const doub
   tgba_status r = emu_prepare(ctx);
   if (r == TGBA_OK) r = emu_slice(ctx, A, lda, 1, K, 0, nullptr, 0.0, M, K, TR, As, xa, st);
   if (r == TGBA_OK) r = emu_slice(ctx, B, ldb, 1, K, 0, nullptr, 0.0, N, K, TC, Bs, xb, st);
-  if (r == TGBA_OK) r = emu_gemm(ctx, As, xa, M, K, Bs, xb, N, K, dt, (int)tiles.size(), C, ldc, st);
+  if (r == TGBA_OK) r = emu_gemm(ctx, As, xa, M, K, Bs, xb, N, K, dt, (int)tiles.size(), n_chunks, C, ldc, st);
   if (r != TGBA_OK) return r;
   unsigned w = 0;
   TGBA_CUDA(cudaMemcpyAsync(&w, ctx.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   TGBA_CUDA(cudaStreamSynchronize(st));
   ctx.d_status = nullptr;
+  ctx.d_emu_part = nullptr;
   if (w & kStTimeout) return fail(TGBA_ETIMEOUT, "a bounded wait of the tensor-core GEMM gave up");
   return TGBA_OK;
 }

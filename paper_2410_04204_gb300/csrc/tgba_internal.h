@@ -160,6 +160,7 @@ struct Basis {
   void* blas = nullptr;            // cublasHandle_t
   double* d_blas_ws = nullptr;     // its workspace (set explicitly, so captured calls allocate nothing)
   int emu_sms = 0;                 // SMs for the tensor-core FP64 products (emu_prepare)
+  double* d_emu_part = nullptr;    // their partial tiles (emu_prepare)
   int quench_terms = 0;            // Chebyshev terms K of the last batched quench propagation
   double quench_flops = 0;         // its algorithmic FP64 flops (K sum 8 n_NS n_R)
   double quench_prep_ms = 0, quench_gram_ms = 0, quench_eval_ms = 0;   // its other stages
@@ -273,11 +274,17 @@ tgba_status run_pfaffian_lists(Basis& b, const unsigned* counts, const int64_t* 
 tgba_status run_pfaffians_smem_classes(Basis& b, cudaStream_t st);
 
 // dgemm_tc.cu: FP64 products on the tensor cores (BF16 slices, exact FP32 chunk sums, 48-bit
-// running sums).  An operand (rows x K) is sliced by emu_slice into tile images of 128 (A) or 64
-// (B) rows; emu_gemm computes C = A B^T over a list of output tiles (row block, column block,
-// columns used n_eff (a multiple of 16, <= 64), K blocks nkb).
+// running sums).  An operand (rows x K) is sliced by emu_slice into tile images of 128 rows (A
+// and B); emu_gemm computes C = A B^T over a list of output tiles (row block, column block,
+// columns used n_eff (a multiple of 16, <= 128), K blocks nkb, and per 16-column group the K
+// blocks gkb that its columns reach (0: all nkb); B must be zero beyond them).  The chunks of
+// all tiles are split evenly over the SMs; emu_number_tiles numbers them (c0) and zeroes the
+// arrival counters, which the kernel leaves at zero again.
 struct EmuTile {
   int32_t rb, cb, n_eff, nkb;
+  int64_t c0;                 // first chunk of the tile in the list's order
+  int32_t arrivals[8];        // CTAs done with each epilogue warp's block of a split tile
+  int16_t gkb[8];             // K blocks per 16-column group
 };
 size_t emu_operand_elems(int rows, int K, int tile_rows);
 int emu_tile_rows_a();
@@ -287,9 +294,11 @@ tgba_status emu_slice(Basis& b, const double* src, int64_t row_stride, int64_t k
                       const double* w, double w_shift, int rows, int K, int tile_rows, __nv_bfloat16* out, int* e,
                       cudaStream_t st);
 tgba_status emu_prepare(Basis& b);
+size_t emu_part_bytes(int sms);
+int64_t emu_number_tiles(std::vector<EmuTile>& tiles);     // total chunks; -1 for an invalid tile
 tgba_status emu_gemm(Basis& b, const __nv_bfloat16* A, const int* ea, int M, int Ka, const __nv_bfloat16* B,
-                     const int* eb, int N, int Kb, const EmuTile* d_tiles, int n_tiles, double* C, int64_t ldc,
-                     cudaStream_t st);
+                     const int* eb, int N, int Kb, EmuTile* d_tiles, int n_tiles, int64_t n_chunks, double* C,
+                     int64_t ldc, cudaStream_t st);
 
 // screen.cu
 struct Screen;

@@ -6,9 +6,13 @@ sums) through the C ABI.
   two base-256 digits, hence only the digit diagonals 0..2, which the design sums exactly, so C
   must equal the integer product bit for bit (K = 4096: 32 chunks, sums up to 2^38).
 * Accuracy: random operands whose rows span six decades, ragged sizes (M, N, K not multiples
-  of the 128 x 64 x 32 tiles), against an extended-precision reference: error <= 3e-13 of
+  of the 128 x 128 x 32 tiles), against an extended-precision reference: error <= 3e-13 of
   sum_k |A_ik B_jk| (the FP32 rounding of the accumulator shared by the digit diagonals 3..5
   dominates: measured up to 1.1e-13), and against cuBLAS FP64.
+* The work split: the chunks (128 K values of one tile) of all tiles are cut evenly over the
+  SMs, so a tile may be summed by several CTAs (partials added by the last to finish).  The
+  shapes cover tiles split over many CTAs at uneven boundaries, whole tiles only, and a mix;
+  two calls give bit-identical results (the partials are added in a fixed order).
 """
 import ctypes
 
@@ -50,7 +54,8 @@ def test_integer_products_are_exact():
     assert np.array_equal(C, exact), np.abs(C - exact).max()
 
 
-@pytest.mark.parametrize("M,N,K", [(300, 100, 1000), (128, 64, 32), (1, 1, 1), (257, 17, 777)])
+@pytest.mark.parametrize("M,N,K", [(300, 100, 1000), (128, 64, 32), (1, 1, 1), (257, 17, 777),
+                                   (700, 300, 5000), (1000, 200, 100), (2000, 129, 700)])
 def test_accuracy_against_extended_precision(M, N, K):
     g = inputs.rng(32 + M)
     A = g.standard_normal((M, K)) * 10.0 ** g.uniform(-3, 3, (M, 1))
@@ -69,3 +74,13 @@ def test_argument_errors():
     with pytest.raises(tgba.TgbaError) as e:
         tgba.tgba_dgemm_tc(0, 1, 1, x, 1, x, 1, x, 1)
     assert e.value.code == tgba.TGBA_EINVAL
+
+
+def test_split_tiles_are_deterministic():
+    # 6 x 3 tiles of 40 chunks over the SMs: every tile is split, at uneven chunk boundaries
+    g = inputs.rng(40)
+    A = g.standard_normal((700, 5000))
+    B = g.standard_normal((300, 5000))
+    C1 = dgemm_tc(A, B)
+    C2 = dgemm_tc(A, B)
+    assert np.array_equal(C1, C2)
