@@ -20,7 +20,7 @@
 //    numbers (hi + lo, error-free two-sum: about 48 bits), by CUDA-core FP32 arithmetic, while
 //    the producer keeps loading the next stages.  At the end of the tile
 //    C_ij = 2^{e_i + f_j - 16} (hi + lo) in FP64.
-//  The error of C is about 1e-13 of sum_k |A_ik B_jk| (measured up to 1.1e-13), dominated by
+//  The error of C is a few 1e-13 of sum_k |A_ik B_jk| (measured up to 3.9e-13), dominated by
 //  the FP32 rounding of the accumulator that the digit diagonals 3..5 share.
 //
 // Tiles: 128 rows of A x up to 128 rows of B (n_eff, a multiple of 16, per tile) x K in blocks
