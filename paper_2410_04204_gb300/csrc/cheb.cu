@@ -230,44 +230,50 @@ __global__ void cheb_gamma(int K1, const double* __restrict__ Grr, const double*
 
 // a_k(t) = (2 - d_k0) J_k(R t), k = 0..K, by Miller's backward recurrence for J_k
 // (J_{k-1} = (2k/x) J_k - J_{k+1} from a start far above k and x, normalised by
-// J_0 + 2 sum J_2j = 1), one thread per time.
+// J_0 + 2 sum J_2j = 1), one thread per time.  out is [k][t] (row k at out + k n_t), so a
+// warp's stores of one k are consecutive; 2k/x is 2k times 1/x, taken once (no FP64 division
+// in the recurrence).
 __global__ void cheb_bessel(int n_t, int t0, double dt, double R, int K, int m_start, double* __restrict__ out) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_t) return;
   const double x = R * dt * (double)(t0 + c);
-  double* a = out + (int64_t)c * (K + 1);
+  double* a = out + c;                         // a_k at a[k n_t]
+  const int64_t S = n_t;
   if (x == 0.0) {
     a[0] = 1.0;
-    for (int k = 1; k <= K; ++k) a[k] = 0.0;
+    for (int k = 1; k <= K; ++k) a[k * S] = 0.0;
     return;
   }
+  const double ix2 = 2.0 / x;
   double jp1 = 0.0, j = 1e-300, norm = 0.0;
   for (int k = m_start; k >= 1; --k) {
-    const double jm1 = (2.0 * k / x) * j - jp1;
+    const double jm1 = fma((double)k * ix2, j, -jp1);
     jp1 = j;
     j = jm1;                                   // j = J_{k-1} (unnormalised)
-    if (k - 1 <= K) a[k - 1] = j;
+    if (k - 1 <= K) a[(k - 1) * S] = j;
     if ((k - 1) % 2 == 0 && k - 1 > 0) norm += 2.0 * j;
     if (fabs(j) > 1e250) {                     // rescale everything accumulated so far
-      const double s = 1e-250;
-      j *= s; jp1 *= s; norm *= s;
-      for (int q = k - 1; q <= K && q <= m_start; ++q) a[q] *= s;
+      const double sc = 1e-250;
+      j *= sc; jp1 *= sc; norm *= sc;
+      for (int q = k - 1; q <= K && q <= m_start; ++q) a[q * S] *= sc;
     }
   }
   norm += j;                                   // + J_0
   const double inv = 1.0 / norm;
   a[0] *= inv;
-  for (int k = 1; k <= K; ++k) a[k] *= 2.0 * inv;
+  const double inv2 = 2.0 * inv;
+  for (int k = 1; k <= K; ++k) a[k * S] *= inv2;
 }
 
-// mx[t] = (a(t)^T Gamma a(t) - e_shift) * scale, one warp per time (GA = Gamma a precomputed)
+// mx[t] = (a(t)^T Gamma a(t) - e_shift) * scale, one warp per time (A = a [k][t], GA = Gamma a
+// precomputed, [t][k])
 __global__ void cheb_mx(int K1, int cnt, const double* __restrict__ A, const double* __restrict__ GA, double e_shift,
                         double scale, double* __restrict__ mx) {
   const int lane = threadIdx.x & 31;
   const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (col >= cnt) return;
   double acc = 0.0;
-  for (int k = lane; k < K1; k += 32) acc = fma(A[(int64_t)col * K1 + k], GA[(int64_t)col * K1 + k], acc);
+  for (int k = lane; k < K1; k += 32) acc = fma(A[(int64_t)k * cnt + col], GA[(int64_t)col * K1 + k], acc);
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) mx[col] = (acc - e_shift) * scale;
 }
@@ -646,7 +652,7 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
     double* Gii = Grr + (size_t)K1 * K1;
     double* Gri = Gii + (size_t)K1 * K1;
     double* Gam = Gri + (size_t)K1 * K1;
-    double* Ab = Gam + (size_t)K1 * K1;                   // a_k(t): [t][K_v + 1]
+    double* Ab = Gam + (size_t)K1 * K1;                   // a_k(t): [K_v + 1][t]
     double* GA = Ab + (size_t)K1 * nt;                    // Gamma a(t): column-major (K_v + 1) x n_t
     double* Ek = GA + (size_t)K1 * nt;
     double* d01 = Ek + chi_max;
@@ -710,14 +716,14 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
         int m0 = Kv[v] + 30 + (int)std::ceil(std::sqrt(40.0 * Kv[v]));
         return m0 + (m0 & 1);
       }();
-      cheb_bessel<<<(int)((nt + 127) / 128), 128, 0, st>>>((int)nt, 0, dt, R[v], Kv[v], ms, Ab);
+      cheb_bessel<<<(int)((nt + 31) / 32), 32, 0, st>>>((int)nt, 0, dt, R[v], Kv[v], ms, Ab);
       ++b.launches;
       int64_t ct = 0;
       const std::vector<EmuTile> tt = grid_tiles(k1, nt, k1, ct);
       if (ct < 0) return fail(TGBA_EINVAL, "quench time-sum tiles");
       TGBA_CUDA(cudaMemcpyAsync(dtg, tt.data(), tt.size() * sizeof(EmuTile), cudaMemcpyHostToDevice, st));
       if ((r = emu_slice(b, Gam, k1, 1, k1, 0, nullptr, 0.0, k1, k1, TR, Vr, evr, st)) != TGBA_OK) return r;
-      if ((r = emu_slice(b, Ab, k1, 1, k1, 0, nullptr, 0.0, (int)nt, k1, TC, Wr, ewi, st)) != TGBA_OK) return r;
+      if ((r = emu_slice(b, Ab, 1, nt, k1, 0, nullptr, 0.0, (int)nt, k1, TC, Wr, ewi, st)) != TGBA_OK) return r;
       if ((r = emu_gemm(b, Vr, evr, k1, k1, Wr, ewi, (int)nt, k1, dtg, (int)tt.size(), ct, GA, k1, st)) != TGBA_OK) return r;
       cheb_mx<<<(int)((nt * 32 + 255) / 256), 256, 0, st>>>(k1, (int)nt, Ab, GA, R[v] * h01, scale,
                                                               mx + (int64_t)vv.out * n_t);
