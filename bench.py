@@ -10,10 +10,12 @@ for each h_x the dense complex H_eff of every sector and all its eigenvalues.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
 value = H_eff (Pfaffian) elements of the step, summed over ranks, per second of the step
-time (CUDA events on the launching stream, max over ranks).  Under torchrun every rank runs
-its own copy of the workload (weak scaling, no data-path collective).  --impl reference times
-the CPU oracle (direct Pfaffians of size 2N+M+M', numpy eigensolver) on the host cores on a
-bounded sample of the same workload.
+time (CUDA events on the launching stream, max over ranks); pfaffian_elements_per_s = the same
+elements per second of the Pfaffian stage alone.  Under torchrun every rank runs its own copy of
+the workload (weak scaling, no data-path collective).  --impl reference times the CPU oracle
+(the reduced form: one Schur complement of the vacuum operators per sector, then a Pfaffian of
+size M+M' per element; the direct Pfaffians of size 2N+M+M' as a context row; numpy
+eigensolver) on the host cores on a bounded sample of the same workload.
 """
 import argparse
 import json
@@ -476,6 +478,7 @@ def run_gb300(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(workload_config(w, n_el, n_states),
                            l2="256 MiB buffer written between steps, outside the step events"),
+            "pfaffian_elements_per_s": n_el / (pf_mean * 1e-3) * world,
             "roofline": roofline,
             "stages_ms": {"table": tab_mean, "pfaffian": pf_mean, "tridiag": tri_mean, "bisect": bis_mean,
                           "heff_fill_and_other": ms - tab_mean - pf_mean - tri_mean - bis_mean},
@@ -718,7 +721,9 @@ def run_stage(args):
             pairs = inputs.sample_pairs(n_ns, n_r, args.pairs, tag=L)
             M = info["nqp"]
             m = 2 * L + M[pairs[:, 0]].astype(np.int64) + M[n_ns + pairs[:, 1]].astype(np.int64)
-            flops = float(sum(4 * mm * (mm - 1) * L + sum(8 * j * (j - 1) + 6 * j for j in range(int(mm) - 2, 0, -2))
+            # per element: the string matrix, two complex products per entry of its strict upper
+            # triangle (the site sums come from per-launch tables), and the complex Parlett-Reid
+            flops = float(sum(12 * mm * (mm - 1) // 2 + sum(8 * j * (j - 1) + 6 * j for j in range(int(mm) - 2, 0, -2))
                               for mm in m))
             p = torch.tensor(pairs, dtype=torch.int32, device="cuda")
             out = torch.empty(len(pairs), dtype=torch.complex128, device="cuda")

@@ -114,11 +114,11 @@ tgba_status tgba_x_pairs(tgba_basis b, int32_t s, const int32_t* pairs_dev, int6
 /* X for explicit pairs, as tgba_x_pairs, but evaluated the paper-literal way (Appendix A,
    Eq. S1-S2): the vacuum expectation of the whole string of 2L + M_a + M_b Bogoliubov operators
    (both vacua, the excitations and sigma^x_1, expanded on the lattice sites), one complex
-   Pfaffian of that size per element, a CTA each.  O((2L)^3) per element instead of the
+   Pfaffian of that size per element, a warp each.  O((2L)^3) per element instead of the
    reduced form's O((M_a + M_b)^3): a GPU cross-check of tgba_x_pairs and an FP64-dense workload.
-   Needs the dense 2L + 2 max_qp string in shared memory: TGBA_EINVAL when it does not fit
-   (e.g. L = 32 with max_qp = 16 fits, L = 60 does not).  Pair and output layout, index checks
-   as tgba_x_pairs; blocks on `stream`. */
+   Needs one warp's dense 2L + 2 max_qp string in shared memory: TGBA_EINVAL when it does not
+   fit (L = 60 with max_qp = 16 fits).  Pair and output layout, index checks as tgba_x_pairs;
+   blocks on `stream`. */
 tgba_status tgba_x_direct(tgba_basis b, int32_t s, const int32_t* pairs_dev, int64_t n_pairs, double* out_dev,
                           void* stream);
 

@@ -30,8 +30,6 @@ namespace tgba {
 namespace {
 
 constexpr int kDirThreads = 128;
-constexpr int kMaxOps = 2 * kMaxL + 2 * kMaxQp + 2 * kMaxL + 2;   // vacua, excitations, middle
-enum OpKind : int { kOpC = 0, kOpCdag = 1, kOpD = 2, kOpDdag = 3, kOpSigma = 4, kOpMajA = 5, kOpMajB = 6 };
 
 __device__ __forceinline__ int pk(int i, int j, int m) { return i * m - ((i * (i + 1)) >> 1) + (j - i - 1); }
 
@@ -125,33 +123,146 @@ __device__ double2 pf_packed(double2* T, int m, double2* rowR, double2* tau) {
   return pf;
 }
 
-__global__ void __launch_bounds__(kDirThreads)
-x_direct_kernel(const int32_t* __restrict__ pairs, int64_t n_pairs, int pa_par, int pb_par, int jmid, int64_t a_off,
-                int64_t b_off, int64_t n_a, int64_t n_b, int L, const double* __restrict__ theta,
-                const int* __restrict__ nlab, const int16_t* __restrict__ modes_ns, const int16_t* __restrict__ modes_r,
-                int max_qp, double vac_norm, double* __restrict__ out, unsigned* __restrict__ status) {
+// One operator of the string, o = sum_j (U(j) c_j^dag + V(j) c_j) with U = a phi and V = b phi
+// for a common site function phi: phi(j) = e^{i pi ph j / L} / sqrt(L) for a mode operator
+// (loc = 0), phi(j) = delta_{j, loc} for a site operator (loc >= 1).  Then Eq. S2's
+// A_uv = sum_j V_u(j) U_v(j) = b_u a_v sum_j phi_u(j) phi_v(j), and the site sum takes one of
+// three forms: G(ph_u + ph_v) = (1/L) sum_{j=1..L} e^{i pi (ph_u + ph_v) j / L} (two mode
+// operators, tabulated once per CTA by summing over the sites), phi_mode(loc) (a mode and a
+// site operator), delta_{loc_u, loc_v} (two site operators).
+struct DirOp {
+  double2 a, b;
+  int ph, loc;
+};
+
+__device__ __forceinline__ int wrap2L(int x, int L) {
+  const int m = 2 * L;
+  x %= m;
+  return x < 0 ? x + m : x;
+}
+
+// Pfaffian of the m x m skew matrix held as its packed strict upper triangle T (destroyed), by
+// one warp: complex Parlett-Reid with partial pivoting, two indices per step, the pivot search
+// by shuffles and only warp barriers.  The rank-2 update walks rows i and m - 1 - (i - k - 2)
+// together (lengths adding up to m - k - 3), so the lanes stay busy on the short rows.  Every
+// lane gets the result.  rowR, tau: m entries of the warp's scratch.
+__device__ double2 pf_packed_warp(double2* T, int m, double2* rowR, double2* tau, int lane) {
+  double2 pf = make_double2(1.0, 0.0);
+  for (int k = 0; k + 1 < m; k += 2) {
+    double best = -1.0;
+    int bi = k + 1;
+    for (int x = k + 1 + lane; x < m; x += 32) {
+      const double2 v = T[pk(k, x, m)];
+      const double a2 = fma(v.x, v.x, v.y * v.y);
+      if (a2 > best) { best = a2; bi = x; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {                 // argmax, ties: the smallest index
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (!(best > 0.0)) { pf = make_double2(0.0, 0.0); break; }    // warp-uniform
+    const int R = k + 1, C = bi;
+    if (C != R) {                                      // exchange indices R and C
+      for (int x = lane; x < m; x += 32) {
+        if (x == R || x == C) continue;
+        const double2 a = get(T, R, x, m), b = get(T, C, x, m);
+        set(T, R, x, m, b);
+        set(T, C, x, m, a);
+      }
+      __syncwarp();
+      if (lane == 0) {
+        const double2 v = T[pk(R, C, m)];
+        T[pk(R, C, m)] = make_double2(-v.x, -v.y);
+      }
+      pf = make_double2(-pf.x, -pf.y);
+      __syncwarp();
+    }
+    const double2 a = T[pk(k, R, m)];
+    pf = cmul(pf, a);
+    const double den = fma(a.x, a.x, a.y * a.y);
+    const double2 ia = make_double2(a.x / den, -a.y / den);
+    for (int x = k + 2 + lane; x < m; x += 32) {
+      tau[x] = cmul(T[pk(k, x, m)], ia);               // Gauss vector
+      rowR[x] = T[pk(R, x, m)];
+    }
+    __syncwarp();
+    // A_ij += A_Ri tau_j - tau_i A_Rj  for k + 2 <= i < j: eight FMAs per complex entry
+    const int span = m - k - 3;                        // entries of rows i1 and i2 together
+    for (int t = 0; 2 * t <= span; ++t) {
+      const int i1 = k + 2 + t, i2 = m - 1 - t;
+      const int len1 = m - 1 - i1, len2 = (i2 > i1) ? m - 1 - i2 : 0;
+      for (int p = lane; p < len1 + len2; p += 32) {
+        const int gi = p < len1 ? i1 : i2;
+        const int gj = gi + 1 + (p < len1 ? p : p - len1);
+        const double2 ri = rowR[gi], ti = tau[gi], rj = rowR[gj], tj = tau[gj];
+        double2* w = T + pk(gi, gj, m);
+        double2 v = *w;
+        v.x = fma(ri.x, tj.x, v.x);
+        v.x = fma(-ri.y, tj.y, v.x);
+        v.x = fma(-ti.x, rj.x, v.x);
+        v.x = fma(ti.y, rj.y, v.x);
+        v.y = fma(ri.x, tj.y, v.y);
+        v.y = fma(ri.y, tj.x, v.y);
+        v.y = fma(-ti.x, rj.y, v.y);
+        v.y = fma(-ti.y, rj.x, v.y);
+        *w = v;
+      }
+    }
+    __syncwarp();
+  }
+  return pf;
+}
+
+// One warp per element (a CTA holds `wpc` warps, each with its own string and packed triangle
+// in shared memory); the site tables W (e^{i pi n / L}, n mod 2L) and G are built once per CTA.
+__global__ void x_direct_kernel(const int32_t* __restrict__ pairs, int64_t n_pairs, int pa_par, int pb_par, int jmid,
+                                int64_t a_off, int64_t b_off, int64_t n_a, int64_t n_b, int L,
+                                const double* __restrict__ theta, const int* __restrict__ nlab,
+                                const int16_t* __restrict__ modes_ns, const int16_t* __restrict__ modes_r, int max_qp,
+                                double vac_norm, int wpc, double* __restrict__ out, unsigned* __restrict__ status) {
   extern __shared__ double smem_d[];
-  __shared__ int kind[kMaxOps];
-  __shared__ double kk[kMaxOps], th[kMaxOps];
-  __shared__ int nops;
-  const int mmax = 2 * L + 2 * max_qp + (jmid > 0 ? 2 * jmid : 0);
-  double2* U = (double2*)smem_d;                 // [m][L]
-  double2* V = U + (size_t)mmax * L;             // [m][L]
-  double2* T = V + (size_t)mmax * L;             // packed strict upper triangle, m (m - 1) / 2
+  const int mmax = 2 * L + 2 * max_qp + (jmid > 0 ? 2 * jmid : 1);
+  double2* Wt = (double2*)smem_d;                        // [2L]: e^{i pi n / L}
+  double2* Gt = Wt + 2 * L;                              // [4L + 1]: G(n), n = -2L .. 2L
+  const size_t per_warp = (size_t)mmax * (mmax - 1) / 2 * sizeof(double2) + 2 * (size_t)mmax * sizeof(double2) +
+                          (size_t)mmax * sizeof(DirOp);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* wbase = (unsigned char*)(Gt + 4 * L + 1) + (size_t)warp * per_warp;
+  double2* T = (double2*)wbase;
   double2* rowR = T + (size_t)mmax * (mmax - 1) / 2;
   double2* tau = rowR + mmax;
-  const double pi = 3.14159265358979323846;
-  for (int64_t q = blockIdx.x; q < n_pairs; q += gridDim.x) {
+  DirOp* ops = (DirOp*)(tau + mmax);
+  for (int n = threadIdx.x; n < 2 * L; n += blockDim.x) {
+    double sn, cs;
+    sincospi((double)n / L, &sn, &cs);
+    Wt[n] = make_double2(cs, sn);
+  }
+  __syncthreads();
+  for (int n = threadIdx.x; n <= 4 * L; n += blockDim.x) {
+    const int ph = n - 2 * L;
+    double2 g = make_double2(0.0, 0.0);
+    for (int j = 1; j <= L; ++j) {
+      const double2 w = Wt[wrap2L(ph * j, L)];
+      g.x += w.x;
+      g.y += w.y;
+    }
+    Gt[n] = make_double2(g.x / L, g.y / L);
+  }
+  __syncthreads();
+  const double rn = rsqrt((double)L);
+  for (int64_t q = (int64_t)blockIdx.x * wpc + warp; q < n_pairs; q += (int64_t)gridDim.x * wpc) {
     const int32_t pa = pairs[2 * q], pb = pairs[2 * q + 1];
-    if (pa < 0 || pa >= n_a || pb < 0 || pb >= n_b) {        // block-uniform
-      if (threadIdx.x == 0) {
+    if (pa < 0 || pa >= n_a || pb < 0 || pb >= n_b) {        // warp-uniform
+      if (lane == 0) {
         atomicOr(status, kStBadIndex);
         out[2 * q] = out[2 * q + 1] = __longlong_as_double(0x7ff8000000000000ll);
       }
       continue;
     }
-    // the operator string (thread 0)
-    if (threadIdx.x == 0) {
+    // the operator string (lane 0), each operator as (a, b, ph, loc)
+    int m = 0;
+    if (lane == 0) {
       const int16_t* sa = (pa_par ? modes_r : modes_ns) + (a_off + pa) * max_qp;
       const int16_t* sb = (pb_par ? modes_r : modes_ns) + (b_off + pb) * max_qp;
       const int oa = pa_par * L, ob = pb_par * L;     // mode tables: NS modes, then R modes
@@ -159,95 +270,83 @@ x_direct_kernel(const int32_t* __restrict__ pairs, int64_t n_pairs, int pa_par, 
       while (ma < max_qp && sa[ma] >= 0) ++ma;
       while (mb < max_qp && sb[mb] >= 0) ++mb;
       int c = 0;
+      auto mode_op = [&](bool dag, int n, double th) {
+        double s2, c2;
+        sincos(0.5 * th, &s2, &c2);
+        DirOp o;
+        o.loc = 0;
+        if (dag) { o.ph = n; o.a = make_double2(s2, 0.0); o.b = make_double2(0.0, c2); }      // s c_k^dag + i c c_{-k}
+        else { o.ph = -n; o.a = make_double2(0.0, -c2); o.b = make_double2(s2, 0.0); }        // s c_k - i c c_{-k}^dag
+        ops[c++] = o;
+      };
+      auto plain_op = [&](bool dag, int n) {           // c_k or c_k^dag at k = pi n / L
+        DirOp o;
+        o.loc = 0;
+        o.ph = dag ? n : -n;
+        o.a = make_double2(dag ? 1.0 : 0.0, 0.0);
+        o.b = make_double2(dag ? 0.0 : 1.0, 0.0);
+        ops[c++] = o;
+      };
+      auto site_op = [&](int l, double bsign) {        // c_l^dag + bsign c_l
+        DirOp o;
+        o.loc = l;
+        o.ph = 0;
+        o.a = make_double2(1.0, 0.0);
+        o.b = make_double2(bsign, 0.0);
+        ops[c++] = o;
+      };
       for (int i = 0; i < L; ++i) {                  // bra vacuum: d_k^dag, ascending (k != pi)
         const int n = nlab[oa + i];
-        if (n == L) continue;
-        kind[c] = kOpDdag; kk[c] = pi * n / L; th[c] = theta[oa + i]; ++c;
+        if (n != L) mode_op(true, n, theta[oa + i]);
       }
       for (int t = ma - 1; t >= 0; --t) {            // bra excitations: d_p, descending ((c_pi^dag)^dag)
         const int i = sa[t], n = nlab[oa + i];
-        if (n == L) { kind[c] = kOpC; kk[c] = pi; th[c] = 0.0; }
-        else { kind[c] = kOpD; kk[c] = pi * n / L; th[c] = theta[oa + i]; }
-        ++c;
+        if (n == L) plain_op(false, L);
+        else mode_op(false, n, theta[oa + i]);
       }
-      if (jmid < 0) {                                // sigma^x_1 = c_1 + c_1^dag
-        kind[c] = kOpSigma; kk[c] = 0.0; th[c] = 0.0; ++c;
+      if (jmid < 0) {
+        site_op(1, 1.0);                             // sigma^x_1 = c_1 + c_1^dag
       } else {                                       // sigma^x_1 sigma^x_{j+1} = B_1 A_2 B_2 ... B_j A_{j+1}
         for (int l = 1; l <= jmid; ++l) {
-          kind[c] = kOpMajB; kk[c] = l; th[c] = 0.0; ++c;
-          kind[c] = kOpMajA; kk[c] = l + 1; th[c] = 0.0; ++c;
+          site_op(l, -1.0);
+          site_op(l + 1, 1.0);
         }
       }
       for (int t = 0; t < mb; ++t) {                 // ket excitations: d_q^dag (c_pi^dag), ascending
         const int i = sb[t], n = nlab[ob + i];
-        if (n == L) { kind[c] = kOpCdag; kk[c] = pi; th[c] = 0.0; }
-        else { kind[c] = kOpDdag; kk[c] = pi * n / L; th[c] = theta[ob + i]; }
-        ++c;
+        if (n == L) plain_op(true, L);
+        else mode_op(true, n, theta[ob + i]);
       }
       for (int i = L - 1; i >= 0; --i) {             // ket vacuum: d_k (k != pi), descending
         const int n = nlab[ob + i];
-        if (n == L) continue;
-        kind[c] = kOpD; kk[c] = pi * n / L; th[c] = theta[ob + i]; ++c;
+        if (n != L) mode_op(false, n, theta[ob + i]);
       }
-      nops = c;
+      m = c;
     }
-    __syncthreads();
-    const int m = nops;
-    // coefficients of every operator on every site j = 1..L
-    const double rn = rsqrt((double)L);
-    for (int e = threadIdx.x; e < m * L; e += kDirThreads) {
-      const int u = e / L, j = e - u * L + 1;
-      double sn, cs;
-      sincos(kk[u] * j, &sn, &cs);
-      const double2 ep = make_double2(cs * rn, sn * rn), em = make_double2(cs * rn, -sn * rn);
-      double s2, c2;
-      sincos(0.5 * th[u], &s2, &c2);
-      double2 cu = make_double2(0.0, 0.0), cv = make_double2(0.0, 0.0);
-      switch (kind[u]) {
-        case kOpC: cv = em; break;
-        case kOpCdag: cu = ep; break;
-        case kOpD:                                   // s c_k - i c c_{-k}^dag
-          cv = make_double2(s2 * em.x, s2 * em.y);
-          cu = make_double2(c2 * em.y, -c2 * em.x);
-          break;
-        case kOpDdag:                                // s c_k^dag + i c c_{-k}
-          cu = make_double2(s2 * ep.x, s2 * ep.y);
-          cv = make_double2(-c2 * ep.y, c2 * ep.x);
-          break;
-        case kOpMajA:                                // c_l^dag + c_l at site l = kk
-          if (j == (int)kk[u]) { cu = make_double2(1.0, 0.0); cv = cu; }
-          break;
-        case kOpMajB:                                // c_l^dag - c_l
-          if (j == (int)kk[u]) { cu = make_double2(1.0, 0.0); cv = make_double2(-1.0, 0.0); }
-          break;
-        default:
-          if (j == 1) { cu = make_double2(1.0, 0.0); cv = cu; }
-      }
-      U[(size_t)u * L + (j - 1)] = cu;
-      V[(size_t)u * L + (j - 1)] = cv;
-    }
-    __syncthreads();
-    // A_uv = sum_j V_u(j) U_v(j), u < v (Eq. S2)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = kDirThreads / 32;
-    for (int u = warp; u < m; u += nwarp)               // a warp per row, lanes along it
+    m = __shfl_sync(0xffffffffu, m, 0);
+    __syncwarp();
+    // A_uv = b_u a_v sum_j phi_u(j) phi_v(j), u < v (Eq. S2), the site sum from the tables
+    for (int u = 0; u < m; ++u) {
+      const DirOp ou = ops[u];
       for (int v = u + 1 + lane; v < m; v += 32) {
-        double2 acc = make_double2(0.0, 0.0);
-        for (int j = 0; j < L; ++j) {
-          const double2 a = V[(size_t)u * L + j], b = U[(size_t)v * L + j];
-          acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
-          acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
-        }
-        T[pk(u, v, m)] = acc;
+        const DirOp ov = ops[v];
+        double2 sj;
+        if (ou.loc == 0 && ov.loc == 0) sj = Gt[ou.ph + ov.ph + 2 * L];
+        else if (ou.loc == 0) { const double2 w = Wt[wrap2L(ou.ph * ov.loc, L)]; sj = make_double2(w.x * rn, w.y * rn); }
+        else if (ov.loc == 0) { const double2 w = Wt[wrap2L(ov.ph * ou.loc, L)]; sj = make_double2(w.x * rn, w.y * rn); }
+        else sj = make_double2(ou.loc == ov.loc ? 1.0 : 0.0, 0.0);
+        T[pk(u, v, m)] = cmul(cmul(ou.b, ov.a), sj);
       }
-    __syncthreads();
-    const double2 pf = pf_packed(T, m, rowR, tau);
-    if (threadIdx.x == 0) {
+    }
+    __syncwarp();
+    const double2 pf = pf_packed_warp(T, m, rowR, tau, lane);
+    if (lane == 0) {
       const double re = vac_norm * pf.x, im = vac_norm * pf.y;
       if (!(isfinite(re) && isfinite(im))) atomicOr(status, kStNan);
       out[2 * q] = re;
       out[2 * q + 1] = im;
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
@@ -332,9 +431,13 @@ tgba_status z_reduced_elements(Basis& b, int s, int parity, int j, int J, const 
   return TGBA_OK;
 }
 
-size_t x_direct_smem(int L, int max_qp, int jmid) {
-  const size_t m = (size_t)(2 * L + 2 * max_qp + (jmid > 0 ? 2 * jmid : 0));
-  return sizeof(double2) * (2 * m * L + m * (m - 1) / 2 + 2 * m);
+// shared memory of one warp's element (string, packed triangle, scratch) and of the CTA tables
+size_t x_direct_warp_smem(int L, int max_qp, int jmid) {
+  const size_t m = (size_t)(2 * L + 2 * max_qp + (jmid > 0 ? 2 * jmid : 1));
+  return sizeof(double2) * (m * (m - 1) / 2 + 2 * m) + sizeof(DirOp) * m;
+}
+size_t x_direct_smem(int L, int max_qp, int jmid) {       // one warp per CTA: the least that must fit
+  return sizeof(double2) * (size_t)(6 * L + 1) + x_direct_warp_smem(L, max_qp, jmid);
 }
 
 // Elements <phi_a|O|phi_b> for explicit (a, b) pairs of sector s: O = sigma^x_1 between NS bra
@@ -343,18 +446,26 @@ tgba_status direct_elements(Basis& b, int s, int parity, int jmid, const int32_t
                             cudaStream_t st) {
   if (n == 0) return TGBA_OK;
   const Sector& sec = b.sectors[s];
-  const size_t smem = x_direct_smem(b.L, b.max_qp, jmid);
-  TGBA_CUDA(cudaFuncSetAttribute(x_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int sms = 0;
+  // warps per CTA: as many elements as fit in about half of an SM's shared memory (two CTAs
+  // per SM), at most 8
+  int limit = 0, sms = 0;
+  TGBA_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.device));
   TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
-  const int64_t grid = std::min<int64_t>(n, (int64_t)sms * 8);
+  const size_t tables = sizeof(double2) * (size_t)(6 * b.L + 1), per_warp = x_direct_warp_smem(b.L, b.max_qp, jmid);
+  if (tables + per_warp > (size_t)limit) return fail(TGBA_EINVAL, "direct string does not fit in shared memory");
+  const int wpc = (int)std::max<size_t>(1, std::min<size_t>(8, ((size_t)limit / 2 - tables) / per_warp));
+  const size_t smem = tables + (size_t)wpc * per_warp;
+  TGBA_CUDA(cudaFuncSetAttribute(x_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  TGBA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, x_direct_kernel, 32 * wpc, smem));
+  const int64_t grid = std::min<int64_t>((n + wpc - 1) / wpc, (int64_t)sms * std::max(1, per_sm));
   const int pa_par = jmid < 0 ? 0 : parity, pb_par = jmid < 0 ? 1 : parity;
   const int64_t a_off = pa_par ? sec.r_off : sec.ns_off, b_off = pb_par ? sec.r_off : sec.ns_off;
   const int64_t n_a = pa_par ? sec.n_r : sec.n_ns, n_b = pb_par ? sec.n_r : sec.n_ns;
   const double norm = jmid < 0 ? b.vac_norm : (parity ? b.norm_r * b.norm_r : b.norm_ns * b.norm_ns);
-  x_direct_kernel<<<(unsigned)grid, kDirThreads, smem, st>>>(pairs, n, pa_par, pb_par, jmid, a_off, b_off, n_a, n_b, b.L,
-                                                             b.d_theta, b.d_nlab, b.d_modes_ns, b.d_modes_r, b.max_qp,
-                                                             norm, out, b.d_status);
+  x_direct_kernel<<<(unsigned)grid, 32 * wpc, smem, st>>>(pairs, n, pa_par, pb_par, jmid, a_off, b_off, n_a, n_b, b.L,
+                                                          b.d_theta, b.d_nlab, b.d_modes_ns, b.d_modes_r, b.max_qp,
+                                                          norm, wpc, out, b.d_status);
   TGBA_CUDA(cudaGetLastError());
   ++b.launches;
   return TGBA_OK;

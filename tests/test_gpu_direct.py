@@ -1,6 +1,6 @@
 """The paper-literal evaluation of X (tgba_x_direct: one complex Pfaffian of size 2L + M_a + M_b
-per element, Eq. S1-S2) against the reduced form on the GPU (tgba_x_pairs) and against the
-oracle's direct Pfaffians."""
+per element, Eq. S1-S2, a warp per element) against the reduced form on the GPU (tgba_x_pairs)
+and against the oracle's direct Pfaffians, up to the paper's L = 60."""
 import numpy as np
 import pytest
 import torch
@@ -29,7 +29,7 @@ def _both(b, s, pairs):
 
 
 @pytest.mark.parametrize("L,h,m,mq,cut,count", [(12, 1.0, 0, 12, None, 600), (10, 0.6, 3, 10, None, 400),
-                                                (24, 1.0, 7, 6, 11.925, 1500)])
+                                                (24, 1.0, 7, 6, 11.925, 1500), (60, 1.0, 0, 4, 3.0, 300)])
 def test_direct_equals_reduced_and_oracle(L, h, m, mq, cut, count):
     b = tgba.tgba_build_basis(L, h, [m], mq, -1.0 if cut is None else cut)
     try:
@@ -51,7 +51,7 @@ def test_direct_equals_reduced_and_oracle(L, h, m, mq, cut, count):
 
 
 def test_direct_rejects_too_long_strings_and_bad_indices():
-    b = tgba.tgba_build_basis(60, 1.0, [0], 2, 3.0)       # string of 124 operators: too big
+    b = tgba.tgba_build_basis(80, 1.0, [0], 2, 3.0)       # string of 164 operators: too big for one warp's triangle
     try:
         tgba.tgba_compute_x(b)
         p = torch.zeros((1, 2), dtype=torch.int32, device="cuda")
