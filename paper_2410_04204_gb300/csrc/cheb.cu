@@ -232,7 +232,10 @@ __global__ void cheb_gamma(int K1, const double* __restrict__ Grr, const double*
 // (J_{k-1} = (2k/x) J_k - J_{k+1} from a start far above k and x, normalised by
 // J_0 + 2 sum J_2j = 1), one thread per time.  out is [k][t] (row k at out + k n_t), so a
 // warp's stores of one k are consecutive; 2k/x is 2k times 1/x, taken once (no FP64 division
-// in the recurrence).
+// in the recurrence).  When the unnormalised values pass 1e250 the recurrence is rescaled by
+// 1e-250 without touching the values already stored: an entry stored before one rescaling
+// gets the factor 1e-250 at the end, one stored before two or more is below 1e-236 of the
+// result and becomes 0, so only the positions of the last two rescalings are kept.
 __global__ void cheb_bessel(int n_t, int t0, double dt, double R, int K, int m_start, double* __restrict__ out) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_t) return;
@@ -246,23 +249,27 @@ __global__ void cheb_bessel(int n_t, int t0, double dt, double R, int K, int m_s
   }
   const double ix2 = 2.0 / x;
   double jp1 = 0.0, j = 1e-300, norm = 0.0;
+  int k_last = 1 << 30, k_prev = 1 << 30;     // the last two rescalings (entry q was stored before
+                                               // the one at k iff q + 1 >= k)
   for (int k = m_start; k >= 1; --k) {
     const double jm1 = fma((double)k * ix2, j, -jp1);
     jp1 = j;
     j = jm1;                                   // j = J_{k-1} (unnormalised)
     if (k - 1 <= K) a[(k - 1) * S] = j;
     if ((k - 1) % 2 == 0 && k - 1 > 0) norm += 2.0 * j;
-    if (fabs(j) > 1e250) {                     // rescale everything accumulated so far
+    if (fabs(j) > 1e250) {
       const double sc = 1e-250;
       j *= sc; jp1 *= sc; norm *= sc;
-      for (int q = k - 1; q <= K && q <= m_start; ++q) a[q * S] *= sc;
+      k_prev = k_last;
+      k_last = k;
     }
   }
   norm += j;                                   // + J_0
   const double inv = 1.0 / norm;
-  a[0] *= inv;
-  const double inv2 = 2.0 * inv;
-  for (int k = 1; k <= K; ++k) a[k * S] *= inv2;
+  for (int q = 0; q <= K; ++q) {
+    const double f = (q + 1 >= k_prev) ? 0.0 : (q + 1 >= k_last ? 1e-250 : 1.0);
+    a[q * S] *= (q == 0 ? inv : 2.0 * inv) * f;
+  }
 }
 
 // mx[t] = (a(t)^T Gamma a(t) - e_shift) * scale, one warp per time (A = a [k][t], GA = Gamma a
