@@ -348,6 +348,9 @@ def screening_leg(b24, tgba, inputs, torch, bf16_peak_tflops):
 # DRAM bytes of one sytrd_groups launch on the L = 24 all-sector workload, measured with ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum); None until measured for the current kernel.
 SYTRD_TRAFFIC = 487853093632 + 493968308224
+# DRAM bytes (read + write) of the Pfaffian stage's one launch on this workload, from one ncu
+# capture (profiles/pf_reg_queue_L24_all_sectors.md)
+PF_TRAFFIC = 966912 + 116337664
 
 
 def eigen_solver_leg(b, w, evs, tgba, torch):
@@ -436,7 +439,10 @@ def run_gb300(args):
     peak_src = "live FP64 DFMA-chain kernel (tgba_fp64_peak); MEASURED_PEAKS.json has no FP64 entry"
     pf_roof = {"bound": "alu", "kernel": "pf_reg_queue / pf_tiles (FP64 Parlett-Reid Pfaffians)",
                "achieved": pf_gflops, "peak": peak_gflops, "unit": "GFLOP/s", "frac": pf_gflops / peak_gflops,
-               "traffic": None, "peak_source": peak_src, "flops_per_launch": prof["pfaffian_flops"],
+               "traffic": PF_TRAFFIC if prof["pfaffian_launches"] == 1 else None,
+               "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of the stage's one launch on this "
+                                 "workload (one ncu capture)",
+               "peak_source": peak_src, "flops_per_launch": prof["pfaffian_flops"],
                "ms": pf_mean, "launches_per_stage": prof["pfaffian_launches"],
                "autotune": {"mode": prof["tune_mode"], "threads": prof["tune_threads"],
                             "candidates_ms": [round(x, 3) for x in prof["tune_ms"]]}}
