@@ -24,14 +24,12 @@
 //  the FP32 rounding of the accumulator that the digit diagonals 3..5 share.
 //
 // Tiles: 128 rows of A x up to 128 rows of B (n_eff, a multiple of 16, per tile) x K in blocks
-// of 16 (32-byte rows, 32-byte swizzle: one MMA of K = 16 per slice pair).  The slices of one
-// (row block, K block) are stored contiguously, already in the shared-memory image the MMA
-// descriptors read, so each stage is two bulk copies (cp.async.bulk: 24 KB of A slices, 24 KB
-// of B slices) completing on an mbarrier.  Warp 0 issues the copies, warp 1 the MMAs (one
-// thread each), warps 2-9 fold the accumulators and write C (each TMEM lane quarter by two
-// warps, 64 columns each).  Four smem stages: with K blocks of 32 only two stages of 96 KB
-// fitted, and the copies of A from HBM did not keep up with the MMAs (DRAM at 30% of its
-// peak with the tensor pipe busy 43% of the cycles).  N = 128 per MMA instead of 64 halves the shared-memory operand traffic per flop
+// of 32 (64-byte rows, 64-byte swizzle).  The slices of one (row block, K block) are stored
+// contiguously, already in the shared-memory image the MMA descriptors read, so each stage is
+// two bulk copies (cp.async.bulk: 48 KB of A slices, 48 KB of B slices) completing on an
+// mbarrier.  Warp 0 issues the copies, warp 1 the MMAs (one thread each), warps 2-9 fold the
+// accumulators and write C (each TMEM lane quarter by two warps, 64 columns each).  Two smem
+// stages.  N = 128 per MMA instead of 64 halves the shared-memory operand traffic per flop
 // (measured at N = 64, the tensor pipe was busy 72% of the active cycles for 31% of its peak
 // FLOP rate).  A tile may use fewer columns in later K blocks: per 16-column group the tile
 // lists how many K blocks its columns reach, and each block's MMAs take N = the columns still
@@ -62,15 +60,15 @@ namespace tgba {
 namespace {
 
 constexpr int kS = 6;                     // slices per operand (base-256 digits)
-constexpr int kKB = 16;                   // K per block (32-byte rows: one MMA of K = 16)
+constexpr int kKB = 32;                   // K per block (64-byte rows)
 constexpr int kTMr = 128;                 // rows of A per tile
 constexpr int kTNr = 128;                 // rows of B per tile
-constexpr int kChunkBlocks = 8;           // K blocks per exact FP32 chunk (128 K values)
-constexpr uint32_t kASlice = kTMr * kKB * 2;          // 4 KB
-constexpr uint32_t kBSlice = kTNr * kKB * 2;          // 4 KB
-constexpr uint32_t kAStage = kS * kASlice;            // 24 KB
-constexpr uint32_t kBStage = kS * kBSlice;            // 24 KB
-constexpr int kStages = 4;
+constexpr int kChunkBlocks = 4;           // K blocks per exact FP32 chunk (128 K values)
+constexpr uint32_t kASlice = kTMr * kKB * 2;          // 8 KB
+constexpr uint32_t kBSlice = kTNr * kKB * 2;          // 8 KB
+constexpr uint32_t kAStage = kS * kASlice;            // 48 KB
+constexpr uint32_t kBStage = kS * kBSlice;            // 48 KB
+constexpr int kStages = 2;
 constexpr uint32_t kSmem = 1024 + kStages * (kAStage + kBStage) + 256;
 constexpr unsigned kWait = 1u << 24;                   // polls of a bounded wait
 constexpr int kThreads = 320;
@@ -78,17 +76,16 @@ constexpr int kEpiWarps = 8;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// byte offset of element (r, k) in a tile slice: 32-byte rows, the two 16-byte chunks of row
-// r swapped when bit 2 of r is set (the 32-byte swizzle: byte-offset bit 4 XOR bit 7)
-__host__ __device__ __forceinline__ uint32_t sw32(int r, int k) {
-  return (uint32_t)(r * 32 + ((((k >> 3) ^ (r >> 2)) & 1) << 4) + (k & 7) * 2);
+// byte offset of element (r, k) in a tile slice: 64-byte rows, 16-byte chunks XOR (r / 2) mod 4
+__host__ __device__ __forceinline__ uint32_t sw64(int r, int k) {
+  return (uint32_t)(r * 64 + ((((k >> 3) ^ (r >> 1)) & 3) << 4) + (k & 7) * 2);
 }
 
-// Descriptor: start >> 4, LBO 1 (unused for swizzled K-major), SBO 256 B (8-row groups),
-// version 1, swizzle mode 6 = 32 B.
-__device__ __forceinline__ uint64_t desc32(uint32_t addr) {
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(256 >> 4) << 32) | ((uint64_t)1 << 46) |
-         ((uint64_t)6 << 61);
+// Descriptor: start >> 4, LBO 1 (unused for swizzled K-major), SBO 512 B (8-row groups),
+// version 1, swizzle mode 4 = 64 B.
+__device__ __forceinline__ uint64_t desc64(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) |
+         ((uint64_t)4 << 61);
 }
 
 __device__ __forceinline__ uint32_t idesc_f16(int n) {        // D f32, A/B bf16, K-major, M = 128
@@ -313,7 +310,10 @@ __global__ void __maxnreg__(168) dgemm_tc_kernel(GemmArgs g) {   // 320 threads 
                 // first write of accumulator d in this chunk overwrites it: pair (0, d) for d <= 2,
                 // (0, 3) for the shared one, at the chunk's first K block
                 const bool first = kb == kb0 && p == 0 && q == (d < 3 ? d : 3);
-                mma(tmem + (uint32_t)d * 128u, desc32(a0 + p * kASlice), desc32(b0 + q * kBSlice), id, first ? 0u : 1u);
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks)
+                  mma(tmem + (uint32_t)d * 128u, desc64(a0 + p * kASlice + ks * 32), desc64(b0 + q * kBSlice + ks * 32), id,
+                      (first && ks == 0) ? 0u : 1u);
               }
             commit(empty + st);                       // the stage's smem is free once these complete
             last = empty + st;
@@ -487,15 +487,15 @@ __global__ void row_exponents_long(int rows, int K, const double* __restrict__ s
 }
 
 // Slices of X (rows x K, element (i, k) at src[i row_stride + k k_stride (+ k_jump for k >= k_split)],
-// optionally times w[k] - w_shift) as tile images [row block][K block][slice][tile rows][16] (bf16,
-// 32-byte swizzle); rows and K beyond the matrix are zero.  The value 2^-e x (|.| < 1) is rounded
+// optionally times w[k] - w_shift) as tile images [row block][K block][slice][tile rows][32] (bf16,
+// 64-byte swizzle); rows and K beyond the matrix are zero.  The value 2^-e x (|.| < 1) is rounded
 // to a 48-bit fixed-point integer F (from the mantissa and exponent fields), which is cut into
 // six balanced base-256 digits, d_p = round(F / 2^(40 - 8p)), F -= d_p 2^(40 - 8p).
 __global__ void slice_tiles(int rows, int K, const double* __restrict__ src, int64_t row_stride, int64_t k_stride,
                             int k_split, int64_t k_jump, const double* __restrict__ w, double w_shift,
                             const int* __restrict__ e, int tile_rows, int n_kb, __nv_bfloat16* __restrict__ out) {
   // one thread per 8 consecutive K values of a row: each slice gets one 16-byte store (the
-  // 32-byte swizzle moves whole 16-byte chunks, so the 8 values stay contiguous)
+  // 64-byte swizzle moves whole 16-byte chunks, so the 8 values stay contiguous)
   const int n_rb = (rows + tile_rows - 1) / tile_rows;
   const int64_t k8s = (int64_t)n_kb * (kKB / 8);
   const int64_t total = (int64_t)n_rb * tile_rows * k8s;
@@ -525,7 +525,7 @@ __global__ void slice_tiles(int rows, int K, const double* __restrict__ src, int
         }
       }
     }
-    unsigned char* tile = (unsigned char*)out + ((size_t)rb * n_kb + kb) * kS * slice_bytes + sw32(r, kk);
+    unsigned char* tile = (unsigned char*)out + ((size_t)rb * n_kb + kb) * kS * slice_bytes + sw64(r, kk);
 #pragma unroll
     for (int p = 0; p < kS; ++p) {
       const int shp = 40 - 8 * p;
