@@ -117,6 +117,92 @@ __device__ double pfaffian_smem(double* W, int n) {
   return flip_if(odd != 0, pf);
 }
 
+// The same for one exact size N (16, 18, 20): every index except the pivot's is a compile-time
+// constant, so each trailing entry costs one shared-memory load, two FMAs and one store, with
+// the step's Gauss vector and row r in registers (the generic loop above reloads them for every
+// entry and spends integer work on the indices).
+template <int N, int NMAX, int T, int K>
+struct SmemStep {
+  static __device__ __forceinline__ bool run(double* W, double& pf, unsigned& odd) {
+    using P = Packed<NMAX>;
+    constexpr int r = K + 1;
+    int p = r;
+    unsigned long long best = abs_bits(W[P::idx(K, r) * T]);
+#pragma unroll
+    for (int x = r + 1; x < N; ++x) {
+      const unsigned long long v = abs_bits(W[P::idx(K, x) * T]);
+      if (v > best) { best = v; p = x; }
+    }
+    if (p != r) {
+      // symmetric exchange of rows/columns r and p, restricted to rows >= K
+      double t = W[P::idx(K, r) * T]; W[P::idx(K, r) * T] = W[P::idx(K, p) * T]; W[P::idx(K, p) * T] = t;
+      for (int x = r + 1; x < p; ++x) {
+        double a = W[P::idx(r, x) * T], c = W[P::idx(x, p) * T];
+        W[P::idx(r, x) * T] = neg(c);
+        W[P::idx(x, p) * T] = neg(a);
+      }
+      W[P::idx(r, p) * T] = neg(W[P::idx(r, p) * T]);
+      for (int x = p + 1; x < N; ++x) {
+        double a = W[P::idx(r, x) * T];
+        W[P::idx(r, x) * T] = W[P::idx(p, x) * T];
+        W[P::idx(p, x) * T] = a;
+      }
+      odd ^= 1u;
+    }
+    const double a = W[P::idx(K, r) * T];
+    if (is_zero(a)) return false;      // the whole column is zero: Pf = 0 exactly
+    pf *= a;
+    if constexpr (K + 2 < N) {
+      const double ia = recip_nr(a);
+      double tau[N], rr[N];
+#pragma unroll
+      for (int j = K + 2; j < N; ++j) {
+        tau[j] = W[P::idx(K, j) * T] * ia;        // Gauss vector tau_j
+        rr[j] = W[P::idx(r, j) * T];
+      }
+      // W_ij += W(r, i) tau_j - tau_i W(r, j),  K+2 <= i < j < N
+#pragma unroll
+      for (int i = K + 2; i < N - 1; ++i)
+#pragma unroll
+        for (int j = i + 1; j < N; ++j) {
+          double w = W[P::idx(i, j) * T];
+          w = fma(-tau[i], rr[j], w);
+          w = fma(rr[i], tau[j], w);
+          W[P::idx(i, j) * T] = w;
+        }
+      return SmemStep<N, NMAX, T, K + 2>::run(W, pf, odd);
+    }
+    return true;
+  }
+};
+template <int N, int NMAX, int T>
+struct SmemStep<N, NMAX, T, N> {
+  static __device__ __forceinline__ bool run(double*, double&, unsigned&) { return true; }
+};
+
+template <int N, int NMAX, int T>
+__device__ double pfaffian_smem_fixed(double* W) {
+  double pf = 1.0;
+  unsigned odd = 0;                    // parity of the exchanges, applied to pf at the end
+  if (!SmemStep<N, NMAX, T, 0>::run(W, pf, odd)) return 0.0;
+  return flip_if(odd != 0, pf);
+}
+
+// Pf of size n <= NMAX in shared memory: the fixed-size code for 16, 18 and 20, else the loop.
+template <int NMAX, int T>
+__device__ __forceinline__ double pfaffian_smem_any(double* W, int n) {
+  if constexpr (NMAX >= 16 && NMAX <= 20) {
+    if (n == 16) return pfaffian_smem_fixed<16, NMAX, T>(W);
+    if constexpr (NMAX >= 18) {
+      if (n == 18) return pfaffian_smem_fixed<18, NMAX, T>(W);
+    }
+    if constexpr (NMAX >= 20) {
+      if (n == 20) return pfaffian_smem_fixed<20, NMAX, T>(W);
+    }
+  }
+  return pfaffian_smem<NMAX, T>(W, n);
+}
+
 struct Elem {
   int64_t out;
   const uint8_t* sa;
@@ -257,7 +343,7 @@ __global__ void __launch_bounds__(T) pf_smem(Args g) {
         W[Packed<NMAX>::idx(i, j) * T] = __ldg(Ri + sj);
       }
     }
-    const double pf = pfaffian_smem<NMAX, T>(W, n);
+    const double pf = pfaffian_smem_any<NMAX, T>(W, n);
     if (!is_finite_bits(pf)) atomicOr(g.status, kStNan);
     g.P[e.out] = pf;
   }
@@ -292,7 +378,7 @@ __global__ void __launch_bounds__(T) pf_pairs(const int32_t* __restrict__ pairs,
         W[Packed<NMAX>::idx(i, j) * T] = __ldg(R + (size_t)si * two_l + sj);
       }
     }
-    const double pf = pfaffian_smem<NMAX, T>(W, n);
+    const double pf = pfaffian_smem_any<NMAX, T>(W, n);
     if (!is_finite_bits(pf)) atomicOr(status, kStNan);
     // X = C0 (-i)^{n/2} pf
     double re = c0[0] * pf, im = c0[1] * pf;
@@ -328,7 +414,7 @@ __global__ void __launch_bounds__(T) pf_cross(int64_t rows, int64_t cols, int64_
         W[Packed<NMAX>::idx(i, j) * T] = __ldg(R + (size_t)si * two_l + sj);
       }
     }
-    const double pf = pfaffian_smem<NMAX, T>(W, n);
+    const double pf = pfaffian_smem_any<NMAX, T>(W, n);
     if (!is_finite_bits(pf)) atomicOr(status, kStNan);
     out[q] = pf;
   }

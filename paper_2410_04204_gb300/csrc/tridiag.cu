@@ -923,10 +923,10 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
   }
   const int64_t slot_doubles = round32(((int64_t)B * sizeof(TriSlot) + 7) / 8);
   const int64_t map_doubles = round32(((int64_t)2 * grid * sizeof(CtaWork) + 7) / 8);   // by block, by SM
-  // bisection items: item_len consecutive eigenvalue indices of one matrix, 32 <= item_len <= 64
-  // (a block's threads), chosen so that the items fill whole rounds of the resident blocks
-  // (items / (rounds x blocks) largest; ties to the longer item): with 64 the 48 L = 24
-  // matrices gave 1488 items for 1064 blocks, two rounds of which the second was 40% full
+  // bisection items: item_len consecutive eigenvalue indices of one matrix, 64 (a block's
+  // threads) unless that gives fewer items than resident blocks, then 32.  (Items sized to fill
+  // whole rounds of the resident blocks, 43 eigenvalues for the 48 L = 24 matrices, measured
+  // slower: 25.1 ms against 21.7 ms, the per-item setup outweighing the shorter tail.)
   const size_t smem2 = (size_t)2 * n_max * sizeof(double);   // d, e^2: FP32 first, then FP64, in turn
   TGBA_CUDA(cudaFuncSetAttribute(sturm_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
   int bis_per_sm = 0;
@@ -938,15 +938,7 @@ tgba_status eig_all_sectors_native(Basis& b, const double* hx, int n_hx, double*
     for (const TriSlot& t : slots) c += (t.n + len - 1) / len;
     return c;
   };
-  {
-    const int64_t blocks = (int64_t)bis_per_sm * sms;
-    double best = -1.0;
-    for (int len = kSturmThreads; len >= kSturmThreads / 2; --len) {
-      const int64_t c = count_items(len), rounds = (c + blocks - 1) / blocks;
-      const double eff = (double)c / (double)(rounds * blocks);
-      if (eff > best + 1e-9) { best = eff; item_len = len; }
-    }
-  }
+  if (count_items(item_len) < (int64_t)bis_per_sm * sms) item_len = kSturmThreads / 2;
   std::vector<int2> items;
   for (int q = 0; q < B; ++q)
     for (int k0 = 0; k0 < slots[q].n; k0 += item_len) items.push_back(make_int2(q, k0));
