@@ -210,13 +210,15 @@ __global__ void cheb_dot01(int64_t n, const double* __restrict__ v0, const doubl
   if (threadIdx.x == 0) *out = s;
 }
 
-// Gamma_kl = Re(i^{k-l} mu_kl), mu = (G_rr + G_ii) + i (G_ri - G_ri^T), G column-major K1 x K1
+// Gamma_kl = Re(i^{k-l} mu_kl), mu = (G_rr + G_ii) + i (G_ri - G_ri^T), G column-major K1 x K1;
+// G_rr and G_ii are symmetric and only their lower triangle (row >= column) is computed
 __global__ void cheb_gamma(int K1, const double* __restrict__ Grr, const double* __restrict__ Gii,
                            const double* __restrict__ Gri, double* __restrict__ Gam) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)K1 * K1; q += (int64_t)gridDim.x * blockDim.x) {
     const int l = (int)(q / K1), k = (int)(q % K1);
     const int64_t kl = (int64_t)l * K1 + k, lk = (int64_t)k * K1 + l;
-    const double re = Grr[kl] + Gii[kl], im = Gri[kl] - Gri[lk];
+    const int64_t low = k >= l ? kl : lk;
+    const double re = Grr[low] + Gii[low], im = Gri[kl] - Gri[lk];
     double g;
     switch (((k - l) % 4 + 4) % 4) {
       case 0: g = re; break;
@@ -654,7 +656,7 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
     DevBuf mbuf(st);
     const size_t mdoubles = 4 * (size_t)K1 * K1 + 2 * (size_t)K1 * nt + chi_max + 8;
     TGBA_CUDA(cudaMallocAsync(&mbuf.p, mdoubles * 8 + (2 * sa + 2 * sb) * 2 + 4 * ((size_t)K1 + nt) * 4 +
-                                           n_tiles_max * sizeof(EmuTile) + 1024, st));
+                                           2 * n_tiles_max * sizeof(EmuTile) + 1024, st));
     double* Grr = (double*)mbuf.p;
     double* Gii = Grr + (size_t)K1 * K1;
     double* Gri = Gii + (size_t)K1 * K1;
@@ -664,7 +666,8 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
     double* Ek = GA + (size_t)K1 * nt;
     double* d01 = Ek + chi_max;
     EmuTile* dtg = (EmuTile*)(((uintptr_t)(d01 + 8) + 15) & ~(uintptr_t)15);
-    __nv_bfloat16* Vr = (__nv_bfloat16*)(((uintptr_t)(dtg + n_tiles_max) + 255) & ~(uintptr_t)255);
+    EmuTile* dlo = dtg + n_tiles_max;                     // the lower-triangle tiles of the Gram matrices
+    __nv_bfloat16* Vr = (__nv_bfloat16*)(((uintptr_t)(dlo + n_tiles_max) + 255) & ~(uintptr_t)255);
     __nv_bfloat16* Vi = Vr + sa;
     __nv_bfloat16* Wr = Vi + sa;
     __nv_bfloat16* Wi = Wr + sb;
@@ -672,10 +675,12 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
     int* evi = evr + K1;
     int* ewr = evi + K1;
     int* ewi = ewr + (K1 > nt ? K1 : nt);
-    auto grid_tiles = [&](int64_t rows, int64_t cols, int64_t kdim, int64_t& n_chunks) {
+    // output tiles of a product (lower: only the tiles on or below the diagonal, for a
+    // symmetric result that is read through its lower triangle; TR == TC)
+    auto grid_tiles = [&](int64_t rows, int64_t cols, int64_t kdim, int64_t& n_chunks, bool lower = false) {
       std::vector<EmuTile> t;
       for (int64_t rb = 0; rb * TR < rows; ++rb)
-        for (int64_t cb = 0; cb * TC < cols; ++cb)
+        for (int64_t cb = 0; cb * TC < cols && (!lower || cb <= rb); ++cb)
           t.push_back(EmuTile{(int32_t)rb, (int32_t)cb, (int32_t)std::min<int64_t>(TC, r16(cols - cb * TC)),
                               (int32_t)((kdim + emu_k_block() - 1) / emu_k_block())});
       n_chunks = emu_number_tiles(t);
@@ -692,10 +697,11 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
       kept_energy<<<blocks_for(chi), 256, 0, st>>>(kn, kr, kn_max, E, Ek);
       cheb_dot01<<<1, kRedThreads, 0, st>>>(n_un, vre, vre + S, d01);
       b.launches += 2;
-      int64_t cg = 0;
-      const std::vector<EmuTile> tgv = grid_tiles(k1, k1, chi, cg);
-      if (cg < 0) return fail(TGBA_EINVAL, "quench moment tiles");
+      int64_t cg = 0, cl = 0;
+      const std::vector<EmuTile> tgv = grid_tiles(k1, k1, chi, cg), tlo = grid_tiles(k1, k1, chi, cl, true);
+      if (cg < 0 || cl < 0) return fail(TGBA_EINVAL, "quench moment tiles");
       TGBA_CUDA(cudaMemcpyAsync(dtg, tgv.data(), tgv.size() * sizeof(EmuTile), cudaMemcpyHostToDevice, st));
+      TGBA_CUDA(cudaMemcpyAsync(dlo, tlo.data(), tlo.size() * sizeof(EmuTile), cudaMemcpyHostToDevice, st));
       // rows k of V (K = the kept rows in their own order: kn NS rows, then kr R rows)
       const int64_t jump = kn_max - kn;
       if ((r = emu_slice(b, vre, S, 1, (int)kn, jump, nullptr, 0.0, k1, (int)chi, TR, Vr, evr, st)) != TGBA_OK) return r;
@@ -704,9 +710,9 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
       if ((r = emu_slice(b, vre, S, 1, (int)kn, jump, Ek, ec[v], k1, (int)chi, TC, Wr, ewr, st)) != TGBA_OK) return r;
       if ((r = emu_slice(b, vre + n_un, S, 1, (int)kn, jump, Ek, ec[v], k1, (int)chi, TC, Wi, ewi, st)) != TGBA_OK)
         return r;
-      if ((r = emu_gemm(b, Vr, evr, k1, (int)chi, Wr, ewr, k1, (int)chi, dtg, (int)tgv.size(), cg, Grr, k1, st)) != TGBA_OK)
+      if ((r = emu_gemm(b, Vr, evr, k1, (int)chi, Wr, ewr, k1, (int)chi, dlo, (int)tlo.size(), cl, Grr, k1, st)) != TGBA_OK)
         return r;
-      if ((r = emu_gemm(b, Vi, evi, k1, (int)chi, Wi, ewi, k1, (int)chi, dtg, (int)tgv.size(), cg, Gii, k1, st)) != TGBA_OK)
+      if ((r = emu_gemm(b, Vi, evi, k1, (int)chi, Wi, ewi, k1, (int)chi, dlo, (int)tlo.size(), cl, Gii, k1, st)) != TGBA_OK)
         return r;
       if ((r = emu_gemm(b, Vr, evr, k1, (int)chi, Wi, ewi, k1, (int)chi, dtg, (int)tgv.size(), cg, Gri, k1, st)) != TGBA_OK)
         return r;
