@@ -62,6 +62,31 @@ __device__ __forceinline__ int find_rect(const Rect* __restrict__ rects, int n, 
   return lo;
 }
 
+// Symmetric exchange of rows/columns r = k + 1 and p >= r of the packed matrix, restricted to
+// rows >= k, as one loop of the same length for every lane whatever its pivot (lanes of a warp
+// pivot differently; separate loops below and above p would diverge): entry (r, x) trades with
+// (x, p) negated for x < p, with (p, x) for x > p, and (r, p) is negated.  The addresses and the
+// sign are integer selects; p == r makes every step a no-op.
+template <int NMAX, int T>
+__device__ __forceinline__ void exchange_smem(double* W, int k, int p, int n) {
+  using P = Packed<NMAX>;
+  const int r = k + 1;
+  {
+    const int a1 = P::idx(k, r) * T, a2 = P::idx(k, p) * T;
+    const double v1 = W[a1], v2 = W[a2];
+    W[a1] = v2;
+    W[a2] = v1;
+  }
+  for (int x = r + 1; x < n; ++x) {
+    const bool below = x <= p;
+    const int a1 = P::idx(r, x) * T;
+    const int a2 = (x < p ? P::idx(x, p) : (x == p ? P::idx(r, p) : P::idx(p, x))) * T;
+    const double v1 = W[a1], v2 = W[a2];
+    W[a1] = flip_if(below, v2);
+    W[a2] = flip_if(below, v1);
+  }
+}
+
 // Pf of the n x n skew matrix whose strict upper triangle is in W (packed, stride T).
 template <int NMAX, int T>
 __device__ double pfaffian_smem(double* W, int n) {
@@ -76,22 +101,8 @@ __device__ double pfaffian_smem(double* W, int n) {
       unsigned long long v = abs_bits(W[P::idx(k, x) * T]);
       if (v > best) { best = v; p = x; }
     }
-    if (p != r) {
-      // symmetric exchange of rows/columns r and p, restricted to rows >= k
-      double t = W[P::idx(k, r) * T]; W[P::idx(k, r) * T] = W[P::idx(k, p) * T]; W[P::idx(k, p) * T] = t;
-      for (int x = r + 1; x < p; ++x) {
-        double a = W[P::idx(r, x) * T], c = W[P::idx(x, p) * T];
-        W[P::idx(r, x) * T] = neg(c);
-        W[P::idx(x, p) * T] = neg(a);
-      }
-      W[P::idx(r, p) * T] = neg(W[P::idx(r, p) * T]);
-      for (int x = p + 1; x < n; ++x) {
-        double a = W[P::idx(r, x) * T];
-        W[P::idx(r, x) * T] = W[P::idx(p, x) * T];
-        W[P::idx(p, x) * T] = a;
-      }
-      odd ^= 1u;
-    }
+    exchange_smem<NMAX, T>(W, k, p, n);
+    odd ^= (p != r) ? 1u : 0u;
     const double a = W[P::idx(k, r) * T];
     if (is_zero(a)) return 0.0;        // the whole column is zero: Pf = 0 exactly
     pf *= a;
@@ -133,22 +144,8 @@ struct SmemStep {
       const unsigned long long v = abs_bits(W[P::idx(K, x) * T]);
       if (v > best) { best = v; p = x; }
     }
-    if (p != r) {
-      // symmetric exchange of rows/columns r and p, restricted to rows >= K
-      double t = W[P::idx(K, r) * T]; W[P::idx(K, r) * T] = W[P::idx(K, p) * T]; W[P::idx(K, p) * T] = t;
-      for (int x = r + 1; x < p; ++x) {
-        double a = W[P::idx(r, x) * T], c = W[P::idx(x, p) * T];
-        W[P::idx(r, x) * T] = neg(c);
-        W[P::idx(x, p) * T] = neg(a);
-      }
-      W[P::idx(r, p) * T] = neg(W[P::idx(r, p) * T]);
-      for (int x = p + 1; x < N; ++x) {
-        double a = W[P::idx(r, x) * T];
-        W[P::idx(r, x) * T] = W[P::idx(p, x) * T];
-        W[P::idx(p, x) * T] = a;
-      }
-      odd ^= 1u;
-    }
+    exchange_smem<NMAX, T>(W, K, p, N);
+    odd ^= (p != r) ? 1u : 0u;
     const double a = W[P::idx(K, r) * T];
     if (is_zero(a)) return false;      // the whole column is zero: Pf = 0 exactly
     pf *= a;
