@@ -658,9 +658,9 @@ __device__ __forceinline__ int sturm_count32(const float* __restrict__ d, const 
 // single-precision bisection down to a bracket of 2^-21 ||T|| (FP32 runs at 64 times the FP64
 // rate on this GPU); the bracket widened by the FP32 count's error bound is checked with two
 // FP64 counts (if the check fails the FP64 bisection restarts from the Gershgorin interval),
-// then, for an eigenvalue alone in its bracket, Newton's method on det(T - x) (two or three
-// evaluations of five FP64 operations per row instead of about 30 counts of three), else FP64
-// bisection to 4 eps ||T||.
+// then FP64 bisection to 4 eps ||T||, which hands over to Newton's method on det(T - x) as soon
+// as the bracket holds the eigenvalue alone (two or three evaluations of five FP64 operations per
+// row instead of about 30 counts of three).
 __global__ void __launch_bounds__(kSturmThreads)
 sturm_bisect(const TriSlot* __restrict__ slots, const int2* __restrict__ items, int n_items, int item_len,
              unsigned* __restrict__ queue, const double* __restrict__ ws, double* __restrict__ evals,
@@ -750,41 +750,49 @@ sturm_bisect(const TriSlot* __restrict__ slots, const int2* __restrict__ items, 
     // FP64: the FP32 bracket widened by the bound, checked; else the Gershgorin interval
     const double dl = (double)dl32 / sig;
     double a = (double)a32 / sig - dl, b = (double)b32 / sig + dl;
-    const int ca = sturm_count(d, e2, n, a), cb = sturm_count(d, e2, n, b);
+    int ca = sturm_count(d, e2, n, a), cb = sturm_count(d, e2, n, b);
     if (!(ca <= k && cb > k)) {
       a = lo - fudge;
       b = hi + fudge;
+      ca = 0;
+      cb = n;
     }
     const double tol = 4.0 * eps * tnorm + 0x1p-1000;
-    if (ca == k && cb == k + 1) {
-      // the bracket holds this eigenvalue alone: Newton's method on det(T - x), kept inside the
-      // bracket, which every evaluation narrows (sign(det(T - x)) = (-1)^count(x), and
-      // count(a) = k); a step that leaves it is replaced by the midpoint.  Converged when a
-      // step is below tol; otherwise the bisection below finishes from the bracket.
-      const bool neg_at_a = (ca & 1) != 0;
-      double x = 0.5 * (a + b);
-      for (int i2 = 0; i2 < 8 && b - a > tol; ++i2) {
-        double pv, dpv;
-        char_poly(d, e2, n, x, pv, dpv);
-        if (!(isfinite(pv) && isfinite(dpv))) break;
-        if (((unsigned)__double2hiint(pv) >> 31) == (neg_at_a ? 1u : 0u)) a = x;
-        else b = x;
-        if (pv == 0.0) { a = b = x; break; }
-        double xn = x - pv / dpv;
-        if (fabs(xn - x) <= tol) {                          // converged (the step may touch a bracket end)
-          x = fmin(fmax(xn, a), b);
-          a = b = x;
-          break;
-        }
-        if (!(xn > a && xn < b)) xn = 0.5 * (a + b);
-        x = xn;
-      }
-    }
+    // FP64 bisection, keeping the counts of the bracket ends; as soon as the bracket holds
+    // this eigenvalue alone (count(a) = k, count(b) = k + 1: at once for most eigenvalues,
+    // after a few steps for near-degenerate ones), Newton's method on det(T - x) takes over,
+    // kept inside the bracket, which every evaluation narrows (sign(det(T - x)) =
+    // (-1)^count(x)); a step that leaves it is replaced by the midpoint.  Converged when a step
+    // is below tol; otherwise the bisection finishes from the narrowed bracket.
+    bool newton_tried = false;
     for (int i2 = 0; i2 < 200 && b - a > tol; ++i2) {
+      if (!newton_tried && ca == k && cb == k + 1) {
+        newton_tried = true;
+        const bool neg_at_a = (ca & 1) != 0;
+        double x = 0.5 * (a + b);
+        for (int i3 = 0; i3 < 8 && b - a > tol; ++i3) {
+          double pv, dpv;
+          char_poly(d, e2, n, x, pv, dpv);
+          if (!(isfinite(pv) && isfinite(dpv))) break;
+          if (((unsigned)__double2hiint(pv) >> 31) == (neg_at_a ? 1u : 0u)) a = x;
+          else b = x;
+          if (pv == 0.0) { a = b = x; break; }
+          double xn = x - pv / dpv;
+          if (fabs(xn - x) <= tol) {                        // converged (the step may touch a bracket end)
+            x = fmin(fmax(xn, a), b);
+            a = b = x;
+            break;
+          }
+          if (!(xn > a && xn < b)) xn = 0.5 * (a + b);
+          x = xn;
+        }
+        continue;
+      }
       const double mid = 0.5 * (a + b);
       if (mid <= a || mid >= b) break;
-      if (sturm_count(d, e2, n, mid) <= k) a = mid;
-      else b = mid;
+      const int c = sturm_count(d, e2, n, mid);
+      if (c <= k) { a = mid; ca = c; }
+      else { b = mid; cb = c; }
     }
     evals[S.out_off + k] = 0.5 * (a + b);
   }
