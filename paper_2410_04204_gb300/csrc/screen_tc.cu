@@ -4,8 +4,11 @@
 //
 // A pair (a, b) has h1 = relu(A_a + B_b) (the per-state layer-1 partials, FP32), z2 = W2 h1 + b2,
 // y = w3 . relu(z2) + b3.  One persistent CTA per SM holds W2 (BF16, 256 x 256, 128 KB) in
-// shared memory for the whole launch.  Per tile of 128 pairs of one rectangle of uniform
-// (M_a, M_b) (hence uniform Pfaffian size n):
+// shared memory for the whole launch.  Per tile of 8 x 16 pairs (8 NS states by 16 R states)
+// of one rectangle of uniform (M_a, M_b) (hence uniform Pfaffian size n):
+//   0. the CTA loads the tile's 8 + 16 partial rows (24 KB, coalesced) into shared memory, once
+//      per tile instead of once per pair (a tile of 128 pairs along one row read 128 R rows
+//      and one NS row, 129 KB, through L1);
 //   1. each of the 128 threads builds its pair's row of h1 (BF16) in shared memory, in the
 //      K-major layout with the 128-byte swizzle that the MMA's shared-memory descriptors read;
 //   2. one thread issues 16 MMAs (M = 128, N = 256, K = 16 each: D[128 x 256] += A B^T) into a
@@ -29,10 +32,14 @@ namespace {
 
 constexpr int kH = 256;                 // MLP width (N and K of the layer-2 MMA)
 constexpr int kTM = 128;                // pairs per tile (M of the MMA)
+constexpr int kTR = 8, kTC = 16;        // the tile's NS states x R states
+constexpr int kPartStride = kH + 4;     // floats per staged partial row (16 B of padding: the 16
+                                        // R rows a warp reads start in different banks)
 constexpr int kModelQp = 8;             // quasiparticles the features hold per state
 constexpr uint32_t kBBytes = kH * kH * 2;             // W2 in BF16: 128 KB
 constexpr uint32_t kABytes = kTM * kH * 2;            // one h1 tile: 64 KB
-constexpr uint32_t kSmemBytes = 1024 + kBBytes + kABytes + 2 * kH * 4 + 64;
+constexpr uint32_t kPartBytes = (kTR + kTC) * kPartStride * 4;   // staged partials: 24.4 KB
+constexpr uint32_t kSmemBytes = 1024 + kBBytes + kABytes + 2 * kH * 4 + 64 + kPartBytes;
 constexpr unsigned kWaitLimit = 1u << 22;             // polls of a bounded mbarrier wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -116,7 +123,7 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
 
 struct ScoreArgs {
   const Rect* rects;          // rectangles of uniform (M_a, M_b)
-  const int64_t* prefix;      // [n_rects + 1] first 128-pair tile of each rectangle
+  const int64_t* prefix;      // [n_rects + 1] first 8 x 16 tile of each rectangle
   int n_rects;
   int64_t n_tiles;
   const float* Apart;         // per NS state (global index): A_a [kH]
@@ -155,6 +162,8 @@ __global__ void __launch_bounds__(kTM, 1) score_tc(ScoreArgs g) {
   float* w3s = b2s + kH;
   uint64_t* bar = (uint64_t*)(w3s + kH);
   uint32_t* tmem_slot = (uint32_t*)(bar + 1);
+  float* partA = (float*)(tmem_slot + 14);        // [kTR][kPartStride] (16-byte aligned)
+  float* partB = partA + kTR * kPartStride;       // [kTC][kPartStride]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   __shared__ unsigned s_cnt[5];                   // kept pairs per warp of the tile, then the tile's base
 
@@ -186,24 +195,40 @@ __global__ void __launch_bounds__(kTM, 1) score_tc(ScoreArgs g) {
   for (int64_t t = blockIdx.x; t < g.n_tiles; t += gridDim.x) {
     const int ri = tile_rect(g.prefix, g.n_rects, t);
     const Rect rc = g.rects[ri];
-    const int64_t lin = (t - g.prefix[ri]) * kTM + tid;
-    const bool valid = lin < (int64_t)rc.rows * rc.w;
-    const int row = valid ? (int)(lin / rc.w) : 0, col = valid ? (int)(lin - (lin / rc.w) * rc.w) : 0;
+    const int n_tc = (rc.w + kTC - 1) / kTC;
+    const int64_t it = t - g.prefix[ri];
+    const int row0 = (int)(it / n_tc) * kTR, col0 = (int)(it % n_tc) * kTC;
+    const int row = row0 + (tid >> 4), col = col0 + (tid & 15);
+    const bool valid = row < rc.rows && col < rc.w;
     const int64_t a = rc.ns0 + row, b = rc.r0 + col;
     const int64_t out = rc.out0 + (int64_t)row * rc.ld + col;
     const int mb = rc.n - rc.Ma;
     const bool model = rc.Ma <= kModelQp && mb <= kModelQp;     // uniform over the tile
     float y = 0.f;
     if (model) {
+      // 0. the tile's partial rows (rows and columns beyond the rectangle: zeros, never used)
+      for (int e = tid; e < (kTR + kTC) * (kH / 4); e += kTM) {
+        const int q = e / (kH / 4), c4 = e - q * (kH / 4);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (q < kTR) {
+          if (row0 + q < rc.rows) v = __ldg(reinterpret_cast<const float4*>(g.Apart + (rc.ns0 + row0 + q) * kH) + c4);
+          *reinterpret_cast<float4*>(partA + q * kPartStride + 4 * c4) = v;
+        } else {
+          const int qb = q - kTR;
+          if (col0 + qb < rc.w) v = __ldg(reinterpret_cast<const float4*>(g.Bpart + (rc.r0 + col0 + qb) * kH) + c4);
+          *reinterpret_cast<float4*>(partB + qb * kPartStride + 4 * c4) = v;
+        }
+      }
+      __syncthreads();
       // 1. this pair's row of h1 = relu(A_a + B_b) in BF16
-      const float4* ap = reinterpret_cast<const float4*>(g.Apart + a * kH);
-      const float4* bp = reinterpret_cast<const float4*>(g.Bpart + b * kH);
+      const float4* ap = reinterpret_cast<const float4*>(partA + (tid >> 4) * kPartStride);
+      const float4* bp = reinterpret_cast<const float4*>(partB + (tid & 15) * kPartStride);
 #pragma unroll 4
       for (int c16 = 0; c16 < kH / 8; ++c16) {
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (valid) {
-          const float4 a0 = __ldg(ap + 2 * c16), a1 = __ldg(ap + 2 * c16 + 1);
-          const float4 b0 = __ldg(bp + 2 * c16), b1v = __ldg(bp + 2 * c16 + 1);
+          const float4 a0 = ap[2 * c16], a1 = ap[2 * c16 + 1];
+          const float4 b0 = bp[2 * c16], b1v = bp[2 * c16 + 1];
           v.x = pack2(fmaxf(a0.x + b0.x, 0.f), fmaxf(a0.y + b0.y, 0.f));
           v.y = pack2(fmaxf(a0.z + b0.z, 0.f), fmaxf(a0.w + b0.w, 0.f));
           v.z = pack2(fmaxf(a1.x + b1v.x, 0.f), fmaxf(a1.y + b1v.y, 0.f));
@@ -290,7 +315,7 @@ tgba_status score_rects_tc(Basis& b, const std::vector<Rect>& rects, const float
   if (rects.empty()) return TGBA_OK;
   std::vector<int64_t> prefix(rects.size() + 1, 0);
   for (size_t i = 0; i < rects.size(); ++i)
-    prefix[i + 1] = prefix[i] + ((int64_t)rects[i].rows * rects[i].w + kTM - 1) / kTM;
+    prefix[i + 1] = prefix[i] + (int64_t)((rects[i].rows + kTR - 1) / kTR) * ((rects[i].w + kTC - 1) / kTC);
   const int64_t n_tiles = prefix.back();
   if (n_tiles == 0) return TGBA_OK;
   void* buf = nullptr;
