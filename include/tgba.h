@@ -349,7 +349,7 @@ tgba_status tgba_profile(tgba_basis b, tgba_prof* out);
  * C + i + j ldc); all device pointers, FP64.  Each operand row is scaled by a power of two and cut
  * into six signed 8-bit digits held exactly in BF16; the tensor cores (tcgen05 MMAs, FP32
  * accumulation in tensor memory) sum the digit products, exactly for the three leading digit
- * diagonals over chunks of 128 K values, and the chunks are added into a 48-bit running sum
+ * diagonals over chunks of 256 K values, and the chunks are added into a 48-bit running sum
  * (a pair of FP32 numbers).  The error is a few 1e-13 of sum_k |A_ik B_jk| (below 1e-12).  M, N, K >= 1
  * (TGBA_EINVAL otherwise); the slice buffers (12 bytes per input element) are allocated for the
  * call (TGBA_ENOMEM).  Blocks on `stream`. */

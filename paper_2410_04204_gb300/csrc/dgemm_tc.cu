@@ -9,13 +9,15 @@
 //    d_p 2^{-8p} in BF16 (exact: at most 8 significant bits).  So A_ik = 2^{e_i - 8} sum_p
 //    slice_p + O(2^{e_i - 49}).  B's rows (the columns of C) are cut the same way.
 //  * Products.  C_ij = 2^{e_i + f_j - 16} sum_{p + q <= 5} (A_p B_q^T)_ij.  The products of
-//    digit diagonal d = p + q carry the scale 2^{-8d}; over a chunk of 128 K values each of
-//    the sums of diagonals 0, 1 and 2 stays below 2^24 units of its scale, so FP32
-//    accumulation of those diagonals is exact, and they get one TMEM accumulator each.
+//    digit diagonal d = p + q carry the scale 2^{-8d}; over a chunk of 256 K values each of
+//    the sums of diagonals 0, 1 and 2 stays within 2^24 units of its scale (diagonal 0:
+//    256 terms of at most 256 x 256; diagonal 1: 256 x 2 x 256 x 128; diagonal 2 below
+//    5 x 2^21), integers that FP32 holds exactly, so FP32 accumulation of those diagonals is
+//    exact, and they get one TMEM accumulator each.
 //    Diagonals 3..5 share a fourth accumulator, whose FP32 rounding stays near 2^-48 of the
 //    leading term (measured: an earlier base-128 split with the shared accumulator from
 //    diagonal 3 erred by up to 1.5e-12).
-//  * Chunks.  After every 128 K values the four accumulators (4 x 128 columns = all 512 TMEM
+//  * Chunks.  After every 256 K values the four accumulators (4 x 128 columns = all 512 TMEM
 //    columns) are folded into a running sum per element kept as an unevaluated pair of FP32
 //    numbers (hi + lo, error-free two-sum: about 48 bits), by CUDA-core FP32 arithmetic, while
 //    the producer keeps loading the next stages.  At the end of the tile
@@ -63,7 +65,7 @@ constexpr int kS = 6;                     // slices per operand (base-256 digits
 constexpr int kKB = 32;                   // K per block (64-byte rows)
 constexpr int kTMr = 128;                 // rows of A per tile
 constexpr int kTNr = 128;                 // rows of B per tile
-constexpr int kChunkBlocks = 4;           // K blocks per exact FP32 chunk (128 K values)
+constexpr int kChunkBlocks = 8;           // K blocks per exact FP32 chunk (256 K values)
 constexpr uint32_t kASlice = kTMr * kKB * 2;          // 8 KB
 constexpr uint32_t kBSlice = kTNr * kKB * 2;          // 8 KB
 constexpr uint32_t kAStage = kS * kASlice;            // 48 KB

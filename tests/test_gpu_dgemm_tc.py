@@ -1,19 +1,21 @@
 """FP64 products on the tensor cores (tgba_dgemm_tc: BF16 slices of the FP64 operands, tcgen05
-MMAs, exact FP32 sums of the leading digit diagonals per chunk of 128 K values, 48-bit running
+MMAs, exact FP32 sums of the leading digit diagonals per chunk of 256 K values, 48-bit running
 sums) through the C ABI.
 
 * Exactness of the tensor cores' FP32 accumulation: integer operands of at most 14 bits have
   two base-256 digits, hence only the digit diagonals 0..2, which the design sums exactly, so C
-  must equal the integer product bit for bit (K = 4096: 32 chunks, sums up to 2^38).
+  must equal the integer product bit for bit (K = 4096: 16 chunks, sums up to 2^38).
 * Accuracy: random operands whose rows span six decades, ragged sizes (M, N, K not multiples
   of the 128 x 128 x 32 tiles), against an extended-precision reference: error <= 1e-12 of
   sum_k |A_ik B_jk|, and against cuBLAS FP64.  The FP32 rounding of the accumulator shared by
-  the digit diagonals 3..5 dominates: per chunk it takes 120 MMA additions (15 slice pairs x 8
-  MMAs of K = 16), each rounded to 2^-25 of its magnitude (at most 3/4 of a leading-digit unit),
-  against a chunk sum of about 4e5 such units for normal rows (mean |digit| 58 of 256): a
-  random walk gives ~6e-13 (measured up to 3.9e-13, at K = 100); the worst case, all roundings
-  of one sign, is ten times that.
-* The work split: the chunks (128 K values of one tile) of all tiles are cut evenly over the
+  the digit diagonals 3..5 dominates: a chunk of 128 K values takes 120 MMA additions (15 slice
+  pairs x 8 MMAs of K = 16), each rounded to 2^-25 of its magnitude (at most 3/4 of a
+  leading-digit unit), against a chunk sum of about 4e5 such units for normal rows (mean |digit|
+  58 of 256): a random walk gives ~6e-13 (measured up to 3.9e-13, at K = 100); the worst case,
+  all roundings of one sign, is ten times that.  A longer chunk does not raise the relative
+  error of its own sum (the rounding noise and the sum both grow), and more chunks average it
+  down, so a single short chunk is the worst case.
+* The work split: the chunks (256 K values of one tile) of all tiles are cut evenly over the
   SMs, so a tile may be summed by several CTAs (partials added by the last to finish).  The
   shapes cover tiles split over many CTAs at uneven boundaries, whole tiles only, and a mix;
   two calls give bit-identical results (the partials are added in a fixed order).
