@@ -233,8 +233,8 @@ __global__ void __maxnreg__(168) dgemm_tc_kernel(GemmArgs g) {   // 320 threads 
   uint64_t* full = bars;               // [kStages] stage loaded
   uint64_t* empty = bars + kStages;    // [kStages] stage consumed by the MMAs
   uint64_t* accf = bars + 2 * kStages; // accumulators written (one set)
-  uint64_t* acce = accf + 1;           // [4] accumulator d read by every folding warp
-  uint32_t* tslot = (uint32_t*)(acce + 4);
+  uint64_t* acce = accf + 1;           // accumulators read
+  uint32_t* tslot = (uint32_t*)(acce + 1);
   __shared__ volatile int s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -243,7 +243,7 @@ __global__ void __maxnreg__(168) dgemm_tc_kernel(GemmArgs g) {   // 320 threads 
       bar_init(empty + s, 1);
     }
     bar_init(accf, 1);
-    for (int d = 0; d < 4; ++d) bar_init(acce + d, kEpiWarps);
+    bar_init(acce, kEpiWarps);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -291,6 +291,9 @@ __global__ void __maxnreg__(168) dgemm_tc_kernel(GemmArgs g) {   // 320 threads 
            c = g.tiles[sg.t].c0 + tile_chunks(g.tiles[sg.t])) {
         const EmuTile tl = g.tiles[sg.t];
         for (int kb0 = sg.kb0; kb0 < sg.kb1 && !s_abort; kb0 += kChunkBlocks, ++chunk) {
+          // the epilogue has read the previous chunk's accumulators
+          if (!bar_wait(acce, (chunk & 1u) ^ 1u, &s_abort)) { atomicOr(g.status, kStTimeout); s_abort = 1; break; }
+          fence_after();
           const int kb1 = min(sg.kb1, kb0 + kChunkBlocks);
           for (int kb = kb0; kb < kb1; ++kb, ++it) {
             const int st = it % kStages;
@@ -301,42 +304,19 @@ __global__ void __maxnreg__(168) dgemm_tc_kernel(GemmArgs g) {   // 320 threads 
             // every column that the epilogue reads
             const uint32_t id = idesc_f16(active_cols(tl, kb));
             const uint32_t a0 = su32(sA + st * kAStage), b0 = su32(sB + st * kBStage);
-            if (kb == kb0) {
-              // the chunk's first block, accumulator by accumulator in the order the folding warps
-              // release them (3, 0, 1, 2): the 15 slice pairs of the shared accumulator start while
-              // the other three are still being read; the first MMA of each overwrites it
 #pragma unroll 1
-              for (int o = 0; o < 4 && !s_abort; ++o) {
-                const int d = (o + 3) & 3;
-                if (!bar_wait(acce + d, (chunk & 1u) ^ 1u, &s_abort)) { atomicOr(g.status, kStTimeout); s_abort = 1; break; }
-                fence_after();
-                bool first = true;
+            for (int p = 0; p < kS; ++p)
 #pragma unroll 1
-                for (int p = 0; p < kS; ++p)
-#pragma unroll 1
-                  for (int q = 0; p + q < kS; ++q) {
-                    if (min(p + q, 3) != d) continue;
+              for (int q = 0; p + q < kS; ++q) {
+                const int d = min(p + q, 3);
+                // first write of accumulator d in this chunk overwrites it: pair (0, d) for d <= 2,
+                // (0, 3) for the shared one, at the chunk's first K block
+                const bool first = kb == kb0 && p == 0 && q == (d < 3 ? d : 3);
 #pragma unroll
-                    for (int ks = 0; ks < 2; ++ks) {
-                      mma(tmem + (uint32_t)d * 128u, desc64(a0 + p * kASlice + ks * 32), desc64(b0 + q * kBSlice + ks * 32),
-                          id, first ? 0u : 1u);
-                      first = false;
-                    }
-                  }
+                for (int ks = 0; ks < 2; ++ks)
+                  mma(tmem + (uint32_t)d * 128u, desc64(a0 + p * kASlice + ks * 32), desc64(b0 + q * kBSlice + ks * 32), id,
+                      (first && ks == 0) ? 0u : 1u);
               }
-              if (s_abort) break;
-            } else {
-#pragma unroll 1
-              for (int p = 0; p < kS; ++p)
-#pragma unroll 1
-                for (int q = 0; p + q < kS; ++q) {
-                  const int d = min(p + q, 3);
-#pragma unroll
-                  for (int ks = 0; ks < 2; ++ks)
-                    mma(tmem + (uint32_t)d * 128u, desc64(a0 + p * kASlice + ks * 32), desc64(b0 + q * kBSlice + ks * 32), id,
-                        1u);
-                }
-            }
             commit(empty + st);                       // the stage's smem is free once these complete
             last = empty + st;
           }
@@ -373,24 +353,21 @@ __global__ void __maxnreg__(168) dgemm_tc_kernel(GemmArgs g) {   // 320 threads 
         fence_after();
         const int na = active_cols(tl, kb0);          // columns the chunk's MMAs wrote
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * kCols);
-        // accumulator by accumulator, the shared one first, each released as soon as it is read
-        // (the next chunk's MMAs into it may then start)
 #pragma unroll
-        for (int o = 0; o < 4; ++o) {
-          const int d = (o + 3) & 3;
+        for (int h = 0; h < kCols / 16; ++h) {
+          if (half * kCols + h * 16 < na) {
 #pragma unroll
-          for (int h = 0; h < kCols / 16; ++h) {
-            if (half * kCols + h * 16 < na) {
+            for (int d = 0; d < 4; ++d) {
               float v[16];
               ld16(lane_base + (uint32_t)d * (uint32_t)kTNr + (uint32_t)h * 16u, v);
 #pragma unroll
               for (int j = 0; j < 16; ++j) two_sum_add(hi[h * 16 + j], lo[h * 16 + j], v[j]);
             }
           }
-          fence_before();
-          __syncwarp();
-          if (lane == 0) bar_arrive(acce + d);
         }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) bar_arrive(acce);
       }
       if (s_abort) break;
       const int i = tl.rb * kTMr + r;
