@@ -411,15 +411,18 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
   };
   // off-diagonal product Y = A x on the union layout (x, Y: n_un x cols, ld n_un)
   auto offdiag = [&](const double* x, double* Y, int cols, __nv_bfloat16* Bs, int* eb, EmuTile* t_ns, int n_ns,
-                     int64_t c_ns, EmuTile* t_r, int n_r, int64_t c_r) -> tgba_status {
+                     int64_t c_ns, EmuTile* t_r, int n_r, int64_t c_r, int ns) -> tgba_status {
     tgba_status q = emu_slice(b, x + kn_max, n_un, 1, (int)kr_max, 0, nullptr, 0.0, cols, (int)kr_max, TC, Bs, eb, st);
-    if (q == TGBA_OK) q = emu_gemm(b, A_ns, e_ns, (int)kn_max, (int)kr_max, Bs, eb, cols, (int)kr_max, t_ns, n_ns, c_ns, Y, n_un, st);
+    if (q == TGBA_OK) q = emu_gemm(b, A_ns, e_ns, (int)kn_max, (int)kr_max, Bs, eb, cols, (int)kr_max, t_ns, n_ns, c_ns, Y, n_un, st, ns);
     if (q == TGBA_OK) q = emu_slice(b, x, n_un, 1, (int)kn_max, 0, nullptr, 0.0, cols, (int)kn_max, TC, Bs, eb, st);
     if (q == TGBA_OK)
-      q = emu_gemm(b, A_r, e_r, (int)kr_max, (int)kn_max, Bs, eb, cols, (int)kn_max, t_r, n_r, c_r, Y + kn_max, n_un, st);
+      q = emu_gemm(b, A_r, e_r, (int)kr_max, (int)kn_max, Bs, eb, cols, (int)kn_max, t_r, n_r, c_r, Y + kn_max, n_un, st, ns);
     return q;
   };
-  // ---- Lanczos bounds on the union for each distinct field
+  // ---- Lanczos bounds on the union for each distinct field.  The products take only the two
+  // leading digit slices of each operand (X's relative error about 2^-16 of its row scale, a
+  // third of the slice traffic): the bounds are widened by 2% and checked after the
+  // propagation, so they need the spectrum's edges to a few digits, not to FP64
   std::vector<double> fields;
   for (const ChebVariant& v : vars)
     if (std::find(fields.begin(), fields.end(), v.hx) == fields.end()) fields.push_back(v.hx);
@@ -461,7 +464,7 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
     double *qp = q0, *qc = q1, *qn = q2;
     for (int j = 0; j < m; ++j) {
       if (coupled) {
-        if ((r = offdiag(qc, Y, nhp, Bs, eb, dt, (int)tn.size(), cn, dt + tn.size(), (int)tr.size(), cr_)) != TGBA_OK) return r;
+        if ((r = offdiag(qc, Y, nhp, Bs, eb, dt, (int)tn.size(), cn, dt + tn.size(), (int)tr.size(), cr_, 2)) != TGBA_OK) return r;
       }
       lz_step<<<nh, kRedThreads, 0, st>>>(n_un, E, g, Y, qp, qc, qn, al, be, j, m);
       ++b.launches;
@@ -591,7 +594,7 @@ tgba_status quench_cheb_batch(Basis& b, const double* Q, int64_t kn_max, int64_t
     for (int k = 0; k < K && cr == TGBA_OK; ++k) {
       double* vk = V + (size_t)k * S;
       if (coupled)
-        cr = offdiag(vk, Y, ncolp, Bs, eb, dtl, (int)tn.size(), cn, dtl + tn.size(), (int)tr.size(), cr_);
+        cr = offdiag(vk, Y, ncolp, Bs, eb, dtl, (int)tn.size(), cn, dtl + tn.size(), (int)tr.size(), cr_, 6);
       if (cr != TGBA_OK) break;
       cheb_step<<<blocks_for(S), 256, 0, cap>>>(n_un, kn_max, ncolp, E, prm, k == 0 ? 1.0 : 2.0, 1.0, Y, vk,
                                                  k == 0 ? nullptr : vk - S, vk + S);

@@ -176,6 +176,7 @@ struct GemmArgs {
   int64_t ldc;
   double* part;               // [2 gridDim.x][kTNr][kTMr] partial tiles of the split tiles
   unsigned* status;
+  int ns;                     // slices used per operand: 6, or 2 for a product good to ~2^-16
 };
 
 // Work split (stream-K): the chunks of all tiles, tile after tile, are cut into gridDim.x
@@ -270,9 +271,12 @@ __global__ void __maxnreg__(168) dgemm_tc_kernel(GemmArgs g) {   // 320 threads 
         for (int kb = sg.kb0; kb < sg.kb1; ++kb, ++it) {
           const int st = it % kStages;
           if (!bar_wait(empty + st, ((it / kStages) & 1u) ^ 1u, &s_abort)) { atomicOr(g.status, kStTimeout); s_abort = 1; break; }
-          bar_expect(full + st, kAStage + kBStage);
-          bulk_load(sA + st * kAStage, g.A + ((size_t)tl.rb * g.a_kb + kb) * (kAStage / 2), kAStage, full + st);
-          bulk_load(sB + st * kBStage, g.B + ((size_t)tl.cb * g.b_kb + kb) * (kBStage / 2), kBStage, full + st);
+          // the first ns slices of a K block are the first ns x 8 KB of its image
+          bar_expect(full + st, (uint32_t)g.ns * (kASlice + kBSlice));
+          bulk_load(sA + st * kAStage, g.A + ((size_t)tl.rb * g.a_kb + kb) * (kAStage / 2), (uint32_t)g.ns * kASlice,
+                    full + st);
+          bulk_load(sB + st * kBStage, g.B + ((size_t)tl.cb * g.b_kb + kb) * (kBStage / 2), (uint32_t)g.ns * kBSlice,
+                    full + st);
         }
       }
       if (s_abort) {                                  // copies still in flight land before the CTA leaves
@@ -305,9 +309,9 @@ __global__ void __maxnreg__(168) dgemm_tc_kernel(GemmArgs g) {   // 320 threads 
             const uint32_t id = idesc_f16(active_cols(tl, kb));
             const uint32_t a0 = su32(sA + st * kAStage), b0 = su32(sB + st * kBStage);
 #pragma unroll 1
-            for (int p = 0; p < kS; ++p)
+            for (int p = 0; p < g.ns; ++p)
 #pragma unroll 1
-              for (int q = 0; p + q < kS; ++q) {
+              for (int q = 0; p + q < g.ns; ++q) {
                 const int d = min(p + q, 3);
                 // first write of accumulator d in this chunk overwrites it: pair (0, d) for d <= 2,
                 // (0, 3) for the shared one, at the chunk's first K block
@@ -358,6 +362,7 @@ __global__ void __maxnreg__(168) dgemm_tc_kernel(GemmArgs g) {   // 320 threads 
           if (half * kCols + h * 16 < na) {
 #pragma unroll
             for (int d = 0; d < 4; ++d) {
+              if (d >= g.ns) break;                   // with 2 slices only diagonals 0 and 1 are written
               float v[16];
               ld16(lane_base + (uint32_t)d * (uint32_t)kTNr + (uint32_t)h * 16u, v);
 #pragma unroll
@@ -620,7 +625,8 @@ int64_t emu_number_tiles(std::vector<EmuTile>& tiles) {
 // emu_number_tiles, n_chunks its result; emu_prepare first).
 tgba_status emu_gemm(Basis& b, const __nv_bfloat16* A, const int* ea, int M, int Ka, const __nv_bfloat16* B,
                      const int* eb, int N, int Kb, EmuTile* d_tiles, int n_tiles, int64_t n_chunks, double* C,
-                     int64_t ldc, cudaStream_t st) {
+                     int64_t ldc, cudaStream_t st, int n_slices) {
+  if (n_slices != 2 && n_slices != kS) return fail(TGBA_EINVAL, "emu_gemm: 2 or 6 slices");
   if (n_tiles == 0) return TGBA_OK;
   if (b.emu_sms <= 0 || !b.d_emu_part) return fail(TGBA_EINVAL, "emu_prepare was not called");
   if (n_chunks < n_tiles) return fail(TGBA_EINVAL, "tiles not numbered (emu_number_tiles)");
@@ -630,6 +636,7 @@ tgba_status emu_gemm(Basis& b, const __nv_bfloat16* A, const int* ea, int M, int
   g.a_kb = (Ka + kKB - 1) / kKB;
   g.b_kb = (Kb + kKB - 1) / kKB;
   g.ea = ea; g.eb = eb; g.M = M; g.N = N; g.C = C; g.ldc = ldc; g.part = b.d_emu_part; g.status = b.d_status;
+  g.ns = n_slices;
   dgemm_tc_kernel<<<(int)std::min<int64_t>(n_chunks, b.emu_sms), kThreads, kSmem, st>>>(g);
   TGBA_CUDA(cudaGetLastError());
   ++b.launches;

@@ -298,7 +298,7 @@ size_t emu_part_bytes(int sms);
 int64_t emu_number_tiles(std::vector<EmuTile>& tiles);     // total chunks; -1 for an invalid tile
 tgba_status emu_gemm(Basis& b, const __nv_bfloat16* A, const int* ea, int M, int Ka, const __nv_bfloat16* B,
                      const int* eb, int N, int Kb, EmuTile* d_tiles, int n_tiles, int64_t n_chunks, double* C,
-                     int64_t ldc, cudaStream_t st);
+                     int64_t ldc, cudaStream_t st, int n_slices = 6);   // 2: only the two leading digits (~2^-16)
 
 // screen.cu
 struct Screen;
