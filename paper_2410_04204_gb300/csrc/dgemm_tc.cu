@@ -176,7 +176,6 @@ struct GemmArgs {
   int64_t ldc;
   double* part;               // [2 gridDim.x][kTNr][kTMr] partial tiles of the split tiles
   unsigned* status;
-  int ns;                     // slices used per operand: 6, or 2 for a product good to ~2^-16
 };
 
 // Work split (stream-K): the chunks of all tiles, tile after tile, are cut into gridDim.x
@@ -224,6 +223,8 @@ __device__ __forceinline__ int active_cols(const EmuTile& tl, int kb) {
   return n;
 }
 
+// NS: slices used per operand, kS (the FP64 product) or 2 (the two leading digits: ~2^-16)
+template <int NS>
 __global__ void __maxnreg__(168) dgemm_tc_kernel(GemmArgs g) {   // 320 threads x 168 registers, one CTA per SM
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = su32(smem_raw);
@@ -272,10 +273,10 @@ __global__ void __maxnreg__(168) dgemm_tc_kernel(GemmArgs g) {   // 320 threads 
           const int st = it % kStages;
           if (!bar_wait(empty + st, ((it / kStages) & 1u) ^ 1u, &s_abort)) { atomicOr(g.status, kStTimeout); s_abort = 1; break; }
           // the first ns slices of a K block are the first ns x 8 KB of its image
-          bar_expect(full + st, (uint32_t)g.ns * (kASlice + kBSlice));
-          bulk_load(sA + st * kAStage, g.A + ((size_t)tl.rb * g.a_kb + kb) * (kAStage / 2), (uint32_t)g.ns * kASlice,
+          bar_expect(full + st, (uint32_t)NS * (kASlice + kBSlice));
+          bulk_load(sA + st * kAStage, g.A + ((size_t)tl.rb * g.a_kb + kb) * (kAStage / 2), (uint32_t)NS * kASlice,
                     full + st);
-          bulk_load(sB + st * kBStage, g.B + ((size_t)tl.cb * g.b_kb + kb) * (kBStage / 2), (uint32_t)g.ns * kBSlice,
+          bulk_load(sB + st * kBStage, g.B + ((size_t)tl.cb * g.b_kb + kb) * (kBStage / 2), (uint32_t)NS * kBSlice,
                     full + st);
         }
       }
@@ -309,9 +310,9 @@ __global__ void __maxnreg__(168) dgemm_tc_kernel(GemmArgs g) {   // 320 threads 
             const uint32_t id = idesc_f16(active_cols(tl, kb));
             const uint32_t a0 = su32(sA + st * kAStage), b0 = su32(sB + st * kBStage);
 #pragma unroll 1
-            for (int p = 0; p < g.ns; ++p)
+            for (int p = 0; p < NS; ++p)
 #pragma unroll 1
-              for (int q = 0; p + q < g.ns; ++q) {
+              for (int q = 0; p + q < NS; ++q) {
                 const int d = min(p + q, 3);
                 // first write of accumulator d in this chunk overwrites it: pair (0, d) for d <= 2,
                 // (0, 3) for the shared one, at the chunk's first K block
@@ -361,8 +362,7 @@ __global__ void __maxnreg__(168) dgemm_tc_kernel(GemmArgs g) {   // 320 threads 
         for (int h = 0; h < kCols / 16; ++h) {
           if (half * kCols + h * 16 < na) {
 #pragma unroll
-            for (int d = 0; d < 4; ++d) {
-              if (d >= g.ns) break;                   // with 2 slices only diagonals 0 and 1 are written
+            for (int d = 0; d < (NS < 4 ? NS : 4); ++d) {   // with 2 slices only diagonals 0 and 1 are written
               float v[16];
               ld16(lane_base + (uint32_t)d * (uint32_t)kTNr + (uint32_t)h * 16u, v);
 #pragma unroll
@@ -587,14 +587,16 @@ tgba_status emu_prepare(Basis& b) {
   static int sms_of[64] = {0};
   if (b.device < 0 || b.device >= 64) return fail(TGBA_ELIMIT, "device index");
   if (sms_of[b.device] == 0) {
-    TGBA_CUDA(cudaFuncSetAttribute(dgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
-    cudaFuncAttributes fa;
-    TGBA_CUDA(cudaFuncGetAttributes(&fa, dgemm_tc_kernel));
-    if (fa.maxThreadsPerBlock < kThreads) {
-      char msg[200];
-      snprintf(msg, sizeof msg, "dgemm_tc_kernel: %d registers, %zu B local, %zu B static shared: at most %d threads",
-               fa.numRegs, fa.localSizeBytes, fa.sharedSizeBytes, fa.maxThreadsPerBlock);
-      return fail(TGBA_ELIMIT, msg);
+    for (const void* k : {(const void*)dgemm_tc_kernel<kS>, (const void*)dgemm_tc_kernel<2>}) {
+      TGBA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
+      cudaFuncAttributes fa;
+      TGBA_CUDA(cudaFuncGetAttributes(&fa, k));
+      if (fa.maxThreadsPerBlock < kThreads) {
+        char msg[200];
+        snprintf(msg, sizeof msg, "dgemm_tc_kernel: %d registers, %zu B local, %zu B static shared: at most %d threads",
+                 fa.numRegs, fa.localSizeBytes, fa.sharedSizeBytes, fa.maxThreadsPerBlock);
+        return fail(TGBA_ELIMIT, msg);
+      }
     }
     int sms = 0;
     TGBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b.device));
@@ -636,8 +638,9 @@ tgba_status emu_gemm(Basis& b, const __nv_bfloat16* A, const int* ea, int M, int
   g.a_kb = (Ka + kKB - 1) / kKB;
   g.b_kb = (Kb + kKB - 1) / kKB;
   g.ea = ea; g.eb = eb; g.M = M; g.N = N; g.C = C; g.ldc = ldc; g.part = b.d_emu_part; g.status = b.d_status;
-  g.ns = n_slices;
-  dgemm_tc_kernel<<<(int)std::min<int64_t>(n_chunks, b.emu_sms), kThreads, kSmem, st>>>(g);
+  const int grid = (int)std::min<int64_t>(n_chunks, b.emu_sms);
+  if (n_slices == kS) dgemm_tc_kernel<kS><<<grid, kThreads, kSmem, st>>>(g);
+  else dgemm_tc_kernel<2><<<grid, kThreads, kSmem, st>>>(g);
   TGBA_CUDA(cudaGetLastError());
   ++b.launches;
   return TGBA_OK;
