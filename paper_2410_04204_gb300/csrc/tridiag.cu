@@ -414,9 +414,6 @@ __device__ __noinline__ bool sytrd_matrix(const TriSlot S, int C, int rank, unsi
           const double* rr = RP + (int64_t)i * G;
           double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
           int g = g0 + q4;
-          // unrolled so that 16 loads per lane are in flight (each row sum is a chain of L2
-          // reads; the order of the additions, hence the result, is unchanged)
-#pragma unroll 4
           for (; g + 12 <= gi; g += 16) {
             y0 += __ldcg(rr + g);
             y1 += __ldcg(rr + g + 4);
