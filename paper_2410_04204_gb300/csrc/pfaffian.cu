@@ -448,6 +448,7 @@ KernelFn kernel_of(int kind, int n, int T) {
     return pf_reg_queue<14, 128, 2>;
   }
   if (kind == 2) {
+    if (n <= 16 && T == 64) return pf_smem<16, 64>;
     if (n <= 16 && T == 128) return pf_smem<16, 128>;
     if (n <= 20 && T == 128) return pf_smem<20, 128>;
     if (n <= 24 && T == 64) return pf_smem<24, 64>;
@@ -484,7 +485,8 @@ tgba_status plan_pfaffians(Basis& b) {
       }
     } else {
       kind = 2; size = L.nmax;
-      T = L.nmax <= 20 ? 128 : L.nmax <= 24 ? 64 : 32;
+      // size 16: 64-thread blocks of 61 KB, three per SM (six warps; 128 threads fit one block)
+      T = L.nmax <= 16 ? 64 : L.nmax <= 20 ? 128 : L.nmax <= 24 ? 64 : 32;
     }
     KernelFn k = kernel_of(kind, size, T);
     if (!k) return fail(TGBA_ELIMIT, "no Pfaffian kernel for size " + std::to_string(size));
